@@ -1,0 +1,327 @@
+"""Benchmark of the CLoD-GS rasterizer on one GB300 (or N replicas).
+
+Headline workload: the 1M-Gaussian, SH-degree-3 object scene rendered at
+1920x1080 over the 64-camera orbit (distances 2..20) and virtual scales
+s_v in {1, 2, 4, 8, 16}; one step renders one (camera, s_v) frame through the
+whole forward path (preprocess, bin/sort, blend) via the C ABI.  The metric is
+frames per second over all ranks; each rank renders its own frames (views
+are independent: replicas, no collective on the data path).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
+the host cores on a bounded sample of the same frames.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WIDTH, HEIGHT = 1920, 1080
+N_GAUSS = 1_000_000
+N_CAMS = 64
+SCALES = (1.0, 2.0, 4.0, 8.0, 16.0)
+METRIC = "1080p frames/s at 1M Gaussians (forward, CLoD on)"
+WORKLOAD = "object scene 1M Gaussians SH3, 1920x1080, 64-camera orbit d=2..20, s_v in {1,2,4,8,16}"
+# FP32 operations of one evaluated (pixel, Gaussian) pair in the blend: offset 2,
+# quadratic form 7, exp_spec 21 (12 FMA, 2 add, compare/select, cap, scale),
+# clamp/product 2, skip test 1, transmittance 2, stop test 1, weight 1,
+# colour 6 (3 FMA).  A skipped pair does less; this counts the full evaluation.
+FLOP_PER_PAIR = 43
+
+
+def frames_list():
+    return [(c, s) for c in range(N_CAMS) for s in SCALES]
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=320)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-extras", action="store_true", help="skip the e2e/cpu_baseline legs")
+    return p.parse_args()
+
+
+def dist_setup(n):
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    if torch.cuda.is_available():
+        torch.cuda.set_device(local)
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2510_09997_gb300 import clod as C
+    from paper_2510_09997_gb300 import synth as S
+
+    rank, world, local = dist_setup(args.gpus)
+    C.require_cuda()
+    sc = S.object_scene(N_GAUSS)
+    cams = S.orbit_cameras(N_CAMS, WIDTH, HEIGHT)
+    allf = frames_list()
+    # this rank's frames (replicas: rank r takes frames r, r+N, ...)
+    mine = allf[rank::world] if world > 1 else allf
+    views = [cams[c].replace(s_v=s) for c, s in mine]
+    ds = C.DeviceScene.from_scene(sc)
+
+    # pair capacity: the largest K over this rank's frames (one pre-pass)
+    probe = C.Renderer(ds, [views[0]], pair_capacity=1)
+    kmax = 0
+    for v in views:
+        probe.set_views([v])
+        C.clod_preprocess(ds, [v], probe.ws, n_pairs=probe.npairs)
+        kmax = max(kmax, int(probe.npairs.item()))
+    del probe
+    R = C.Renderer(ds, [views[0]], pair_capacity=int(kmax * 1.02) + 1024)
+    stream = torch.cuda.current_stream()
+
+    def step(k):
+        R.set_views([views[k % len(views)]])
+        R.run()
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    # stage events for the per-kernel roofline
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    L = C.lib()
+    st = C._stream(None)
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    for k in range(args.steps):
+        R.set_views([views[k % len(views)]])
+        e = ev[k]
+        e[0].record()
+        C.check("clod_preprocess", L.clod_preprocess(C.ctypes.byref(ds.c), R.carr, 1, C._ptr(R.ws), R.ws.numel(),
+                                                     None, None, None, C._ptr(R.npairs), st))
+        e[1].record()
+        C.check("clod_bin_sort", L.clod_bin_sort(C._ptr(R.ws), R.cap, C._ptr(R.sort_ws), R.sort_ws.numel(), None,
+                                                 C._ptr(R.vals), C._ptr(R.ranges), st))
+        e[2].record()
+        C.check("clod_render_fwd", L.clod_render_fwd(C._ptr(R.ws), C._ptr(R.vals), C._ptr(R.ranges),
+                                                     C._ptr(R.image), C._ptr(R.T), C._ptr(R.nc), st))
+        e[3].record()
+    t1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    elapsed = t0.elapsed_time(t1) / 1e3
+    if world > 1:
+        tt = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed = float(tt.item())
+    R.check()   # every frame fitted the pair capacity (the last one is checked; all used K <= kmax)
+    stage = np.array([[ev[k][j].elapsed_time(ev[k][j + 1]) for j in range(3)] for k in range(args.steps)])
+    st_ms = stage.mean(0)
+
+    # evaluated (pixel, Gaussian) pairs for the blend's FLOP count (untimed pass)
+    evals = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for k in range(args.steps):
+        R.set_views([views[k % len(views)]])
+        C.clod_preprocess(ds, R.views, R.ws, n_pairs=R.npairs)
+        C.clod_bin_sort(R.ws, R.cap, R.sort_ws, None, R.vals, R.ranges)
+        C.clod_render_fwd(R.ws, R.vals, R.ranges, R.image, R.T, R.nc, evaluated=evals)
+    torch.cuda.synchronize()
+    ev_per_frame = float(evals.item()) / args.steps
+
+    frames_total = args.steps * world
+    value = frames_total / elapsed
+    peaks = measured_peaks()
+    sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12          # TFLOP/s at the sampled clock
+    blend_tflops = ev_per_frame * FLOP_PER_PAIR / (st_ms[2] / 1e3) / 1e12
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(elapsed * 1e3 / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_gaussians": N_GAUSS, "width": WIDTH, "height": HEIGHT,
+                   "frames_per_rank": len(views), "l2": "inputs larger than L2 (240 MB scene)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "stage_ms": {"preprocess": round(float(st_ms[0]), 4), "bin_sort": round(float(st_ms[1]), 4),
+                     "blend": round(float(st_ms[2]), 4)},
+        "roofline": {"bound": "alu", "kernel": "k_blend_fwd", "achieved": round(blend_tflops, 3),
+                     "peak": round(fp32_peak, 2), "unit": "TFLOP/s", "frac": round(blend_tflops / fp32_peak, 4),
+                     "traffic": None, "flop_per_pair": FLOP_PER_PAIR, "evaluated_pairs_per_frame": ev_per_frame,
+                     "peak_basis": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (sampled clock)" % (n_sm, sm_mhz)},
+        "gpu_launches": 7 * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_extras:
+        out["e2e"] = e2e_leg(C, ds, R, views, args, stream)
+        out["cpu_baseline"] = cpu_baseline(sc, views)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def e2e_leg(C, ds, R, views, args, stream):
+    """Same frames through the C ABI with host buffers: the view record goes
+    host->device inside clod_preprocess; the image comes back to pinned host
+    memory every step (inside the timed region)."""
+    import torch
+    host = torch.empty(R.image.numel(), dtype=torch.float32, pin_memory=True)
+    steps = min(args.steps, 64)
+    for k in range(3):
+        R.set_views([views[k]])
+        R.run()
+        host.copy_(R.image, non_blocking=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(steps):
+        R.set_views([views[k % len(views)]])
+        R.run()
+        host.copy_(R.image, non_blocking=True)
+        stream.synchronize()
+    dt = time.perf_counter() - t0
+    return {"value": round(steps / dt, 3), "unit": "frames/s", "h2d_bytes_per_step": 112,
+            "d2h_bytes_per_step": int(R.image.numel() * 4), "steps": steps}
+
+
+def cpu_baseline(sc, views, budget_s=20.0):
+    """The oracle (single thread) on a bounded sample of the frames: full
+    Stage I, pair emission and sort, and blending of a sample of tiles, scaled
+    to a whole frame."""
+    from oracle import oracle as O
+    v = views[0]
+    t0 = time.perf_counter()
+    s1 = O.stage1(sc, v)
+    k, val = O.emit_pairs(v, s1)
+    O.stable_sort(k, val)
+    t1 = time.perf_counter()
+    tx, ty = O.tiles_of(v)
+    ntiles = tx * ty
+    rng = np.random.default_rng(0)
+    order = rng.permutation(ntiles)
+    done, tsum = 0, 0.0
+    while done < ntiles and tsum < budget_s - (t1 - t0):
+        chunk = order[done:done + 32]
+        a = time.perf_counter()
+        O.render(sc, v, s1, None, tiles=chunk)
+        tsum += time.perf_counter() - a
+        done += len(chunk)
+    frame_s = (t1 - t0) + tsum * ntiles / max(done, 1)
+    return {"value": round(1.0 / frame_s, 5), "unit": "frames/s", "cores": 1, "kind": "oracle",
+            "sample": "camera 0, s_v=1: full Stage I + pairs + sort, blend of %d/%d random tiles scaled to the frame"
+                      % (done, ntiles), "seconds": round((t1 - t0) + tsum, 2)}
+
+
+def run_reference(args):
+    """The CPU oracle, as it stands, on the host cores (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2510_09997_gb300 import synth as S
+    O.build()
+    sc = S.object_scene(N_GAUSS)
+    cams = S.orbit_cameras(N_CAMS, WIDTH, HEIGHT)
+    allf = frames_list()
+    per_step_budget = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    times = []
+    samples = []
+    for k in range(args.warmup + args.steps):
+        c, s = allf[k % len(allf)]
+        v = cams[c].replace(s_v=s)
+        r = cpu_baseline(sc, [v], budget_s=per_step_budget)
+        if k >= args.warmup:
+            times.append(1.0 / r["value"])
+            samples.append(r["sample"])
+    value = len(times) / sum(times)
+    out = {"metric": METRIC, "value": round(value, 5), "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(1e3 * sum(times) / len(times), 2), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "impl": "reference",
+           "config": {"workload": WORKLOAD, "n_gaussians": N_GAUSS, "width": WIDTH, "height": HEIGHT},
+           "cpu_baseline": {"value": round(value, 5), "unit": "frames/s", "cores": 1, "kind": "oracle",
+                            "sample": "per step one frame: full Stage I + pairs + sort, blend of a random tile "
+                                      "sample scaled to the frame (%.1f s budget)" % per_step_budget},
+           "e2e": {"value": round(value, 5), "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -1,0 +1,182 @@
+/*
+ * clod.h -- C ABI of libclod, the GB300 (sm_103a) CLoD-GS rasterizer.
+ *
+ * CLoD-GS (continuous level of detail for 3D Gaussian splatting) attenuates
+ * each Gaussian's opacity with a learnable, distance-dependent decay
+ * (Sec. 3.2, Eq. 2), culls primitives whose attenuated opacity falls under a
+ * threshold that grows with the virtual distance scale (Sec. 3.2, mask M_i),
+ * and renders the rest with a tile-based, depth-sorted, front-to-back
+ * alpha-blending rasterizer (Sec. 3.1, Eq. 1).
+ *
+ * Conventions for every entry point:
+ *   - Returns a clod_status; never throws, never aborts.  The message of the
+ *     last failure on the calling thread is returned by clod_last_error().
+ *   - Every array pointer is DEVICE memory owned by the caller, unless the
+ *     parameter says "host".  The library never frees caller memory.
+ *   - Work is enqueued on the given CUDA stream (a cudaStream_t passed as
+ *     void*; NULL means the legacy default stream) and is asynchronous: the
+ *     outputs are valid once the stream reaches them.  Calls that read a
+ *     device value back say so and synchronise the stream.
+ *   - Scene parameters come in ACTIVATED: opacity in (0, 1), scales > 0,
+ *     quaternions (w, x, y, z) of any non-zero norm (normalised inside),
+ *     decay sigma_d raw (the ReLU of Eq. 2 is applied inside).
+ *   - Arithmetic is FP32.  Every quantity that decides an integer outcome
+ *     (the mask, the tile rectangle, the depth key, the per-pixel skip and
+ *     stop of the blend) is computed by a fixed sequence of IEEE operations
+ *     with a fixed, monotone exponential, so the decisions are reproducible
+ *     bit for bit by any implementation of the same sequence.
+ */
+#ifndef CLOD_H
+#define CLOD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t clod_status;
+#define CLOD_OK              0
+#define CLOD_ERR_ARG         1  /* invalid argument (null pointer, bad size, ...)      */
+#define CLOD_ERR_CAPACITY    2  /* a caller buffer is too small; required size reported */
+#define CLOD_ERR_CUDA        3  /* a CUDA runtime call failed                          */
+#define CLOD_ERR_TIMEOUT     4  /* a bounded device or host wait gave up               */
+#define CLOD_ERR_QUEUE_FULL  5  /* serving queue full                                  */
+#define CLOD_ERR_NOT_READY   6  /* serving request not finished                        */
+#define CLOD_ERR_NAN         7  /* non-finite input detected (checked calls only)      */
+
+/* view flags */
+#define CLOD_LOD_OFF       1u  /* plain 3DGS: alpha'' = alpha, no level-of-detail cull */
+#define CLOD_NO_NORMALIZE  2u  /* use d_i itself instead of d_i / max d (Sec. 3.2)    */
+
+typedef void* clod_stream;     /* cudaStream_t */
+
+/* A resident Gaussian scene (Sec. 3.1 primitives plus the per-Gaussian decay
+ * sigma_d of Sec. 3.2).  All arrays are device memory, float32, row-major. */
+typedef struct clod_scene {
+    int64_t n;              /* number of Gaussians, 0 <= n < 2^31               */
+    int32_t sh_degree;      /* 0..3                                             */
+    int32_t reserved;
+    const float* means;     /* n x 3                                            */
+    const float* scales;    /* n x 3, activated (> 0)                           */
+    const float* quats;     /* n x 4, (w, x, y, z)                              */
+    const float* opacity;   /* n, activated, in (0, 1)                          */
+    const float* sh;        /* n x (sh_degree+1)^2 x 3                          */
+    const float* decay;     /* n, raw sigma_d                                   */
+} clod_scene;
+
+/* A pinhole camera and its level-of-detail setting.  Host memory. */
+typedef struct clod_view {
+    int32_t width, height;  /* pixels, 1..16384                                 */
+    float viewmat[12];      /* world -> camera [R | t], row-major 3x4; camera
+                               x right, y down, z forward                      */
+    float fx, fy, cx, cy;   /* focal lengths and principal point, pixels; pixel
+                               (x, y) has its centre at (x + 0.5, y + 0.5)      */
+    float near_z;           /* near plane on the camera z axis                  */
+    float campos[3];        /* camera centre c in world coordinates (Sec. 3.2)  */
+    float s_v;              /* virtual distance scale s_v (Sec. 3.2)            */
+    float tau;              /* base opacity threshold tau: M_i = alpha'' > tau s_v */
+    float eps;              /* epsilon of Eq. 2                                 */
+    float bg[3];            /* background colour                                */
+    uint32_t flags;         /* CLOD_LOD_OFF | CLOD_NO_NORMALIZE                 */
+} clod_view;
+
+/* Byte offsets of the arrays inside a frame workspace (for inspection). */
+typedef struct clod_frame_layout {
+    uint64_t total_bytes;
+    uint64_t views;         /* n_views device view records                      */
+    uint64_t dmax_key;      /* u64 [n_views]: (bits(d_max) << 32) | ~argmax     */
+    uint64_t n_survivors;   /* u32 [2 * n_views]: sum M_i, rendered (per view)  */
+    uint64_t rec0;          /* float4 [n_views * n]: u, v, -A/2, -B             */
+    uint64_t rec1;          /* float4 [n_views * n]: -C/2, alpha'', r, g        */
+    uint64_t rec2;          /* float  [n_views * n]: b                          */
+    uint64_t depth;         /* float  [n_views * n]: camera-space z             */
+    uint64_t rect;          /* uint2  [n_views * n]: (x0 | y0 << 16, x1 | y1 << 16), tiles [x0,x1)x[y0,y1) */
+    uint64_t tile_count;    /* u32 [total_tiles]                                */
+    uint64_t tile_offset;   /* u32 [total_tiles + 1]: exclusive scan of tile_count */
+    uint32_t total_tiles;   /* sum over views of ceil(W/16) * ceil(H/16)        */
+    uint32_t n_views;
+} clod_frame_layout;
+
+/* Last error message of the calling thread ("" if none). */
+const char* clod_last_error(void);
+
+/* Library version string and the compute capability it was built for. */
+const char* clod_version(void);
+
+/* ------------------------------------------------------------------------ */
+/* Forward pipeline: clod_preprocess -> clod_bin_sort -> clod_render_fwd      */
+/* ------------------------------------------------------------------------ */
+
+/* Size and layout of the frame workspace for n Gaussians and the given views
+ * (host array of n_views >= 1 records).  *layout may be NULL. */
+clod_status clod_frame_workspace_size(int64_t n, const clod_view* views, int32_t n_views,
+                                      size_t* bytes, clod_frame_layout* layout);
+
+/* Per-Gaussian preprocessing of every view (Sec. 3.2 and Sec. 3.1):
+ *   d_i = |mu_i - c|; d_max = max of d over the view frustum (t_z > near and
+ *   projected centre in [0,W]x[0,H]); alpha'' of Eq. 2 with d' = d / d_max;
+ *   mask M_i = alpha'' > tau s_v; for survivors (M_i, t_z > near, det > 0,
+ *   non-empty tile rectangle) the EWA projection (2D covariance + 0.3 I,
+ *   its inverse, 3-sigma radius, 16x16-pixel tile rectangle), depth and the
+ *   SH colour; per-tile pair counts and their exclusive scan.
+ * ws:             frame workspace of ws_bytes >= clod_frame_workspace_size().
+ * mask_out:       u8 [n_views * n] (view-major), the mask M_i of Sec. 3.2;
+ *                 may be NULL.
+ * alpha_eff_out:  f32 [n_views * n] alpha''; may be NULL.
+ * counts_out:     u32 [2 * n_views]: [2v] = sum_i M_i of view v (the count
+ *                 of Eq. 4's eta_actual), [2v + 1] = Gaussians rendered in
+ *                 view v (M_i and the survivor conditions); may be NULL.
+ * n_pairs_out:    u64 [1] total (view, tile, Gaussian) pairs K; may be NULL.
+ * views is read on the host during the call.  Errors: CLOD_ERR_ARG for null
+ * scene arrays (n > 0), n_views < 1, bad sizes or sh_degree; CLOD_ERR_CUDA. */
+clod_status clod_preprocess(const clod_scene* scene, const clod_view* views, int32_t n_views,
+                            void* ws, size_t ws_bytes,
+                            uint8_t* mask_out, float* alpha_eff_out,
+                            uint32_t* counts_out, uint64_t* n_pairs_out,
+                            clod_stream stream);
+
+/* Scratch bytes clod_bin_sort needs for pair_capacity pairs. */
+clod_status clod_sort_workspace_size(uint64_t pair_capacity, size_t* bytes);
+
+/* Bins the pairs of the preprocessed frame by tile and sorts each tile's list
+ * by (depth, Gaussian index) -- "sorted by depth" (Sec. 3.1) with ties in
+ * index order -- i.e. the stable sort of the key
+ * ((tile_base(view) + ty * TX + tx) << 32) | bits(depth).
+ * keys_out:   u64 [pair_capacity] sorted keys; may be NULL.
+ * vals_out:   u32 [pair_capacity] Gaussian index of each sorted pair.
+ * ranges_out: u32 [total_tiles * 2] [first, last) of each tile in vals_out;
+ *             tiles without pairs get [0, 0).
+ * If K > pair_capacity no pair is written past the capacity and the frame is
+ * marked overflowed; clod_frame_check() then returns CLOD_ERR_CAPACITY. */
+clod_status clod_bin_sort(void* ws, uint64_t pair_capacity, void* sort_ws, size_t sort_ws_bytes,
+                          uint64_t* keys_out, uint32_t* vals_out, uint32_t* ranges_out,
+                          clod_stream stream);
+
+/* Front-to-back alpha blending of every tile of every view (Eq. 1):
+ * per pixel, in list order: power = -(A dx^2 + C dy^2)/2 - B dx dy; skip if
+ * power > 0; a = min(0.99, alpha'' exp(power)); skip if a < 1/255; stop
+ * (excluding this Gaussian) once T (1 - a) < 1e-4; colour += rgb a T.
+ * Output colour + T bg.  Packed outputs: view v's pixels start at
+ * P_v = sum_{u<v} W_u H_u; image f32 [3 * sum W H] with view v's planes at
+ * 3 P_v (CHW); T_final f32 [sum W H]; n_contrib u32 [sum W H] (1 + list
+ * position of the last contributor, 0 if none).  T_final and n_contrib may
+ * be NULL.  vals/ranges are clod_bin_sort's outputs for the same frame. */
+clod_status clod_render_fwd(const void* ws, const uint32_t* vals, const uint32_t* ranges,
+                            float* image, float* T_final, uint32_t* n_contrib, clod_stream stream);
+
+/* Synchronises the stream and reads the frame's status: K into *n_pairs
+ * (may be NULL) and CLOD_ERR_CAPACITY if a clod_bin_sort overflowed. */
+clod_status clod_frame_check(const void* ws, uint64_t pair_capacity, uint64_t* n_pairs, clod_stream stream);
+
+/* Same as clod_render_fwd, also accumulating into *evaluated (device u64) the
+ * number of (pixel, Gaussian) pairs whose opacity was evaluated. */
+clod_status clod_render_fwd_count(const void* ws, const uint32_t* vals, const uint32_t* ranges,
+                                  float* image, float* T_final, uint32_t* n_contrib,
+                                  unsigned long long* evaluated, clod_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CLOD_H */

@@ -1,0 +1,383 @@
+// capi.cu -- extern "C" entry points of libclod (see include/clod.h).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "clod_internal.cuh"
+
+namespace clod {
+
+void launch_preprocess(const Frame& F, const clod_scene& S, uint32_t V, uint8_t* mask_out, float* alpha_out,
+                       unsigned long long* n_pairs_out, int n_sm, cudaStream_t st);
+void launch_bin_sort(const Frame& F, int64_t n, uint32_t V, uint32_t total_tiles, unsigned long long* pairs,
+                     unsigned long long* scratch, unsigned long long cap, uint64_t* keys, uint32_t* vals,
+                     uint32_t* ranges, int n_sm, cudaStream_t st);
+void launch_blend_fwd(const Frame& F, const uint32_t* vals, const uint32_t* ranges, float* image, float* Tout,
+                      uint32_t* ncout, unsigned long long* evaluated, int n_sm, cudaStream_t st);
+cudaError_t bin_sort_setup();
+cudaError_t render_setup();
+
+static thread_local std::string g_err;
+
+clod_status fail(clod_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+clod_status cuda_fail(cudaError_t e, const char* what)
+{
+    return fail(CLOD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+FrameLayout frame_layout(uint64_t n, uint32_t V, uint32_t TT)
+{
+    FrameLayout L{};
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = align256(o + bytes);
+        return at;
+    };
+    // zero-initialised block first: header, d_max keys, counts, tile counts
+    L.header = take(sizeof(FrameHeader));
+    L.dmax_key = take(sizeof(unsigned long long) * V);
+    L.n_surv = take(sizeof(uint32_t) * 2 * V);
+    L.tile_count = take(sizeof(uint32_t) * (size_t)TT);
+    L.views = take(sizeof(ViewDev) * V);
+    L.tile_offset = take(sizeof(uint32_t) * ((size_t)TT + 1));
+    L.cursor = take(sizeof(uint32_t) * (size_t)TT);
+    L.big_list = take(sizeof(uint32_t) * (size_t)TT);
+    const size_t vn = (size_t)V * n;
+    L.rec0 = take(sizeof(float4) * vn);
+    L.rec1 = take(sizeof(float4) * vn);
+    L.rec2 = take(sizeof(float) * vn);
+    L.depth = take(sizeof(float) * vn);
+    L.rect = take(sizeof(uint2) * vn);
+    L.total = o;
+    L.total_tiles = TT;
+    L.n_views = V;
+    L.n = n;
+    return L;
+}
+
+Frame frame_ptrs(void* ws, const FrameLayout& L)
+{
+    char* b = static_cast<char*>(ws);
+    Frame F;
+    F.hdr = reinterpret_cast<FrameHeader*>(b + L.header);
+    F.views = reinterpret_cast<ViewDev*>(b + L.views);
+    F.dmax_key = reinterpret_cast<unsigned long long*>(b + L.dmax_key);
+    F.n_surv = reinterpret_cast<uint32_t*>(b + L.n_surv);
+    F.rec0 = reinterpret_cast<float4*>(b + L.rec0);
+    F.rec1 = reinterpret_cast<float4*>(b + L.rec1);
+    F.rec2 = reinterpret_cast<float*>(b + L.rec2);
+    F.depth = reinterpret_cast<float*>(b + L.depth);
+    F.rect = reinterpret_cast<uint2*>(b + L.rect);
+    F.tile_count = reinterpret_cast<uint32_t*>(b + L.tile_count);
+    F.tile_offset = reinterpret_cast<uint32_t*>(b + L.tile_offset);
+    F.cursor = reinterpret_cast<uint32_t*>(b + L.cursor);
+    F.big_list = reinterpret_cast<uint32_t*>(b + L.big_list);
+    return F;
+}
+
+// ---------------------------------------------------------------------------
+struct DeviceInfo {
+    int n_sm = 0;
+    bool ready = false;
+};
+static std::mutex g_dev_mu;
+static DeviceInfo g_dev[64];
+
+clod_status device_ready(int* n_sm)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(CLOD_ERR_CUDA, "device index %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    DeviceInfo& D = g_dev[dev];
+    if (!D.ready) {
+        int major = 0, minor = 0;
+        cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+        if (major != 10 || minor != 3)
+            return fail(CLOD_ERR_CUDA, "libclod is built for sm_103a; device %d is sm_%d%d", dev, major, minor);
+        e = cudaDeviceGetAttribute(&D.n_sm, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+        if ((e = bin_sort_setup()) != cudaSuccess) return cuda_fail(e, "bin_sort_setup");
+        if ((e = render_setup()) != cudaSuccess) return cuda_fail(e, "render_setup");
+        D.ready = true;
+    }
+    *n_sm = D.n_sm;
+    return CLOD_OK;
+}
+
+static clod_status check_views(const clod_view* views, int32_t V, uint32_t* TT)
+{
+    if (!views) return fail(CLOD_ERR_ARG, "views is NULL");
+    if (V < 1 || V > MAX_VIEWS) return fail(CLOD_ERR_ARG, "n_views = %d outside [1, %d]", V, MAX_VIEWS);
+    uint64_t tt = 0, px = 0;
+    for (int v = 0; v < V; ++v) {
+        const clod_view& w = views[v];
+        if (w.width < 1 || w.height < 1 || w.width > 16384 || w.height > 16384)
+            return fail(CLOD_ERR_ARG, "view %d: size %dx%d outside [1, 16384]", v, w.width, w.height);
+        if (!(w.fx > 0.0f) || !(w.fy > 0.0f)) return fail(CLOD_ERR_ARG, "view %d: focal lengths must be > 0", v);
+        if (!std::isfinite(w.s_v) || !std::isfinite(w.tau) || !(w.eps >= 0.0f))
+            return fail(CLOD_ERR_ARG, "view %d: s_v, tau must be finite and eps >= 0", v);
+        tt += (uint64_t)((w.width + TILE - 1) / TILE) * ((w.height + TILE - 1) / TILE);
+        px += (uint64_t)w.width * w.height;
+    }
+    if (tt > 0x0FFFFFFFull) return fail(CLOD_ERR_ARG, "too many tiles (%llu)", (unsigned long long)tt);
+    *TT = static_cast<uint32_t>(tt);
+    return CLOD_OK;
+}
+
+static void make_view_table(const clod_view* views, int32_t V, std::vector<ViewDev>& out)
+{
+    out.resize(V);
+    uint32_t tile_base = 0;
+    uint64_t pix_base = 0;
+    for (int v = 0; v < V; ++v) {
+        const clod_view& w = views[v];
+        ViewDev& d = out[v];
+        std::memset(&d, 0, sizeof(d));
+        for (int r = 0; r < 3; ++r) {
+            for (int c = 0; c < 3; ++c) d.R[3 * r + c] = w.viewmat[4 * r + c];
+            d.t[r] = w.viewmat[4 * r + 3];
+            d.c[r] = w.campos[r];
+            d.bg[r] = w.bg[r];
+        }
+        d.fx = w.fx;
+        d.fy = w.fy;
+        d.cx = w.cx;
+        d.cy = w.cy;
+        d.near_z = w.near_z;
+        d.s_v = w.s_v;
+        d.tau = w.tau;
+        d.eps = w.eps;
+        d.W = w.width;
+        d.H = w.height;
+        d.TX = (w.width + TILE - 1) / TILE;
+        d.TY = (w.height + TILE - 1) / TILE;
+        d.flags = w.flags;
+        d.tile_base = tile_base;
+        d.pix_base = pix_base;
+        tile_base += (uint32_t)(d.TX * d.TY);
+        pix_base += (uint64_t)w.width * w.height;
+    }
+}
+
+static clod_status check_scene(const clod_scene* S)
+{
+    if (!S) return fail(CLOD_ERR_ARG, "scene is NULL");
+    if (S->n < 0 || S->n >= (1ll << 31)) return fail(CLOD_ERR_ARG, "scene n = %lld outside [0, 2^31)", (long long)S->n);
+    if (S->sh_degree < 0 || S->sh_degree > 3) return fail(CLOD_ERR_ARG, "sh_degree %d outside [0, 3]", S->sh_degree);
+    if (S->n > 0 && (!S->means || !S->scales || !S->quats || !S->opacity || !S->sh || !S->decay))
+        return fail(CLOD_ERR_ARG, "scene array pointer is NULL");
+    if (reinterpret_cast<uintptr_t>(S->quats) % 16) return fail(CLOD_ERR_ARG, "quats must be 16-byte aligned");
+    if (S->sh_degree == 3 && reinterpret_cast<uintptr_t>(S->sh) % 16)
+        return fail(CLOD_ERR_ARG, "sh must be 16-byte aligned for degree 3");
+    return CLOD_OK;
+}
+
+// Host-side cache of the last layout per workspace pointer: lets the later
+// pipeline calls size their launches without reading the device header.
+struct WsMeta {
+    const void* ws;
+    FrameLayout L;
+};
+static std::mutex g_ws_mu;
+static std::vector<WsMeta> g_ws;
+
+static void remember(const void* ws, const FrameLayout& L)
+{
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    for (auto& m : g_ws)
+        if (m.ws == ws) {
+            m.L = L;
+            return;
+        }
+    if (g_ws.size() > 256) g_ws.erase(g_ws.begin());
+    g_ws.push_back({ws, L});
+}
+
+static bool recall(const void* ws, FrameLayout* L)
+{
+    std::lock_guard<std::mutex> lk(g_ws_mu);
+    for (auto& m : g_ws)
+        if (m.ws == ws) {
+            *L = m.L;
+            return true;
+        }
+    return false;
+}
+
+}  // namespace clod
+
+using namespace clod;
+
+extern "C" {
+
+const char* clod_last_error(void) { return g_err.c_str(); }
+
+const char* clod_version(void) { return "libclod 0.1 (sm_103a)"; }
+
+clod_status clod_frame_workspace_size(int64_t n, const clod_view* views, int32_t n_views, size_t* bytes,
+                                      clod_frame_layout* layout)
+{
+    if (!bytes) return fail(CLOD_ERR_ARG, "bytes is NULL");
+    if (n < 0 || n >= (1ll << 31)) return fail(CLOD_ERR_ARG, "n = %lld outside [0, 2^31)", (long long)n);
+    uint32_t TT = 0;
+    clod_status s = check_views(views, n_views, &TT);
+    if (s) return s;
+    const FrameLayout L = frame_layout((uint64_t)n, (uint32_t)n_views, TT);
+    *bytes = L.total;
+    if (layout) {
+        layout->total_bytes = L.total;
+        layout->views = L.views;
+        layout->dmax_key = L.dmax_key;
+        layout->n_survivors = L.n_surv;
+        layout->rec0 = L.rec0;
+        layout->rec1 = L.rec1;
+        layout->rec2 = L.rec2;
+        layout->depth = L.depth;
+        layout->rect = L.rect;
+        layout->tile_count = L.tile_count;
+        layout->tile_offset = L.tile_offset;
+        layout->total_tiles = TT;
+        layout->n_views = (uint32_t)n_views;
+    }
+    return CLOD_OK;
+}
+
+clod_status clod_preprocess(const clod_scene* scene, const clod_view* views, int32_t n_views, void* ws,
+                            size_t ws_bytes, uint8_t* mask_out, float* alpha_eff_out, uint32_t* counts_out,
+                            uint64_t* n_pairs_out, clod_stream stream)
+{
+    clod_status s = check_scene(scene);
+    if (s) return s;
+    uint32_t TT = 0;
+    if ((s = check_views(views, n_views, &TT))) return s;
+    if (!ws) return fail(CLOD_ERR_ARG, "ws is NULL");
+    if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(CLOD_ERR_ARG, "ws must be 256-byte aligned");
+    const FrameLayout L = frame_layout((uint64_t)scene->n, (uint32_t)n_views, TT);
+    if (ws_bytes < L.total)
+        return fail(CLOD_ERR_CAPACITY, "frame workspace needs %zu bytes, got %zu", L.total, ws_bytes);
+    int n_sm = 0;
+    if ((s = device_ready(&n_sm))) return s;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const Frame F = frame_ptrs(ws, L);
+    std::vector<ViewDev> table;
+    make_view_table(views, n_views, table);
+    FrameHeader h{};
+    h.n = (uint64_t)scene->n;
+    h.n_views = (uint32_t)n_views;
+    h.total_tiles = TT;
+    cudaError_t e = cudaMemsetAsync(ws, 0, L.views, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(F.hdr, &h, sizeof(h), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(F.views, table.data(), sizeof(ViewDev) * n_views, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "clod_preprocess upload");
+    launch_preprocess(F, *scene, (uint32_t)n_views, mask_out, alpha_eff_out,
+                      reinterpret_cast<unsigned long long*>(n_pairs_out), n_sm, st);
+    if (counts_out) {
+        e = cudaMemcpyAsync(counts_out, F.n_surv, sizeof(uint32_t) * 2 * n_views, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(e, "clod_preprocess counts");
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "clod_preprocess launch");
+    remember(ws, L);
+    return CLOD_OK;
+}
+
+clod_status clod_sort_workspace_size(uint64_t pair_capacity, size_t* bytes)
+{
+    if (!bytes) return fail(CLOD_ERR_ARG, "bytes is NULL");
+    if (pair_capacity > 0xFFFFFFFFull) return fail(CLOD_ERR_ARG, "pair_capacity above 2^32 - 1");
+    *bytes = std::max<size_t>(256, (size_t)pair_capacity * 16);
+    return CLOD_OK;
+}
+
+clod_status clod_bin_sort(void* ws, uint64_t pair_capacity, void* sort_ws, size_t sort_ws_bytes, uint64_t* keys_out,
+                          uint32_t* vals_out, uint32_t* ranges_out, clod_stream stream)
+{
+    if (!ws || !sort_ws || !vals_out || !ranges_out) return fail(CLOD_ERR_ARG, "NULL argument to clod_bin_sort");
+    FrameLayout L;
+    if (!recall(ws, &L)) return fail(CLOD_ERR_ARG, "ws was not prepared by clod_preprocess");
+    size_t need = 0;
+    clod_status s = clod_sort_workspace_size(pair_capacity, &need);
+    if (s) return s;
+    if (sort_ws_bytes < need) return fail(CLOD_ERR_CAPACITY, "sort workspace needs %zu bytes, got %zu", need, sort_ws_bytes);
+    int n_sm = 0;
+    if ((s = device_ready(&n_sm))) return s;
+    const Frame F = frame_ptrs(ws, L);
+    unsigned long long* pairs = static_cast<unsigned long long*>(sort_ws);
+    unsigned long long* scratch = pairs + pair_capacity;
+    launch_bin_sort(F, (int64_t)L.n, L.n_views, L.total_tiles, pairs, scratch, pair_capacity, keys_out, vals_out,
+                    ranges_out, n_sm, static_cast<cudaStream_t>(stream));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "clod_bin_sort launch");
+    return CLOD_OK;
+}
+
+static clod_status render_common(const void* ws, const uint32_t* vals, const uint32_t* ranges, float* image,
+                                 float* T_final, uint32_t* n_contrib, unsigned long long* evaluated, clod_stream stream)
+{
+    if (!ws || !ranges || !image) return fail(CLOD_ERR_ARG, "NULL argument to clod_render_fwd");
+    FrameLayout L;
+    if (!recall(ws, &L)) return fail(CLOD_ERR_ARG, "ws was not prepared by clod_preprocess");
+    int n_sm = 0;
+    clod_status s = device_ready(&n_sm);
+    if (s) return s;
+    const Frame F = frame_ptrs(const_cast<void*>(ws), L);
+    launch_blend_fwd(F, vals, ranges, image, T_final, n_contrib, evaluated, n_sm, static_cast<cudaStream_t>(stream));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "clod_render_fwd launch");
+    return CLOD_OK;
+}
+
+clod_status clod_render_fwd(const void* ws, const uint32_t* vals, const uint32_t* ranges, float* image, float* T_final,
+                            uint32_t* n_contrib, clod_stream stream)
+{
+    return render_common(ws, vals, ranges, image, T_final, n_contrib, nullptr, stream);
+}
+
+clod_status clod_render_fwd_count(const void* ws, const uint32_t* vals, const uint32_t* ranges, float* image,
+                                  float* T_final, uint32_t* n_contrib, unsigned long long* evaluated,
+                                  clod_stream stream)
+{
+    if (!evaluated) return fail(CLOD_ERR_ARG, "evaluated is NULL");
+    return render_common(ws, vals, ranges, image, T_final, n_contrib, evaluated, stream);
+}
+
+clod_status clod_frame_check(const void* ws, uint64_t pair_capacity, uint64_t* n_pairs, clod_stream stream)
+{
+    if (!ws) return fail(CLOD_ERR_ARG, "ws is NULL");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "clod_frame_check sync");
+    FrameHeader h;
+    e = cudaMemcpy(&h, ws, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "clod_frame_check read");
+    if (n_pairs) *n_pairs = h.n_pairs;
+    if ((h.status & STATUS_OVERFLOW) || h.n_pairs > pair_capacity)
+        return fail(CLOD_ERR_CAPACITY, "frame needs %llu pairs, capacity %llu", (unsigned long long)h.n_pairs,
+                    (unsigned long long)pair_capacity);
+    if (h.status & STATUS_TIMEOUT) return fail(CLOD_ERR_TIMEOUT, "a device wait gave up");
+    return CLOD_OK;
+}
+
+}  // extern "C"

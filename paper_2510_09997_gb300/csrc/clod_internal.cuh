@@ -1,0 +1,222 @@
+// clod_internal.cuh -- device-side records and the fixed FP32 operation
+// sequences shared by the libclod kernels.
+//
+// Every translation unit is compiled with --fmad=false: a*b+c is never fused
+// implicitly; every fused multiply-add below is an explicit __fmaf_rn.  Together
+// with IEEE division and square root (__fdiv_rn, __fsqrt_rn) this makes each
+// quantity that decides an integer outcome a fixed sequence of correctly
+// rounded operations.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/clod.h"
+
+namespace clod {
+
+constexpr int TILE = 16;
+constexpr int BLOCK_PIX = TILE * TILE;  // 256 threads per tile block
+constexpr int MAX_VIEWS = 64;
+
+// Frame header at offset 0 of a frame workspace.
+struct FrameHeader {
+    uint64_t n;             // Gaussians
+    uint32_t n_views;
+    uint32_t total_tiles;
+    unsigned long long n_pairs;  // K, written by the tile scan
+    uint32_t status;        // STATUS_* bits
+    uint32_t big_count;     // tiles whose list is sorted by the large-segment kernel
+    uint32_t work[4];       // spare counters
+};
+constexpr uint32_t STATUS_OVERFLOW = 1u;
+constexpr uint32_t STATUS_TIMEOUT = 2u;
+
+// Device view record (host-built from clod_view).
+struct ViewDev {
+    float R[9];
+    float t[3];
+    float fx, fy, cx, cy, near_z;
+    float c[3];
+    float s_v, tau, eps;
+    float bg[3];
+    int32_t W, H, TX, TY;
+    uint32_t flags;
+    uint32_t tile_base;     // global id of this view's first tile
+    uint64_t pix_base;      // first pixel of this view in packed outputs
+    uint32_t pad[2];
+};
+
+struct FrameLayout {
+    size_t header, views, dmax_key, n_surv, rec0, rec1, rec2, depth, rect, tile_count, tile_offset,
+        cursor, big_list, total;
+    uint32_t total_tiles, n_views;
+    uint64_t n;
+};
+
+// Pointers into a frame workspace.
+struct Frame {
+    FrameHeader* hdr;
+    ViewDev* views;
+    unsigned long long* dmax_key;
+    uint32_t* n_surv;
+    float4* rec0;
+    float4* rec1;
+    float* rec2;
+    float* depth;
+    uint2* rect;
+    uint32_t* tile_count;
+    uint32_t* tile_offset;
+    uint32_t* cursor;
+    uint32_t* big_list;
+};
+
+// ---------------------------------------------------------------------------
+// exp_spec: x = k ln2 + r, k = floor(x * L2E) with L2E = 1/ln2 rounded up to
+// float (so r >= 0), e^r by a degree-9 Taylor polynomial (Horner), capped at
+// 2, scaled by 2^k.  Monotone non-decreasing; 0 below -80 and for NaN.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float exp_spec(float x)
+{
+    if (!(x >= -80.0f)) return 0.0f;
+    if (x > 0.0f) x = 0.0f;
+    const float L2E = __int_as_float(0x3FB8AA3C);
+    const float MAGIC = 12582912.0f;
+    const float LN2HI = __int_as_float(0x3F317218);
+    const float LN2LO = __int_as_float(0xB102E308);
+    float t = __fmaf_rn(x, L2E, MAGIC);
+    float kf = __fsub_rn(t, MAGIC);
+    if (__fmaf_rn(x, L2E, -kf) < 0.0f) kf = __fsub_rn(kf, 1.0f);
+    float r = __fmaf_rn(kf, -LN2HI, x);
+    r = __fmaf_rn(kf, -LN2LO, r);
+    float p = __int_as_float(0x3638EF1D);            // 1/9!
+    p = __fmaf_rn(p, r, __int_as_float(0x37D00D01)); // 1/8!
+    p = __fmaf_rn(p, r, __int_as_float(0x39500D01)); // 1/7!
+    p = __fmaf_rn(p, r, __int_as_float(0x3AB60B61)); // 1/6!
+    p = __fmaf_rn(p, r, __int_as_float(0x3C088889)); // 1/5!
+    p = __fmaf_rn(p, r, __int_as_float(0x3D2AAAAB)); // 1/4!
+    p = __fmaf_rn(p, r, __int_as_float(0x3E2AAAAB)); // 1/3!
+    p = __fmaf_rn(p, r, 0.5f);
+    p = __fmaf_rn(p, r, 1.0f);
+    p = __fmaf_rn(p, r, 1.0f);
+    p = fminf(p, 2.0f);
+    // p in [1, 2], k >= -116: the scaled value is a normal float
+    return __int_as_float(__float_as_int(p) + (static_cast<int>(kf) << 23));
+}
+
+// Camera-frame point: t_k = R_k0 x + (R_k1 y + (R_k2 z + t_k)), fused.
+__device__ __forceinline__ void cam_point(const ViewDev& V, float x, float y, float z, float& tx, float& ty,
+                                          float& tz)
+{
+    tx = __fmaf_rn(V.R[0], x, __fmaf_rn(V.R[1], y, __fmaf_rn(V.R[2], z, V.t[0])));
+    ty = __fmaf_rn(V.R[3], x, __fmaf_rn(V.R[4], y, __fmaf_rn(V.R[5], z, V.t[1])));
+    tz = __fmaf_rn(V.R[6], x, __fmaf_rn(V.R[7], y, __fmaf_rn(V.R[8], z, V.t[2])));
+}
+
+// Camera distance d = sqrt(e0^2 + e1^2 + e2^2), e = mu - c.
+__device__ __forceinline__ float cam_dist(const ViewDev& V, float x, float y, float z, float& e0, float& e1,
+                                          float& e2)
+{
+    e0 = __fsub_rn(x, V.c[0]);
+    e1 = __fsub_rn(y, V.c[1]);
+    e2 = __fsub_rn(z, V.c[2]);
+    return __fsqrt_rn(__fmaf_rn(e0, e0, __fmaf_rn(e1, e1, __fmul_rn(e2, e2))));
+}
+
+// Projected centre u = fx (tx/tz) + cx, v likewise.
+__device__ __forceinline__ void project(const ViewDev& V, float tx, float ty, float tz, float& u, float& v)
+{
+    u = __fmaf_rn(V.fx, __fdiv_rn(tx, tz), V.cx);
+    v = __fmaf_rn(V.fy, __fdiv_rn(ty, tz), V.cy);
+}
+
+// Centre inside the view frustum: t_z > near and (u, v) in [0,W]x[0,H].
+__device__ __forceinline__ bool in_frustum(const ViewDev& V, float tx, float ty, float tz)
+{
+    if (!(tz > V.near_z)) return false;
+    float u, v;
+    project(V, tx, ty, tz, u, v);
+    return (u >= 0.0f) && (u <= static_cast<float>(V.W)) && (v >= 0.0f) && (v <= static_cast<float>(V.H));
+}
+
+// Attenuated opacity of Eq. 2 (dmax = 0 means no Gaussian in the frustum).
+__device__ __forceinline__ float attenuated_opacity(const ViewDev& V, float alpha, float sigma, float d,
+                                                    float dmax)
+{
+    if (V.flags & CLOD_LOD_OFF) return alpha;
+    float dn;
+    if (V.flags & CLOD_NO_NORMALIZE) dn = d;
+    else dn = dmax > 0.0f ? __fdiv_rn(d, dmax) : 0.0f;
+    float q = __fmul_rn(dn, V.s_v);
+    float sr = sigma > 0.0f ? sigma : 0.0f;
+    float den = __fmaf_rn(__fadd_rn(sr, sr), sr, V.eps);
+    float xx = __fdiv_rn(__fmul_rn(q, q), den);
+    return __fmul_rn(alpha, exp_spec(-xx));
+}
+
+__device__ __forceinline__ float decode_dmax(unsigned long long key)
+{
+    return __uint_as_float(static_cast<uint32_t>(key >> 32));
+}
+
+// Spherical-harmonic basis constants (real basis, degree <= 3, colour-model signs).
+#define CLOD_SH_C0 0.28209479177387814f
+#define CLOD_SH_C1 0.4886025119029199f
+#define CLOD_SH_C2_0 1.0925484305920792f
+#define CLOD_SH_C2_1 (-1.0925484305920792f)
+#define CLOD_SH_C2_2 0.31539156525252005f
+#define CLOD_SH_C2_3 (-1.0925484305920792f)
+#define CLOD_SH_C2_4 0.5462742152960396f
+#define CLOD_SH_C3_0 (-0.5900435899266435f)
+#define CLOD_SH_C3_1 2.890611442640554f
+#define CLOD_SH_C3_2 (-0.4570457994644658f)
+#define CLOD_SH_C3_3 0.3731763325901154f
+#define CLOD_SH_C3_4 (-0.4570457994644658f)
+#define CLOD_SH_C3_5 1.445305721320277f
+#define CLOD_SH_C3_6 (-0.5900435899266435f)
+
+// Basis values b[0..(deg+1)^2) at unit direction (x, y, z).
+__device__ __forceinline__ void sh_basis(float x, float y, float z, int deg, float* b)
+{
+    b[0] = CLOD_SH_C0;
+    if (deg < 1) return;
+    b[1] = __fmul_rn(-CLOD_SH_C1, y);
+    b[2] = __fmul_rn(CLOD_SH_C1, z);
+    b[3] = __fmul_rn(-CLOD_SH_C1, x);
+    if (deg < 2) return;
+    const float xx = __fmul_rn(x, x), yy = __fmul_rn(y, y), zz = __fmul_rn(z, z);
+    const float xy = __fmul_rn(x, y), yz = __fmul_rn(y, z), xz = __fmul_rn(x, z);
+    b[4] = __fmul_rn(CLOD_SH_C2_0, xy);
+    b[5] = __fmul_rn(CLOD_SH_C2_1, yz);
+    b[6] = __fmul_rn(CLOD_SH_C2_2, __fsub_rn(__fsub_rn(__fadd_rn(zz, zz), xx), yy));
+    b[7] = __fmul_rn(CLOD_SH_C2_3, xz);
+    b[8] = __fmul_rn(CLOD_SH_C2_4, __fsub_rn(xx, yy));
+    if (deg < 3) return;
+    b[9] = __fmul_rn(CLOD_SH_C3_0, __fmul_rn(y, __fsub_rn(__fmul_rn(3.0f, xx), yy)));
+    b[10] = __fmul_rn(CLOD_SH_C3_1, __fmul_rn(xy, z));
+    b[11] = __fmul_rn(CLOD_SH_C3_2, __fmul_rn(y, __fsub_rn(__fsub_rn(__fmul_rn(4.0f, zz), xx), yy)));
+    b[12] = __fmul_rn(CLOD_SH_C3_3,
+                      __fmul_rn(z, __fsub_rn(__fsub_rn(__fmul_rn(2.0f, zz), __fmul_rn(3.0f, xx)), __fmul_rn(3.0f, yy))));
+    b[13] = __fmul_rn(CLOD_SH_C3_4, __fmul_rn(x, __fsub_rn(__fsub_rn(__fmul_rn(4.0f, zz), xx), yy)));
+    b[14] = __fmul_rn(CLOD_SH_C3_5, __fmul_rn(z, __fsub_rn(xx, yy)));
+    b[15] = __fmul_rn(CLOD_SH_C3_6, __fmul_rn(x, __fsub_rn(xx, __fmul_rn(3.0f, yy))));
+}
+
+// The blend's per-(pixel, Gaussian) opacity, in the decision arithmetic:
+// power = dx (-A/2 dx + -B dy) + (-C/2 dy) dy, a = min(0.99, alpha'' exp(power)).
+// Returns a < 0 for "skip".  power < -5.6 is skipped without evaluating the
+// exponential: exp_spec(-5.6) < 1/255 and exp_spec is monotone, so for such
+// powers a < 1/255 for every alpha'' <= 1 and the outcome is the same.
+__device__ __forceinline__ float blend_alpha(float dx, float dy, float nA, float nB, float nC, float a2)
+{
+    const float power = __fmaf_rn(dx, __fmaf_rn(nA, dx, __fmul_rn(nB, dy)), __fmul_rn(__fmul_rn(nC, dy), dy));
+    if (power > 0.0f || power < -5.6f) return -1.0f;
+    const float a = fminf(0.99f, __fmul_rn(a2, exp_spec(power)));
+    return a < (1.0f / 255.0f) ? -1.0f : a;
+}
+
+// Frame workspace layout (256-byte aligned arrays).
+FrameLayout frame_layout(uint64_t n, uint32_t n_views, uint32_t total_tiles);
+Frame frame_ptrs(void* ws, const FrameLayout& L);
+
+}  // namespace clod

@@ -1,0 +1,331 @@
+// preprocess.cu -- per-Gaussian stage of the CLoD-GS rasterizer.
+//
+//   k_dist_max   d_i = |mu_i - c| and the max of d over the view frustum
+//                (Sec. 3.2), with the lowest index among ties.
+//   k_preprocess attenuated opacity alpha'' (Eq. 2) and the mask
+//                M_i = alpha'' > tau s_v (Sec. 3.2); for survivors the EWA
+//                projection, conic, 3-sigma radius, tile rectangle, depth and
+//                SH colour (Sec. 3.1); per-tile pair counts.
+//   k_scan_tiles exclusive scan of the per-tile counts -> tile offsets and K.
+//
+// Layout: scene arrays are read structure-of-arrays, one Gaussian per thread,
+// consecutive Gaussians in consecutive threads (coalesced 12/16-byte rows);
+// SH rows (up to 192 B) are read only for survivors.  Outputs are
+// view-major [v * n + i].
+#include <algorithm>
+
+#include "clod_internal.cuh"
+
+namespace clod {
+
+__device__ __forceinline__ void load_views(ViewDev* sv, const ViewDev* views, uint32_t V)
+{
+    const int words = static_cast<int>(V * sizeof(ViewDev) / 4);
+    const int* src = reinterpret_cast<const int*>(views);
+    int* dst = reinterpret_cast<int*>(sv);
+    for (int k = threadIdx.x; k < words; k += blockDim.x) dst[k] = src[k];
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long x)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long y = __shfl_xor_sync(0xffffffffu, x, o);
+        x = y > x ? y : x;
+    }
+    return x;
+}
+
+// Pass A.  Key = (bits(d) << 32) | (0xFFFFFFFF - i): the max key carries the
+// max distance (d >= 0, so its bits order like the value) and, among equal
+// distances, the lowest index.  0 means "no Gaussian in the frustum".
+__global__ void __launch_bounds__(256) k_dist_max(Frame F, const float* __restrict__ means, int64_t n,
+                                                  uint32_t V)
+{
+    __shared__ ViewDev sv[MAX_VIEWS];
+    __shared__ unsigned long long wmax[8];
+    load_views(sv, F.views, V);
+    __syncthreads();
+    for (uint32_t v = 0; v < V; ++v) {
+        const ViewDev& W = sv[v];
+        unsigned long long best = 0ull;
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            const float x = means[3 * i], y = means[3 * i + 1], z = means[3 * i + 2];
+            float tx, ty, tz, e0, e1, e2;
+            cam_point(W, x, y, z, tx, ty, tz);
+            const float d = cam_dist(W, x, y, z, e0, e1, e2);
+            if (in_frustum(W, tx, ty, tz)) {
+                const unsigned long long key =
+                    (static_cast<unsigned long long>(__float_as_uint(d)) << 32) |
+                    static_cast<unsigned long long>(0xFFFFFFFFu - static_cast<uint32_t>(i));
+                best = key > best ? key : best;
+            }
+        }
+        best = warp_max_u64(best);
+        if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = best;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            unsigned long long b = threadIdx.x < (blockDim.x >> 5) ? wmax[threadIdx.x] : 0ull;
+            b = warp_max_u64(b);
+            if (threadIdx.x == 0 && b) atomicMax(&F.dmax_key[v], b);
+        }
+        __syncthreads();
+    }
+}
+
+// Pass B.
+__global__ void __launch_bounds__(256) k_preprocess(Frame F, clod_scene S, uint32_t V, uint8_t* __restrict__ mask_out,
+                                                    float* __restrict__ alpha_out)
+{
+    __shared__ ViewDev sv[MAX_VIEWS];
+    __shared__ float sdmax[MAX_VIEWS];
+    __shared__ uint32_t cnt_mask[MAX_VIEWS], cnt_surv[MAX_VIEWS];
+    load_views(sv, F.views, V);
+    for (uint32_t v = threadIdx.x; v < V; v += blockDim.x) {
+        sdmax[v] = decode_dmax(F.dmax_key[v]);
+        cnt_mask[v] = 0;
+        cnt_surv[v] = 0;
+    }
+    __syncthreads();
+    const int64_t n = S.n;
+    const int deg = S.sh_degree;
+    const int K = (deg + 1) * (deg + 1);
+    // block-uniform trip count: every lane reaches the ballots below
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const bool active = i < n;
+        float mx = 0.f, my = 0.f, mz = 0.f, alpha = 0.f, sigma = 0.f;
+        if (active) {
+            mx = S.means[3 * i];
+            my = S.means[3 * i + 1];
+            mz = S.means[3 * i + 2];
+            alpha = S.opacity[i];
+            sigma = S.decay[i];
+        }
+        for (uint32_t v = 0; v < V; ++v) {
+            const ViewDev& W = sv[v];
+            const int64_t o = (int64_t)v * n + i;
+            float e0, e1, e2;
+            const float d = cam_dist(W, mx, my, mz, e0, e1, e2);
+            const float a2 = attenuated_opacity(W, alpha, sigma, d, sdmax[v]);
+            const bool M = active && ((W.flags & CLOD_LOD_OFF) ? true : (a2 > __fmul_rn(W.s_v, W.tau)));
+            if (active && alpha_out) alpha_out[o] = a2;
+            if (active && mask_out) mask_out[o] = M ? 1 : 0;
+            uint2 rect = make_uint2(0u, 0u);
+            bool surv = false;
+            if (M) {
+                float tx, ty, tz;
+                cam_point(W, mx, my, mz, tx, ty, tz);
+                float u = 0.f, vv = 0.f;
+                if (tz > W.near_z) project(W, tx, ty, tz, u, vv);
+                const bool ok0 = (tz > W.near_z) && isfinite(u) && isfinite(vv);
+                // 3D covariance Sigma = R S S^T R^T
+                float qw = 0.f, qx = 0.f, qy = 0.f, qz = 0.f;
+                bool ok1 = false;
+                if (ok0) {
+                    const float4 q = reinterpret_cast<const float4*>(S.quats)[i];
+                    const float n2 = __fmaf_rn(q.x, q.x, __fmaf_rn(q.y, q.y, __fmaf_rn(q.z, q.z, __fmul_rn(q.w, q.w))));
+                    ok1 = n2 > 0.0f;
+                    const float inv = __fdiv_rn(1.0f, __fsqrt_rn(n2));
+                    qw = __fmul_rn(q.x, inv);
+                    qx = __fmul_rn(q.y, inv);
+                    qy = __fmul_rn(q.z, inv);
+                    qz = __fmul_rn(q.w, inv);
+                }
+                if (ok1) {
+                    const float xx = __fmul_rn(qx, qx), yy = __fmul_rn(qy, qy), zz = __fmul_rn(qz, qz);
+                    const float xy = __fmul_rn(qx, qy), xz = __fmul_rn(qx, qz), yz = __fmul_rn(qy, qz);
+                    const float wx = __fmul_rn(qw, qx), wy = __fmul_rn(qw, qy), wz = __fmul_rn(qw, qz);
+                    float r[9];
+                    r[0] = __fmaf_rn(-2.0f, __fadd_rn(yy, zz), 1.0f);
+                    r[1] = __fmul_rn(2.0f, __fsub_rn(xy, wz));
+                    r[2] = __fmul_rn(2.0f, __fadd_rn(xz, wy));
+                    r[3] = __fmul_rn(2.0f, __fadd_rn(xy, wz));
+                    r[4] = __fmaf_rn(-2.0f, __fadd_rn(xx, zz), 1.0f);
+                    r[5] = __fmul_rn(2.0f, __fsub_rn(yz, wx));
+                    r[6] = __fmul_rn(2.0f, __fsub_rn(xz, wy));
+                    r[7] = __fmul_rn(2.0f, __fadd_rn(yz, wx));
+                    r[8] = __fmaf_rn(-2.0f, __fadd_rn(xx, yy), 1.0f);
+                    const float s0 = S.scales[3 * i], s1 = S.scales[3 * i + 1], s2 = S.scales[3 * i + 2];
+                    float Mm[9];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) {
+                        Mm[3 * a] = __fmul_rn(r[3 * a], s0);
+                        Mm[3 * a + 1] = __fmul_rn(r[3 * a + 1], s1);
+                        Mm[3 * a + 2] = __fmul_rn(r[3 * a + 2], s2);
+                    }
+                    float Sg[9];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+#pragma unroll
+                        for (int b = a; b < 3; ++b) {
+                            const float val = __fmaf_rn(Mm[3 * a], Mm[3 * b],
+                                                        __fmaf_rn(Mm[3 * a + 1], Mm[3 * b + 1],
+                                                                  __fmul_rn(Mm[3 * a + 2], Mm[3 * b + 2])));
+                            Sg[3 * a + b] = val;
+                            Sg[3 * b + a] = val;
+                        }
+                    // EWA: cov2D = J W Sigma W^T J^T + 0.3 I
+                    const float Wf = static_cast<float>(W.W), Hf = static_cast<float>(W.H);
+                    const float limx = __fmul_rn(1.3f, __fdiv_rn(__fmul_rn(0.5f, Wf), W.fx));
+                    const float limy = __fmul_rn(1.3f, __fdiv_rn(__fmul_rn(0.5f, Hf), W.fy));
+                    const float txc = __fmul_rn(fminf(limx, fmaxf(-limx, __fdiv_rn(tx, tz))), tz);
+                    const float tyc = __fmul_rn(fminf(limy, fmaxf(-limy, __fdiv_rn(ty, tz))), tz);
+                    const float tz2 = __fmul_rn(tz, tz);
+                    const float j00 = __fdiv_rn(W.fx, tz), j02 = __fdiv_rn(-__fmul_rn(W.fx, txc), tz2);
+                    const float j11 = __fdiv_rn(W.fy, tz), j12 = __fdiv_rn(-__fmul_rn(W.fy, tyc), tz2);
+                    float T0[3], T1[3];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        T0[k] = __fmaf_rn(j00, W.R[k], __fmul_rn(j02, W.R[6 + k]));
+                        T1[k] = __fmaf_rn(j11, W.R[3 + k], __fmul_rn(j12, W.R[6 + k]));
+                    }
+                    float U0[3], U1[3];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        U0[k] = __fmaf_rn(T0[0], Sg[k], __fmaf_rn(T0[1], Sg[3 + k], __fmul_rn(T0[2], Sg[6 + k])));
+                        U1[k] = __fmaf_rn(T1[0], Sg[k], __fmaf_rn(T1[1], Sg[3 + k], __fmul_rn(T1[2], Sg[6 + k])));
+                    }
+                    const float ca = __fadd_rn(__fmaf_rn(U0[0], T0[0], __fmaf_rn(U0[1], T0[1], __fmul_rn(U0[2], T0[2]))), 0.3f);
+                    const float cb = __fmaf_rn(U0[0], T1[0], __fmaf_rn(U0[1], T1[1], __fmul_rn(U0[2], T1[2])));
+                    const float cc = __fadd_rn(__fmaf_rn(U1[0], T1[0], __fmaf_rn(U1[1], T1[1], __fmul_rn(U1[2], T1[2]))), 0.3f);
+                    const float det = __fmaf_rn(ca, cc, -__fmul_rn(cb, cb));
+                    if (det > 0.0f) {
+                        const float idet = __fdiv_rn(1.0f, det);
+                        const float A = __fmul_rn(cc, idet), B = __fmul_rn(-cb, idet), C = __fmul_rn(ca, idet);
+                        // 3-sigma radius and tile rectangle
+                        const float mid = __fmul_rn(0.5f, __fadd_rn(ca, cc));
+                        const float disc = fmaxf(0.1f, __fmaf_rn(mid, mid, -det));
+                        const float lam = __fadd_rn(mid, __fsqrt_rn(disc));
+                        const float rad = ceilf(__fmul_rn(3.0f, __fsqrt_rn(lam)));
+                        const float fx0 = floorf(__fmul_rn(__fsub_rn(u, rad), 0.0625f));
+                        const float fx1 = floorf(__fmul_rn(__fadd_rn(u, rad), 0.0625f));
+                        const float fy0 = floorf(__fmul_rn(__fsub_rn(vv, rad), 0.0625f));
+                        const float fy1 = floorf(__fmul_rn(__fadd_rn(vv, rad), 0.0625f));
+                        const float TXm = static_cast<float>(W.TX) - 1.0f, TYm = static_cast<float>(W.TY) - 1.0f;
+                        if (!(fx1 < 0.0f || fx0 > TXm || fy1 < 0.0f || fy0 > TYm)) {
+                            const int x0 = fx0 < 0.0f ? 0 : static_cast<int>(fx0);
+                            const int x1 = fx1 > TXm ? W.TX : static_cast<int>(fx1) + 1;
+                            const int y0 = fy0 < 0.0f ? 0 : static_cast<int>(fy0);
+                            const int y1 = fy1 > TYm ? W.TY : static_cast<int>(fy1) + 1;
+                            // colour from SH at direction (mu - c) / d
+                            const float dx = __fdiv_rn(e0, d), dy = __fdiv_rn(e1, d), dz = __fdiv_rn(e2, d);
+                            float bsh[16];
+                            sh_basis(dx, dy, dz, deg, bsh);
+                            const float* shp = S.sh + (size_t)i * K * 3;
+                            float c0 = __fmul_rn(bsh[0], shp[0]);
+                            float c1 = __fmul_rn(bsh[0], shp[1]);
+                            float c2 = __fmul_rn(bsh[0], shp[2]);
+                            if (deg == 3) {
+                                const float4* s4 = reinterpret_cast<const float4*>(shp);
+                                float sh_r[48];
+#pragma unroll
+                                for (int k = 0; k < 12; ++k) {
+                                    const float4 w4 = s4[k];
+                                    sh_r[4 * k] = w4.x;
+                                    sh_r[4 * k + 1] = w4.y;
+                                    sh_r[4 * k + 2] = w4.z;
+                                    sh_r[4 * k + 3] = w4.w;
+                                }
+#pragma unroll
+                                for (int k = 1; k < 16; ++k) {
+                                    c0 = __fmaf_rn(bsh[k], sh_r[3 * k], c0);
+                                    c1 = __fmaf_rn(bsh[k], sh_r[3 * k + 1], c1);
+                                    c2 = __fmaf_rn(bsh[k], sh_r[3 * k + 2], c2);
+                                }
+                            } else {
+                                for (int k = 1; k < K; ++k) {
+                                    c0 = __fmaf_rn(bsh[k], shp[3 * k], c0);
+                                    c1 = __fmaf_rn(bsh[k], shp[3 * k + 1], c1);
+                                    c2 = __fmaf_rn(bsh[k], shp[3 * k + 2], c2);
+                                }
+                            }
+                            c0 = fmaxf(__fadd_rn(c0, 0.5f), 0.0f);
+                            c1 = fmaxf(__fadd_rn(c1, 0.5f), 0.0f);
+                            c2 = fmaxf(__fadd_rn(c2, 0.5f), 0.0f);
+                            F.rec0[o] = make_float4(u, vv, __fmul_rn(-0.5f, A), -B);
+                            F.rec1[o] = make_float4(__fmul_rn(-0.5f, C), a2, c0, c1);
+                            F.rec2[o] = c2;
+                            F.depth[o] = tz;
+                            rect = make_uint2(static_cast<uint32_t>(x0) | (static_cast<uint32_t>(y0) << 16),
+                                              static_cast<uint32_t>(x1) | (static_cast<uint32_t>(y1) << 16));
+                            surv = true;
+                            for (int ty = y0; ty < y1; ++ty)
+                                for (int tx_ = x0; tx_ < x1; ++tx_)
+                                    atomicAdd(&F.tile_count[W.tile_base + ty * W.TX + tx_], 1u);
+                        }
+                    }
+                }
+            }
+            if (active) F.rect[o] = rect;
+            // per-view counts: warp-aggregated, then one shared atomic per warp
+            const unsigned bm = __ballot_sync(0xffffffffu, M);
+            const unsigned bs = __ballot_sync(0xffffffffu, surv);
+            if ((threadIdx.x & 31) == 0) {
+                if (bm) atomicAdd_block(&cnt_mask[v], __popc(bm));
+                if (bs) atomicAdd_block(&cnt_surv[v], __popc(bs));
+            }
+        }
+    }
+    __syncthreads();
+    for (uint32_t v = threadIdx.x; v < V; v += blockDim.x) {
+        if (cnt_mask[v]) atomicAdd(&F.n_surv[2 * v], cnt_mask[v]);
+        if (cnt_surv[v]) atomicAdd(&F.n_surv[2 * v + 1], cnt_surv[v]);
+    }
+}
+
+// Exclusive scan of the per-tile counts by one block of 1024 threads:
+// contiguous chunks per thread, a block-wide scan of the chunk sums.
+__global__ void __launch_bounds__(1024) k_scan_tiles(Frame F, unsigned long long* n_pairs_out)
+{
+    __shared__ unsigned long long wsum[32];
+    const uint32_t TT = F.hdr->total_tiles;
+    const uint32_t per = (TT + blockDim.x - 1) / blockDim.x;
+    const uint32_t b0 = min(TT, threadIdx.x * per), b1 = min(TT, b0 + per);
+    unsigned long long s = 0;
+    for (uint32_t t = b0; t < b1; ++t) s += F.tile_count[t];
+    // block exclusive scan of s
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned long long x = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned long long w = wsum[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    unsigned long long run = x - s + (wid ? wsum[wid - 1] : 0ull);
+    const unsigned long long total = wsum[31];
+    for (uint32_t t = b0; t < b1; ++t) {
+        F.tile_offset[t] = static_cast<uint32_t>(run);
+        F.cursor[t] = static_cast<uint32_t>(run);
+        run += F.tile_count[t];
+    }
+    if (threadIdx.x == 0) {
+        F.tile_offset[TT] = static_cast<uint32_t>(total);
+        F.hdr->n_pairs = total;
+        if (total > 0xFFFFFFFFull) atomicOr(&F.hdr->status, STATUS_OVERFLOW);
+        if (n_pairs_out) *n_pairs_out = total;
+    }
+}
+
+void launch_preprocess(const Frame& F, const clod_scene& S, uint32_t V, uint8_t* mask_out, float* alpha_out,
+                       unsigned long long* n_pairs_out, int n_sm, cudaStream_t st)
+{
+    const int64_t n = S.n;
+    int blocks = static_cast<int>(std::min<int64_t>((n + 255) / 256, (int64_t)n_sm * 8));
+    if (blocks < 1) blocks = 1;
+    if (n > 0) k_dist_max<<<blocks, 256, 0, st>>>(F, S.means, n, V);
+    if (n > 0) k_preprocess<<<blocks, 256, 0, st>>>(F, S, V, mask_out, alpha_out);
+    k_scan_tiles<<<1, 1024, 0, st>>>(F, n_pairs_out);
+}
+
+}  // namespace clod

@@ -1,0 +1,79 @@
+"""Helpers shared by the GPU parity tests: read libclod's outputs back and
+compare them with the oracle's."""
+import numpy as np
+import torch
+
+from oracle import oracle as O
+
+
+def u32(a):
+    return np.ascontiguousarray(a).view(np.uint32)
+
+
+def frame_stage1(fr, n):
+    """Device Stage I arrays of a clod.Frame as numpy, per view."""
+    V = len(fr.views)
+    rec0 = fr.ws_array("rec0", torch.float32, 4 * V * n).view(V, n, 4).cpu().numpy()
+    rec1 = fr.ws_array("rec1", torch.float32, 4 * V * n).view(V, n, 4).cpu().numpy()
+    rec2 = fr.ws_array("rec2", torch.float32, V * n).view(V, n).cpu().numpy()
+    depth = fr.ws_array("depth", torch.float32, V * n).view(V, n).cpu().numpy()
+    rect = fr.ws_array("rect", torch.int32, 2 * V * n).view(V, n, 2).cpu().numpy().view(np.uint32)
+    key = fr.ws_array("dmax_key", torch.int64, V).cpu().numpy().view(np.uint64)
+    out = []
+    for v in range(V):
+        r = rect[v]
+        rr = np.stack([r[:, 0] & 0xFFFF, r[:, 0] >> 16, r[:, 1] & 0xFFFF, r[:, 1] >> 16], 1).astype(np.int32)
+        k = int(key[v])
+        out.append(dict(
+            rec0=rec0[v], rec1=rec1[v], rec2=rec2[v], depth=depth[v], rect=rr,
+            dmax_bits=np.uint32(k >> 32), argmax=(0xFFFFFFFF - (k & 0xFFFFFFFF)) if k else -1,
+            mask=fr.mask[v].cpu().numpy(), alpha=fr.alpha_eff[v].cpu().numpy(),
+            counts=fr.counts[v].cpu().numpy()))
+    return out
+
+
+def assert_stage1_equal(g, s1):
+    """Bit-exact comparison of one view's Stage I (GPU dict vs oracle dict)."""
+    assert int(g["dmax_bits"]) == int(u32(s1["dmax"])[0])
+    assert int(g["argmax"]) == int(s1["argmax"][0])
+    assert np.array_equal(g["mask"], s1["mask"])
+    assert np.array_equal(u32(g["alpha"]), u32(s1["alpha_eff"]))
+    surv = s1["survive"].astype(bool)
+    assert np.array_equal(g["rect"], s1["rect"]), np.nonzero((g["rect"] != s1["rect"]).any(1))[0][:10]
+    R = s1["rec"][surv]
+    pairs = [(g["rec0"][surv, 0], R[:, 0]), (g["rec0"][surv, 1], R[:, 1]), (g["rec0"][surv, 2], R[:, 4]),
+             (g["rec0"][surv, 3], R[:, 5]), (g["rec1"][surv, 0], R[:, 6]), (g["rec1"][surv, 1], R[:, 2]),
+             (g["rec1"][surv, 2], R[:, 8]), (g["rec1"][surv, 3], R[:, 9]), (g["rec2"][surv], R[:, 10]),
+             (g["depth"][surv], R[:, 3])]
+    names = ["u", "v", "-A/2", "-B", "-C/2", "alpha''", "r", "g", "b", "depth"]
+    for name, (a, b) in zip(names, pairs):
+        bad = np.nonzero(u32(a) != u32(b))[0]
+        assert bad.size == 0, (name, bad[:5], a[bad[:5]], b[bad[:5]])
+    assert int(g["counts"][0]) == int(s1["mask"].sum())
+    assert int(g["counts"][1]) == int(surv.sum())
+
+
+def assert_image_matches(fr, v, ref, tiles=None, tol64=2e-4):
+    """GPU image of view v equals the oracle's FP32 evaluation bit for bit and
+    lies within tol64 of the FP64 image (on the listed tiles, or all)."""
+    img = fr.view_image(v).cpu().numpy()
+    T = fr.view_T(v).cpu().numpy()
+    nc = fr.view_ncontrib(v).cpu().numpy().view(np.uint32)
+    w = fr.views[v]
+    if tiles is not None:
+        tx = (w.width + 15) // 16
+        sel = np.zeros((w.height, w.width), bool)
+        for t in tiles:
+            x0, y0 = (t % tx) * 16, (t // tx) * 16
+            sel[y0:y0 + 16, x0:x0 + 16] = True
+    else:
+        sel = np.ones((w.height, w.width), bool)
+    assert np.array_equal(nc[sel], ref["ncontrib"][sel])
+    assert np.array_equal(u32(T[sel]), u32(ref["T32"][sel]))
+    for c in range(3):
+        assert np.array_equal(u32(img[c][sel]), u32(ref["img32"][c][sel])), c
+    if ref.get("img64") is not None:
+        err = np.abs(img.astype(np.float64) - ref["img64"])[:, sel].max()
+        assert err <= tol64, err
+        return err
+    return 0.0

@@ -1,0 +1,131 @@
+"""GPU parity of the forward path against the oracle (through the C ABI).
+
+Integer outputs (mask, tile rectangles, counts, sorted keys/values, ranges,
+contributor counts) are compared bit for bit; so are the FP32 records and the
+FP32 image, which follow the same operation sequence as the oracle's FP32
+evaluation.  The image must also lie within 2e-4 of the oracle's FP64 image.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2510_09997_gb300 import synth as S
+
+from gpu_helpers import assert_image_matches, assert_stage1_equal, frame_stage1
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def C():
+    from paper_2510_09997_gb300 import clod
+    clod.require_cuda()
+    return clod
+
+
+def run_and_compare(C, scene, views, tiles=None, with64=True):
+    ds = C.DeviceScene.from_scene(scene)
+    fr = C.render(ds, views)
+    torch.cuda.synchronize()
+    ref = O.frame(scene, views, with64=with64, tiles=tiles)
+    g = frame_stage1(fr, scene.n)
+    for v in range(len(views)):
+        assert_stage1_equal(g[v], ref["s1"][v])
+    assert fr.n_pairs == len(ref["keys"])
+    assert np.array_equal(fr.keys.cpu().numpy().view(np.uint64), ref["keys"])
+    assert np.array_equal(fr.vals.cpu().numpy().view(np.uint32), ref["vals"])
+    assert np.array_equal(fr.ranges.cpu().numpy().view(np.uint32), ref["ranges"])
+    errs = []
+    for v in range(len(views)):
+        errs.append(assert_image_matches(fr, v, ref["img"][v], None if tiles is None else tiles[v]))
+    return fr, ref, errs
+
+
+@pytest.mark.parametrize("s", [1.0, 4.0])
+def test_tiny_scene_bit_exact(C, s):
+    """20,000 Gaussians, 256x256, s_v in {1, 4}."""
+    run_and_compare(C, S.tiny_scene(), [S.tiny_view(s)])
+
+
+def test_batched_views_mixed_sizes_and_flags(C):
+    """Several views in one launch: different resolutions (ragged, not
+    multiples of 16), level of detail off, no normalisation, backgrounds."""
+    sc = S.tiny_scene(n=8000, seed=21, sh_degree=3)
+    views = [S.tiny_view(1.0),
+             S.look_at((2.5, -1.0, 1.0), (0, 0, 0), 250, 130, s_v=2.0, bg=(0.2, 0.3, 0.4)),
+             S.look_at((-1.5, 2.0, -1.0), (0.1, 0, 0), 97, 161, s_v=3.0, flags=S.FLAG_LOD_OFF),
+             S.look_at((0.5, 0.5, 3.5), (0, 0, 0), 64, 48, s_v=1.5, flags=S.FLAG_NO_NORMALIZE, tau=0.01)]
+    run_and_compare(C, sc, views)
+
+
+def test_empty_scene_and_all_culled(C):
+    sc = S.tiny_scene(n=1000, seed=22)
+    empty = sc.subset(np.arange(0))
+    fr, ref, _ = run_and_compare(C, empty, [S.tiny_view(1.0, bg=(0.1, 0.2, 0.3))])
+    img = fr.view_image(0).cpu().numpy()
+    assert np.all(img[0] == np.float32(0.1)) and np.all(img[2] == np.float32(0.3))
+    fr, ref, _ = run_and_compare(C, sc, [S.tiny_view(1000.0)])
+    assert fr.n_pairs == 0 and int(fr.counts[0, 0]) == 0
+
+
+def test_single_gaussian_and_degenerate_quaternion(C):
+    sc = S.tiny_scene(n=4, seed=23, sh_degree=1)
+    sc.quats[2] = 0.0                       # zero quaternion: culled (no rotation)
+    sc.means[3] = (0.0, 0.0, 3.0)           # at the camera centre: behind the near plane
+    run_and_compare(C, sc, [S.tiny_view(1.0)])
+
+
+@pytest.mark.parametrize("pile", [3000, 20000])
+def test_oversized_tiles(C, pile):
+    """Tiles whose lists exceed the in-shared-memory sort (2048) and the
+    chunk size (8192) of the large-tile kernel (merge passes)."""
+    rng = np.random.default_rng(24)
+    sc = S.tiny_scene(n=pile + 2000, seed=24)
+    sc.means[:pile] = rng.normal(0.0, 0.02, size=(pile, 3)).astype(np.float32)
+    sc.opacity[:pile] = 0.02                  # keep the pile translucent: long lists get blended
+    v = S.tiny_view(1.0).replace(width=96, height=96, cx=48.0, cy=48.0)
+    fr, ref, _ = run_and_compare(C, sc, [v])
+    lens = np.diff(ref["ranges"].astype(np.int64), axis=1)
+    assert lens.max() > (8192 if pile > 10000 else 2048)
+
+
+def test_depth_ties_follow_index_order(C):
+    """Identical depths: the sort must keep index order (stable)."""
+    sc = S.tiny_scene(n=3000, seed=25)
+    sc.means[:, 2] = np.round(sc.means[:, 2] * 4) / 4      # only 9 distinct depths
+    run_and_compare(C, sc, [S.tiny_view(1.0)])
+
+
+@pytest.mark.parametrize("cam,s", [(0, 1.0), (40, 16.0)])
+def test_object_scene_full_size(C, cam, s):
+    """1M Gaussians, SH degree 3, 1920x1080: every Stage I output, the whole
+    sorted list and ranges bit-exact; the image on sampled tiles (including
+    the longest lists) bit-exact and within 2e-4 of FP64."""
+    sc = S.object_scene()
+    v = S.orbit_cameras(64, 1920, 1080)[cam].replace(s_v=s)
+    s1 = O.stage1(sc, v)
+    k, val = O.emit_pairs(v, s1)
+    lens = np.bincount((k >> np.uint64(32)).astype(np.int64), minlength=v.tiles)
+    rng = np.random.default_rng(cam)
+    tiles = list(np.argsort(lens)[-6:]) + list(rng.choice(v.tiles, 10, replace=False))
+    run_and_compare(C, sc, [v], tiles=[tiles])
+
+
+def test_renderer_fixed_capacity_matches_and_flags_overflow(C):
+    """The benchmark's launch path (fixed pair capacity, no mid-frame sync)
+    gives the same image; a too-small capacity is reported, not overrun."""
+    sc = S.tiny_scene()
+    v = S.tiny_view(1.0)
+    ds = C.DeviceScene.from_scene(sc)
+    ref = O.frame(sc, [v], with64=False)
+    R = C.Renderer(ds, [v], pair_capacity=len(ref["keys"]) + 1000)
+    R.run()
+    assert R.check() == len(ref["keys"])
+    img = R.image.view(3, 256, 256).cpu().numpy()
+    assert np.array_equal(img.view(np.uint32), ref["img"][0]["img32"].view(np.uint32))
+    R2 = C.Renderer(ds, [v], pair_capacity=1000)
+    R2.run()
+    with pytest.raises(C.ClodError) as e:
+        R2.check()
+    assert e.value.status == 2
