@@ -176,6 +176,40 @@ clod_status clod_render_fwd_count(const void* ws, const uint32_t* vals, const ui
                                   float* image, float* T_final, uint32_t* n_contrib,
                                   unsigned long long* evaluated, clod_stream stream);
 
+/* ------------------------------------------------------------------------ */
+/* Backward pass                                                              */
+/* ------------------------------------------------------------------------ */
+
+/* Scratch bytes of clod_render_bwd for n Gaussians and n_views views. */
+clod_status clod_backward_workspace_size(int64_t n, int32_t n_views, size_t* bytes);
+
+/* Gradients of a scalar loss L with respect to the six activated parameter
+ * groups, given dL/d(image) of the frame rendered from ws/vals/ranges (the
+ * forward's outputs, unchanged since) and, optionally, an external
+ * dL/d(alpha'') for every (view, Gaussian) -- the training step's
+ * straight-through gradient of the point-count regulariser (Eq. 4).
+ * Differentiates Eq. 1 (blending, with the forward's skip/stop decisions and
+ * the 0.99 opacity clamp), the EWA projection, Sigma = R S S^T R^T, the SH
+ * colour (clamped at 0) and Eq. 2 (alpha, sigma_d with its ReLU, and mu
+ * through d_i and through d_max = d_{j*}, j* the lowest-index farthest
+ * Gaussian in the view frustum).
+ * T_final, n_contrib: the forward's packed outputs.  dL_dimage: packed like
+ * the image.  dL_dalpha_eff: f32 [n_views * n] or NULL.
+ * Outputs are ACCUMULATED (+=): dmeans n x 3, dscales n x 3, dquats n x 4,
+ * dopacity n, dsh n x (deg+1)^2 x 3, ddecay n. */
+clod_status clod_render_bwd(const clod_scene* scene, const void* ws, const uint32_t* vals,
+                            const uint32_t* ranges, const float* T_final, const uint32_t* n_contrib,
+                            const float* dL_dimage, const float* dL_dalpha_eff,
+                            void* bwd_ws, size_t bwd_ws_bytes,
+                            float* dmeans, float* dscales, float* dquats, float* dopacity,
+                            float* dsh, float* ddecay, clod_stream stream);
+
+/* L1 term of the rendering loss (Sec. 3.3): *loss += scale * mean |image -
+ * target| over count elements (device f32 scalar, may be NULL) and
+ * dL_dimage = scale * sign(image - target) / count (may be NULL). */
+clod_status clod_l1_loss(const float* image, const float* target, int64_t count, float scale,
+                         float* loss, float* dL_dimage, clod_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

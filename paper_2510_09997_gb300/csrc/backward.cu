@@ -1,0 +1,560 @@
+// backward.cu -- hand-written reverse pass of the rasterizer.
+//
+//   k_blend_bwd      per tile, per pixel, the contributors in reverse order:
+//                    T before each one is recovered as T_after / (1 - a);
+//                    with the suffix S = sum_{k>j} c_k a_k T_k + T_final bg,
+//                    dC/da_j = c_j T_j - S / (1 - a_j) (Eq. 1 differentiated).
+//                    The skip decisions are re-taken with the forward's FP32
+//                    sequence, so exactly the forward's contributors are
+//                    visited.  Per-Gaussian 2D gradients (u, v, A, B, C,
+//                    alpha'', r, g, b) are warp-reduced and added with vector
+//                    atomics into a per-(view, Gaussian) buffer.
+//   k_preprocess_bwd per Gaussian, over the views: chain rule through the
+//                    conic (inverse 2D covariance), the EWA Jacobian, the
+//                    projection, Sigma = R S S^T R^T, the SH colour and the
+//                    attenuated opacity of Eq. 2 (alpha, sigma_d, and mu via
+//                    d and d_max); accumulates into the parameter gradients.
+//   k_dmax_bwd       the d_max term: d_max = d_{j*} passes the summed
+//                    dL/d d_max to mu_{j*}.
+#include <algorithm>
+
+#include "clod_internal.cuh"
+
+namespace clod {
+
+struct BwdLayout {
+    size_t g2d, dmax_grad, total;
+};
+
+BwdLayout bwd_layout(uint64_t n, uint32_t V)
+{
+    BwdLayout L{};
+    size_t o = 0;
+    L.g2d = o;
+    o += ((size_t)V * n * 3 * sizeof(float4) + 255) & ~size_t(255);
+    L.dmax_grad = o;
+    o += ((size_t)V * sizeof(float) + 255) & ~size_t(255);
+    L.total = o;
+    return L;
+}
+
+__device__ __forceinline__ float warp_sum(float x)
+{
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+__global__ void __launch_bounds__(BLOCK_PIX) k_blend_bwd(Frame F, const uint32_t* __restrict__ vals,
+                                                         const uint32_t* __restrict__ ranges,
+                                                         const float* __restrict__ Tfin,
+                                                         const uint32_t* __restrict__ ncon,
+                                                         const float* __restrict__ dimg, float4* __restrict__ g2d)
+{
+    __shared__ float4 s0[BLOCK_PIX];
+    __shared__ float4 s1[BLOCK_PIX];
+    __shared__ float s2[BLOCK_PIX];
+    __shared__ int64_t sg[BLOCK_PIX];
+    __shared__ uint32_t s_tile, s_max;
+    __shared__ int s_view;
+    const FrameHeader* hdr = F.hdr;
+    if (hdr->status & STATUS_OVERFLOW) return;
+    const uint32_t TT = hdr->total_tiles;
+    const uint32_t V = hdr->n_views;
+    const int64_t n = static_cast<int64_t>(hdr->n);
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const uint32_t t = atomicAdd(&F.hdr->work[1], 1u);
+            s_tile = t;
+            s_max = 0;
+            int v = 0;
+            if (t < TT)
+                for (uint32_t u = 0; u < V; ++u) {
+                    const ViewDev& W = F.views[u];
+                    if (t >= W.tile_base && t < W.tile_base + (uint32_t)(W.TX * W.TY)) {
+                        v = (int)u;
+                        break;
+                    }
+                }
+            s_view = v;
+        }
+        __syncthreads();
+        const uint32_t t = s_tile;
+        if (t >= TT) break;
+        const ViewDev& W = F.views[s_view];
+        const uint32_t local = t - W.tile_base;
+        const int tx = (int)(local % (uint32_t)W.TX), ty = (int)(local / (uint32_t)W.TX);
+        const int px = tx * TILE + (int)(threadIdx.x & 15), py = ty * TILE + (int)(threadIdx.x >> 4);
+        const bool inside = px < W.W && py < W.H;
+        const float fpx = __fadd_rn(static_cast<float>(px), 0.5f);
+        const float fpy = __fadd_rn(static_cast<float>(py), 0.5f);
+        const uint32_t start = ranges[2 * t], end = ranges[2 * t + 1];
+        const int64_t vn = (int64_t)s_view * n;
+        float T = 1.0f, d0 = 0.f, d1 = 0.f, d2 = 0.f, S0 = 0.f, S1 = 0.f, S2 = 0.f;
+        uint32_t last = 0;
+        if (inside) {
+            const size_t plane = (size_t)W.W * W.H, p = (size_t)py * W.W + px;
+            T = Tfin[W.pix_base + p];
+            last = ncon[W.pix_base + p];
+            const float* di = dimg + 3 * W.pix_base;
+            d0 = di[p];
+            d1 = di[plane + p];
+            d2 = di[2 * plane + p];
+            S0 = T * W.bg[0];
+            S1 = T * W.bg[1];
+            S2 = T * W.bg[2];
+        }
+        // longest contributor prefix in the block
+        uint32_t m = last;
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0 && m) atomicMax(&s_max, m);
+        __syncthreads();
+        const uint32_t blast = start + s_max;
+        for (uint32_t bend = blast; bend > start;) {
+            const uint32_t bstart = bend - start > BLOCK_PIX ? bend - BLOCK_PIX : start;
+            const int cnt = (int)(bend - bstart);
+            if ((int)threadIdx.x < cnt) {
+                const int64_t g = vn + vals[bstart + threadIdx.x];
+                sg[threadIdx.x] = g;
+                s0[threadIdx.x] = F.rec0[g];
+                s1[threadIdx.x] = F.rec1[g];
+                s2[threadIdx.x] = F.rec2[g];
+            }
+            __syncthreads();
+            for (int k = cnt - 1; k >= 0; --k) {
+                const uint32_t pos = bstart - start + (uint32_t)k;   // list position
+                const float4 a = s0[k];
+                const float4 c = s1[k];
+                float gu = 0.f, gv = 0.f, gA = 0.f, gB = 0.f, gC = 0.f, ga = 0.f, gr = 0.f, gg = 0.f, gb = 0.f;
+                bool contrib = false;
+                if (inside && pos < last) {
+                    const float dx = __fsub_rn(a.x, fpx), dy = __fsub_rn(a.y, fpy);
+                    const float al = blend_alpha(dx, dy, a.z, a.w, c.x, c.y);
+                    if (al >= 0.0f) {
+                        contrib = true;
+                        const float power =
+                            __fmaf_rn(dx, __fmaf_rn(a.z, dx, __fmul_rn(a.w, dy)), __fmul_rn(__fmul_rn(c.x, dy), dy));
+                        const float G = exp_spec(power);
+                        const float raw = c.y * G;
+                        const float om = 1.0f - al;
+                        const float Tb = T / om;
+                        const float cb = s2[k];
+                        const float w = al * Tb;
+                        gr = w * d0;
+                        gg = w * d1;
+                        gb = w * d2;
+                        const float dal = d0 * (c.z * Tb - S0 / om) + d1 * (c.w * Tb - S1 / om) + d2 * (cb * Tb - S2 / om);
+                        S0 += c.z * w;
+                        S1 += c.w * w;
+                        S2 += cb * w;
+                        T = Tb;
+                        if (!(raw > 0.99f)) {
+                            ga = dal * G;
+                            const float gp = dal * al;
+                            gu = gp * (2.0f * a.z * dx + a.w * dy);
+                            gv = gp * (a.w * dx + 2.0f * c.x * dy);
+                            gA = gp * (-0.5f * dx * dx);
+                            gB = gp * (-dx * dy);
+                            gC = gp * (-0.5f * dy * dy);
+                        }
+                    }
+                }
+                if (__any_sync(0xffffffffu, contrib)) {
+                    gu = warp_sum(gu);
+                    gv = warp_sum(gv);
+                    gA = warp_sum(gA);
+                    gB = warp_sum(gB);
+                    gC = warp_sum(gC);
+                    ga = warp_sum(ga);
+                    gr = warp_sum(gr);
+                    gg = warp_sum(gg);
+                    gb = warp_sum(gb);
+                    if (lane == 0) {
+                        float4* dst = g2d + 3 * sg[k];
+                        atomicAdd(dst, make_float4(gu, gv, gA, gB));
+                        atomicAdd(dst + 1, make_float4(gC, ga, gr, gg));
+                        atomicAdd(reinterpret_cast<float*>(dst + 2), gb);
+                    }
+                }
+            }
+            __syncthreads();
+            bend = bstart;
+        }
+        __syncthreads();
+    }
+}
+
+// SH basis and its derivative with respect to the direction (x, y, z).
+__device__ __forceinline__ void sh_basis_grad(float x, float y, float z, int deg, float* b, float* bx, float* by,
+                                              float* bz)
+{
+    const float C1 = CLOD_SH_C1;
+    b[0] = CLOD_SH_C0;
+    bx[0] = by[0] = bz[0] = 0.f;
+    if (deg < 1) return;
+    b[1] = -C1 * y; bx[1] = 0.f; by[1] = -C1; bz[1] = 0.f;
+    b[2] = C1 * z;  bx[2] = 0.f; by[2] = 0.f; bz[2] = C1;
+    b[3] = -C1 * x; bx[3] = -C1; by[3] = 0.f; bz[3] = 0.f;
+    if (deg < 2) return;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    b[4] = CLOD_SH_C2_0 * x * y; bx[4] = CLOD_SH_C2_0 * y; by[4] = CLOD_SH_C2_0 * x; bz[4] = 0.f;
+    b[5] = CLOD_SH_C2_1 * y * z; bx[5] = 0.f; by[5] = CLOD_SH_C2_1 * z; bz[5] = CLOD_SH_C2_1 * y;
+    b[6] = CLOD_SH_C2_2 * (2.f * zz - xx - yy);
+    bx[6] = -2.f * CLOD_SH_C2_2 * x; by[6] = -2.f * CLOD_SH_C2_2 * y; bz[6] = 4.f * CLOD_SH_C2_2 * z;
+    b[7] = CLOD_SH_C2_3 * x * z; bx[7] = CLOD_SH_C2_3 * z; by[7] = 0.f; bz[7] = CLOD_SH_C2_3 * x;
+    b[8] = CLOD_SH_C2_4 * (xx - yy); bx[8] = 2.f * CLOD_SH_C2_4 * x; by[8] = -2.f * CLOD_SH_C2_4 * y; bz[8] = 0.f;
+    if (deg < 3) return;
+    b[9] = CLOD_SH_C3_0 * y * (3.f * xx - yy);
+    bx[9] = 6.f * CLOD_SH_C3_0 * x * y; by[9] = CLOD_SH_C3_0 * (3.f * xx - 3.f * yy); bz[9] = 0.f;
+    b[10] = CLOD_SH_C3_1 * x * y * z;
+    bx[10] = CLOD_SH_C3_1 * y * z; by[10] = CLOD_SH_C3_1 * x * z; bz[10] = CLOD_SH_C3_1 * x * y;
+    b[11] = CLOD_SH_C3_2 * y * (4.f * zz - xx - yy);
+    bx[11] = -2.f * CLOD_SH_C3_2 * x * y; by[11] = CLOD_SH_C3_2 * (4.f * zz - xx - 3.f * yy);
+    bz[11] = 8.f * CLOD_SH_C3_2 * y * z;
+    b[12] = CLOD_SH_C3_3 * z * (2.f * zz - 3.f * xx - 3.f * yy);
+    bx[12] = -6.f * CLOD_SH_C3_3 * x * z; by[12] = -6.f * CLOD_SH_C3_3 * y * z;
+    bz[12] = CLOD_SH_C3_3 * (6.f * zz - 3.f * xx - 3.f * yy);
+    b[13] = CLOD_SH_C3_4 * x * (4.f * zz - xx - yy);
+    bx[13] = CLOD_SH_C3_4 * (4.f * zz - 3.f * xx - yy); by[13] = -2.f * CLOD_SH_C3_4 * x * y;
+    bz[13] = 8.f * CLOD_SH_C3_4 * x * z;
+    b[14] = CLOD_SH_C3_5 * z * (xx - yy);
+    bx[14] = 2.f * CLOD_SH_C3_5 * x * z; by[14] = -2.f * CLOD_SH_C3_5 * y * z; bz[14] = CLOD_SH_C3_5 * (xx - yy);
+    b[15] = CLOD_SH_C3_6 * x * (xx - 3.f * yy);
+    bx[15] = CLOD_SH_C3_6 * (3.f * xx - 3.f * yy); by[15] = -6.f * CLOD_SH_C3_6 * x * y; bz[15] = 0.f;
+}
+
+struct ParamGrads {
+    float* dmeans;
+    float* dscales;
+    float* dquats;
+    float* dopacity;
+    float* dsh;
+    float* ddecay;
+};
+
+__global__ void __launch_bounds__(128) k_preprocess_bwd(Frame F, clod_scene S, const float4* __restrict__ g2d,
+                                                        const float* __restrict__ g_alpha_ext,
+                                                        float* __restrict__ dmax_grad, ParamGrads P)
+{
+    __shared__ ViewDev sv[MAX_VIEWS];
+    __shared__ float sdmax[MAX_VIEWS];
+    __shared__ float sdmg[MAX_VIEWS];
+    const uint32_t V = F.hdr->n_views;
+    {
+        const int words = static_cast<int>(V * sizeof(ViewDev) / 4);
+        const int* src = reinterpret_cast<const int*>(F.views);
+        int* dst = reinterpret_cast<int*>(sv);
+        for (int k = threadIdx.x; k < words; k += blockDim.x) dst[k] = src[k];
+        for (uint32_t v = threadIdx.x; v < V; v += blockDim.x) {
+            sdmax[v] = decode_dmax(F.dmax_key[v]);
+            sdmg[v] = 0.f;
+        }
+    }
+    __syncthreads();
+    const int64_t n = S.n;
+    const int deg = S.sh_degree;
+    const int K = (deg + 1) * (deg + 1);
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        const bool active = i < n;
+        float gm0 = 0.f, gm1 = 0.f, gm2 = 0.f, gs0 = 0.f, gs1 = 0.f, gs2 = 0.f;
+        float gq0 = 0.f, gq1 = 0.f, gq2 = 0.f, gq3 = 0.f, gop = 0.f, gdec = 0.f;
+        float mx = 0.f, my = 0.f, mz = 0.f, alpha = 0.f, sigma = 0.f;
+        if (active) {
+            mx = S.means[3 * i];
+            my = S.means[3 * i + 1];
+            mz = S.means[3 * i + 2];
+            alpha = S.opacity[i];
+            sigma = S.decay[i];
+        }
+        for (uint32_t v = 0; v < V; ++v) {
+            if (!active) break;
+            const ViewDev& W = sv[v];
+            const int64_t o = (int64_t)v * n + i;
+            const uint2 rc = F.rect[o];
+            const bool surv = (rc.y & 0xFFFFu) > (rc.x & 0xFFFFu);
+            float g_a2 = g_alpha_ext ? g_alpha_ext[o] : 0.f;
+            float e0, e1, e2;
+            const float d = cam_dist(W, mx, my, mz, e0, e1, e2);
+            if (surv) {
+                const float4 G0 = g2d[3 * o], G1 = g2d[3 * o + 1];
+                const float Gb = reinterpret_cast<const float*>(g2d + 3 * o + 2)[0];
+                const float g_u = G0.x, g_v = G0.y, g_A = G0.z, g_B = G0.w, g_C = G1.x;
+                g_a2 += G1.y;
+                const float g_col[3] = {G1.z, G1.w, Gb};
+                // ---- colour (SH) -------------------------------------------------
+                const float inv_d = 1.0f / d;
+                const float dx = e0 * inv_d, dy = e1 * inv_d, dz = e2 * inv_d;
+                float b[16], bx[16], by[16], bz[16];
+                sh_basis_grad(dx, dy, dz, deg, b, bx, by, bz);
+                const float* shp = S.sh + (size_t)i * K * 3;
+                float* dshp = P.dsh + (size_t)i * K * 3;
+                float gdx = 0.f, gdy = 0.f, gdz = 0.f;
+                for (int ch = 0; ch < 3; ++ch) {
+                    float acc = 0.f;
+                    for (int k = 0; k < K; ++k) acc += b[k] * shp[3 * k + ch];
+                    if (acc + 0.5f > 0.0f && g_col[ch] != 0.0f) {
+                        const float gc = g_col[ch];
+                        for (int k = 0; k < K; ++k) {
+                            dshp[3 * k + ch] += b[k] * gc;
+                            const float s = shp[3 * k + ch] * gc;
+                            gdx += bx[k] * s;
+                            gdy += by[k] * s;
+                            gdz += bz[k] * s;
+                        }
+                    }
+                }
+                // direction = e / |e|
+                const float dotg = gdx * dx + gdy * dy + gdz * dz;
+                gm0 += (gdx - dx * dotg) * inv_d;
+                gm1 += (gdy - dy * dotg) * inv_d;
+                gm2 += (gdz - dz * dotg) * inv_d;
+
+                // ---- forward recomputation of the projection --------------------
+                float tx, ty, tz;
+                cam_point(W, mx, my, mz, tx, ty, tz);
+                const float4 q = reinterpret_cast<const float4*>(S.quats)[i];
+                const float qn = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+                const float qw = q.x / qn, qx = q.y / qn, qy = q.z / qn, qz = q.w / qn;
+                float r[9];
+                r[0] = 1.f - 2.f * (qy * qy + qz * qz);
+                r[1] = 2.f * (qx * qy - qw * qz);
+                r[2] = 2.f * (qx * qz + qw * qy);
+                r[3] = 2.f * (qx * qy + qw * qz);
+                r[4] = 1.f - 2.f * (qx * qx + qz * qz);
+                r[5] = 2.f * (qy * qz - qw * qx);
+                r[6] = 2.f * (qx * qz - qw * qy);
+                r[7] = 2.f * (qy * qz + qw * qx);
+                r[8] = 1.f - 2.f * (qx * qx + qy * qy);
+                const float sc[3] = {S.scales[3 * i], S.scales[3 * i + 1], S.scales[3 * i + 2]};
+                float Mm[9], Sg[9];
+                for (int a_ = 0; a_ < 3; ++a_)
+                    for (int b_ = 0; b_ < 3; ++b_) Mm[3 * a_ + b_] = r[3 * a_ + b_] * sc[b_];
+                for (int a_ = 0; a_ < 3; ++a_)
+                    for (int b_ = 0; b_ < 3; ++b_)
+                        Sg[3 * a_ + b_] = Mm[3 * a_] * Mm[3 * b_] + Mm[3 * a_ + 1] * Mm[3 * b_ + 1] + Mm[3 * a_ + 2] * Mm[3 * b_ + 2];
+                const float limx = 1.3f * (0.5f * (float)W.W / W.fx), limy = 1.3f * (0.5f * (float)W.H / W.fy);
+                const float txz = tx / tz, tyz = ty / tz;
+                const bool clx = txz < -limx || txz > limx, cly = tyz < -limy || tyz > limy;
+                const float txc = fminf(limx, fmaxf(-limx, txz)) * tz;
+                const float tyc = fminf(limy, fmaxf(-limy, tyz)) * tz;
+                const float itz = 1.0f / tz, itz2 = itz * itz;
+                const float j00 = W.fx * itz, j02 = -W.fx * txc * itz2;
+                const float j11 = W.fy * itz, j12 = -W.fy * tyc * itz2;
+                float T0[3], T1[3];
+                for (int k = 0; k < 3; ++k) {
+                    T0[k] = j00 * W.R[k] + j02 * W.R[6 + k];
+                    T1[k] = j11 * W.R[3 + k] + j12 * W.R[6 + k];
+                }
+                float ST0[3], ST1[3];  // Sigma T0^T, Sigma T1^T
+                for (int k = 0; k < 3; ++k) {
+                    ST0[k] = Sg[3 * k] * T0[0] + Sg[3 * k + 1] * T0[1] + Sg[3 * k + 2] * T0[2];
+                    ST1[k] = Sg[3 * k] * T1[0] + Sg[3 * k + 1] * T1[1] + Sg[3 * k + 2] * T1[2];
+                }
+                const float ca = T0[0] * ST0[0] + T0[1] * ST0[1] + T0[2] * ST0[2] + 0.3f;
+                const float cb = T0[0] * ST1[0] + T0[1] * ST1[1] + T0[2] * ST1[2];
+                const float cc = T1[0] * ST1[0] + T1[1] * ST1[1] + T1[2] * ST1[2] + 0.3f;
+                const float det = ca * cc - cb * cb;
+                const float id = 1.0f / det, id2 = id * id;
+                // ---- conic -> 2D covariance --------------------------------------
+                const float g_ca = g_A * (-cc * cc * id2) + g_B * (cb * cc * id2) + g_C * (id - ca * cc * id2);
+                const float g_cb = g_A * (2.f * cb * cc * id2) + g_B * (-id - 2.f * cb * cb * id2) + g_C * (2.f * ca * cb * id2);
+                const float g_cc = g_A * (id - ca * cc * id2) + g_B * (ca * cb * id2) + g_C * (-ca * ca * id2);
+                // ---- 2D covariance -> Sigma and T ---------------------------------
+                float gS[9];
+                for (int k = 0; k < 3; ++k)
+                    for (int l = 0; l < 3; ++l)
+                        gS[3 * k + l] = g_ca * T0[k] * T0[l] + g_cb * T0[k] * T1[l] + g_cc * T1[k] * T1[l];
+                float gT0[3], gT1[3];
+                for (int k = 0; k < 3; ++k) {
+                    gT0[k] = 2.f * g_ca * ST0[k] + g_cb * ST1[k];
+                    gT1[k] = 2.f * g_cc * ST1[k] + g_cb * ST0[k];
+                }
+                // ---- T = J W -> J -> camera point -----------------------------------
+                float gj00 = 0.f, gj02 = 0.f, gj11 = 0.f, gj12 = 0.f;
+                for (int k = 0; k < 3; ++k) {
+                    gj00 += gT0[k] * W.R[k];
+                    gj02 += gT0[k] * W.R[6 + k];
+                    gj11 += gT1[k] * W.R[3 + k];
+                    gj12 += gT1[k] * W.R[6 + k];
+                }
+                float gtx = 0.f, gty = 0.f, gtz = 0.f;
+                gtz += gj00 * (-W.fx * itz2) + gj11 * (-W.fy * itz2);
+                if (clx) gtz += gj02 * (W.fx * (txc * itz) * itz2);          // j02 = -fx L / tz
+                else {
+                    gtx += gj02 * (-W.fx * itz2);
+                    gtz += gj02 * (2.f * W.fx * tx * itz2 * itz);
+                }
+                if (cly) gtz += gj12 * (W.fy * (tyc * itz) * itz2);
+                else {
+                    gty += gj12 * (-W.fy * itz2);
+                    gtz += gj12 * (2.f * W.fy * ty * itz2 * itz);
+                }
+                // mean2d
+                gtx += g_u * W.fx * itz;
+                gty += g_v * W.fy * itz;
+                gtz += -(g_u * W.fx * tx + g_v * W.fy * ty) * itz2;
+                gm0 += W.R[0] * gtx + W.R[3] * gty + W.R[6] * gtz;
+                gm1 += W.R[1] * gtx + W.R[4] * gty + W.R[7] * gtz;
+                gm2 += W.R[2] * gtx + W.R[5] * gty + W.R[8] * gtz;
+                // ---- Sigma = M M^T, M = R(q) diag(s) ------------------------------
+                float gM[9];
+                for (int a_ = 0; a_ < 3; ++a_)
+                    for (int b_ = 0; b_ < 3; ++b_) {
+                        float acc = 0.f;
+                        for (int k = 0; k < 3; ++k) acc += (gS[3 * a_ + k] + gS[3 * k + a_]) * Mm[3 * k + b_];
+                        gM[3 * a_ + b_] = acc;
+                    }
+                float gR[9];
+                for (int a_ = 0; a_ < 3; ++a_)
+                    for (int b_ = 0; b_ < 3; ++b_) gR[3 * a_ + b_] = gM[3 * a_ + b_] * sc[b_];
+                gs0 += gM[0] * r[0] + gM[3] * r[3] + gM[6] * r[6];
+                gs1 += gM[1] * r[1] + gM[4] * r[4] + gM[7] * r[7];
+                gs2 += gM[2] * r[2] + gM[5] * r[5] + gM[8] * r[8];
+                const float gw = 2.f * (-qz * gR[1] + qy * gR[2] + qz * gR[3] - qx * gR[5] - qy * gR[6] + qx * gR[7]);
+                const float gx = 2.f * (qy * gR[1] + qz * gR[2] + qy * gR[3] - 2.f * qx * gR[4] - qw * gR[5] + qz * gR[6] +
+                                        qw * gR[7] - 2.f * qx * gR[8]);
+                const float gy = 2.f * (-2.f * qy * gR[0] + qx * gR[1] + qw * gR[2] + qx * gR[3] + qz * gR[5] - qw * gR[6] +
+                                        qz * gR[7] - 2.f * qy * gR[8]);
+                const float gz = 2.f * (-2.f * qz * gR[0] - qw * gR[1] + qx * gR[2] + qw * gR[3] - 2.f * qz * gR[4] +
+                                        qy * gR[5] + qx * gR[6] + qy * gR[7]);
+                const float dot = gw * qw + gx * qx + gy * qy + gz * qz;
+                gq0 += (gw - qw * dot) / qn;
+                gq1 += (gx - qx * dot) / qn;
+                gq2 += (gy - qy * dot) / qn;
+                gq3 += (gz - qz * dot) / qn;
+            }
+            // ---- attenuated opacity (Eq. 2) ----------------------------------------
+            if (g_a2 != 0.0f) {
+                if (W.flags & CLOD_LOD_OFF) {
+                    gop += g_a2;
+                } else {
+                    const float dmax = sdmax[v];
+                    const bool norm = !(W.flags & CLOD_NO_NORMALIZE);
+                    const float dn = norm ? (dmax > 0.f ? d / dmax : 0.f) : d;
+                    const float sr = sigma > 0.f ? sigma : 0.f;
+                    const float D = 2.f * sr * sr + W.eps;
+                    const float q = dn * W.s_v;
+                    const float x = q * q / D;
+                    const float E = exp_spec(-x);
+                    const float a2 = alpha * E;
+                    gop += g_a2 * E;
+                    if (sigma > 0.f) gdec += g_a2 * a2 * x * 4.f * sr / D;
+                    const float gdn = g_a2 * a2 * (-2.f * dn * W.s_v * W.s_v / D);
+                    float gd = 0.f;
+                    if (!norm) gd = gdn;
+                    else if (dmax > 0.f) {
+                        gd = gdn / dmax;
+                        atomicAdd_block(&sdmg[v], -gdn * d / (dmax * dmax));
+                    }
+                    if (d > 0.f) {
+                        gm0 += gd * e0 / d;
+                        gm1 += gd * e1 / d;
+                        gm2 += gd * e2 / d;
+                    }
+                }
+            }
+        }
+        if (active) {
+            P.dmeans[3 * i] += gm0;
+            P.dmeans[3 * i + 1] += gm1;
+            P.dmeans[3 * i + 2] += gm2;
+            P.dscales[3 * i] += gs0;
+            P.dscales[3 * i + 1] += gs1;
+            P.dscales[3 * i + 2] += gs2;
+            P.dquats[4 * i] += gq0;
+            P.dquats[4 * i + 1] += gq1;
+            P.dquats[4 * i + 2] += gq2;
+            P.dquats[4 * i + 3] += gq3;
+            P.dopacity[i] += gop;
+            P.ddecay[i] += gdec;
+        }
+    }
+    __syncthreads();
+    for (uint32_t v = threadIdx.x; v < V; v += blockDim.x)
+        if (sdmg[v] != 0.f) atomicAdd(&dmax_grad[v], sdmg[v]);
+}
+
+// d_max = d_{j*}: dL/dmu_{j*} += (dL/d d_max) (mu_{j*} - c) / d_{j*}.
+__global__ void k_dmax_bwd(Frame F, clod_scene S, const float* __restrict__ dmax_grad, float* __restrict__ dmeans)
+{
+    const uint32_t V = F.hdr->n_views;
+    for (uint32_t v = threadIdx.x; v < V; v += blockDim.x) {
+        const unsigned long long key = F.dmax_key[v];
+        const float g = dmax_grad[v];
+        if (!key || g == 0.f) continue;
+        const uint32_t j = 0xFFFFFFFFu - static_cast<uint32_t>(key & 0xFFFFFFFFull);
+        const ViewDev& W = F.views[v];
+        float e0, e1, e2;
+        const float d = cam_dist(W, S.means[3 * j], S.means[3 * j + 1], S.means[3 * j + 2], e0, e1, e2);
+        if (d > 0.f) {
+            atomicAdd(&dmeans[3 * j], g * e0 / d);
+            atomicAdd(&dmeans[3 * j + 1], g * e1 / d);
+            atomicAdd(&dmeans[3 * j + 2], g * e2 / d);
+        }
+    }
+}
+
+// L1 loss: loss += scale * sum |img - target| / count; grad = scale * sign(img - target) / count.
+__global__ void k_l1_loss(const float* __restrict__ img, const float* __restrict__ tgt, int64_t count, float scale,
+                          float* __restrict__ loss, float* __restrict__ grad)
+{
+    float acc = 0.f;
+    const float w = scale / static_cast<float>(count);
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x) {
+        const float dlt = img[k] - tgt[k];
+        acc += fabsf(dlt);
+        if (grad) grad[k] = dlt > 0.f ? w : (dlt < 0.f ? -w : 0.f);
+    }
+    acc = warp_sum(acc);
+    __shared__ float ws[32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float a = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0.f;
+        a = warp_sum(a);
+        if (threadIdx.x == 0 && loss) atomicAdd(loss, a * w);
+    }
+}
+
+static int g_bwd_blocks_per_sm = 0;
+
+cudaError_t backward_setup()
+{
+    int b = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_blend_bwd, BLOCK_PIX, 0);
+    if (e != cudaSuccess) return e;
+    g_bwd_blocks_per_sm = b > 0 ? b : 1;
+    return cudaSuccess;
+}
+
+void launch_backward(const Frame& F, const clod_scene& S, uint32_t V, const uint32_t* vals, const uint32_t* ranges,
+                     const float* Tfin, const uint32_t* ncon, const float* dimg, const float* g_alpha_ext,
+                     void* bwd_ws, float* dmeans, float* dscales, float* dquats, float* dopacity, float* dsh,
+                     float* ddecay, int n_sm, cudaStream_t st)
+{
+    const BwdLayout L = bwd_layout((uint64_t)S.n, V);
+    char* b = static_cast<char*>(bwd_ws);
+    float4* g2d = reinterpret_cast<float4*>(b + L.g2d);
+    float* dmg = reinterpret_cast<float*>(b + L.dmax_grad);
+    cudaMemsetAsync(bwd_ws, 0, L.total, st);
+    cudaMemsetAsync(&F.hdr->work[1], 0, sizeof(uint32_t), st);
+    k_blend_bwd<<<n_sm * std::max(1, g_bwd_blocks_per_sm), BLOCK_PIX, 0, st>>>(F, vals, ranges, Tfin, ncon, dimg, g2d);
+    ParamGrads P{dmeans, dscales, dquats, dopacity, dsh, ddecay};
+    int blocks = static_cast<int>(std::min<int64_t>((S.n + 127) / 128, (int64_t)n_sm * 16));
+    if (blocks < 1) blocks = 1;
+    if (S.n > 0) k_preprocess_bwd<<<blocks, 128, 0, st>>>(F, S, g2d, g_alpha_ext, dmg, P);
+    k_dmax_bwd<<<1, 64, 0, st>>>(F, S, dmg, dmeans);
+}
+
+size_t backward_ws_bytes(uint64_t n, uint32_t V) { return bwd_layout(n, V).total; }
+
+void launch_l1(const float* img, const float* tgt, int64_t count, float scale, float* loss, float* grad, int n_sm,
+               cudaStream_t st)
+{
+    int blocks = static_cast<int>(std::min<int64_t>((count + 255) / 256, (int64_t)n_sm * 4));
+    if (blocks < 1) blocks = 1;
+    k_l1_loss<<<blocks, 256, 0, st>>>(img, tgt, count, scale, loss, grad);
+}
+
+}  // namespace clod

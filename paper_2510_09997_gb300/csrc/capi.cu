@@ -21,6 +21,14 @@ void launch_blend_fwd(const Frame& F, const uint32_t* vals, const uint32_t* rang
                       uint32_t* ncout, unsigned long long* evaluated, int n_sm, cudaStream_t st);
 cudaError_t bin_sort_setup();
 cudaError_t render_setup();
+cudaError_t backward_setup();
+void launch_backward(const Frame& F, const clod_scene& S, uint32_t V, const uint32_t* vals, const uint32_t* ranges,
+                     const float* Tfin, const uint32_t* ncon, const float* dimg, const float* g_alpha_ext,
+                     void* bwd_ws, float* dmeans, float* dscales, float* dquats, float* dopacity, float* dsh,
+                     float* ddecay, int n_sm, cudaStream_t st);
+size_t backward_ws_bytes(uint64_t n, uint32_t V);
+void launch_l1(const float* img, const float* tgt, int64_t count, float scale, float* loss, float* grad, int n_sm,
+               cudaStream_t st);
 
 static thread_local std::string g_err;
 
@@ -119,6 +127,7 @@ clod_status device_ready(int* n_sm)
         if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
         if ((e = bin_sort_setup()) != cudaSuccess) return cuda_fail(e, "bin_sort_setup");
         if ((e = render_setup()) != cudaSuccess) return cuda_fail(e, "render_setup");
+        if ((e = backward_setup()) != cudaSuccess) return cuda_fail(e, "backward_setup");
         D.ready = true;
     }
     *n_sm = D.n_sm;
@@ -377,6 +386,57 @@ clod_status clod_frame_check(const void* ws, uint64_t pair_capacity, uint64_t* n
         return fail(CLOD_ERR_CAPACITY, "frame needs %llu pairs, capacity %llu", (unsigned long long)h.n_pairs,
                     (unsigned long long)pair_capacity);
     if (h.status & STATUS_TIMEOUT) return fail(CLOD_ERR_TIMEOUT, "a device wait gave up");
+    return CLOD_OK;
+}
+
+clod_status clod_backward_workspace_size(int64_t n, int32_t n_views, size_t* bytes)
+{
+    if (!bytes) return fail(CLOD_ERR_ARG, "bytes is NULL");
+    if (n < 0 || n >= (1ll << 31)) return fail(CLOD_ERR_ARG, "n = %lld outside [0, 2^31)", (long long)n);
+    if (n_views < 1 || n_views > MAX_VIEWS) return fail(CLOD_ERR_ARG, "n_views = %d outside [1, %d]", n_views, MAX_VIEWS);
+    *bytes = backward_ws_bytes((uint64_t)n, (uint32_t)n_views);
+    return CLOD_OK;
+}
+
+clod_status clod_render_bwd(const clod_scene* scene, const void* ws, const uint32_t* vals, const uint32_t* ranges,
+                            const float* T_final, const uint32_t* n_contrib, const float* dL_dimage,
+                            const float* dL_dalpha_eff, void* bwd_ws, size_t bwd_ws_bytes, float* dmeans,
+                            float* dscales, float* dquats, float* dopacity, float* dsh, float* ddecay,
+                            clod_stream stream)
+{
+    clod_status s = check_scene(scene);
+    if (s) return s;
+    if (!ws || !ranges || !T_final || !n_contrib || !dL_dimage || !bwd_ws)
+        return fail(CLOD_ERR_ARG, "NULL argument to clod_render_bwd");
+    if (scene->n > 0 && (!dmeans || !dscales || !dquats || !dopacity || !dsh || !ddecay))
+        return fail(CLOD_ERR_ARG, "NULL gradient output");
+    FrameLayout L;
+    if (!recall(ws, &L)) return fail(CLOD_ERR_ARG, "ws was not prepared by clod_preprocess");
+    if (L.n != (uint64_t)scene->n) return fail(CLOD_ERR_ARG, "scene has %lld Gaussians, the frame %llu",
+                                               (long long)scene->n, (unsigned long long)L.n);
+    const size_t need = backward_ws_bytes(L.n, L.n_views);
+    if (bwd_ws_bytes < need) return fail(CLOD_ERR_CAPACITY, "backward workspace needs %zu bytes, got %zu", need, bwd_ws_bytes);
+    if (reinterpret_cast<uintptr_t>(bwd_ws) % 256) return fail(CLOD_ERR_ARG, "bwd_ws must be 256-byte aligned");
+    int n_sm = 0;
+    if ((s = device_ready(&n_sm))) return s;
+    const Frame F = frame_ptrs(const_cast<void*>(ws), L);
+    launch_backward(F, *scene, L.n_views, vals, ranges, T_final, n_contrib, dL_dimage, dL_dalpha_eff, bwd_ws, dmeans,
+                    dscales, dquats, dopacity, dsh, ddecay, n_sm, static_cast<cudaStream_t>(stream));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "clod_render_bwd launch");
+    return CLOD_OK;
+}
+
+clod_status clod_l1_loss(const float* image, const float* target, int64_t count, float scale, float* loss,
+                         float* dL_dimage, clod_stream stream)
+{
+    if (!image || !target || count < 1) return fail(CLOD_ERR_ARG, "bad argument to clod_l1_loss");
+    int n_sm = 0;
+    clod_status s = device_ready(&n_sm);
+    if (s) return s;
+    launch_l1(image, target, count, scale, loss, dL_dimage, n_sm, static_cast<cudaStream_t>(stream));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "clod_l1_loss launch");
     return CLOD_OK;
 }
 
