@@ -173,8 +173,7 @@ def run_ours(args):
         C.check("clod_preprocess", L.clod_preprocess(C.ctypes.byref(ds.c), R.carr, 1, C._ptr(R.ws), R.ws.numel(),
                                                      None, None, None, C._ptr(R.npairs), st))
         e[1].record()
-        C.check("clod_bin_sort", L.clod_bin_sort(C._ptr(R.ws), R.cap, C._ptr(R.sort_ws), R.sort_ws.numel(), None,
-                                                 C._ptr(R.vals), C._ptr(R.ranges), st))
+        C.check("clod_bin_sort", L.clod_bin_sort(C._ptr(R.ws), R.cap, None, C._ptr(R.vals), C._ptr(R.ranges), st))
         e[2].record()
         C.check("clod_render_fwd", L.clod_render_fwd(C._ptr(R.ws), C._ptr(R.vals), C._ptr(R.ranges),
                                                      C._ptr(R.image), C._ptr(R.T), C._ptr(R.nc), st))
@@ -196,7 +195,7 @@ def run_ours(args):
     for k in range(args.steps):
         R.set_views([views[k % len(views)]])
         C.clod_preprocess(ds, R.views, R.ws, n_pairs=R.npairs)
-        C.clod_bin_sort(R.ws, R.cap, R.sort_ws, None, R.vals, R.ranges)
+        C.clod_bin_sort(R.ws, R.cap, None, R.vals, R.ranges)
         C.clod_render_fwd(R.ws, R.vals, R.ranges, R.image, R.T, R.nc, evaluated=evals)
     torch.cuda.synchronize()
     ev_per_frame = float(evals.item()) / args.steps

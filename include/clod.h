@@ -137,20 +137,20 @@ clod_status clod_preprocess(const clod_scene* scene, const clod_view* views, int
                             uint32_t* counts_out, uint64_t* n_pairs_out,
                             clod_stream stream);
 
-/* Scratch bytes clod_bin_sort needs for pair_capacity pairs. */
-clod_status clod_sort_workspace_size(uint64_t pair_capacity, size_t* bytes);
-
-/* Bins the pairs of the preprocessed frame by tile and sorts each tile's list
- * by (depth, Gaussian index) -- "sorted by depth" (Sec. 3.1) with ties in
- * index order -- i.e. the stable sort of the key
- * ((tile_base(view) + ty * TX + tx) << 32) | bits(depth).
+/* Emits every (view, tile, Gaussian) pair of the preprocessed frame in the
+ * order of the key ((tile_base(view) + ty * TX + tx) << 32) | bits(depth),
+ * equal keys in Gaussian-index order -- "sorted by depth" per tile
+ * (Sec. 3.1) -- and the tile ranges.  Built from a stable radix sort of the
+ * survivors' depths (depth ranks) and an order-preserving walk of the tile
+ * rectangles in rank order; no pair is sorted or written twice.
  * keys_out:   u64 [pair_capacity] sorted keys; may be NULL.
  * vals_out:   u32 [pair_capacity] Gaussian index of each sorted pair.
  * ranges_out: u32 [total_tiles * 2] [first, last) of each tile in vals_out;
  *             tiles without pairs get [0, 0).
- * If K > pair_capacity no pair is written past the capacity and the frame is
- * marked overflowed; clod_frame_check() then returns CLOD_ERR_CAPACITY. */
-clod_status clod_bin_sort(void* ws, uint64_t pair_capacity, void* sort_ws, size_t sort_ws_bytes,
+ * If K > pair_capacity nothing is written to keys_out/vals_out and the frame
+ * is marked overflowed: clod_render_fwd then writes nothing and
+ * clod_frame_check() returns CLOD_ERR_CAPACITY with the required K. */
+clod_status clod_bin_sort(void* ws, uint64_t pair_capacity,
                           uint64_t* keys_out, uint32_t* vals_out, uint32_t* ranges_out,
                           clod_stream stream);
 

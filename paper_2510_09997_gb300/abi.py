@@ -59,8 +59,7 @@ SIGNATURES = {
     "clod_version": ([], ctypes.c_char_p),
     "clod_frame_workspace_size": ([ctypes.c_int64, P, ctypes.c_int32, P, P], c_status),
     "clod_preprocess": ([P, P, ctypes.c_int32, P, ctypes.c_size_t, P, P, P, P, P], c_status),
-    "clod_sort_workspace_size": ([ctypes.c_uint64, P], c_status),
-    "clod_bin_sort": ([P, ctypes.c_uint64, P, ctypes.c_size_t, P, P, P, P], c_status),
+    "clod_bin_sort": ([P, ctypes.c_uint64, P, P, P, P], c_status),
     "clod_render_fwd": ([P, P, P, P, P, P, P], c_status),
     "clod_render_fwd_count": ([P, P, P, P, P, P, P, P], c_status),
     "clod_frame_check": ([P, ctypes.c_uint64, P, P], c_status),

@@ -108,12 +108,6 @@ def frame_layout(n: int, views: Sequence):
     return int(nbytes.value), lay
 
 
-def sort_workspace_size(cap: int) -> int:
-    b = ctypes.c_size_t()
-    check("clod_sort_workspace_size", lib().clod_sort_workspace_size(cap, ctypes.byref(b)))
-    return int(b.value)
-
-
 # ---------------------------------------------------------------------------
 # Entry points with the C-ABI names
 # ---------------------------------------------------------------------------
@@ -125,9 +119,9 @@ def clod_preprocess(scene: DeviceScene, views, ws: torch.Tensor, mask=None, alph
                                                    _stream(stream)))
 
 
-def clod_bin_sort(ws, cap: int, sort_ws, keys, vals, ranges, stream=None):
-    check("clod_bin_sort", lib().clod_bin_sort(_ptr(ws), cap, _ptr(sort_ws), sort_ws.numel(), _ptr(keys),
-                                               _ptr(vals), _ptr(ranges), _stream(stream)))
+def clod_bin_sort(ws, cap: int, keys, vals, ranges, stream=None):
+    check("clod_bin_sort", lib().clod_bin_sort(_ptr(ws), cap, _ptr(keys), _ptr(vals), _ptr(ranges),
+                                               _stream(stream)))
 
 
 def clod_render_fwd(ws, vals, ranges, image, T_final=None, n_contrib=None, stream=None, evaluated=None):
@@ -210,11 +204,10 @@ def render(scene: DeviceScene, views, want_keys: bool = True, stream=None, evalu
     clod_preprocess(scene, views, ws, mask, alpha, counts, npairs, stream)
     K = int(npairs.item())
     cap = max(K, 1)
-    sort_ws = torch.empty(sort_workspace_size(cap), dtype=torch.uint8, device=dev)
     keys = torch.empty(cap, dtype=torch.int64, device=dev) if want_keys else None
     vals = torch.empty(cap, dtype=torch.int32, device=dev)
     ranges = torch.empty((lay.total_tiles, 2), dtype=torch.int32, device=dev)
-    clod_bin_sort(ws, cap, sort_ws, keys, vals, ranges, stream)
+    clod_bin_sort(ws, cap, keys, vals, ranges, stream)
     bases = pixel_bases(views)
     P = sum(v.width * v.height for v in views)
     image = torch.empty(3 * P, dtype=torch.float32, device=dev)
@@ -237,7 +230,6 @@ class Renderer:
         nbytes, self.layout = frame_layout(scene.n, self.views)
         self.ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
         self.cap = int(pair_capacity)
-        self.sort_ws = torch.empty(sort_workspace_size(self.cap), dtype=torch.uint8, device=dev)
         self.keys = torch.empty(self.cap, dtype=torch.int64, device=dev) if want_keys else None
         self.vals = torch.empty(self.cap, dtype=torch.int32, device=dev)
         self.ranges = torch.empty((self.layout.total_tiles, 2), dtype=torch.int32, device=dev)
@@ -261,8 +253,8 @@ class Renderer:
         check("clod_preprocess", L.clod_preprocess(ctypes.byref(self.scene.c), self.carr, len(self.views),
                                                    _ptr(self.ws), self.ws.numel(), None, None, None,
                                                    _ptr(self.npairs), st))
-        check("clod_bin_sort", L.clod_bin_sort(_ptr(self.ws), self.cap, _ptr(self.sort_ws), self.sort_ws.numel(),
-                                               _ptr(self.keys), _ptr(self.vals), _ptr(self.ranges), st))
+        check("clod_bin_sort", L.clod_bin_sort(_ptr(self.ws), self.cap, _ptr(self.keys), _ptr(self.vals),
+                                               _ptr(self.ranges), st))
         check("clod_render_fwd", L.clod_render_fwd(_ptr(self.ws), _ptr(self.vals), _ptr(self.ranges),
                                                    _ptr(self.image), _ptr(self.T), _ptr(self.nc), st))
 

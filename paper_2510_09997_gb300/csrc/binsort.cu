@@ -1,214 +1,338 @@
-// binsort.cu -- pair emission and the (tile, depth) sort.
+// binsort.cu -- pair emission in (tile, depth, index) order.
 //
 // The list the blend needs is every (view, tile, Gaussian) pair sorted by the
 // 64-bit key ((tile_base(view) + tile) << 32) | bits(depth) -- "sorted by
-// depth" (Sec. 3.1) per tile -- with equal keys in Gaussian-index order (the
-// stable sort of the index-ordered emission).  It is built as a most-
-// significant-digit radix sort whose first digit is the whole global tile id:
+// depth" (Sec. 3.1) per tile -- with equal keys in Gaussian-index order.  It
+// is built without sorting the K pairs and without per-pair atomics:
 //
-//   k_scatter       counting-sort scatter: each surviving (view, Gaussian)
-//                   writes (bits(depth) << 32 | index) into the bucket of
-//                   every tile of its rectangle (bucket offsets = exclusive
-//                   scan of the per-tile counts made during preprocessing;
-//                   slot by atomic cursor, so order inside a bucket is
-//                   arbitrary);
-//   k_tile_sort     one block per tile sorts its bucket in shared memory by
-//                   the 64-bit (depth, index) value -- a total order, so the
-//                   result is unique and equals the stable key sort -- and
-//                   writes values, keys and the tile's range;
-//   k_tile_sort_big tiles longer than the small kernel's capacity: chunks
-//                   sorted in shared memory, then merge-path merges through
-//                   a scratch buffer.
+//   1. depth-rank sort: a stable LSD radix sort (8-bit digits, four passes)
+//      of the survivors' depth bits per view, values = Gaussian index in
+//      index order, culled Gaussians keyed all-ones (sorted last).  The last
+//      pass also gathers each survivor's tile rectangle into rank order.
+//   2. the survivors of a view are cut into chunks of consecutive ranks; one
+//      warp per (chunk, tile row) walks the chunk's rectangles in rank order
+//      and counts, per tile of its row, the pairs the chunk contributes
+//      (k_rows<false>);
+//   3. per tile, an exclusive scan over the chunks (k_chunk_scan), then over
+//      the tiles (k_scan_tiles: tile offsets, K, ranges);
+//   4. the same walk again (k_rows<true>): pair (Gaussian, tile) goes to
+//      tile_offset + chunk offset + (number of earlier-ranked Gaussians of the
+//      chunk in that tile) -- its final sorted position.
 //
-// HBM traffic per pair: 8 B scattered, 8 B read back, 4 B (values) + 8 B
-// (keys, optional) written -- against ~150 B per pair for an LSD radix sort
-// over 45-50 key bits.
+// Work is O(n) for the rank sort, O(K) writes for the emission; nothing is
+// atomic but per-block counters, so the result is deterministic and equals
+// the stable sort of the index-ordered emission by key.
 #include <algorithm>
 
 #include "clod_internal.cuh"
 
 namespace clod {
 
-constexpr int SMALL_CAP = 2048;         // k_tile_sort, 256 threads, 16 KB
-constexpr int BIG_THREADS = 1024;
-constexpr int BIG_CHUNK = 8192;         // k_tile_sort_big, 64 KB chunks
-
-__global__ void __launch_bounds__(256) k_scatter(Frame F, int64_t n, uint32_t V, unsigned long long* __restrict__ pairs,
-                                                 unsigned long long cap)
+__device__ __forceinline__ uint32_t lanemask_lt()
 {
-    __shared__ uint32_t s_base[MAX_VIEWS];
-    __shared__ int32_t s_tx[MAX_VIEWS];
-    const unsigned long long K = F.hdr->n_pairs;
-    if (K > cap || (F.hdr->status & STATUS_OVERFLOW)) {
-        if (threadIdx.x == 0) atomicOr(&F.hdr->status, STATUS_OVERFLOW);
-        return;
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// ---------------------------------------------------------------------------
+// 1. depth-rank sort
+// ---------------------------------------------------------------------------
+// Per-warp digit counts of the block's items: warp w owns items
+// [w * 512, w * 512 + 512) of the block, in order.
+__device__ __forceinline__ void rs_warp_counts(const uint32_t* __restrict__ keys, int64_t base, int cnt, int shift,
+                                               uint32_t (*h)[256])
+{
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int k = lane; k < 256; k += 32) h[w][k] = 0;
+    __syncwarp();
+    constexpr int PER_WARP = RS_ITEMS / (RS_THREADS / 32);
+    for (int r = 0; r < PER_WARP; r += 32) {
+        const int idx = w * PER_WARP + r + lane;
+        const bool valid = idx < cnt;
+        const uint32_t d = valid ? ((keys[base + idx] >> shift) & 255u) : 256u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        if (valid && (__ffs(peers) - 1) == lane) h[w][d] += __popc(peers);
+        __syncwarp();
     }
-    for (uint32_t v = threadIdx.x; v < V; v += blockDim.x) {
-        s_base[v] = F.views[v].tile_base;
-        s_tx[v] = F.views[v].TX;
+}
+
+__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint32_t* __restrict__ keys, int64_t n, int nb, int shift,
+                                                        uint32_t* __restrict__ hist)
+{
+    __shared__ uint32_t h[RS_THREADS / 32][256];
+    const int b = blockIdx.x, v = b / nb, lb = b % nb;
+    const int64_t base = (int64_t)v * n + (int64_t)lb * RS_ITEMS;
+    const int cnt = (int)min((int64_t)RS_ITEMS, n - (int64_t)lb * RS_ITEMS);
+    rs_warp_counts(keys, base, cnt, shift, h);
+    __syncthreads();
+    uint32_t s = 0;
+    for (int w = 0; w < RS_THREADS / 32; ++w) s += h[w][threadIdx.x];
+    hist[((size_t)v * 256 + threadIdx.x) * nb + lb] = s;
+}
+
+// Exclusive scan of one view's 256 * nb counts (digit-major) by one block.
+__global__ void __launch_bounds__(1024) k_rs_scan(uint32_t* __restrict__ hist, int nb)
+{
+    __shared__ uint32_t wsum[32];
+    uint32_t* h = hist + (size_t)blockIdx.x * 256 * nb;
+    const int total = 256 * nb;
+    const int per = (total + blockDim.x - 1) / blockDim.x;
+    const int b0 = min(total, (int)threadIdx.x * per), b1 = min(total, b0 + per);
+    uint32_t s = 0;
+    for (int k = b0; k < b1; ++k) s += h[k];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t x = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t w = wsum[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        wsum[lane] = w;
     }
     __syncthreads();
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        for (uint32_t v = 0; v < V; ++v) {
-            const int64_t o = (int64_t)v * n + i;
-            const uint2 r = F.rect[o];
-            const uint32_t x0 = r.x & 0xFFFFu, y0 = r.x >> 16, x1 = r.y & 0xFFFFu, y1 = r.y >> 16;
-            if (x1 <= x0 || y1 <= y0) continue;
-            const unsigned long long val =
-                (static_cast<unsigned long long>(__float_as_uint(F.depth[o])) << 32) | static_cast<uint32_t>(i);
-            for (uint32_t ty = y0; ty < y1; ++ty)
-                for (uint32_t tx = x0; tx < x1; ++tx) {
-                    const uint32_t t = s_base[v] + ty * s_tx[v] + tx;
-                    const uint32_t pos = atomicAdd(&F.cursor[t], 1u);
-                    pairs[pos] = val;
-                }
-        }
+    uint32_t run = x - s + (wid ? wsum[wid - 1] : 0u);
+    for (int k = b0; k < b1; ++k) {
+        const uint32_t c = h[k];
+        h[k] = run;
+        run += c;
     }
 }
 
-// Bitonic sort of s[0, n2) (n2 a power of two) by nthreads threads.
-__device__ __forceinline__ void bitonic_sort(unsigned long long* s, int n2)
+// Stable scatter of one digit pass; on the last pass also gathers the tile
+// rectangle of every survivor into rank order.
+__global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                                           uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                           int64_t n, int nb, int shift, const uint32_t* __restrict__ hist,
+                                                           const uint2* __restrict__ rect, uint2* __restrict__ srect)
 {
-    for (int k = 2; k <= n2; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int t = threadIdx.x; t < (n2 >> 1); t += blockDim.x) {
-                const int a = 2 * t - (t & (j - 1));
-                const int b = a + j;
-                const bool up = (a & k) == 0;
-                const unsigned long long x = s[a], y = s[b];
-                if ((x > y) == up) {
-                    s[a] = y;
-                    s[b] = x;
-                }
+    __shared__ uint32_t h[RS_THREADS / 32][256];
+    __shared__ uint32_t wb[RS_THREADS / 32][256];
+    const int b = blockIdx.x, v = b / nb, lb = b % nb;
+    const int64_t vbase = (int64_t)v * n;
+    const int64_t base = vbase + (int64_t)lb * RS_ITEMS;
+    const int cnt = (int)min((int64_t)RS_ITEMS, n - (int64_t)lb * RS_ITEMS);
+    rs_warp_counts(kin, base, cnt, shift, h);
+    __syncthreads();
+    {
+        uint32_t run = hist[((size_t)v * 256 + threadIdx.x) * nb + lb];
+        for (int w = 0; w < RS_THREADS / 32; ++w) {
+            wb[w][threadIdx.x] = run;
+            run += h[w][threadIdx.x];
+        }
+    }
+    __syncthreads();
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t lt = lanemask_lt();
+    constexpr int PER_WARP = RS_ITEMS / (RS_THREADS / 32);
+    for (int r = 0; r < PER_WARP; r += 32) {
+        const int idx = w * PER_WARP + r + lane;
+        const bool valid = idx < cnt;
+        const uint32_t key = valid ? kin[base + idx] : 0u;
+        const uint32_t d = valid ? ((key >> shift) & 255u) : 256u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        if (valid) {
+            const uint32_t pos = wb[w][d] + __popc(peers & lt);
+            const uint32_t val = vin[base + idx];
+            kout[vbase + pos] = key;
+            vout[vbase + pos] = val;
+            if (srect && key != 0xFFFFFFFFu) srect[vbase + pos] = rect[vbase + val];
+        }
+        __syncwarp();
+        if (valid && (__ffs(peers) - 1) == lane) wb[w][d] += __popc(peers);
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 2./4. per (chunk, tile row) walks
+// ---------------------------------------------------------------------------
+// Block -> (view, chunk, row block) through the views' rb_base.
+__device__ __forceinline__ int find_view_rb(const ViewDev* views, uint32_t V, uint32_t b)
+{
+    int v = 0;
+    for (uint32_t u = 1; u < V; ++u)
+        if (b >= views[u].rb_base) v = (int)u;
+    return v;
+}
+
+template <bool EMIT>
+__global__ void __launch_bounds__(ROWS_PER_BLOCK * 32) k_rows(Frame F, uint32_t* __restrict__ vals,
+                                                             unsigned long long* __restrict__ keys)
+{
+    extern __shared__ uint32_t sm[];
+    __shared__ uint2 s_rect[STAGE];
+    __shared__ uint32_t s_id[STAGE];
+    __shared__ uint32_t s_key[STAGE];
+    const FrameHeader* hdr = F.hdr;
+    if (EMIT && (hdr->status & STATUS_OVERFLOW)) return;
+    const uint32_t V = hdr->n_views;
+    const uint32_t CH = hdr->n_chunks;
+    const int64_t n = (int64_t)hdr->n;
+    const int v = find_view_rb(F.views, V, blockIdx.x);
+    const ViewDev& W = F.views[v];
+    const uint32_t rbn = (uint32_t)(W.TY + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK;
+    const uint32_t local = blockIdx.x - W.rb_base;
+    const uint32_t c = local / rbn, rb = local % rbn;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int row = (int)rb * ROWS_PER_BLOCK + w;
+    const bool row_ok = row < W.TY;
+    const int TX = W.TX;
+    const uint32_t T = (uint32_t)(W.TX * W.TY);
+    uint32_t* ctr = sm + (size_t)w * hdr->max_tx;
+    uint32_t* cnt_row = F.cnt + (size_t)CH * W.tile_base + (size_t)c * T + (size_t)row * TX;
+    const uint32_t Ns = F.n_surv[2 * v + 1];
+    const uint32_t C = (Ns + CH - 1) / CH;
+    const uint32_t r0 = min(Ns, c * C), r1 = min(Ns, r0 + C);
+    if (row_ok)
+        for (int x = lane; x < TX; x += 32)
+            ctr[x] = EMIT ? F.tile_offset[W.tile_base + row * TX + x] + cnt_row[x] : 0u;
+    const int64_t vb = (int64_t)v * n;
+    for (uint32_t s0 = r0; s0 < r1; s0 += STAGE) {
+        const int m = (int)min((uint32_t)STAGE, r1 - s0);
+        __syncthreads();
+        for (int k = threadIdx.x; k < m; k += blockDim.x) {
+            s_rect[k] = F.srect[vb + s0 + k];
+            if (EMIT) {
+                s_id[k] = F.val0[vb + s0 + k];
+                s_key[k] = F.key0[vb + s0 + k];
             }
-            __syncthreads();
+        }
+        __syncthreads();
+        if (!row_ok) continue;
+        for (int g0 = 0; g0 < m; g0 += 32) {
+            const int g = g0 + lane;
+            uint2 rc = make_uint2(0u, 0u);
+            if (g < m) rc = s_rect[g];
+            const int y0 = (int)(rc.x >> 16), y1 = (int)(rc.y >> 16);
+            unsigned hit = __ballot_sync(0xffffffffu, g < m && row >= y0 && row < y1);
+            while (hit) {
+                const int bsrc = __ffs(hit) - 1;
+                hit &= hit - 1;
+                const uint32_t rx0 = __shfl_sync(0xffffffffu, rc.x, bsrc), rx1 = __shfl_sync(0xffffffffu, rc.y, bsrc);
+                const int x0 = (int)(rx0 & 0xFFFFu), x1 = (int)(rx1 & 0xFFFFu);
+                for (int x = x0 + lane; x < x1; x += 32) {
+                    const uint32_t p = ctr[x];
+                    ctr[x] = p + 1u;
+                    if (EMIT) {
+                        vals[p] = s_id[g0 + bsrc];
+                        if (keys)
+                            keys[p] = ((unsigned long long)(W.tile_base + (uint32_t)(row * TX + x)) << 32) |
+                                      s_key[g0 + bsrc];
+                    }
+                }
+                __syncwarp();
+            }
         }
     }
+    if (!EMIT && row_ok)
+        for (int x = lane; x < TX; x += 32) cnt_row[x] = ctr[x];
 }
 
-__device__ __forceinline__ void write_sorted(unsigned long long v, uint32_t tile, uint32_t pos,
-                                             uint32_t* __restrict__ vals, unsigned long long* __restrict__ keys)
+// 3a. per tile: exclusive scan of the chunk counts; tile_count = total.
+__global__ void __launch_bounds__(256) k_chunk_scan(Frame F)
 {
-    vals[pos] = static_cast<uint32_t>(v);
-    if (keys) keys[pos] = (static_cast<unsigned long long>(tile) << 32) | (v >> 32);
-}
-
-__global__ void __launch_bounds__(256) k_tile_sort(Frame F, const unsigned long long* __restrict__ pairs,
-                                                   unsigned long long cap, uint32_t* __restrict__ vals,
-                                                   unsigned long long* __restrict__ keys, uint32_t* __restrict__ ranges)
-{
-    __shared__ unsigned long long s[SMALL_CAP];
     const uint32_t TT = F.hdr->total_tiles;
-    if (F.hdr->status & STATUS_OVERFLOW) return;
-    for (uint32_t t = blockIdx.x; t < TT; t += gridDim.x) {
-        const uint32_t start = F.tile_offset[t], end = F.tile_offset[t + 1];
-        const uint32_t cnt = end - start;
-        if (threadIdx.x == 0) {
-            ranges[2 * t] = cnt ? start : 0u;
-            ranges[2 * t + 1] = cnt ? end : 0u;
+    const uint32_t V = F.hdr->n_views;
+    const uint32_t CH = F.hdr->n_chunks;
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= TT) return;
+    int v = 0;
+    for (uint32_t u = 1; u < V; ++u)
+        if (t >= F.views[u].tile_base) v = (int)u;
+    const ViewDev& W = F.views[v];
+    const uint32_t T = (uint32_t)(W.TX * W.TY);
+    uint32_t* col = F.cnt + (size_t)CH * W.tile_base + (t - W.tile_base);
+    uint32_t acc = 0;
+    for (uint32_t c = 0; c < CH; ++c) {
+        const uint32_t x = col[(size_t)c * T];
+        col[(size_t)c * T] = acc;
+        acc += x;
+    }
+    F.tile_count[t] = acc;
+}
+
+// 3b. exclusive scan of the tile counts by one block of 1024 threads; writes
+// the tile offsets, the ranges ([0, 0) for empty tiles) and checks K.
+__global__ void __launch_bounds__(1024) k_scan_tiles(Frame F, uint32_t* __restrict__ ranges, unsigned long long cap)
+{
+    __shared__ unsigned long long wsum[32];
+    const uint32_t TT = F.hdr->total_tiles;
+    const uint32_t per = (TT + blockDim.x - 1) / blockDim.x;
+    const uint32_t b0 = min(TT, threadIdx.x * per), b1 = min(TT, b0 + per);
+    unsigned long long s = 0;
+    for (uint32_t t = b0; t < b1; ++t) s += F.tile_count[t];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned long long x = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned long long w = wsum[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
         }
-        if (cnt == 0) continue;
-        if (cnt > SMALL_CAP) {
-            if (threadIdx.x == 0) {
-                const uint32_t k = atomicAdd(&F.hdr->big_count, 1u);
-                F.big_list[k] = t;
-            }
-            continue;
-        }
-        int n2 = 1;
-        while (n2 < (int)cnt) n2 <<= 1;
-        for (int k = threadIdx.x; k < n2; k += blockDim.x) s[k] = k < (int)cnt ? pairs[start + k] : ~0ull;
-        __syncthreads();
-        if (n2 > 1) bitonic_sort(s, n2);
-        for (int k = threadIdx.x; k < (int)cnt; k += blockDim.x) write_sorted(s[k], t, start + k, vals, keys);
-        __syncthreads();
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    unsigned long long run = x - s + (wid ? wsum[wid - 1] : 0ull);
+    const unsigned long long total = wsum[31];
+    for (uint32_t t = b0; t < b1; ++t) {
+        const uint32_t c = F.tile_count[t];
+        F.tile_offset[t] = static_cast<uint32_t>(run);
+        ranges[2 * t] = c ? static_cast<uint32_t>(run) : 0u;
+        ranges[2 * t + 1] = c ? static_cast<uint32_t>(run + c) : 0u;
+        run += c;
+    }
+    if (threadIdx.x == 0) {
+        F.tile_offset[TT] = static_cast<uint32_t>(total);
+        if (total != F.hdr->n_pairs || total > cap || total > 0xFFFFFFFFull) atomicOr(&F.hdr->status, STATUS_OVERFLOW);
     }
 }
 
-// Merge-path split: number of elements taken from A among the first k
-// outputs of merge(A[0,na), B[0,nb)) (all values distinct).
-__device__ __forceinline__ int merge_split(const unsigned long long* A, int na, const unsigned long long* B, int nb,
-                                           int k)
-{
-    int lo = max(0, k - nb), hi = min(k, na);
-    while (lo < hi) {
-        const int m = (lo + hi) >> 1;
-        if (A[m] < B[k - m - 1]) lo = m + 1;
-        else hi = m;
-    }
-    return lo;
-}
+static int g_rows_smem_max = 0;
 
-__global__ void __launch_bounds__(BIG_THREADS) k_tile_sort_big(Frame F, unsigned long long* __restrict__ pairs,
-                                                               unsigned long long* __restrict__ scratch,
-                                                               uint32_t* __restrict__ vals,
-                                                               unsigned long long* __restrict__ keys)
+void launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long long cap, uint64_t* keys, uint32_t* vals,
+                     uint32_t* ranges, cudaStream_t st)
 {
-    extern __shared__ unsigned long long sb[];
-    if (F.hdr->status & STATUS_OVERFLOW) return;
-    const uint32_t nb = F.hdr->big_count;
-    for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
-        const uint32_t t = F.big_list[b];
-        const uint32_t start = F.tile_offset[t];
-        const int len = static_cast<int>(F.tile_offset[t + 1] - start);
-        unsigned long long* src = pairs + start;
-        unsigned long long* dst = scratch + start;
-        // 1. sort chunks of BIG_CHUNK in shared memory, in place
-        for (int c0 = 0; c0 < len; c0 += BIG_CHUNK) {
-            const int cl = min(BIG_CHUNK, len - c0);
-            int n2 = 1;
-            while (n2 < cl) n2 <<= 1;
-            for (int k = threadIdx.x; k < n2; k += blockDim.x) sb[k] = k < cl ? src[c0 + k] : ~0ull;
-            __syncthreads();
-            bitonic_sort(sb, n2);
-            for (int k = threadIdx.x; k < cl; k += blockDim.x) src[c0 + k] = sb[k];
-            __syncthreads();
+    const int64_t n = (int64_t)L.n;
+    const int nb = (int)L.n_rs_blocks;
+    const uint32_t V = L.n_views;
+    if (n > 0) {
+        uint32_t *ki = F.key0, *vi = F.val0, *ko = F.key1, *vo = F.val1;
+        for (int pass = 0; pass < 4; ++pass) {
+            k_rs_hist<<<V * nb, RS_THREADS, 0, st>>>(ki, n, nb, 8 * pass, F.rs_hist);
+            k_rs_scan<<<V, 1024, 0, st>>>(F.rs_hist, nb);
+            k_rs_scatter<<<V * nb, RS_THREADS, 0, st>>>(ki, vi, ko, vo, n, nb, 8 * pass, F.rs_hist, F.rect,
+                                                        pass == 3 ? F.srect : nullptr);
+            std::swap(ki, ko);
+            std::swap(vi, vo);
         }
-        // 2. merge runs of width w into the other buffer, w = chunk, 2 chunk, ...
-        constexpr int E = 8;   // outputs per thread per step
-        for (int w = BIG_CHUNK; w < len; w <<= 1) {
-            for (int o0 = threadIdx.x * E; o0 < len; o0 += blockDim.x * E) {
-                const int a = (o0 / (2 * w)) * (2 * w);
-                const int mid = min(a + w, len), end = min(a + 2 * w, len);
-                const int na = mid - a, nbb = end - mid;
-                const int k = o0 - a;
-                int i = merge_split(src + a, na, src + mid, nbb, k);
-                int j = k - i;
-                const int cnt = min(E, end - o0);
-                for (int e = 0; e < cnt; ++e) {
-                    const bool takeA = j >= nbb || (i < na && src[a + i] < src[mid + j]);
-                    dst[o0 + e] = takeA ? src[a + i] : src[mid + j];
-                    if (takeA) ++i;
-                    else ++j;
-                }
-            }
-            __syncthreads();
-            unsigned long long* tmp = src;
-            src = dst;
-            dst = tmp;
-        }
-        for (int k = threadIdx.x; k < len; k += blockDim.x) write_sorted(src[k], t, start + k, vals, keys);
-        __syncthreads();
     }
-}
-
-void launch_bin_sort(const Frame& F, int64_t n, uint32_t V, uint32_t total_tiles, unsigned long long* pairs,
-                     unsigned long long* scratch, unsigned long long cap, uint64_t* keys, uint32_t* vals,
-                     uint32_t* ranges, int n_sm, cudaStream_t st)
-{
-    int blocks = static_cast<int>(std::min<int64_t>((n + 255) / 256, (int64_t)n_sm * 8));
-    if (blocks < 1) blocks = 1;
-    if (n > 0) k_scatter<<<blocks, 256, 0, st>>>(F, n, V, pairs, cap);
-    const int tblocks = static_cast<int>(std::max<uint32_t>(1u, std::min<uint32_t>(total_tiles, 65535u * 4u)));
-    k_tile_sort<<<tblocks, 256, 0, st>>>(F, pairs, cap, vals, reinterpret_cast<unsigned long long*>(keys), ranges);
-    k_tile_sort_big<<<n_sm, BIG_THREADS, BIG_CHUNK * sizeof(unsigned long long), st>>>(
-        F, pairs, scratch, vals, reinterpret_cast<unsigned long long*>(keys));
+    const size_t smem = (size_t)ROWS_PER_BLOCK * L.max_tx * sizeof(uint32_t);
+    k_rows<false><<<L.rb_total, ROWS_PER_BLOCK * 32, smem, st>>>(F, nullptr, nullptr);
+    k_chunk_scan<<<(L.total_tiles + 255) / 256, 256, 0, st>>>(F);
+    k_scan_tiles<<<1, 1024, 0, st>>>(F, ranges, cap);
+    k_rows<true><<<L.rb_total, ROWS_PER_BLOCK * 32, smem, st>>>(F, vals, reinterpret_cast<unsigned long long*>(keys));
 }
 
 cudaError_t bin_sort_setup()
 {
-    return cudaFuncSetAttribute(k_tile_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                BIG_CHUNK * (int)sizeof(unsigned long long));
+    const int bytes = ROWS_PER_BLOCK * 1024 * (int)sizeof(uint32_t);
+    cudaError_t e = cudaFuncSetAttribute(k_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
 }
 
 }  // namespace clod

@@ -14,9 +14,8 @@ namespace clod {
 
 void launch_preprocess(const Frame& F, const clod_scene& S, uint32_t V, uint8_t* mask_out, float* alpha_out,
                        unsigned long long* n_pairs_out, int n_sm, cudaStream_t st);
-void launch_bin_sort(const Frame& F, int64_t n, uint32_t V, uint32_t total_tiles, unsigned long long* pairs,
-                     unsigned long long* scratch, unsigned long long cap, uint64_t* keys, uint32_t* vals,
-                     uint32_t* ranges, int n_sm, cudaStream_t st);
+void launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long long cap, uint64_t* keys, uint32_t* vals,
+                     uint32_t* ranges, cudaStream_t st);
 void launch_blend_fwd(const Frame& F, const uint32_t* vals, const uint32_t* ranges, float* image, float* Tout,
                       uint32_t* ncout, unsigned long long* evaluated, int n_sm, cudaStream_t st);
 cudaError_t bin_sort_setup();
@@ -50,9 +49,19 @@ clod_status cuda_fail(cudaError_t e, const char* what)
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-FrameLayout frame_layout(uint64_t n, uint32_t V, uint32_t TT)
+static uint32_t n_chunks_for(uint64_t n)
+{
+    uint64_t c = (n + 1023) / 1024;
+    return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(c, MAX_CHUNKS));
+}
+
+FrameLayout frame_layout(uint64_t n, uint32_t V, uint32_t TT, uint32_t rb_total, uint32_t max_tx)
 {
     FrameLayout L{};
+    L.n_chunks = n_chunks_for(n);
+    L.n_rs_blocks = (uint32_t)((n + RS_ITEMS - 1) / RS_ITEMS);
+    L.rb_total = rb_total;
+    L.max_tx = max_tx;
     size_t o = 0;
     auto take = [&](size_t bytes) {
         const size_t at = o;
@@ -66,14 +75,19 @@ FrameLayout frame_layout(uint64_t n, uint32_t V, uint32_t TT)
     L.tile_count = take(sizeof(uint32_t) * (size_t)TT);
     L.views = take(sizeof(ViewDev) * V);
     L.tile_offset = take(sizeof(uint32_t) * ((size_t)TT + 1));
-    L.cursor = take(sizeof(uint32_t) * (size_t)TT);
-    L.big_list = take(sizeof(uint32_t) * (size_t)TT);
     const size_t vn = (size_t)V * n;
     L.rec0 = take(sizeof(float4) * vn);
     L.rec1 = take(sizeof(float4) * vn);
     L.rec2 = take(sizeof(float) * vn);
     L.depth = take(sizeof(float) * vn);
     L.rect = take(sizeof(uint2) * vn);
+    L.key0 = take(sizeof(uint32_t) * vn);
+    L.val0 = take(sizeof(uint32_t) * vn);
+    L.key1 = take(sizeof(uint32_t) * vn);
+    L.val1 = take(sizeof(uint32_t) * vn);
+    L.srect = take(sizeof(uint2) * vn);
+    L.rs_hist = take(sizeof(uint32_t) * 256 * (size_t)V * L.n_rs_blocks);
+    L.cnt = take(sizeof(uint32_t) * (size_t)L.n_chunks * TT);
     L.total = o;
     L.total_tiles = TT;
     L.n_views = V;
@@ -96,8 +110,13 @@ Frame frame_ptrs(void* ws, const FrameLayout& L)
     F.rect = reinterpret_cast<uint2*>(b + L.rect);
     F.tile_count = reinterpret_cast<uint32_t*>(b + L.tile_count);
     F.tile_offset = reinterpret_cast<uint32_t*>(b + L.tile_offset);
-    F.cursor = reinterpret_cast<uint32_t*>(b + L.cursor);
-    F.big_list = reinterpret_cast<uint32_t*>(b + L.big_list);
+    F.key0 = reinterpret_cast<uint32_t*>(b + L.key0);
+    F.val0 = reinterpret_cast<uint32_t*>(b + L.val0);
+    F.key1 = reinterpret_cast<uint32_t*>(b + L.key1);
+    F.val1 = reinterpret_cast<uint32_t*>(b + L.val1);
+    F.srect = reinterpret_cast<uint2*>(b + L.srect);
+    F.rs_hist = reinterpret_cast<uint32_t*>(b + L.rs_hist);
+    F.cnt = reinterpret_cast<uint32_t*>(b + L.cnt);
     return F;
 }
 
@@ -134,7 +153,11 @@ clod_status device_ready(int* n_sm)
     return CLOD_OK;
 }
 
-static clod_status check_views(const clod_view* views, int32_t V, uint32_t* TT)
+struct ViewGeom {
+    uint32_t TT, rb_total, max_tx;
+};
+
+static clod_status check_views(const clod_view* views, int32_t V, uint64_t n, ViewGeom* G)
 {
     if (!views) return fail(CLOD_ERR_ARG, "views is NULL");
     if (V < 1 || V > MAX_VIEWS) return fail(CLOD_ERR_ARG, "n_views = %d outside [1, %d]", V, MAX_VIEWS);
@@ -150,15 +173,27 @@ static clod_status check_views(const clod_view* views, int32_t V, uint32_t* TT)
         px += (uint64_t)w.width * w.height;
     }
     if (tt > 0x0FFFFFFFull) return fail(CLOD_ERR_ARG, "too many tiles (%llu)", (unsigned long long)tt);
-    *TT = static_cast<uint32_t>(tt);
+    G->TT = static_cast<uint32_t>(tt);
+    const uint32_t CH = n_chunks_for(n);
+    uint64_t rb = 0;
+    uint32_t mtx = 1;
+    for (int v = 0; v < V; ++v) {
+        const int TX = (views[v].width + TILE - 1) / TILE, TY = (views[v].height + TILE - 1) / TILE;
+        rb += (uint64_t)CH * ((TY + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK);
+        mtx = std::max<uint32_t>(mtx, (uint32_t)TX);
+    }
+    if (rb > 0x7FFFFFFFull) return fail(CLOD_ERR_ARG, "frame too large");
+    G->rb_total = (uint32_t)rb;
+    G->max_tx = mtx;
     return CLOD_OK;
 }
 
-static void make_view_table(const clod_view* views, int32_t V, std::vector<ViewDev>& out)
+static void make_view_table(const clod_view* views, int32_t V, uint64_t n, std::vector<ViewDev>& out)
 {
     out.resize(V);
-    uint32_t tile_base = 0;
+    uint32_t tile_base = 0, rb_base = 0;
     uint64_t pix_base = 0;
+    const uint32_t CH = n_chunks_for(n);
     for (int v = 0; v < V; ++v) {
         const clod_view& w = views[v];
         ViewDev& d = out[v];
@@ -184,8 +219,10 @@ static void make_view_table(const clod_view* views, int32_t V, std::vector<ViewD
         d.flags = w.flags;
         d.tile_base = tile_base;
         d.pix_base = pix_base;
+        d.rb_base = rb_base;
         tile_base += (uint32_t)(d.TX * d.TY);
         pix_base += (uint64_t)w.width * w.height;
+        rb_base += CH * (uint32_t)((d.TY + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK);
     }
 }
 
@@ -249,10 +286,11 @@ clod_status clod_frame_workspace_size(int64_t n, const clod_view* views, int32_t
 {
     if (!bytes) return fail(CLOD_ERR_ARG, "bytes is NULL");
     if (n < 0 || n >= (1ll << 31)) return fail(CLOD_ERR_ARG, "n = %lld outside [0, 2^31)", (long long)n);
-    uint32_t TT = 0;
-    clod_status s = check_views(views, n_views, &TT);
+    ViewGeom G;
+    clod_status s = check_views(views, n_views, (uint64_t)n, &G);
     if (s) return s;
-    const FrameLayout L = frame_layout((uint64_t)n, (uint32_t)n_views, TT);
+    const uint32_t TT = G.TT;
+    const FrameLayout L = frame_layout((uint64_t)n, (uint32_t)n_views, TT, G.rb_total, G.max_tx);
     *bytes = L.total;
     if (layout) {
         layout->total_bytes = L.total;
@@ -278,11 +316,12 @@ clod_status clod_preprocess(const clod_scene* scene, const clod_view* views, int
 {
     clod_status s = check_scene(scene);
     if (s) return s;
-    uint32_t TT = 0;
-    if ((s = check_views(views, n_views, &TT))) return s;
+    ViewGeom G;
+    if ((s = check_views(views, n_views, (uint64_t)scene->n, &G))) return s;
+    const uint32_t TT = G.TT;
     if (!ws) return fail(CLOD_ERR_ARG, "ws is NULL");
     if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(CLOD_ERR_ARG, "ws must be 256-byte aligned");
-    const FrameLayout L = frame_layout((uint64_t)scene->n, (uint32_t)n_views, TT);
+    const FrameLayout L = frame_layout((uint64_t)scene->n, (uint32_t)n_views, TT, G.rb_total, G.max_tx);
     if (ws_bytes < L.total)
         return fail(CLOD_ERR_CAPACITY, "frame workspace needs %zu bytes, got %zu", L.total, ws_bytes);
     int n_sm = 0;
@@ -290,11 +329,14 @@ clod_status clod_preprocess(const clod_scene* scene, const clod_view* views, int
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const Frame F = frame_ptrs(ws, L);
     std::vector<ViewDev> table;
-    make_view_table(views, n_views, table);
+    make_view_table(views, n_views, (uint64_t)scene->n, table);
     FrameHeader h{};
     h.n = (uint64_t)scene->n;
     h.n_views = (uint32_t)n_views;
     h.total_tiles = TT;
+    h.n_chunks = L.n_chunks;
+    h.n_rs_blocks = L.n_rs_blocks;
+    h.max_tx = L.max_tx;
     cudaError_t e = cudaMemsetAsync(ws, 0, L.views, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(F.hdr, &h, sizeof(h), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
@@ -312,31 +354,19 @@ clod_status clod_preprocess(const clod_scene* scene, const clod_view* views, int
     return CLOD_OK;
 }
 
-clod_status clod_sort_workspace_size(uint64_t pair_capacity, size_t* bytes)
+clod_status clod_bin_sort(void* ws, uint64_t pair_capacity, uint64_t* keys_out, uint32_t* vals_out,
+                          uint32_t* ranges_out, clod_stream stream)
 {
-    if (!bytes) return fail(CLOD_ERR_ARG, "bytes is NULL");
+    if (!ws || !ranges_out) return fail(CLOD_ERR_ARG, "NULL argument to clod_bin_sort");
+    if (pair_capacity > 0 && !vals_out) return fail(CLOD_ERR_ARG, "vals_out is NULL");
     if (pair_capacity > 0xFFFFFFFFull) return fail(CLOD_ERR_ARG, "pair_capacity above 2^32 - 1");
-    *bytes = std::max<size_t>(256, (size_t)pair_capacity * 16);
-    return CLOD_OK;
-}
-
-clod_status clod_bin_sort(void* ws, uint64_t pair_capacity, void* sort_ws, size_t sort_ws_bytes, uint64_t* keys_out,
-                          uint32_t* vals_out, uint32_t* ranges_out, clod_stream stream)
-{
-    if (!ws || !sort_ws || !vals_out || !ranges_out) return fail(CLOD_ERR_ARG, "NULL argument to clod_bin_sort");
     FrameLayout L;
     if (!recall(ws, &L)) return fail(CLOD_ERR_ARG, "ws was not prepared by clod_preprocess");
-    size_t need = 0;
-    clod_status s = clod_sort_workspace_size(pair_capacity, &need);
-    if (s) return s;
-    if (sort_ws_bytes < need) return fail(CLOD_ERR_CAPACITY, "sort workspace needs %zu bytes, got %zu", need, sort_ws_bytes);
     int n_sm = 0;
-    if ((s = device_ready(&n_sm))) return s;
+    clod_status s = device_ready(&n_sm);
+    if (s) return s;
     const Frame F = frame_ptrs(ws, L);
-    unsigned long long* pairs = static_cast<unsigned long long*>(sort_ws);
-    unsigned long long* scratch = pairs + pair_capacity;
-    launch_bin_sort(F, (int64_t)L.n, L.n_views, L.total_tiles, pairs, scratch, pair_capacity, keys_out, vals_out,
-                    ranges_out, n_sm, static_cast<cudaStream_t>(stream));
+    launch_bin_sort(F, L, pair_capacity, keys_out, vals_out, ranges_out, static_cast<cudaStream_t>(stream));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "clod_bin_sort launch");
     return CLOD_OK;

@@ -19,15 +19,24 @@ constexpr int TILE = 16;
 constexpr int BLOCK_PIX = TILE * TILE;  // 256 threads per tile block
 constexpr int MAX_VIEWS = 64;
 
+// Depth-rank sort and emission geometry.
+constexpr int RS_THREADS = 256;
+constexpr int RS_ITEMS = 4096;          // keys per radix-sort block (16 per thread)
+constexpr int ROWS_PER_BLOCK = 8;       // tile rows per emission block (one warp each)
+constexpr int MAX_CHUNKS = 256;         // rank chunks per view
+constexpr int STAGE = 1024;             // rectangles staged in shared memory at a time
+
 // Frame header at offset 0 of a frame workspace.
 struct FrameHeader {
     uint64_t n;             // Gaussians
     uint32_t n_views;
     uint32_t total_tiles;
-    unsigned long long n_pairs;  // K, written by the tile scan
+    unsigned long long n_pairs;  // K = sum of tiles touched over survivors
     uint32_t status;        // STATUS_* bits
-    uint32_t big_count;     // tiles whose list is sorted by the large-segment kernel
-    uint32_t work[4];       // spare counters
+    uint32_t n_chunks;      // rank chunks per view
+    uint32_t n_rs_blocks;   // radix-sort blocks per view
+    uint32_t max_tx;        // widest view, in tiles
+    uint32_t work[4];       // scheduling counters
 };
 constexpr uint32_t STATUS_OVERFLOW = 1u;
 constexpr uint32_t STATUS_TIMEOUT = 2u;
@@ -44,13 +53,14 @@ struct ViewDev {
     uint32_t flags;
     uint32_t tile_base;     // global id of this view's first tile
     uint64_t pix_base;      // first pixel of this view in packed outputs
-    uint32_t pad[2];
+    uint32_t rb_base;       // first block of this view in the emission grids
+    uint32_t pad;
 };
 
 struct FrameLayout {
     size_t header, views, dmax_key, n_surv, rec0, rec1, rec2, depth, rect, tile_count, tile_offset,
-        cursor, big_list, total;
-    uint32_t total_tiles, n_views;
+        key0, val0, key1, val1, srect, rs_hist, cnt, total;
+    uint32_t total_tiles, n_views, n_chunks, n_rs_blocks, rb_total, max_tx;
     uint64_t n;
 };
 
@@ -67,8 +77,13 @@ struct Frame {
     uint2* rect;
     uint32_t* tile_count;
     uint32_t* tile_offset;
-    uint32_t* cursor;
-    uint32_t* big_list;
+    uint32_t* key0;         // depth-rank sort ping-pong: keys (depth bits) / values (index)
+    uint32_t* val0;
+    uint32_t* key1;
+    uint32_t* val1;
+    uint2* srect;           // tile rectangles in depth-rank order
+    uint32_t* rs_hist;      // radix-sort digit counts [view][256][block]
+    uint32_t* cnt;          // per (view, chunk, tile) pair counts, then offsets
 };
 
 // ---------------------------------------------------------------------------
@@ -216,7 +231,7 @@ __device__ __forceinline__ float blend_alpha(float dx, float dy, float nA, float
 }
 
 // Frame workspace layout (256-byte aligned arrays).
-FrameLayout frame_layout(uint64_t n, uint32_t n_views, uint32_t total_tiles);
+FrameLayout frame_layout(uint64_t n, uint32_t n_views, uint32_t total_tiles, uint32_t rb_total, uint32_t max_tx);
 Frame frame_ptrs(void* ws, const FrameLayout& L);
 
 }  // namespace clod

@@ -5,8 +5,9 @@
 //   k_preprocess attenuated opacity alpha'' (Eq. 2) and the mask
 //                M_i = alpha'' > tau s_v (Sec. 3.2); for survivors the EWA
 //                projection, conic, 3-sigma radius, tile rectangle, depth and
-//                SH colour (Sec. 3.1); per-tile pair counts.
-//   k_scan_tiles exclusive scan of the per-tile counts -> tile offsets and K.
+//                SH colour (Sec. 3.1); the depth key of every (view,
+//                Gaussian) for the depth-rank sort (all ones when culled)
+//                and K, the sum of the tiles touched.
 //
 // Layout: scene arrays are read structure-of-arrays, one Gaussian per thread,
 // consecutive Gaussians in consecutive threads (coalesced 12/16-byte rows);
@@ -80,13 +81,16 @@ __global__ void __launch_bounds__(256) k_preprocess(Frame F, clod_scene S, uint3
     __shared__ ViewDev sv[MAX_VIEWS];
     __shared__ float sdmax[MAX_VIEWS];
     __shared__ uint32_t cnt_mask[MAX_VIEWS], cnt_surv[MAX_VIEWS];
+    __shared__ unsigned long long s_pairs;
     load_views(sv, F.views, V);
     for (uint32_t v = threadIdx.x; v < V; v += blockDim.x) {
         sdmax[v] = decode_dmax(F.dmax_key[v]);
         cnt_mask[v] = 0;
         cnt_surv[v] = 0;
     }
+    if (threadIdx.x == 0) s_pairs = 0ull;
     __syncthreads();
+    unsigned long long my_pairs = 0ull;
     const int64_t n = S.n;
     const int deg = S.sh_degree;
     const int K = (deg + 1) * (deg + 1);
@@ -250,14 +254,16 @@ __global__ void __launch_bounds__(256) k_preprocess(Frame F, clod_scene S, uint3
                             rect = make_uint2(static_cast<uint32_t>(x0) | (static_cast<uint32_t>(y0) << 16),
                                               static_cast<uint32_t>(x1) | (static_cast<uint32_t>(y1) << 16));
                             surv = true;
-                            for (int ty = y0; ty < y1; ++ty)
-                                for (int tx_ = x0; tx_ < x1; ++tx_)
-                                    atomicAdd(&F.tile_count[W.tile_base + ty * W.TX + tx_], 1u);
+                            my_pairs += (unsigned long long)((x1 - x0) * (y1 - y0));
                         }
                     }
                 }
             }
-            if (active) F.rect[o] = rect;
+            if (active) {
+                F.rect[o] = rect;
+                F.key0[o] = surv ? __float_as_uint(F.depth[o]) : 0xFFFFFFFFu;
+                F.val0[o] = static_cast<uint32_t>(i);
+            }
             // per-view counts: warp-aggregated, then one shared atomic per warp
             const unsigned bm = __ballot_sync(0xffffffffu, M);
             const unsigned bs = __ballot_sync(0xffffffffu, surv);
@@ -267,54 +273,14 @@ __global__ void __launch_bounds__(256) k_preprocess(Frame F, clod_scene S, uint3
             }
         }
     }
+    for (int o = 16; o > 0; o >>= 1) my_pairs += __shfl_xor_sync(0xffffffffu, my_pairs, o);
+    if ((threadIdx.x & 31) == 0 && my_pairs) atomicAdd(&s_pairs, my_pairs);
     __syncthreads();
     for (uint32_t v = threadIdx.x; v < V; v += blockDim.x) {
         if (cnt_mask[v]) atomicAdd(&F.n_surv[2 * v], cnt_mask[v]);
         if (cnt_surv[v]) atomicAdd(&F.n_surv[2 * v + 1], cnt_surv[v]);
     }
-}
-
-// Exclusive scan of the per-tile counts by one block of 1024 threads:
-// contiguous chunks per thread, a block-wide scan of the chunk sums.
-__global__ void __launch_bounds__(1024) k_scan_tiles(Frame F, unsigned long long* n_pairs_out)
-{
-    __shared__ unsigned long long wsum[32];
-    const uint32_t TT = F.hdr->total_tiles;
-    const uint32_t per = (TT + blockDim.x - 1) / blockDim.x;
-    const uint32_t b0 = min(TT, threadIdx.x * per), b1 = min(TT, b0 + per);
-    unsigned long long s = 0;
-    for (uint32_t t = b0; t < b1; ++t) s += F.tile_count[t];
-    // block exclusive scan of s
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    unsigned long long x = s;
-    for (int o = 1; o < 32; o <<= 1) {
-        unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) wsum[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-        unsigned long long w = wsum[lane];
-        for (int o = 1; o < 32; o <<= 1) {
-            unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
-        }
-        wsum[lane] = w;
-    }
-    __syncthreads();
-    unsigned long long run = x - s + (wid ? wsum[wid - 1] : 0ull);
-    const unsigned long long total = wsum[31];
-    for (uint32_t t = b0; t < b1; ++t) {
-        F.tile_offset[t] = static_cast<uint32_t>(run);
-        F.cursor[t] = static_cast<uint32_t>(run);
-        run += F.tile_count[t];
-    }
-    if (threadIdx.x == 0) {
-        F.tile_offset[TT] = static_cast<uint32_t>(total);
-        F.hdr->n_pairs = total;
-        if (total > 0xFFFFFFFFull) atomicOr(&F.hdr->status, STATUS_OVERFLOW);
-        if (n_pairs_out) *n_pairs_out = total;
-    }
+    if (threadIdx.x == 0 && s_pairs) atomicAdd(&F.hdr->n_pairs, s_pairs);
 }
 
 void launch_preprocess(const Frame& F, const clod_scene& S, uint32_t V, uint8_t* mask_out, float* alpha_out,
@@ -325,7 +291,8 @@ void launch_preprocess(const Frame& F, const clod_scene& S, uint32_t V, uint8_t*
     if (blocks < 1) blocks = 1;
     if (n > 0) k_dist_max<<<blocks, 256, 0, st>>>(F, S.means, n, V);
     if (n > 0) k_preprocess<<<blocks, 256, 0, st>>>(F, S, V, mask_out, alpha_out);
-    k_scan_tiles<<<1, 1024, 0, st>>>(F, n_pairs_out);
+    if (n_pairs_out)
+        cudaMemcpyAsync(n_pairs_out, &F.hdr->n_pairs, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st);
 }
 
 }  // namespace clod
