@@ -210,6 +210,30 @@ clod_status clod_render_bwd(const clod_scene* scene, const void* ws, const uint3
 clod_status clod_l1_loss(const float* image, const float* target, int64_t count, float scale,
                          float* loss, float* dL_dimage, clod_stream stream);
 
+/* ------------------------------------------------------------------------ */
+/* Allocation-free forward render                                             */
+/* ------------------------------------------------------------------------ */
+
+/* One view rendered like clod_preprocess + clod_bin_sort + clod_render_fwd,
+ * without any device allocation, for callers that cannot call cudaMalloc
+ * (device memory owned by another framework's allocator, loops that must not
+ * allocate after start-up, plug-ins given only raw pointers).  The paper has
+ * no counterpart; it is an interface convenience.
+ * All scratch lives in one file-scope __device__ array of about 16 MB that
+ * every GPU loading the library holds until the process exits.  Limits:
+ * scene->n <= 65536, width and height <= 1024, at most 2^21 pairs; larger
+ * scenes or views are rejected with CLOD_ERR_ARG before any work, a frame
+ * with more pairs returns CLOD_ERR_CAPACITY (with the count) and writes no
+ * image.  image (3 x H x W), T_final (H x W, may be NULL), n_contrib (H x W,
+ * may be NULL) are caller device buffers.  The call waits for the frame on
+ * its stream before returning.  Calls share the array: calls whose work
+ * overlaps on the GPU race and must be serialised by the caller.  The first
+ * call on a device looks up the array's device address; make it before any
+ * stream capture. */
+clod_status clod_render_noalloc(const clod_scene* scene, const clod_view* view,
+                                float* image, float* T_final, uint32_t* n_contrib,
+                                clod_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,55 @@
+"""clod_render_noalloc: the forward render for callers that cannot allocate
+device memory (its scratch is a fixed array inside the library).  Checked
+through the C ABI against the allocating path (clod_preprocess /
+clod_bin_sort / clod_render_fwd), bit for bit, on two calls in a row: the
+second call must not see anything the first left in the shared array.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2510_09997_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+
+def test_noalloc_matches_allocating_path_two_calls():
+    from paper_2510_09997_gb300 import clod as C
+    C.require_cuda()
+    L = C.lib()
+    sc = S.tiny_scene(n=20000, seed=0, sh_degree=1)
+    ds = C.DeviceScene.from_scene(sc)
+    views = [S.tiny_view(1.0, bg=(0.1, 0.2, 0.3)),
+             S.look_at((2.0, 1.0, 1.5), (0, 0, 0), 200, 150, s_v=4.0, bg=(0.0, 0.0, 0.0))]
+    for v in views:
+        fr = C.render(ds, [v], want_keys=False)
+        img = torch.full((3, v.height, v.width), -1.0, device="cuda")
+        T = torch.full((v.height, v.width), -1.0, device="cuda")
+        nc = torch.full((v.height, v.width), -1, dtype=torch.int32, device="cuda")
+        cv = C.cview(v)
+        st = L.clod_render_noalloc(ctypes.byref(ds.c), ctypes.byref(cv), C._ptr(img), C._ptr(T), C._ptr(nc),
+                                   C._stream(None))
+        C.check("clod_render_noalloc", st)
+        torch.cuda.synchronize()
+        assert torch.equal(img, fr.view_image(0))
+        assert torch.equal(T, fr.view_T(0))
+        assert torch.equal(nc, fr.view_ncontrib(0))
+
+
+def test_noalloc_rejects_oversize():
+    from paper_2510_09997_gb300 import clod as C
+    C.require_cuda()
+    L = C.lib()
+    sc = S.tiny_scene(n=70000, seed=1)
+    ds = C.DeviceScene.from_scene(sc)
+    v = S.tiny_view(1.0)
+    img = torch.zeros((3, v.height, v.width), device="cuda")
+    cv = C.cview(v)
+    assert L.clod_render_noalloc(ctypes.byref(ds.c), ctypes.byref(cv), C._ptr(img), None, None, C._stream(None)) == 1
+    assert b"65536" in L.clod_last_error()
+    big = C.cview(v.replace(width=2048, height=64, cx=1024.0))
+    small = C.DeviceScene.from_scene(sc.subset(np.arange(100)))
+    assert L.clod_render_noalloc(ctypes.byref(small.c), ctypes.byref(big), C._ptr(img), None, None,
+                                 C._stream(None)) == 1
