@@ -96,6 +96,7 @@ class TrainStep:
             scales = [self.sample_scale() for _ in views]
         views = [v.replace(s_v=s) for v, s in zip(views, scales)]
         imgs, alpha, mask, counts = A.render(*self.model.activated(), views)
+        self.last = dict(images=imgs, alpha=alpha, views=views)
         N = self.model.n
         total = 0.0
         info = []
