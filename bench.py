@@ -31,11 +31,14 @@ N_CAMS = 64
 SCALES = (1.0, 2.0, 4.0, 8.0, 16.0)
 METRIC = "1080p frames/s at 1M Gaussians (forward, CLoD on)"
 WORKLOAD = "object scene 1M Gaussians SH3, 1920x1080, 64-camera orbit d=2..20, s_v in {1,2,4,8,16}"
-# FP32 operations of one evaluated (pixel, Gaussian) pair in the blend: offset 2,
-# quadratic form 7, exp_spec 21 (12 FMA, 2 add, compare/select, cap, scale),
-# clamp/product 2, skip test 1, transmittance 2, stop test 1, weight 1,
-# colour 6 (3 FMA).  A skipped pair does less; this counts the full evaluation.
-FLOP_PER_PAIR = 43
+# FP32 FLOPs of the blend's arithmetic (FMA = 2): every visited (pixel,
+# Gaussian) pair: offset 2 + quadratic form 7 = 9; a pair whose power lies in
+# [-5.6, 0]: + exp_spec 31 (13 FMA, 2 subtractions, cap) + opacity 2 = 33; a
+# contributing pair: + transmittance 2 + weight 1 + colour 6 = 9.
+FLOP_VISIT, FLOP_EXP, FLOP_CONTRIB = 9, 33, 9
+# kernels per frame: k_dist_max, k_preprocess; 4 x (k_rs_hist, k_rs_scan,
+# k_rs_scatter); k_chunk_count, k_chunk_scan, k_scan_tiles, k_rows<emit>; k_blend_fwd
+LAUNCHES_PER_FRAME = 19
 
 
 def frames_list():
@@ -48,7 +51,11 @@ def parse():
     p.add_argument("--steps", type=int, default=320)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--no-extras", action="store_true", help="skip the e2e/cpu_baseline legs")
+    p.add_argument("--no-extras", action="store_true", help="skip the e2e/cpu_baseline/train/serving legs")
+    p.add_argument("--no-train", action="store_true")
+    p.add_argument("--no-serve", action="store_true")
+    p.add_argument("--train-steps", type=int, default=10)
+    p.add_argument("--serve-seconds", type=float, default=2.0)
     return p.parse_args()
 
 
@@ -191,14 +198,16 @@ def run_ours(args):
     st_ms = stage.mean(0)
 
     # evaluated (pixel, Gaussian) pairs for the blend's FLOP count (untimed pass)
-    evals = torch.zeros(1, dtype=torch.int64, device="cuda")
+    evals = torch.zeros(3, dtype=torch.int64, device="cuda")
     for k in range(args.steps):
         R.set_views([views[k % len(views)]])
         C.clod_preprocess(ds, R.views, R.ws, n_pairs=R.npairs)
         C.clod_bin_sort(R.ws, R.cap, None, R.vals, R.ranges)
         C.clod_render_fwd(R.ws, R.vals, R.ranges, R.image, R.T, R.nc, evaluated=evals)
     torch.cuda.synchronize()
-    ev_per_frame = float(evals.item()) / args.steps
+    cnt3 = evals.cpu().numpy().astype(np.float64) / args.steps
+    ev_per_frame = float(cnt3[0])
+    flop_per_frame = FLOP_VISIT * cnt3[0] + FLOP_EXP * cnt3[1] + FLOP_CONTRIB * cnt3[2]
 
     frames_total = args.steps * world
     value = frames_total / elapsed
@@ -206,7 +215,7 @@ def run_ours(args):
     sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     n_sm = torch.cuda.get_device_properties(0).multi_processor_count
     fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12          # TFLOP/s at the sampled clock
-    blend_tflops = ev_per_frame * FLOP_PER_PAIR / (st_ms[2] / 1e3) / 1e12
+    blend_tflops = flop_per_frame / (st_ms[2] / 1e3) / 1e12
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "frames/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(elapsed * 1e3 / args.steps, 4), "higher_is_better": True,
@@ -218,14 +227,22 @@ def run_ours(args):
                      "blend": round(float(st_ms[2]), 4)},
         "roofline": {"bound": "alu", "kernel": "k_blend_fwd", "achieved": round(blend_tflops, 3),
                      "peak": round(fp32_peak, 2), "unit": "TFLOP/s", "frac": round(blend_tflops / fp32_peak, 4),
-                     "traffic": None, "flop_per_pair": FLOP_PER_PAIR, "evaluated_pairs_per_frame": ev_per_frame,
+                     "traffic": None, "flop_model": "9 per visited pair + 33 per exp + 9 per contributor",
+                     "pairs_per_frame": {"visited": round(cnt3[0]), "exp": round(cnt3[1]), "contrib": round(cnt3[2])},
                      "peak_basis": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (sampled clock)" % (n_sm, sm_mhz)},
-        "gpu_launches": 7 * args.steps,
+        "gpu_launches": LAUNCHES_PER_FRAME * args.steps,
         "clocks": clk,
     }
     if rank == 0 and not args.no_extras:
         out["e2e"] = e2e_leg(C, ds, R, views, args, stream)
         out["cpu_baseline"] = cpu_baseline(sc, views)
+        del R, ds
+        torch.cuda.empty_cache()
+        if not args.no_train:
+            out["train"] = train_leg(args)
+            torch.cuda.empty_cache()
+        if not args.no_serve:
+            out["serving"] = serve_leg(args)
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
@@ -282,6 +299,156 @@ def cpu_baseline(sc, views, budget_s=20.0):
     return {"value": round(1.0 / frame_s, 5), "unit": "frames/s", "cores": 1, "kind": "oracle",
             "sample": "camera 0, s_v=1: full Stage I + pairs + sort, blend of %d/%d random tiles scaled to the frame"
                       % (done, ntiles), "seconds": round((t1 - t0) + tsum, 2)}
+
+
+def train_leg(args):
+    """Differentiable training step: 3M Gaussians over a 10x10x4 box, 4 views
+    at 1920x1080 per step, s_v log-uniform on [1, 16], L1 + L_reg with
+    lambda = 1, forward + hand-written backward + Adam."""
+    import torch
+    from paper_2510_09997_gb300 import synth as S
+    from paper_2510_09997_gb300 import train as T
+    sc = S.outdoor_scene(3_000_000)
+    cams = S.orbit_cameras(16, WIDTH, HEIGHT, d_min=9.0, d_max=16.0, elev_deg=25.0, seed=2)
+    targets = [torch.tensor(S.target_image(HEIGHT, WIDTH, seed=k), device="cuda") for k in range(4)]
+    model = T.GaussianModel(sc)
+    step = T.TrainStep(model, s_max=16.0, lam_reg=1.0, seed=0, extent=5.0)
+
+    def batch(k):
+        return [cams[(4 * k + j) % len(cams)] for j in range(4)]
+
+    for k in range(3):
+        step.step(batch(k), targets)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    infos = []
+    loss = None
+    e0.record()
+    for k in range(args.train_steps):
+        loss, info = step.step(batch(k + 3), targets)
+        infos.append(info)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.train_steps
+    rendered = float(np.mean([i["rendered"] for inf in infos for i in inf]))
+    return {"metric": "fwd+bwd training steps/s at 3M Gaussians", "value": round(1e3 / ms, 3), "unit": "steps/s",
+            "ms_per_step": round(ms, 3), "steps": args.train_steps, "warmup": 3,
+            "workload": "outdoor scene 3M Gaussians SH3 (10x10x4 box), 4 views/step 1920x1080, "
+                        "s_v log-uniform [1,16], L1 + L_reg (lambda 1), Adam",
+            "mean_rendered_per_view": round(rendered, 1), "last_loss": round(float(loss), 6)}
+
+
+def serve_leg(args):
+    """Serving: resident 2M-Gaussian SH3 scene, Poisson arrivals (2000/s),
+    resolutions mixed among 512x512, 1280x720, 1920x1080, 3840x2160, random
+    poses at distances 1..50, s_v log-uniform [1, 32].  The continuous-batching
+    server and the plain path (one frame per launch sequence, arrival order,
+    one stream, read K back, sort, blend) replay the same trace and write the
+    same images.  Latency = completion - scheduled arrival."""
+    import torch
+    from paper_2510_09997_gb300 import clod as C
+    from paper_2510_09997_gb300 import serve as SV
+    from paper_2510_09997_gb300 import synth as S
+    sizes = [(512, 512), (1280, 720), (1920, 1080), (3840, 2160)]
+    sc = S.object_scene(2_000_000, seed=4)
+    ds = C.DeviceScene.from_scene(sc)
+    rate = 2000.0
+    n_req = int(rate * args.serve_seconds)
+    views = S.random_cameras(n_req, sizes, d_range=(1.0, 50.0), s_range=(1.0, 32.0), seed=4)
+    warm = S.random_cameras(32, sizes, d_range=(1.0, 50.0), s_range=(1.0, 32.0), seed=40)
+    arrivals = np.cumsum(np.random.default_rng(44).exponential(1.0 / rate, size=n_req))
+    ring = 32
+    bufs = {wh: [torch.empty((3, wh[1], wh[0]), device="cuda") for _ in range(ring)] for wh in sizes}
+    counters = {wh: 0 for wh in sizes}
+    slot_of = []
+    for v in views:
+        wh = (v.width, v.height)
+        slot_of.append((wh, counters[wh] % ring))
+        counters[wh] += 1
+
+    def buf(k, vs=None, so=None):
+        wh, i = (so or slot_of)[k]
+        return bufs[wh][i]
+
+    rend = {}
+
+    def plain_frame(v, out):
+        key = (v.width, v.height)
+        if key not in rend:
+            rend[key] = C.Renderer(ds, [v], pair_capacity=1 << 22)
+        R = rend[key]
+        R.set_views([v])
+        C.clod_preprocess(ds, R.views, R.ws, n_pairs=R.npairs)
+        K = int(R.npairs.item())
+        if K > R.cap:
+            R.cap = int(K * 1.25)
+            R.vals = torch.empty(R.cap, dtype=torch.int32, device="cuda")
+        C.clod_bin_sort(R.ws, R.cap, None, R.vals, R.ranges)
+        C.clod_render_fwd(R.ws, R.vals, R.ranges, out, None, None)
+        torch.cuda.current_stream().synchronize()
+
+    def run_plain():
+        for v in warm:
+            plain_frame(v, bufs[(v.width, v.height)][0])
+        t0 = time.monotonic()
+        lat = np.zeros(n_req)
+        done = 0.0
+        for k, v in enumerate(views):
+            now = time.monotonic() - t0
+            if now < arrivals[k]:
+                time.sleep(arrivals[k] - now)
+            plain_frame(v, buf(k))
+            done = time.monotonic() - t0
+            lat[k] = done - arrivals[k]
+        return lat, n_req / (done - arrivals[0])
+
+    def run_server(B=8, slots=3):
+        srv = SV.Server(ds, max_views_per_batch=B, n_slots=slots, use_graphs=True, pair_capacity=1 << 25,
+                        max_pixels_per_batch=3840 * 2160 * 2, max_width=3840, max_height=2160)
+        for v in warm:
+            srv.wait(srv.submit(v, bufs[(v.width, v.height)][0]), 60.0)
+        users = {}
+        tickets = [None] * n_req
+        lat = np.zeros(n_req)
+        bsz = []
+        t0 = time.monotonic()
+        t0_us = t0 * 1e6
+
+        def finish(j):
+            st = srv.wait(tickets[j], 120.0)
+            lat[j] = (st.done_us - t0_us) / 1e6 - arrivals[j]
+            bsz.append(st.batch_size)
+            tickets[j] = None
+            return st.done_us
+
+        last = t0_us
+        for k, v in enumerate(views):
+            now = time.monotonic() - t0
+            if now < arrivals[k]:
+                time.sleep(arrivals[k] - now)
+            key = slot_of[k]
+            j = users.get(key)
+            if j is not None and tickets[j] is not None:
+                last = max(last, finish(j))
+            users[key] = k
+            tickets[k] = srv.submit(v, buf(k))
+        for j in range(n_req):
+            if tickets[j] is not None:
+                last = max(last, finish(j))
+        srv.close()
+        return lat, n_req / ((last - t0_us) / 1e6 - arrivals[0]), float(np.mean(bsz))
+
+    lat_p, fps_p = run_plain()
+    torch.cuda.synchronize()
+    lat_s, fps_s, mean_b = run_server()
+    q = lambda a, p: round(float(np.percentile(a, p)) * 1e3, 3)
+    return {"workload": "object scene 2M Gaussians SH3 resident; %d requests, Poisson %g/s; 512^2/720p/1080p/4K "
+                        "mixed; d in [1,50]; s_v log-uniform [1,32]" % (n_req, rate),
+            "server": {"frames_per_s": round(fps_s, 2), "p50_ms": q(lat_s, 50), "p99_ms": q(lat_s, 99),
+                       "mean_batch": round(mean_b, 2), "max_views_per_batch": 8, "slots": 3, "graphs": True},
+            "plain": {"frames_per_s": round(fps_p, 2), "p50_ms": q(lat_p, 50), "p99_ms": q(lat_p, 99)},
+            "throughput_ratio": round(fps_s / fps_p, 3)}
 
 
 def run_reference(args):

@@ -170,8 +170,11 @@ clod_status clod_render_fwd(const void* ws, const uint32_t* vals, const uint32_t
  * (may be NULL) and CLOD_ERR_CAPACITY if a clod_bin_sort overflowed. */
 clod_status clod_frame_check(const void* ws, uint64_t pair_capacity, uint64_t* n_pairs, clod_stream stream);
 
-/* Same as clod_render_fwd, also accumulating into *evaluated (device u64) the
- * number of (pixel, Gaussian) pairs whose opacity was evaluated. */
+/* Same as clod_render_fwd (without the blend's per-warp skipping, which
+ * changes no output), also accumulating into evaluated[0..2] (device u64):
+ * the (pixel, Gaussian) pairs visited before the pixel stopped, those whose
+ * power fell in [-5.6, 0] (the exponential is evaluated), and those that
+ * contributed. */
 clod_status clod_render_fwd_count(const void* ws, const uint32_t* vals, const uint32_t* ranges,
                                   float* image, float* T_final, uint32_t* n_contrib,
                                   unsigned long long* evaluated, clod_stream stream);
@@ -209,6 +212,63 @@ clod_status clod_render_bwd(const clod_scene* scene, const void* ws, const uint3
  * dL_dimage = scale * sign(image - target) / count (may be NULL). */
 clod_status clod_l1_loss(const float* image, const float* target, int64_t count, float scale,
                          float* loss, float* dL_dimage, clod_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* Serving: continuous batching over a resident scene                         */
+/* ------------------------------------------------------------------------ */
+
+typedef struct clod_server clod_server;
+
+typedef struct clod_server_cfg {
+    int32_t max_views_per_batch;   /* views per launch, 1..64                        */
+    int32_t n_slots;               /* batches in flight at once, 1..16               */
+    int32_t queue_capacity;        /* pending requests before CLOD_ERR_QUEUE_FULL    */
+    int32_t use_graphs;            /* 1: every slot replays one captured CUDA graph  */
+    uint64_t max_pixels_per_batch; /* admission: sum of W*H in one batch; the slots'
+                                      workspaces are sized for it                   */
+    uint64_t pair_capacity;        /* (view, tile, Gaussian) pairs per slot          */
+    int32_t batch_window_us;       /* wait up to this long for a fuller batch (0: no) */
+    int32_t max_width, max_height; /* largest view accepted                          */
+    int32_t reserved;
+} clod_server_cfg;
+
+typedef struct clod_req_stats {
+    int32_t status;                /* CLOD_OK, or the request's error                */
+    int32_t batch_size;            /* views in the launch that rendered it           */
+    double submit_us, launch_us, done_us;  /* steady host clock, microseconds        */
+    uint32_t n_rendered;           /* Gaussians rendered in this view                */
+    uint32_t reserved;
+    uint64_t n_pairs;              /* pairs of its launch                            */
+} clod_req_stats;
+
+/* Creates a server over a scene that stays resident (the scene arrays must
+ * outlive the server).  Allocates n_slots workspaces sized for the largest
+ * batch and starts a worker thread.  Requests are admitted in arrival order
+ * into batches of at most max_views_per_batch views and max_pixels_per_batch
+ * pixels as slots free up; batches on different slots run concurrently on
+ * their own streams.  A batch renders every view with one launch sequence
+ * (the scene is read once per batch).  A batch whose pairs exceed
+ * pair_capacity is re-run one request at a time with buffers sized from its
+ * pair count. */
+clod_status clod_server_create(const clod_scene* scene, const clod_server_cfg* cfg, clod_server** out);
+
+/* Queues one render of *view into image_out (device, 3 x H x W, caller-owned,
+ * must stay valid until the request is done).  Returns a ticket.
+ * CLOD_ERR_QUEUE_FULL when queue_capacity requests are pending; CLOD_ERR_ARG
+ * for views larger than the server's maximum. */
+clod_status clod_serve_submit(clod_server* server, const clod_view* view, float* image_out, uint64_t* ticket);
+
+/* Non-blocking: *done = 1 and stats filled when the request has finished
+ * (its image is then complete in device memory), after which the ticket is
+ * released; otherwise *done = 0 and CLOD_ERR_NOT_READY. */
+clod_status clod_serve_poll(clod_server* server, uint64_t ticket, int32_t* done, clod_req_stats* stats);
+
+/* Blocks up to timeout_us for the request; CLOD_ERR_TIMEOUT if it has not
+ * finished by then (the ticket stays valid). */
+clod_status clod_serve_wait(clod_server* server, uint64_t ticket, int64_t timeout_us, clod_req_stats* stats);
+
+/* Stops the worker after the batches in flight, frees the server. */
+clod_status clod_server_destroy(clod_server* server);
 
 /* ------------------------------------------------------------------------ */
 /* Allocation-free forward render                                             */

@@ -45,7 +45,8 @@ class clod_server_cfg(ctypes.Structure):
     _fields_ = [("max_views_per_batch", ctypes.c_int32), ("n_slots", ctypes.c_int32),
                 ("queue_capacity", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
                 ("max_pixels_per_batch", ctypes.c_uint64), ("pair_capacity", ctypes.c_uint64),
-                ("batch_window_us", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("batch_window_us", ctypes.c_int32), ("max_width", ctypes.c_int32),
+                ("max_height", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class clod_req_stats(ctypes.Structure):

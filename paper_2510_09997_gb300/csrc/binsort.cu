@@ -57,11 +57,13 @@ __device__ __forceinline__ void rs_warp_counts(const uint32_t* __restrict__ keys
     }
 }
 
-__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint32_t* __restrict__ keys, int64_t n, int nb, int shift,
+__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const FrameHeader* __restrict__ hdr,
+                                                        const uint32_t* __restrict__ keys, int64_t n, int nb, int shift,
                                                         uint32_t* __restrict__ hist)
 {
     __shared__ uint32_t h[RS_THREADS / 32][256];
     const int b = blockIdx.x, v = b / nb, lb = b % nb;
+    if ((uint32_t)v >= hdr->n_views) return;
     const int64_t base = (int64_t)v * n + (int64_t)lb * RS_ITEMS;
     const int cnt = (int)min((int64_t)RS_ITEMS, n - (int64_t)lb * RS_ITEMS);
     rs_warp_counts(keys, base, cnt, shift, h);
@@ -71,44 +73,54 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint32_t* __restri
     hist[((size_t)v * 256 + threadIdx.x) * nb + lb] = s;
 }
 
-// Exclusive scan of one view's 256 * nb counts (digit-major) by one block.
-__global__ void __launch_bounds__(1024) k_rs_scan(uint32_t* __restrict__ hist, int nb)
+// Exclusive scan of one view's 256 * nb counts (digit-major) by one block:
+// one warp per digit scans that digit's block counts, then the 256 digit
+// totals are scanned and added back.
+__global__ void __launch_bounds__(1024) k_rs_scan(const FrameHeader* __restrict__ hdr, uint32_t* __restrict__ hist, int nb)
 {
-    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t tot[256];
+    __shared__ uint32_t dbase[256];
+    if (blockIdx.x >= hdr->n_views) return;
     uint32_t* h = hist + (size_t)blockIdx.x * 256 * nb;
-    const int total = 256 * nb;
-    const int per = (total + blockDim.x - 1) / blockDim.x;
-    const int b0 = min(total, (int)threadIdx.x * per), b1 = min(total, b0 + per);
-    uint32_t s = 0;
-    for (int k = b0; k < b1; ++k) s += h[k];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    uint32_t x = s;
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int d = wid; d < 256; d += nw) {
+        uint32_t* hd = h + (size_t)d * nb;
+        uint32_t carry = 0;
+        for (int k0 = 0; k0 < nb; k0 += 32) {
+            const int k = k0 + lane;
+            const uint32_t c = k < nb ? hd[k] : 0u;
+            uint32_t x = c;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (k < nb) hd[k] = carry + x - c;
+            carry += __shfl_sync(0xffffffffu, x, 31);
+        }
+        if (lane == 0) tot[d] = carry;
     }
-    if (lane == 31) wsum[wid] = x;
     __syncthreads();
     if (wid == 0) {
-        uint32_t w = wsum[lane];
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
+        uint32_t run = 0;
+        for (int d0 = 0; d0 < 256; d0 += 32) {
+            const uint32_t c = tot[d0 + lane];
+            uint32_t x = c;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            dbase[d0 + lane] = run + x - c;
+            run += __shfl_sync(0xffffffffu, x, 31);
         }
-        wsum[lane] = w;
     }
     __syncthreads();
-    uint32_t run = x - s + (wid ? wsum[wid - 1] : 0u);
-    for (int k = b0; k < b1; ++k) {
-        const uint32_t c = h[k];
-        h[k] = run;
-        run += c;
-    }
+    for (int k = threadIdx.x; k < 256 * nb; k += blockDim.x) h[k] += dbase[k / nb];
 }
 
 // Stable scatter of one digit pass; on the last pass also gathers the tile
 // rectangle of every survivor into rank order.
-__global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+__global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const FrameHeader* __restrict__ hdr,
+                                                           const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                            uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                            int64_t n, int nb, int shift, const uint32_t* __restrict__ hist,
                                                            const uint2* __restrict__ rect, uint2* __restrict__ srect)
@@ -116,6 +128,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t* __res
     __shared__ uint32_t h[RS_THREADS / 32][256];
     __shared__ uint32_t wb[RS_THREADS / 32][256];
     const int b = blockIdx.x, v = b / nb, lb = b % nb;
+    if ((uint32_t)v >= hdr->n_views) return;
     const int64_t vbase = (int64_t)v * n;
     const int64_t base = vbase + (int64_t)lb * RS_ITEMS;
     const int cnt = (int)min((int64_t)RS_ITEMS, n - (int64_t)lb * RS_ITEMS);
@@ -163,6 +176,15 @@ __device__ __forceinline__ int find_view_rb(const ViewDev* views, uint32_t V, ui
     return v;
 }
 
+// Walk of one warp over the chunk's rectangles for one tile row, in rank
+// order.  A group of 32 consecutive ranks is handled at once: the spans
+// [x0, x1) of the members that cover the row are laid end to end (prefix sum
+// of their widths) and processed 32 slots at a time; slots that fall on the
+// same tile are ordered by __match_any_sync, lower slot = lower rank.
+//   EMIT = false: ctr[x] counts the chunk's pairs of tile x.
+//   EMIT = true:  ctr[x] starts at the tile's offset plus the chunk's offset
+//                 and every slot writes its Gaussian at ctr[x] + (rank among
+//                 the slots of the same tile).
 template <bool EMIT>
 __global__ void __launch_bounds__(ROWS_PER_BLOCK * 32) k_rows(Frame F, uint32_t* __restrict__ vals,
                                                              unsigned long long* __restrict__ keys)
@@ -171,17 +193,23 @@ __global__ void __launch_bounds__(ROWS_PER_BLOCK * 32) k_rows(Frame F, uint32_t*
     __shared__ uint2 s_rect[STAGE];
     __shared__ uint32_t s_id[STAGE];
     __shared__ uint32_t s_key[STAGE];
+    __shared__ uint32_t s_st[ROWS_PER_BLOCK][33];
+    __shared__ uint32_t s_x0[ROWS_PER_BLOCK][32];
+    __shared__ uint32_t s_gi[ROWS_PER_BLOCK][32];
     const FrameHeader* hdr = F.hdr;
     if (EMIT && (hdr->status & STATUS_OVERFLOW)) return;
     const uint32_t V = hdr->n_views;
     const uint32_t CH = hdr->n_chunks;
     const int64_t n = (int64_t)hdr->n;
+    if (blockIdx.x >= hdr->rb_total) return;
     const int v = find_view_rb(F.views, V, blockIdx.x);
     const ViewDev& W = F.views[v];
     const uint32_t rbn = (uint32_t)(W.TY + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK;
     const uint32_t local = blockIdx.x - W.rb_base;
+    if (local >= CH * rbn) return;
     const uint32_t c = local / rbn, rb = local % rbn;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t lt = lanemask_lt();
     const int row = (int)rb * ROWS_PER_BLOCK + w;
     const bool row_ok = row < W.TY;
     const int TX = W.TX;
@@ -212,28 +240,98 @@ __global__ void __launch_bounds__(ROWS_PER_BLOCK * 32) k_rows(Frame F, uint32_t*
             uint2 rc = make_uint2(0u, 0u);
             if (g < m) rc = s_rect[g];
             const int y0 = (int)(rc.x >> 16), y1 = (int)(rc.y >> 16);
-            unsigned hit = __ballot_sync(0xffffffffu, g < m && row >= y0 && row < y1);
-            while (hit) {
-                const int bsrc = __ffs(hit) - 1;
-                hit &= hit - 1;
-                const uint32_t rx0 = __shfl_sync(0xffffffffu, rc.x, bsrc), rx1 = __shfl_sync(0xffffffffu, rc.y, bsrc);
-                const int x0 = (int)(rx0 & 0xFFFFu), x1 = (int)(rx1 & 0xFFFFu);
-                for (int x = x0 + lane; x < x1; x += 32) {
-                    const uint32_t p = ctr[x];
-                    ctr[x] = p + 1u;
+            const bool hit = g < m && row >= y0 && row < y1;
+            const uint32_t x0 = rc.x & 0xFFFFu;
+            const uint32_t wdt = hit ? (rc.y & 0xFFFFu) - x0 : 0u;
+            uint32_t end = wdt;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, end, o);
+                if (lane >= o) end += y;
+            }
+            const uint32_t total = __shfl_sync(0xffffffffu, end, 31);
+            if (total == 0) continue;
+            s_st[w][lane] = end - wdt;
+            s_x0[w][lane] = x0;
+            s_gi[w][lane] = (uint32_t)g;
+            __syncwarp();
+            for (uint32_t q0 = 0; q0 < total; q0 += 32) {
+                const uint32_t q = q0 + lane;
+                const bool valid = q < total;
+                int o = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1)
+                    if (s_st[w][o + step] <= q) o += step;
+                const uint32_t x = valid ? s_x0[w][o] + (q - s_st[w][o]) : 0xFFFFFFFFu;
+                const uint32_t peers = __match_any_sync(0xffffffffu, x);
+                if (valid) {
+                    const uint32_t p = ctr[x] + __popc(peers & lt);
                     if (EMIT) {
-                        vals[p] = s_id[g0 + bsrc];
+                        const uint32_t gi = s_gi[w][o];
+                        vals[p] = s_id[gi];
                         if (keys)
-                            keys[p] = ((unsigned long long)(W.tile_base + (uint32_t)(row * TX + x)) << 32) |
-                                      s_key[g0 + bsrc];
+                            keys[p] = ((unsigned long long)(W.tile_base + (uint32_t)row * TX + x) << 32) | s_key[gi];
                     }
                 }
+                __syncwarp();
+                if (valid && (__ffs(peers) - 1) == lane) ctr[x] += __popc(peers);
                 __syncwarp();
             }
         }
     }
     if (!EMIT && row_ok)
         for (int x = lane; x < TX; x += 32) cnt_row[x] = ctr[x];
+}
+
+// 2'. per (view, chunk): the chunk's pair count of every tile from a 2D
+// difference array in shared memory -- each rectangle [x0,x1)x[y0,y1) adds
+// +1 at (x0,y0), (x1,y1) and -1 at (x1,y0), (x0,y1) -- and a 2D prefix sum.
+// Used when the (TX+1)(TY+1) grid fits in shared memory.
+__global__ void __launch_bounds__(512) k_chunk_count(Frame F)
+{
+    extern __shared__ uint32_t g[];
+    const FrameHeader* hdr = F.hdr;
+    const uint32_t CH = hdr->n_chunks;
+    const int64_t n = (int64_t)hdr->n;
+    const int v = (int)(blockIdx.x / CH);
+    const uint32_t c = blockIdx.x % CH;
+    if ((uint32_t)v >= hdr->n_views) return;
+    const ViewDev& W = F.views[v];
+    const int TX = W.TX, TY = W.TY, GX = TX + 1;
+    const int G = GX * (TY + 1);
+    for (int k = threadIdx.x; k < G; k += blockDim.x) g[k] = 0u;
+    __syncthreads();
+    const uint32_t Ns = F.n_surv[2 * v + 1];
+    const uint32_t C = (Ns + CH - 1) / CH;
+    const uint32_t r0 = min(Ns, c * C), r1 = min(Ns, r0 + C);
+    const uint2* sr = F.srect + (int64_t)v * n;
+    for (uint32_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+        const uint2 rc = sr[r];
+        const int x0 = (int)(rc.x & 0xFFFFu), y0 = (int)(rc.x >> 16), x1 = (int)(rc.y & 0xFFFFu), y1 = (int)(rc.y >> 16);
+        atomicAdd_block(&g[y0 * GX + x0], 1u);
+        atomicAdd_block(&g[y0 * GX + x1], 0xFFFFFFFFu);
+        atomicAdd_block(&g[y1 * GX + x0], 0xFFFFFFFFu);
+        atomicAdd_block(&g[y1 * GX + x1], 1u);
+    }
+    __syncthreads();
+    for (int y = threadIdx.x; y < TY; y += blockDim.x) {
+        uint32_t run = 0;
+        for (int x = 0; x < TX; ++x) {
+            run += g[y * GX + x];
+            g[y * GX + x] = run;
+        }
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < TX; x += blockDim.x) {
+        uint32_t run = 0;
+        for (int y = 0; y < TY; ++y) {
+            run += g[y * GX + x];
+            g[y * GX + x] = run;
+        }
+    }
+    __syncthreads();
+    const uint32_t T = (uint32_t)(TX * TY);
+    uint32_t* out = F.cnt + (size_t)CH * W.tile_base + (size_t)c * T;
+    for (uint32_t t = threadIdx.x; t < T; t += blockDim.x) out[t] = g[(t / TX) * GX + (t % TX)];
 }
 
 // 3a. per tile: exclusive scan of the chunk counts; tile_count = total.
@@ -251,7 +349,19 @@ __global__ void __launch_bounds__(256) k_chunk_scan(Frame F)
     const uint32_t T = (uint32_t)(W.TX * W.TY);
     uint32_t* col = F.cnt + (size_t)CH * W.tile_base + (t - W.tile_base);
     uint32_t acc = 0;
-    for (uint32_t c = 0; c < CH; ++c) {
+    constexpr int B = 8;
+    uint32_t c = 0;
+    for (; c + B <= CH; c += B) {
+        uint32_t x[B];
+#pragma unroll
+        for (int k = 0; k < B; ++k) x[k] = col[(size_t)(c + k) * T];
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+            col[(size_t)(c + k) * T] = acc;
+            acc += x[k];
+        }
+    }
+    for (; c < CH; ++c) {
         const uint32_t x = col[(size_t)c * T];
         col[(size_t)c * T] = acc;
         acc += x;
@@ -301,7 +411,7 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Frame F, uint32_t* __restri
     }
 }
 
-static int g_rows_smem_max = 0;
+constexpr size_t DIFF_SMEM_MAX = 200 * 1024;   // difference grid limit (a 4K view needs 131 KB)
 
 void launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long long cap, uint64_t* keys, uint32_t* vals,
                      uint32_t* ranges, cudaStream_t st)
@@ -312,16 +422,19 @@ void launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long long ca
     if (n > 0) {
         uint32_t *ki = F.key0, *vi = F.val0, *ko = F.key1, *vo = F.val1;
         for (int pass = 0; pass < 4; ++pass) {
-            k_rs_hist<<<V * nb, RS_THREADS, 0, st>>>(ki, n, nb, 8 * pass, F.rs_hist);
-            k_rs_scan<<<V, 1024, 0, st>>>(F.rs_hist, nb);
-            k_rs_scatter<<<V * nb, RS_THREADS, 0, st>>>(ki, vi, ko, vo, n, nb, 8 * pass, F.rs_hist, F.rect,
+            k_rs_hist<<<V * nb, RS_THREADS, 0, st>>>(F.hdr, ki, n, nb, 8 * pass, F.rs_hist);
+            k_rs_scan<<<V, 1024, 0, st>>>(F.hdr, F.rs_hist, nb);
+            k_rs_scatter<<<V * nb, RS_THREADS, 0, st>>>(F.hdr, ki, vi, ko, vo, n, nb, 8 * pass, F.rs_hist, F.rect,
                                                         pass == 3 ? F.srect : nullptr);
             std::swap(ki, ko);
             std::swap(vi, vo);
         }
     }
     const size_t smem = (size_t)ROWS_PER_BLOCK * L.max_tx * sizeof(uint32_t);
-    k_rows<false><<<L.rb_total, ROWS_PER_BLOCK * 32, smem, st>>>(F, nullptr, nullptr);
+    if (L.diff_grid_max * sizeof(uint32_t) <= DIFF_SMEM_MAX)
+        k_chunk_count<<<V * L.n_chunks, 512, L.diff_grid_max * sizeof(uint32_t), st>>>(F);
+    else
+        k_rows<false><<<L.rb_total, ROWS_PER_BLOCK * 32, smem, st>>>(F, nullptr, nullptr);
     k_chunk_scan<<<(L.total_tiles + 255) / 256, 256, 0, st>>>(F);
     k_scan_tiles<<<1, 1024, 0, st>>>(F, ranges, cap);
     k_rows<true><<<L.rb_total, ROWS_PER_BLOCK * 32, smem, st>>>(F, vals, reinterpret_cast<unsigned long long*>(keys));
@@ -332,6 +445,7 @@ cudaError_t bin_sort_setup()
     const int bytes = ROWS_PER_BLOCK * 1024 * (int)sizeof(uint32_t);
     cudaError_t e = cudaFuncSetAttribute(k_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_chunk_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DIFF_SMEM_MAX);
     return e;
 }
 

@@ -55,9 +55,11 @@ static uint32_t n_chunks_for(uint64_t n)
     return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(c, MAX_CHUNKS));
 }
 
-FrameLayout frame_layout(uint64_t n, uint32_t V, uint32_t TT, uint32_t rb_total, uint32_t max_tx)
+FrameLayout frame_layout(uint64_t n, uint32_t V, uint32_t TT, uint32_t rb_total, uint32_t max_tx,
+                         size_t diff_grid_max)
 {
     FrameLayout L{};
+    L.diff_grid_max = diff_grid_max;
     L.n_chunks = n_chunks_for(n);
     L.n_rs_blocks = (uint32_t)((n + RS_ITEMS - 1) / RS_ITEMS);
     L.rb_total = rb_total;
@@ -155,6 +157,7 @@ clod_status device_ready(int* n_sm)
 
 struct ViewGeom {
     uint32_t TT, rb_total, max_tx;
+    size_t diff_max;
 };
 
 static clod_status check_views(const clod_view* views, int32_t V, uint64_t n, ViewGeom* G)
@@ -177,11 +180,14 @@ static clod_status check_views(const clod_view* views, int32_t V, uint64_t n, Vi
     const uint32_t CH = n_chunks_for(n);
     uint64_t rb = 0;
     uint32_t mtx = 1;
+    size_t dmx = 0;
     for (int v = 0; v < V; ++v) {
         const int TX = (views[v].width + TILE - 1) / TILE, TY = (views[v].height + TILE - 1) / TILE;
         rb += (uint64_t)CH * ((TY + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK);
         mtx = std::max<uint32_t>(mtx, (uint32_t)TX);
+        dmx = std::max<size_t>(dmx, (size_t)(TX + 1) * (TY + 1));
     }
+    G->diff_max = dmx;
     if (rb > 0x7FFFFFFFull) return fail(CLOD_ERR_ARG, "frame too large");
     G->rb_total = (uint32_t)rb;
     G->max_tx = mtx;
@@ -290,7 +296,7 @@ clod_status clod_frame_workspace_size(int64_t n, const clod_view* views, int32_t
     clod_status s = check_views(views, n_views, (uint64_t)n, &G);
     if (s) return s;
     const uint32_t TT = G.TT;
-    const FrameLayout L = frame_layout((uint64_t)n, (uint32_t)n_views, TT, G.rb_total, G.max_tx);
+    const FrameLayout L = frame_layout((uint64_t)n, (uint32_t)n_views, TT, G.rb_total, G.max_tx, G.diff_max);
     *bytes = L.total;
     if (layout) {
         layout->total_bytes = L.total;
@@ -321,7 +327,7 @@ clod_status clod_preprocess(const clod_scene* scene, const clod_view* views, int
     const uint32_t TT = G.TT;
     if (!ws) return fail(CLOD_ERR_ARG, "ws is NULL");
     if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(CLOD_ERR_ARG, "ws must be 256-byte aligned");
-    const FrameLayout L = frame_layout((uint64_t)scene->n, (uint32_t)n_views, TT, G.rb_total, G.max_tx);
+    const FrameLayout L = frame_layout((uint64_t)scene->n, (uint32_t)n_views, TT, G.rb_total, G.max_tx, G.diff_max);
     if (ws_bytes < L.total)
         return fail(CLOD_ERR_CAPACITY, "frame workspace needs %zu bytes, got %zu", L.total, ws_bytes);
     int n_sm = 0;
@@ -337,6 +343,7 @@ clod_status clod_preprocess(const clod_scene* scene, const clod_view* views, int
     h.n_chunks = L.n_chunks;
     h.n_rs_blocks = L.n_rs_blocks;
     h.max_tx = L.max_tx;
+    h.rb_total = L.rb_total;
     cudaError_t e = cudaMemsetAsync(ws, 0, L.views, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(F.hdr, &h, sizeof(h), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)

@@ -36,6 +36,7 @@ struct FrameHeader {
     uint32_t n_chunks;      // rank chunks per view
     uint32_t n_rs_blocks;   // radix-sort blocks per view
     uint32_t max_tx;        // widest view, in tiles
+    uint32_t rb_total;      // blocks of the emission grids in use
     uint32_t work[4];       // scheduling counters
 };
 constexpr uint32_t STATUS_OVERFLOW = 1u;
@@ -55,6 +56,9 @@ struct ViewDev {
     uint64_t pix_base;      // first pixel of this view in packed outputs
     uint32_t rb_base;       // first block of this view in the emission grids
     uint32_t pad;
+    float* out_img;         // optional per-view outputs (else packed at pix_base)
+    float* out_T;
+    uint32_t* out_nc;
 };
 
 struct FrameLayout {
@@ -62,6 +66,7 @@ struct FrameLayout {
         key0, val0, key1, val1, srect, rs_hist, cnt, total;
     uint32_t total_tiles, n_views, n_chunks, n_rs_blocks, rb_total, max_tx;
     uint64_t n;
+    size_t diff_grid_max;   // max over views of (TX + 1) (TY + 1)
 };
 
 // Pointers into a frame workspace.
@@ -231,7 +236,8 @@ __device__ __forceinline__ float blend_alpha(float dx, float dy, float nA, float
 }
 
 // Frame workspace layout (256-byte aligned arrays).
-FrameLayout frame_layout(uint64_t n, uint32_t n_views, uint32_t total_tiles, uint32_t rb_total, uint32_t max_tx);
+FrameLayout frame_layout(uint64_t n, uint32_t n_views, uint32_t total_tiles, uint32_t rb_total, uint32_t max_tx,
+                         size_t diff_grid_max);
 Frame frame_ptrs(void* ws, const FrameLayout& L);
 
 }  // namespace clod

@@ -98,7 +98,7 @@ extern "C" clod_status clod_render_noalloc(const clod_scene* scene, const clod_v
     const int TX = (w.width + TILE - 1) / TILE, TY = (w.height + TILE - 1) / TILE;
     const uint32_t CH = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((n + 1023) / 1024, MAX_CHUNKS));
     const uint32_t rb_total = CH * (uint32_t)((TY + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK);
-    const FrameLayout L = frame_layout(n, 1, (uint32_t)(TX * TY), rb_total, (uint32_t)TX);
+    const FrameLayout L = frame_layout(n, 1, (uint32_t)(TX * TY), rb_total, (uint32_t)TX, (size_t)(TX + 1) * (TY + 1));
     if (L.total > NA_FRAME_BYTES) return fail(CLOD_ERR_CAPACITY, "frame needs %zu bytes of scratch, %zu available",
                                               L.total, NA_FRAME_BYTES);
     char* b = static_cast<char*>(base);
@@ -135,6 +135,7 @@ extern "C" clod_status clod_render_noalloc(const clod_scene* scene, const clod_v
     h.n_chunks = L.n_chunks;
     h.n_rs_blocks = L.n_rs_blocks;
     h.max_tx = L.max_tx;
+    h.rb_total = L.rb_total;
 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // the array keeps the previous call's contents: clear what accumulates

@@ -39,9 +39,9 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long x)
 // Pass A.  Key = (bits(d) << 32) | (0xFFFFFFFF - i): the max key carries the
 // max distance (d >= 0, so its bits order like the value) and, among equal
 // distances, the lowest index.  0 means "no Gaussian in the frustum".
-__global__ void __launch_bounds__(256) k_dist_max(Frame F, const float* __restrict__ means, int64_t n,
-                                                  uint32_t V)
+__global__ void __launch_bounds__(256) k_dist_max(Frame F, const float* __restrict__ means, int64_t n)
 {
+    const uint32_t V = F.hdr->n_views;
     __shared__ ViewDev sv[MAX_VIEWS];
     __shared__ unsigned long long wmax[8];
     load_views(sv, F.views, V);
@@ -75,9 +75,10 @@ __global__ void __launch_bounds__(256) k_dist_max(Frame F, const float* __restri
 }
 
 // Pass B.
-__global__ void __launch_bounds__(256) k_preprocess(Frame F, clod_scene S, uint32_t V, uint8_t* __restrict__ mask_out,
+__global__ void __launch_bounds__(256) k_preprocess(Frame F, clod_scene S, uint8_t* __restrict__ mask_out,
                                                     float* __restrict__ alpha_out)
 {
+    const uint32_t V = F.hdr->n_views;
     __shared__ ViewDev sv[MAX_VIEWS];
     __shared__ float sdmax[MAX_VIEWS];
     __shared__ uint32_t cnt_mask[MAX_VIEWS], cnt_surv[MAX_VIEWS];
@@ -289,8 +290,9 @@ void launch_preprocess(const Frame& F, const clod_scene& S, uint32_t V, uint8_t*
     const int64_t n = S.n;
     int blocks = static_cast<int>(std::min<int64_t>((n + 255) / 256, (int64_t)n_sm * 8));
     if (blocks < 1) blocks = 1;
-    if (n > 0) k_dist_max<<<blocks, 256, 0, st>>>(F, S.means, n, V);
-    if (n > 0) k_preprocess<<<blocks, 256, 0, st>>>(F, S, V, mask_out, alpha_out);
+    (void)V;
+    if (n > 0) k_dist_max<<<blocks, 256, 0, st>>>(F, S.means, n);
+    if (n > 0) k_preprocess<<<blocks, 256, 0, st>>>(F, S, mask_out, alpha_out);
     if (n_pairs_out)
         cudaMemcpyAsync(n_pairs_out, &F.hdr->n_pairs, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st);
 }

@@ -1,0 +1,492 @@
+// server.cu -- continuous-batching render server over a resident scene.
+//
+// Requests (a view and a caller device buffer for its image) enter a queue.
+// A worker thread admits them, in arrival order, into batches of at most
+// max_views_per_batch views and max_pixels_per_batch pixels, and launches each
+// batch on a free slot: every slot owns a stream, a frame workspace sized for
+// the largest admissible batch, a pair buffer and pinned staging for the view
+// table and the status read-back.  Batches on different slots overlap on the
+// device; requests that arrive while batches run are admitted as soon as a
+// slot frees.  One batch is one launch sequence over all its views: the
+// scene is read once for the batch (preprocessing loops over the views), the
+// sort and the blend run over every view's tiles in one grid each, and the
+// blend writes straight into each request's buffer.
+//
+// With use_graphs, each slot captures its launch sequence once, sized for the
+// largest batch; the kernels take the batch's actual sizes from the frame
+// header uploaded by the graph's first node, so the one graph replays for
+// every batch shape.  A batch whose pairs exceed the slot's capacity is
+// split: its requests are re-run alone, and a request that still does not
+// fit is rendered through a buffer sized from its pair count.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "clod_internal.cuh"
+
+namespace clod {
+
+void launch_preprocess(const Frame& F, const clod_scene& S, uint32_t V, uint8_t* mask_out, float* alpha_out,
+                       unsigned long long* n_pairs_out, int n_sm, cudaStream_t st);
+void launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long long cap, uint64_t* keys, uint32_t* vals,
+                     uint32_t* ranges, cudaStream_t st);
+void launch_blend_fwd(const Frame& F, const uint32_t* vals, const uint32_t* ranges, float* image, float* Tout,
+                      uint32_t* ncout, unsigned long long* evaluated, int n_sm, cudaStream_t st);
+clod_status fail(clod_status s, const char* fmt, ...);
+clod_status cuda_fail(cudaError_t e, const char* what);
+clod_status device_ready(int* n_sm);
+
+static double now_us()
+{
+    using namespace std::chrono;
+    return duration<double, std::micro>(steady_clock::now().time_since_epoch()).count();
+}
+
+static uint32_t chunks_for(uint64_t n)
+{
+    return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((n + 1023) / 1024, MAX_CHUNKS));
+}
+
+struct Request {
+    clod_view view;
+    float* out = nullptr;
+    double t_submit = 0, t_launch = 0, t_done = 0;
+    int32_t status = CLOD_OK;
+    int32_t batch = 0;
+    uint32_t rendered = 0;
+    uint64_t pairs = 0;
+    bool done = false;
+    bool solo = false;
+};
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev = nullptr;
+    void* ws = nullptr;
+    FrameLayout L{};
+    uint32_t* vals = nullptr;
+    uint32_t* ranges = nullptr;
+    ViewDev* h_views = nullptr;      // pinned staging
+    FrameHeader* h_hdr_up = nullptr; // pinned staging
+    FrameHeader* h_hdr_down = nullptr;
+    uint32_t* h_counts = nullptr;    // pinned: per view sum M, rendered
+    cudaGraphExec_t graph = nullptr;
+    bool busy = false;
+    std::vector<uint64_t> tickets;
+};
+
+}  // namespace clod
+
+using namespace clod;
+
+struct clod_server {
+    clod_scene scene{};
+    clod_server_cfg cfg{};
+    int device = 0;
+    int n_sm = 0;
+    uint32_t max_tiles = 0, max_rb = 0, max_tx = 0;
+    size_t max_diff = 0;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<uint64_t> pending;
+    std::unordered_map<uint64_t, Request> reqs;
+    std::vector<Slot> slots;
+    std::thread worker;
+    bool stop = false;
+    uint64_t next_ticket = 1;
+    clod_status fatal = CLOD_OK;
+};
+
+namespace clod {
+
+static void fill_views(clod_server* S, const std::vector<const Request*>& batch, Slot& sl, FrameHeader& h)
+{
+    const uint32_t CH = chunks_for((uint64_t)S->scene.n);
+    uint32_t tile_base = 0, rb_base = 0, mtx = 1;
+    for (size_t v = 0; v < batch.size(); ++v) {
+        const clod_view& w = batch[v]->view;
+        ViewDev& d = sl.h_views[v];
+        std::memset(&d, 0, sizeof(d));
+        for (int r = 0; r < 3; ++r) {
+            for (int c = 0; c < 3; ++c) d.R[3 * r + c] = w.viewmat[4 * r + c];
+            d.t[r] = w.viewmat[4 * r + 3];
+            d.c[r] = w.campos[r];
+            d.bg[r] = w.bg[r];
+        }
+        d.fx = w.fx;
+        d.fy = w.fy;
+        d.cx = w.cx;
+        d.cy = w.cy;
+        d.near_z = w.near_z;
+        d.s_v = w.s_v;
+        d.tau = w.tau;
+        d.eps = w.eps;
+        d.W = w.width;
+        d.H = w.height;
+        d.TX = (w.width + TILE - 1) / TILE;
+        d.TY = (w.height + TILE - 1) / TILE;
+        d.flags = w.flags;
+        d.tile_base = tile_base;
+        d.rb_base = rb_base;
+        d.out_img = batch[v]->out;
+        tile_base += (uint32_t)(d.TX * d.TY);
+        rb_base += CH * (uint32_t)((d.TY + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK);
+        mtx = std::max<uint32_t>(mtx, (uint32_t)d.TX);
+    }
+    std::memset(&h, 0, sizeof(h));
+    h.n = (uint64_t)S->scene.n;
+    h.n_views = (uint32_t)batch.size();
+    h.total_tiles = tile_base;
+    h.n_chunks = CH;
+    h.n_rs_blocks = (uint32_t)(((uint64_t)S->scene.n + RS_ITEMS - 1) / RS_ITEMS);
+    h.max_tx = S->max_tx;   // shared-memory layout of the emission blocks: fixed per slot
+    h.rb_total = rb_base;
+}
+
+// The launch sequence of one batch on a slot (captured once when graphs are on).
+static void enqueue_batch(clod_server* S, Slot& sl, cudaStream_t st)
+{
+    const Frame F = frame_ptrs(sl.ws, sl.L);
+    const int V = (int)S->cfg.max_views_per_batch;
+    cudaMemsetAsync(sl.ws, 0, sl.L.views, st);
+    cudaMemcpyAsync(F.hdr, sl.h_hdr_up, sizeof(FrameHeader), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(F.views, sl.h_views, sizeof(ViewDev) * V, cudaMemcpyHostToDevice, st);
+    launch_preprocess(F, S->scene, (uint32_t)V, nullptr, nullptr, nullptr, S->n_sm, st);
+    launch_bin_sort(F, sl.L, S->cfg.pair_capacity, nullptr, sl.vals, sl.ranges, st);
+    launch_blend_fwd(F, sl.vals, sl.ranges, nullptr, nullptr, nullptr, nullptr, S->n_sm, st);
+    cudaMemcpyAsync(sl.h_hdr_down, F.hdr, sizeof(FrameHeader), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(sl.h_counts, F.n_surv, sizeof(uint32_t) * 2 * V, cudaMemcpyDeviceToHost, st);
+}
+
+static clod_status slot_init(clod_server* S, Slot& sl)
+{
+    cudaError_t e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "server slot stream");
+    const uint32_t V = (uint32_t)S->cfg.max_views_per_batch;
+    sl.L = frame_layout((uint64_t)S->scene.n, V, S->max_tiles, S->max_rb, S->max_tx, S->max_diff);
+    if ((e = cudaMalloc(&sl.ws, sl.L.total)) != cudaSuccess) return cuda_fail(e, "server workspace");
+    if ((e = cudaMalloc(&sl.vals, sizeof(uint32_t) * std::max<uint64_t>(1, S->cfg.pair_capacity))) != cudaSuccess)
+        return cuda_fail(e, "server pair buffer");
+    if ((e = cudaMalloc(&sl.ranges, sizeof(uint32_t) * 2 * (size_t)S->max_tiles)) != cudaSuccess)
+        return cuda_fail(e, "server ranges");
+    if ((e = cudaMallocHost(&sl.h_views, sizeof(ViewDev) * V)) != cudaSuccess) return cuda_fail(e, "pinned views");
+    if ((e = cudaMallocHost(&sl.h_hdr_up, sizeof(FrameHeader))) != cudaSuccess) return cuda_fail(e, "pinned header");
+    if ((e = cudaMallocHost(&sl.h_hdr_down, sizeof(FrameHeader))) != cudaSuccess) return cuda_fail(e, "pinned header");
+    if ((e = cudaMallocHost(&sl.h_counts, sizeof(uint32_t) * 2 * V)) != cudaSuccess) return cuda_fail(e, "pinned counts");
+    std::memset(sl.h_views, 0, sizeof(ViewDev) * V);
+    if (S->cfg.use_graphs) {
+        // capture the slot's launch sequence once; sizes come from the header at run time
+        cudaGraph_t g = nullptr;
+        e = cudaStreamBeginCapture(sl.stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "begin capture");
+        enqueue_batch(S, sl, sl.stream);
+        e = cudaStreamEndCapture(sl.stream, &g);
+        if (e != cudaSuccess) return cuda_fail(e, "end capture");
+        e = cudaGraphInstantiate(&sl.graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    }
+    return CLOD_OK;
+}
+
+static void slot_free(Slot& sl)
+{
+    if (sl.graph) cudaGraphExecDestroy(sl.graph);
+    if (sl.stream) cudaStreamSynchronize(sl.stream);
+    cudaFree(sl.ws);
+    cudaFree(sl.vals);
+    cudaFree(sl.ranges);
+    cudaFreeHost(sl.h_views);
+    cudaFreeHost(sl.h_hdr_up);
+    cudaFreeHost(sl.h_hdr_down);
+    cudaFreeHost(sl.h_counts);
+    if (sl.ev) cudaEventDestroy(sl.ev);
+    if (sl.stream) cudaStreamDestroy(sl.stream);
+}
+
+// Renders one request alone with a pair buffer of its own (overflow path).
+static clod_status render_alone(clod_server* S, Slot& sl, Request& r)
+{
+    const clod_view& w = r.view;
+    const int TX = (w.width + TILE - 1) / TILE, TY = (w.height + TILE - 1) / TILE;
+    const uint32_t CH = chunks_for((uint64_t)S->scene.n);
+    const uint32_t rb = CH * (uint32_t)((TY + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK);
+    const FrameLayout L = frame_layout((uint64_t)S->scene.n, 1, (uint32_t)(TX * TY), rb, (uint32_t)TX,
+                                       (size_t)(TX + 1) * (TY + 1));
+    std::vector<const Request*> one{&r};
+    FrameHeader h;
+    fill_views(S, one, sl, h);
+    h.max_tx = (uint32_t)TX;
+    const Frame F = frame_ptrs(sl.ws, L);   // a one-view layout fits inside the slot's workspace
+    cudaStream_t st = sl.stream;
+    cudaMemsetAsync(sl.ws, 0, L.views, st);
+    cudaMemcpyAsync(F.hdr, &h, sizeof(h), cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(F.views, sl.h_views, sizeof(ViewDev), cudaMemcpyHostToDevice, st);
+    launch_preprocess(F, S->scene, 1, nullptr, nullptr, nullptr, S->n_sm, st);
+    unsigned long long K = 0;
+    cudaMemcpyAsync(&K, &F.hdr->n_pairs, sizeof(K), cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "render_alone");
+    uint32_t* vals = nullptr;
+    uint32_t* ranges = nullptr;
+    if ((e = cudaMalloc(&vals, sizeof(uint32_t) * std::max<unsigned long long>(K, 1))) != cudaSuccess)
+        return cuda_fail(e, "render_alone pairs");
+    if ((e = cudaMalloc(&ranges, sizeof(uint32_t) * 2 * (size_t)TX * TY)) != cudaSuccess) {
+        cudaFree(vals);
+        return cuda_fail(e, "render_alone ranges");
+    }
+    launch_bin_sort(F, L, K, nullptr, vals, ranges, st);
+    launch_blend_fwd(F, vals, ranges, nullptr, nullptr, nullptr, nullptr, S->n_sm, st);
+    FrameHeader out;
+    cudaMemcpyAsync(&out, F.hdr, sizeof(out), cudaMemcpyDeviceToHost, st);
+    uint32_t cnt[2] = {0, 0};
+    cudaMemcpyAsync(cnt, F.n_surv, sizeof(cnt), cudaMemcpyDeviceToHost, st);
+    e = cudaStreamSynchronize(st);
+    cudaFree(vals);
+    cudaFree(ranges);
+    if (e != cudaSuccess) return cuda_fail(e, "render_alone");
+    r.pairs = out.n_pairs;
+    r.rendered = cnt[1];
+    if (out.status & STATUS_OVERFLOW) return CLOD_ERR_CAPACITY;
+    return CLOD_OK;
+}
+
+static void worker_main(clod_server* S)
+{
+    cudaSetDevice(S->device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    while (!S->stop) {
+        bool progress = false;
+        // 1. completions
+        for (Slot& sl : S->slots) {
+            if (!sl.busy) continue;
+            if (cudaEventQuery(sl.ev) != cudaSuccess) continue;
+            const double t = now_us();
+            const bool overflow = (sl.h_hdr_down->status & STATUS_OVERFLOW) != 0;
+            for (size_t k = 0; k < sl.tickets.size(); ++k) {
+                Request& r = S->reqs[sl.tickets[k]];
+                if (overflow) {
+                    r.solo = true;
+                    continue;
+                }
+                r.done = true;
+                r.t_done = t;
+                r.status = CLOD_OK;
+                r.pairs = sl.h_hdr_down->n_pairs;
+                r.rendered = sl.h_counts[2 * k + 1];
+            }
+            if (overflow)   // re-run each request alone, keeping arrival order
+                for (size_t k = sl.tickets.size(); k-- > 0;) S->pending.push_front(sl.tickets[k]);
+            sl.tickets.clear();
+            sl.busy = false;
+            progress = true;
+        }
+        if (progress) S->cv_done.notify_all();
+        // 2. admissions into free slots
+        for (Slot& sl : S->slots) {
+            if (sl.busy || S->pending.empty()) continue;
+            Request& first = S->reqs[S->pending.front()];
+            if (first.solo) {
+                const uint64_t tk = S->pending.front();
+                S->pending.pop_front();
+                first.t_launch = now_us();
+                first.batch = 1;
+                lk.unlock();
+                const clod_status st = render_alone(S, sl, first);
+                lk.lock();
+                Request& r = S->reqs[tk];
+                r.status = st;
+                r.done = true;
+                r.t_done = now_us();
+                S->cv_done.notify_all();
+                progress = true;
+                continue;
+            }
+            if (S->cfg.batch_window_us > 0 && (int)S->pending.size() < S->cfg.max_views_per_batch &&
+                now_us() - first.t_submit < S->cfg.batch_window_us)
+                continue;   // wait a little for more requests to share the launch
+            std::vector<const Request*> batch;
+            uint64_t pixels = 0;
+            while (!S->pending.empty() && (int)batch.size() < S->cfg.max_views_per_batch) {
+                Request& r = S->reqs[S->pending.front()];
+                const uint64_t p = (uint64_t)r.view.width * r.view.height;
+                if (r.solo || (!batch.empty() && pixels + p > S->cfg.max_pixels_per_batch)) break;
+                pixels += p;
+                batch.push_back(&r);
+                sl.tickets.push_back(S->pending.front());
+                S->pending.pop_front();
+            }
+            FrameHeader h;
+            fill_views(S, batch, sl, h);
+            *sl.h_hdr_up = h;
+            const double t = now_us();
+            for (const Request* r : batch) {
+                Request* rw = const_cast<Request*>(r);
+                rw->t_launch = t;
+                rw->batch = (int32_t)batch.size();
+            }
+            cudaError_t e;
+            if (sl.graph) e = cudaGraphLaunch(sl.graph, sl.stream);
+            else {
+                enqueue_batch(S, sl, sl.stream);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(sl.ev, sl.stream);
+            if (e != cudaSuccess) {
+                for (uint64_t tk : sl.tickets) {
+                    Request& r = S->reqs[tk];
+                    r.status = CLOD_ERR_CUDA;
+                    r.done = true;
+                    r.t_done = now_us();
+                }
+                sl.tickets.clear();
+                S->fatal = CLOD_ERR_CUDA;
+                S->cv_done.notify_all();
+                continue;
+            }
+            sl.busy = true;
+            progress = true;
+        }
+        if (!progress) {
+            bool any_busy = false;
+            for (Slot& sl : S->slots) any_busy |= sl.busy;
+            // poll the device while batches run; sleep on the queue otherwise
+            S->cv_work.wait_for(lk, std::chrono::microseconds(any_busy ? 20 : 500));
+        }
+    }
+}
+
+}  // namespace clod
+
+extern "C" {
+
+clod_status clod_server_create(const clod_scene* scene, const clod_server_cfg* cfg, clod_server** out)
+{
+    if (!scene || !cfg || !out) return fail(CLOD_ERR_ARG, "NULL argument to clod_server_create");
+    if (scene->n < 0 || scene->n >= (1ll << 31) || scene->sh_degree < 0 || scene->sh_degree > 3)
+        return fail(CLOD_ERR_ARG, "bad scene");
+    if (scene->n > 0 && (!scene->means || !scene->scales || !scene->quats || !scene->opacity || !scene->sh || !scene->decay))
+        return fail(CLOD_ERR_ARG, "scene array pointer is NULL");
+    if (cfg->max_views_per_batch < 1 || cfg->max_views_per_batch > MAX_VIEWS || cfg->n_slots < 1 || cfg->n_slots > 16 ||
+        cfg->queue_capacity < 1 || cfg->max_width < 1 || cfg->max_height < 1 || cfg->max_width > 16384 ||
+        cfg->max_height > 16384 || cfg->max_pixels_per_batch < (uint64_t)cfg->max_width * cfg->max_height ||
+        cfg->pair_capacity < 1 || cfg->pair_capacity > 0xFFFFFFFFull)
+        return fail(CLOD_ERR_ARG, "bad server configuration");
+    int n_sm = 0;
+    clod_status s = device_ready(&n_sm);
+    if (s) return s;
+    clod_server* S = new clod_server();
+    S->scene = *scene;
+    S->cfg = *cfg;
+    S->n_sm = n_sm;
+    cudaGetDevice(&S->device);
+    // bounds of the largest admissible batch
+    const uint64_t TXm = (cfg->max_width + TILE - 1) / TILE, TYm = (cfg->max_height + TILE - 1) / TILE;
+    const uint64_t B = (uint64_t)cfg->max_views_per_batch;
+    const uint64_t tiles_by_px = cfg->max_pixels_per_batch / (TILE * TILE) + B * (TXm + TYm + 1);
+    S->max_tiles = (uint32_t)std::min<uint64_t>(B * TXm * TYm, tiles_by_px);
+    S->max_rb = (uint32_t)(B * chunks_for((uint64_t)scene->n) * ((TYm + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK));
+    S->max_tx = (uint32_t)TXm;
+    S->max_diff = (size_t)(TXm + 1) * (TYm + 1);
+    S->slots.resize(cfg->n_slots);
+    for (Slot& sl : S->slots) {
+        if ((s = slot_init(S, sl)) != CLOD_OK) {
+            for (Slot& q : S->slots) slot_free(q);
+            delete S;
+            return s;
+        }
+    }
+    S->worker = std::thread(worker_main, S);
+    *out = S;
+    return CLOD_OK;
+}
+
+clod_status clod_serve_submit(clod_server* S, const clod_view* view, float* image_out, uint64_t* ticket)
+{
+    if (!S || !view || !image_out || !ticket) return fail(CLOD_ERR_ARG, "NULL argument to clod_serve_submit");
+    const clod_view& w = *view;
+    if (w.width < 1 || w.height < 1 || w.width > S->cfg.max_width || w.height > S->cfg.max_height)
+        return fail(CLOD_ERR_ARG, "view %dx%d outside the server's %dx%d", w.width, w.height, S->cfg.max_width,
+                    S->cfg.max_height);
+    if (!(w.fx > 0.0f) || !(w.fy > 0.0f)) return fail(CLOD_ERR_ARG, "focal lengths must be > 0");
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->fatal) return fail(S->fatal, "server stopped after a CUDA error");
+    if ((int)S->pending.size() >= S->cfg.queue_capacity) return fail(CLOD_ERR_QUEUE_FULL, "queue full");
+    const uint64_t t = S->next_ticket++;
+    Request& r = S->reqs[t];
+    r.view = w;
+    r.out = image_out;
+    r.t_submit = now_us();
+    S->pending.push_back(t);
+    *ticket = t;
+    S->cv_work.notify_one();
+    return CLOD_OK;
+}
+
+static void fill_stats(const Request& r, clod_req_stats* st)
+{
+    if (!st) return;
+    st->status = r.status;
+    st->batch_size = r.batch;
+    st->submit_us = r.t_submit;
+    st->launch_us = r.t_launch;
+    st->done_us = r.t_done;
+    st->n_rendered = r.rendered;
+    st->reserved = 0;
+    st->n_pairs = r.pairs;
+}
+
+clod_status clod_serve_poll(clod_server* S, uint64_t ticket, int32_t* done, clod_req_stats* stats)
+{
+    if (!S || !done) return fail(CLOD_ERR_ARG, "NULL argument to clod_serve_poll");
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return fail(CLOD_ERR_ARG, "unknown ticket %llu", (unsigned long long)ticket);
+    *done = it->second.done ? 1 : 0;
+    if (!it->second.done) return CLOD_ERR_NOT_READY;
+    fill_stats(it->second, stats);
+    const clod_status st = it->second.status;
+    S->reqs.erase(it);
+    return st == CLOD_OK ? CLOD_OK : fail(st, "request failed");
+}
+
+clod_status clod_serve_wait(clod_server* S, uint64_t ticket, int64_t timeout_us, clod_req_stats* stats)
+{
+    if (!S) return fail(CLOD_ERR_ARG, "NULL server");
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return fail(CLOD_ERR_ARG, "unknown ticket %llu", (unsigned long long)ticket);
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::microseconds(timeout_us);
+    while (!S->reqs[ticket].done) {
+        if (S->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && !S->reqs[ticket].done)
+            return fail(CLOD_ERR_TIMEOUT, "request %llu not finished after %lld us", (unsigned long long)ticket,
+                        (long long)timeout_us);
+    }
+    Request r = S->reqs[ticket];
+    S->reqs.erase(ticket);
+    fill_stats(r, stats);
+    return r.status == CLOD_OK ? CLOD_OK : fail(r.status, "request failed");
+}
+
+clod_status clod_server_destroy(clod_server* S)
+{
+    if (!S) return fail(CLOD_ERR_ARG, "NULL server");
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv_work.notify_all();
+    if (S->worker.joinable()) S->worker.join();
+    for (Slot& sl : S->slots) slot_free(sl);
+    delete S;
+    return CLOD_OK;
+}
+
+}  // extern "C"
