@@ -197,14 +197,32 @@ def run_ours(args):
     stage = np.array([[ev[k][j].elapsed_time(ev[k][j + 1]) for j in range(3)] for k in range(args.steps)])
     st_ms = stage.mean(0)
 
-    # evaluated (pixel, Gaussian) pairs for the blend's FLOP count (untimed pass)
+    # untimed pass over the same frames: the blend's pair counters (FLOP
+    # model) and each frame's survivors and pairs (byte models)
     evals = torch.zeros(3, dtype=torch.int64, device="cuda")
+    counts = torch.zeros(2, dtype=torch.int32, device="cuda")
+    n_surv, n_pairs = [], []
     for k in range(args.steps):
         R.set_views([views[k % len(views)]])
-        C.clod_preprocess(ds, R.views, R.ws, n_pairs=R.npairs)
+        C.clod_preprocess(ds, R.views, R.ws, counts=counts, n_pairs=R.npairs)
+        n_surv.append(counts[1].item())
+        n_pairs.append(R.npairs.item())
         C.clod_bin_sort(R.ws, R.cap, None, R.vals, R.ranges)
         C.clod_render_fwd(R.ws, R.vals, R.ranges, R.image, R.T, R.nc, evaluated=evals)
     torch.cuda.synchronize()
+    n_surv = np.array(n_surv, np.float64)
+    n_pairs = np.array(n_pairs, np.float64)
+    n = float(N_GAUSS)
+    sh_bytes = 12 * 16
+    # preprocess: means twice (distance pass + main pass), opacity, decay, and per
+    # Gaussian rect + sort key/value written; per survivor scales, quats, SH read
+    # and the 40 B of records written
+    pre_bytes = (12 + 12 + 8 + 16) * n * len(n_surv) + (28 + sh_bytes + 40) * n_surv.sum()
+    # sort as built: 4 radix passes over n keys (4 B read for counts, 8 B read,
+    # 8 B written), rectangles gathered into rank order (16 B per survivor),
+    # chunk counting (8 B per survivor), emission (4 B per pair written)
+    sort_bytes = 80 * n * len(n_surv) + 24 * n_surv.sum() + 4 * n_pairs.sum()
+    radix_equiv = 152 * n_pairs.sum()       # 6-pass LSD sort of K (u64 key, u32 value) pairs
     cnt3 = evals.cpu().numpy().astype(np.float64) / args.steps
     ev_per_frame = float(cnt3[0])
     flop_per_frame = FLOP_VISIT * cnt3[0] + FLOP_EXP * cnt3[1] + FLOP_CONTRIB * cnt3[2]
@@ -216,6 +234,17 @@ def run_ours(args):
     n_sm = torch.cuda.get_device_properties(0).multi_processor_count
     fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12          # TFLOP/s at the sampled clock
     blend_tflops = flop_per_frame / (st_ms[2] / 1e3) / 1e12
+    hbm = measured_peaks().get("hbm_gbs", 6772.2)
+    T_pre = stage[:, 0].sum() / 1e3
+    T_sort = stage[:, 1].sum() / 1e3
+    stage_bw = {
+        "preprocess": {"bytes_per_frame": round(pre_bytes / len(n_surv)), "GB_s": round(pre_bytes / T_pre / 1e9, 1),
+                       "frac_of_measured_hbm": round(pre_bytes / T_pre / 1e9 / hbm, 3)},
+        "bin_sort": {"bytes_per_frame": round(sort_bytes / len(n_surv)), "GB_s": round(sort_bytes / T_sort / 1e9, 1),
+                     "frac_of_measured_hbm": round(sort_bytes / T_sort / 1e9 / hbm, 3),
+                     "radix_equivalent_GB_s": round(radix_equiv / T_sort / 1e9, 1),
+                     "radix_equivalent_frac": round(radix_equiv / T_sort / 1e9 / hbm, 3)},
+        "hbm_peak_GB_s": hbm, "mean_survivors": round(float(n_surv.mean())), "mean_pairs": round(float(n_pairs.mean()))}
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "frames/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(elapsed * 1e3 / args.steps, 4), "higher_is_better": True,
@@ -225,6 +254,7 @@ def run_ours(args):
                    "parallelism": "replicas" if world > 1 else "single"},
         "stage_ms": {"preprocess": round(float(st_ms[0]), 4), "bin_sort": round(float(st_ms[1]), 4),
                      "blend": round(float(st_ms[2]), 4)},
+        "stage_hbm": stage_bw,
         "roofline": {"bound": "alu", "kernel": "k_blend_fwd", "achieved": round(blend_tflops, 3),
                      "peak": round(fp32_peak, 2), "unit": "TFLOP/s", "frac": round(blend_tflops / fp32_peak, 4),
                      "traffic": None, "flop_model": "9 per visited pair + 33 per exp + 9 per contributor",
@@ -388,67 +418,75 @@ def serve_leg(args):
         C.clod_render_fwd(R.ws, R.vals, R.ranges, out, None, None)
         torch.cuda.current_stream().synchronize()
 
-    def run_plain():
+    def run_plain(vs, arr):
         for v in warm:
             plain_frame(v, bufs[(v.width, v.height)][0])
         t0 = time.monotonic()
-        lat = np.zeros(n_req)
+        lat = np.zeros(len(vs))
         done = 0.0
-        for k, v in enumerate(views):
+        for k, v in enumerate(vs):
             now = time.monotonic() - t0
-            if now < arrivals[k]:
-                time.sleep(arrivals[k] - now)
+            if now < arr[k]:
+                time.sleep(arr[k] - now)
             plain_frame(v, buf(k))
             done = time.monotonic() - t0
-            lat[k] = done - arrivals[k]
-        return lat, n_req / (done - arrivals[0])
+            lat[k] = done - arr[k]
+        return lat, len(vs) / (done - arr[0])
 
-    def run_server(B=8, slots=3):
+    def run_server(vs, arr, B=8, slots=3):
         srv = SV.Server(ds, max_views_per_batch=B, n_slots=slots, use_graphs=True, pair_capacity=1 << 25,
                         max_pixels_per_batch=3840 * 2160 * 2, max_width=3840, max_height=2160)
         for v in warm:
             srv.wait(srv.submit(v, bufs[(v.width, v.height)][0]), 60.0)
+        n = len(vs)
         users = {}
-        tickets = [None] * n_req
-        lat = np.zeros(n_req)
+        tickets = [None] * n
+        lat = np.zeros(n)
         bsz = []
         t0 = time.monotonic()
         t0_us = t0 * 1e6
 
         def finish(j):
             st = srv.wait(tickets[j], 120.0)
-            lat[j] = (st.done_us - t0_us) / 1e6 - arrivals[j]
+            lat[j] = (st.done_us - t0_us) / 1e6 - arr[j]
             bsz.append(st.batch_size)
             tickets[j] = None
             return st.done_us
 
         last = t0_us
-        for k, v in enumerate(views):
+        for k, v in enumerate(vs):
             now = time.monotonic() - t0
-            if now < arrivals[k]:
-                time.sleep(arrivals[k] - now)
+            if now < arr[k]:
+                time.sleep(arr[k] - now)
             key = slot_of[k]
             j = users.get(key)
             if j is not None and tickets[j] is not None:
                 last = max(last, finish(j))
             users[key] = k
             tickets[k] = srv.submit(v, buf(k))
-        for j in range(n_req):
+        for j in range(n):
             if tickets[j] is not None:
                 last = max(last, finish(j))
         srv.close()
-        return lat, n_req / ((last - t0_us) / 1e6 - arrivals[0]), float(np.mean(bsz))
+        return lat, n / ((last - t0_us) / 1e6 - arr[0]), float(np.mean(bsz))
 
-    lat_p, fps_p = run_plain()
-    torch.cuda.synchronize()
-    lat_s, fps_s, mean_b = run_server()
     q = lambda a, p: round(float(np.percentile(a, p)) * 1e3, 3)
-    return {"workload": "object scene 2M Gaussians SH3 resident; %d requests, Poisson %g/s; 512^2/720p/1080p/4K "
-                        "mixed; d in [1,50]; s_v log-uniform [1,32]" % (n_req, rate),
+    res = {"workload": "object scene 2M Gaussians SH3 resident; Poisson arrivals; 512^2/720p/1080p/4K mixed; "
+                       "d in [1,50]; s_v log-uniform [1,32]; server: 8 views/batch, 3 slots, CUDA graphs",
+           "latency": "completion minus scheduled arrival"}
+    for lam in (rate, 300.0):
+        n = min(n_req, int(lam * args.serve_seconds))
+        arr = arrivals[:n] * (rate / lam)
+        lat_p, fps_p = run_plain(views[:n], arr)
+        torch.cuda.synchronize()
+        lat_s, fps_s, mean_b = run_server(views[:n], arr)
+        res["at_%d_per_s" % int(lam)] = {
+            "requests": n,
             "server": {"frames_per_s": round(fps_s, 2), "p50_ms": q(lat_s, 50), "p99_ms": q(lat_s, 99),
-                       "mean_batch": round(mean_b, 2), "max_views_per_batch": 8, "slots": 3, "graphs": True},
+                       "mean_batch": round(mean_b, 2)},
             "plain": {"frames_per_s": round(fps_p, 2), "p50_ms": q(lat_p, 50), "p99_ms": q(lat_p, 99)},
             "throughput_ratio": round(fps_s / fps_p, 3)}
+    return res
 
 
 def run_reference(args):
