@@ -213,6 +213,20 @@ clod_status clod_render_bwd(const clod_scene* scene, const void* ws, const uint3
 clod_status clod_l1_loss(const float* image, const float* target, int64_t count, float scale,
                          float* loss, float* dL_dimage, clod_stream stream);
 
+/* Scratch bytes of clod_render_loss for a channels x height x width image. */
+clod_status clod_render_loss_workspace_size(int32_t channels, int32_t height, int32_t width, size_t* bytes);
+
+/* Rendering loss of Sec. 3.3, L_render = (1 - w) L1 + w (1 - SSIM), with
+ * w = dssim_weight in [0, 1] (0.2 in the 3DGS training the paper builds on).
+ * SSIM: 11x11 Gaussian window (sigma 1.5, zero outside the image),
+ * C1 = 0.01^2, C2 = 0.03^2, mean over pixels and channels.  image, target:
+ * device f32 channels x height x width.  *loss (device f32) += L_render;
+ * dL_dimage (may be NULL) = dL_render/dimage, which needs ws (device, size
+ * from clod_render_loss_workspace_size). */
+clod_status clod_render_loss(const float* image, const float* target, int32_t channels, int32_t height,
+                             int32_t width, float dssim_weight, void* ws, size_t ws_bytes,
+                             float* loss, float* dL_dimage, clod_stream stream);
+
 /* ------------------------------------------------------------------------ */
 /* Serving: continuous batching over a resident scene                         */
 /* ------------------------------------------------------------------------ */

@@ -23,6 +23,9 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
            "-Xcompiler", "-ffp-contract=off"]
+# Translation units whose arithmetic decides nothing bit-exact outside the
+# explicit round-to-nearest intrinsics may let nvcc fuse multiply-adds.
+FMAD_OK = {"backward.cu", "loss.cu"}
 
 _lock = threading.Lock()
 _lib = None
@@ -61,7 +64,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = [nv, *ARCH, *NVFLAGS, "-I", INCLUDE, "-c", src, "-o", obj]
+        flags = list(NVFLAGS)
+        if os.path.basename(src) in FMAD_OK:
+            flags[flags.index("--fmad=false")] = "--fmad=true"
+        cmd = [nv, *ARCH, *flags, "-I", INCLUDE, "-c", src, "-o", obj]
         if src.endswith(".cpp"):
             cmd = [nv, *NVFLAGS, "-I", INCLUDE, "-x", "cu", *ARCH, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)

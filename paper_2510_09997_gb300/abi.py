@@ -68,6 +68,9 @@ SIGNATURES = {
     "clod_backward_workspace_size": ([ctypes.c_int64, ctypes.c_int32, P], c_status),
     "clod_render_bwd": ([P, P, P, P, P, P, P, P, P, ctypes.c_size_t, P, P, P, P, P, P, P], c_status),
     "clod_l1_loss": ([P, P, ctypes.c_int64, ctypes.c_float, P, P, P], c_status),
+    "clod_render_loss_workspace_size": ([ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P], c_status),
+    "clod_render_loss": ([P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, P, ctypes.c_size_t,
+                          P, P, P], c_status),
     "clod_render_noalloc": ([P, P, P, P, P, P], c_status),
     # serving
     "clod_server_create": ([P, P, P], c_status),

@@ -95,6 +95,31 @@ class L1Loss(torch.autograd.Function):
         return grad * g, None
 
 
+class RenderLoss(torch.autograd.Function):
+    """(1 - w) L1 + w (1 - SSIM) by clod_render_loss (value and gradient)."""
+
+    @staticmethod
+    def forward(ctx, image, target, dssim_weight: float = 0.2):
+        image = image.contiguous()
+        target = target.contiguous()
+        Cc, H, W = image.shape
+        loss = torch.zeros(1, dtype=torch.float32, device=image.device)
+        grad = torch.empty_like(image)
+        nb = ctypes.c_size_t()
+        C.check("clod_render_loss_workspace_size", C.lib().clod_render_loss_workspace_size(Cc, H, W, ctypes.byref(nb)))
+        ws = torch.empty(int(nb.value), dtype=torch.uint8, device=image.device)
+        C.check("clod_render_loss", C.lib().clod_render_loss(C._ptr(image), C._ptr(target), Cc, H, W,
+                                                             float(dssim_weight), C._ptr(ws), ws.numel(),
+                                                             C._ptr(loss), C._ptr(grad), C._stream(None)))
+        ctx.save_for_backward(grad)
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, g):
+        (grad,) = ctx.saved_tensors
+        return grad * g, None, None
+
+
 def smoke_backward() -> None:
     """Tiny forward + backward on cuda:0 checked against the FP64 oracle."""
     from oracle import grad64 as G

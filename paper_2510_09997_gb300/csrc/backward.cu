@@ -44,29 +44,124 @@ __device__ __forceinline__ float warp_sum(float x)
     return x;
 }
 
-__global__ void __launch_bounds__(BLOCK_PIX) k_blend_bwd(Frame F, const uint32_t* __restrict__ vals,
-                                                         const uint32_t* __restrict__ ranges,
-                                                         const float* __restrict__ Tfin,
-                                                         const uint32_t* __restrict__ ncon,
-                                                         const float* __restrict__ dimg, float4* __restrict__ g2d)
+// Sum of 16 values over the 32 lanes of a warp, scattered: afterwards lane l
+// holds the total of value (l >> 1).  Each butterfly step keeps the half of
+// the values whose index bit matches the lane bit and sends the other half.
+__device__ __forceinline__ float warp_reduce16(float (&v)[16])
 {
-    __shared__ float4 s0[BLOCK_PIX];
-    __shared__ float4 s1[BLOCK_PIX];
-    __shared__ float s2[BLOCK_PIX];
-    __shared__ int64_t sg[BLOCK_PIX];
-    __shared__ uint32_t s_tile, s_max;
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const bool hi = lane & 16;
+        const float keep = hi ? v[8 + i] : v[i], give = hi ? v[i] : v[8 + i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, give, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const bool hi = lane & 8;
+        const float keep = hi ? v[4 + i] : v[i], give = hi ? v[i] : v[4 + i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, give, 8);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const bool hi = lane & 4;
+        const float keep = hi ? v[2 + i] : v[i], give = hi ? v[i] : v[2 + i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, give, 4);
+    }
+    {
+        const bool hi = lane & 2;
+        const float keep = hi ? v[1] : v[0], give = hi ? v[0] : v[1];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, give, 2);
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+// Reach box of a staged Gaussian (same construction as the forward blend's):
+// every pixel centre where the opacity can reach 1/255 lies within
+// (xe, ye) of (u, v); returned widened by the patch half-size.
+__device__ __forceinline__ float2 reach_extent(float4 a, float4 c, float hx, float hy)
+{
+    const float A = -2.0f * a.z, B = -a.w, C = -2.0f * c.x;
+    const float det = A * C - B * B;
+    const float a255 = 255.0f * c.y;
+    if (!(a255 >= 1.0f)) return make_float2(-1.0f, -1.0f);
+    if (!(det > 1e-3f * (A * C)) || !(A > 0.0f) || !(C > 0.0f))
+        return make_float2(__int_as_float(0x7f800000), __int_as_float(0x7f800000));
+    const float P = fminf(5.6f, logf(a255));
+    const float r2 = 2.0f * P * 1.001f + 1e-3f;
+    return make_float2(sqrtf(r2 * (C / det)) * 1.001f + 0.01f + hx, sqrtf(r2 * (A / det)) * 1.001f + 0.01f + hy);
+}
+
+struct BPx {
+    float T, d0, d1, d2, S0, S1, S2;
+    uint32_t last;
+    float fy;
+};
+
+// Reverse blend of one pixel against one staged Gaussian at list position
+// pos (1-based); adds this pixel's 9 gradients into g.
+__device__ __forceinline__ bool bwd_one(BPx& q, float fpx, const float4& a, const float4& c, float cb, uint32_t pos,
+                                        float (&g)[16])
+{
+    if (pos > q.last) return false;
+    // the forward's decision arithmetic (explicit round-to-nearest intrinsics,
+    // never fused): same power, same exponential, same skip
+    const float dx = __fsub_rn(a.x, fpx), dy = __fsub_rn(a.y, q.fy);
+    const float power = __fmaf_rn(dx, __fmaf_rn(a.z, dx, __fmul_rn(a.w, dy)), __fmul_rn(__fmul_rn(c.x, dy), dy));
+    if (power > 0.0f || power < -5.6f) return false;
+    const float G = exp_spec(power);
+    const float raw = __fmul_rn(c.y, G);
+    const float al = fminf(0.99f, raw);
+    if (al < (1.0f / 255.0f)) return false;
+    const float iom = __frcp_rn(1.0f - al);
+    const float Tb = q.T * iom;
+    const float w = al * Tb;
+    g[6] += w * q.d0;
+    g[7] += w * q.d1;
+    g[8] += w * q.d2;
+    const float dal = q.d0 * (c.z * Tb - q.S0 * iom) + q.d1 * (c.w * Tb - q.S1 * iom) + q.d2 * (cb * Tb - q.S2 * iom);
+    q.S0 += c.z * w;
+    q.S1 += c.w * w;
+    q.S2 += cb * w;
+    q.T = Tb;
+    if (!(raw > 0.99f)) {
+        g[5] += dal * G;
+        const float gp = dal * al;
+        g[0] += gp * (2.0f * a.z * dx + a.w * dy);
+        g[1] += gp * (a.w * dx + 2.0f * c.x * dy);
+        g[2] += gp * (-0.5f * dx * dx);
+        g[3] += gp * (-dx * dy);
+        g[4] += gp * (-0.5f * dy * dy);
+    }
+    return true;
+}
+
+constexpr int BWD_THREADS = 128;   // 4 warps per tile, 8x8 pixels per warp, 2 per thread
+
+__global__ void __launch_bounds__(BWD_THREADS) k_blend_bwd(Frame F, const uint32_t* __restrict__ vals,
+                                                           const uint32_t* __restrict__ ranges,
+                                                           const float* __restrict__ Tfin,
+                                                           const uint32_t* __restrict__ ncon,
+                                                           const float* __restrict__ dimg, float* __restrict__ g2d)
+{
+    __shared__ float4 s0[4][32];
+    __shared__ float4 s1[4][32];
+    __shared__ float s2[4][32];
+    __shared__ int64_t sg[4][32];
+    __shared__ uint32_t s_tile;
     __shared__ int s_view;
     const FrameHeader* hdr = F.hdr;
     if (hdr->status & STATUS_OVERFLOW) return;
     const uint32_t TT = hdr->total_tiles;
     const uint32_t V = hdr->n_views;
     const int64_t n = static_cast<int64_t>(hdr->n);
-    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ox = (wid & 1) * 8 + (lane & 7), oy = (wid >> 1) * 8 + (lane >> 3) * 2;
+    const float pcx = (float)((wid & 1) * 8) + 4.0f, pcy = (float)((wid >> 1) * 8) + 4.0f;
     for (;;) {
         if (threadIdx.x == 0) {
             const uint32_t t = atomicAdd(&F.hdr->work[1], 1u);
             s_tile = t;
-            s_max = 0;
             int v = 0;
             if (t < TT)
                 for (uint32_t u = 0; u < V; ++u) {
@@ -84,101 +179,71 @@ __global__ void __launch_bounds__(BLOCK_PIX) k_blend_bwd(Frame F, const uint32_t
         const ViewDev& W = F.views[s_view];
         const uint32_t local = t - W.tile_base;
         const int tx = (int)(local % (uint32_t)W.TX), ty = (int)(local / (uint32_t)W.TX);
-        const int px = tx * TILE + (int)(threadIdx.x & 15), py = ty * TILE + (int)(threadIdx.x >> 4);
-        const bool inside = px < W.W && py < W.H;
+        const int px = tx * TILE + ox;
         const float fpx = __fadd_rn(static_cast<float>(px), 0.5f);
-        const float fpy = __fadd_rn(static_cast<float>(py), 0.5f);
-        const uint32_t start = ranges[2 * t], end = ranges[2 * t + 1];
+        const float wcx = (float)(tx * TILE) + pcx, wcy = (float)(ty * TILE) + pcy;
+        const uint32_t start = ranges[2 * t];
         const int64_t vn = (int64_t)s_view * n;
-        float T = 1.0f, d0 = 0.f, d1 = 0.f, d2 = 0.f, S0 = 0.f, S1 = 0.f, S2 = 0.f;
-        uint32_t last = 0;
-        if (inside) {
-            const size_t plane = (size_t)W.W * W.H, p = (size_t)py * W.W + px;
-            T = Tfin[W.pix_base + p];
-            last = ncon[W.pix_base + p];
-            const float* di = dimg + 3 * W.pix_base;
-            d0 = di[p];
-            d1 = di[plane + p];
-            d2 = di[2 * plane + p];
-            S0 = T * W.bg[0];
-            S1 = T * W.bg[1];
-            S2 = T * W.bg[2];
+        BPx q[2];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int py = ty * TILE + oy + r;
+            q[r].fy = __fadd_rn(static_cast<float>(py), 0.5f);
+            q[r].T = 1.0f;
+            q[r].d0 = q[r].d1 = q[r].d2 = q[r].S0 = q[r].S1 = q[r].S2 = 0.0f;
+            q[r].last = 0;
+            if (px < W.W && py < W.H) {
+                const size_t plane = (size_t)W.W * W.H, p = (size_t)py * W.W + px;
+                q[r].T = Tfin[W.pix_base + p];
+                q[r].last = ncon[W.pix_base + p];
+                const float* di = dimg + 3 * W.pix_base;
+                q[r].d0 = di[p];
+                q[r].d1 = di[plane + p];
+                q[r].d2 = di[2 * plane + p];
+                q[r].S0 = q[r].T * W.bg[0];
+                q[r].S1 = q[r].T * W.bg[1];
+                q[r].S2 = q[r].T * W.bg[2];
+            }
         }
-        // longest contributor prefix in the block
-        uint32_t m = last;
+        // walk from this warp's last contributor back to the start
+        uint32_t m = max(q[0].last, q[1].last);
         for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (lane == 0 && m) atomicMax(&s_max, m);
-        __syncthreads();
-        const uint32_t blast = start + s_max;
-        for (uint32_t bend = blast; bend > start;) {
-            const uint32_t bstart = bend - start > BLOCK_PIX ? bend - BLOCK_PIX : start;
-            const int cnt = (int)(bend - bstart);
-            if ((int)threadIdx.x < cnt) {
-                const int64_t g = vn + vals[bstart + threadIdx.x];
-                sg[threadIdx.x] = g;
-                s0[threadIdx.x] = F.rec0[g];
-                s1[threadIdx.x] = F.rec1[g];
-                s2[threadIdx.x] = F.rec2[g];
+        for (uint32_t hi = m; hi > 0;) {
+            const uint32_t lo = hi > 32 ? hi - 32 : 0;     // positions [lo, hi), 0-based
+            const uint32_t j = lo + lane;
+            bool hit = false;
+            if (j < hi) {
+                const int64_t g = vn + vals[start + j];
+                const float4 a = F.rec0[g];
+                const float4 c = F.rec1[g];
+                s0[wid][lane] = a;
+                s1[wid][lane] = c;
+                s2[wid][lane] = F.rec2[g];
+                sg[wid][lane] = g;
+                const float2 e = reach_extent(a, c, 3.5f, 3.5f);
+                hit = !(fabsf(a.x - wcx) > e.x || fabsf(a.y - wcy) > e.y);
             }
-            __syncthreads();
-            for (int k = cnt - 1; k >= 0; --k) {
-                const uint32_t pos = bstart - start + (uint32_t)k;   // list position
-                const float4 a = s0[k];
-                const float4 c = s1[k];
-                float gu = 0.f, gv = 0.f, gA = 0.f, gB = 0.f, gC = 0.f, ga = 0.f, gr = 0.f, gg = 0.f, gb = 0.f;
-                bool contrib = false;
-                if (inside && pos < last) {
-                    const float dx = __fsub_rn(a.x, fpx), dy = __fsub_rn(a.y, fpy);
-                    const float al = blend_alpha(dx, dy, a.z, a.w, c.x, c.y);
-                    if (al >= 0.0f) {
-                        contrib = true;
-                        const float power =
-                            __fmaf_rn(dx, __fmaf_rn(a.z, dx, __fmul_rn(a.w, dy)), __fmul_rn(__fmul_rn(c.x, dy), dy));
-                        const float G = exp_spec(power);
-                        const float raw = c.y * G;
-                        const float om = 1.0f - al;
-                        const float Tb = T / om;
-                        const float cb = s2[k];
-                        const float w = al * Tb;
-                        gr = w * d0;
-                        gg = w * d1;
-                        gb = w * d2;
-                        const float dal = d0 * (c.z * Tb - S0 / om) + d1 * (c.w * Tb - S1 / om) + d2 * (cb * Tb - S2 / om);
-                        S0 += c.z * w;
-                        S1 += c.w * w;
-                        S2 += cb * w;
-                        T = Tb;
-                        if (!(raw > 0.99f)) {
-                            ga = dal * G;
-                            const float gp = dal * al;
-                            gu = gp * (2.0f * a.z * dx + a.w * dy);
-                            gv = gp * (a.w * dx + 2.0f * c.x * dy);
-                            gA = gp * (-0.5f * dx * dx);
-                            gB = gp * (-dx * dy);
-                            gC = gp * (-0.5f * dy * dy);
-                        }
-                    }
-                }
-                if (__any_sync(0xffffffffu, contrib)) {
-                    gu = warp_sum(gu);
-                    gv = warp_sum(gv);
-                    gA = warp_sum(gA);
-                    gB = warp_sum(gB);
-                    gC = warp_sum(gC);
-                    ga = warp_sum(ga);
-                    gr = warp_sum(gr);
-                    gg = warp_sum(gg);
-                    gb = warp_sum(gb);
-                    if (lane == 0) {
-                        float4* dst = g2d + 3 * sg[k];
-                        atomicAdd(dst, make_float4(gu, gv, gA, gB));
-                        atomicAdd(dst + 1, make_float4(gC, ga, gr, gg));
-                        atomicAdd(reinterpret_cast<float*>(dst + 2), gb);
-                    }
+            unsigned bm = __ballot_sync(0xffffffffu, hit);
+            __syncwarp();
+            while (bm) {
+                const int k = 31 - __clz(bm);         // highest position first
+                bm &= ~(1u << k);
+                const float4 a = s0[wid][k];
+                const float4 c = s1[wid][k];
+                const float cb = s2[wid][k];
+                const uint32_t pos = lo + (uint32_t)k + 1u;
+                float g[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) g[i] = 0.0f;
+                bool any = bwd_one(q[0], fpx, a, c, cb, pos, g);
+                any |= bwd_one(q[1], fpx, a, c, cb, pos, g);
+                if (__any_sync(0xffffffffu, any)) {
+                    const float tot = warp_reduce16(g);
+                    if (!(lane & 1) && lane < 18) atomicAdd(g2d + 12 * sg[wid][k] + (lane >> 1), tot);
                 }
             }
-            __syncthreads();
-            bend = bstart;
+            __syncwarp();
+            hi = lo;
         }
         __syncthreads();
     }
@@ -232,6 +297,7 @@ struct ParamGrads {
     float* ddecay;
 };
 
+template <int DEG>
 __global__ void __launch_bounds__(128) k_preprocess_bwd(Frame F, clod_scene S, const float4* __restrict__ g2d,
                                                         const float* __restrict__ g_alpha_ext,
                                                         float* __restrict__ dmax_grad, ParamGrads P)
@@ -252,8 +318,8 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(Frame F, clod_scene S, c
     }
     __syncthreads();
     const int64_t n = S.n;
-    const int deg = S.sh_degree;
-    const int K = (deg + 1) * (deg + 1);
+    constexpr int deg = DEG;
+    constexpr int K = (DEG + 1) * (DEG + 1);
     for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = base + threadIdx.x;
         const bool active = i < n;
@@ -278,7 +344,7 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(Frame F, clod_scene S, c
             const float d = cam_dist(W, mx, my, mz, e0, e1, e2);
             if (surv) {
                 const float4 G0 = g2d[3 * o], G1 = g2d[3 * o + 1];
-                const float Gb = reinterpret_cast<const float*>(g2d + 3 * o + 2)[0];
+                const float Gb = g2d[3 * o + 2].x;
                 const float g_u = G0.x, g_v = G0.y, g_A = G0.z, g_B = G0.w, g_C = G1.x;
                 g_a2 += G1.y;
                 const float g_col[3] = {G1.z, G1.w, Gb};
@@ -290,11 +356,14 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(Frame F, clod_scene S, c
                 const float* shp = S.sh + (size_t)i * K * 3;
                 float* dshp = P.dsh + (size_t)i * K * 3;
                 float gdx = 0.f, gdy = 0.f, gdz = 0.f;
+#pragma unroll
                 for (int ch = 0; ch < 3; ++ch) {
                     float acc = 0.f;
+#pragma unroll
                     for (int k = 0; k < K; ++k) acc += b[k] * shp[3 * k + ch];
                     if (acc + 0.5f > 0.0f && g_col[ch] != 0.0f) {
                         const float gc = g_col[ch];
+#pragma unroll
                         for (int k = 0; k < K; ++k) {
                             dshp[3 * k + ch] += b[k] * gc;
                             const float s = shp[3 * k + ch] * gc;
@@ -522,7 +591,7 @@ static int g_bwd_blocks_per_sm = 0;
 cudaError_t backward_setup()
 {
     int b = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_blend_bwd, BLOCK_PIX, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_blend_bwd, BWD_THREADS, 0);
     if (e != cudaSuccess) return e;
     g_bwd_blocks_per_sm = b > 0 ? b : 1;
     return cudaSuccess;
@@ -539,11 +608,19 @@ void launch_backward(const Frame& F, const clod_scene& S, uint32_t V, const uint
     float* dmg = reinterpret_cast<float*>(b + L.dmax_grad);
     cudaMemsetAsync(bwd_ws, 0, L.total, st);
     cudaMemsetAsync(&F.hdr->work[1], 0, sizeof(uint32_t), st);
-    k_blend_bwd<<<n_sm * std::max(1, g_bwd_blocks_per_sm), BLOCK_PIX, 0, st>>>(F, vals, ranges, Tfin, ncon, dimg, g2d);
+    k_blend_bwd<<<n_sm * std::max(1, g_bwd_blocks_per_sm), BWD_THREADS, 0, st>>>(F, vals, ranges, Tfin, ncon, dimg,
+                                                                                reinterpret_cast<float*>(g2d));
     ParamGrads P{dmeans, dscales, dquats, dopacity, dsh, ddecay};
     int blocks = static_cast<int>(std::min<int64_t>((S.n + 127) / 128, (int64_t)n_sm * 16));
     if (blocks < 1) blocks = 1;
-    if (S.n > 0) k_preprocess_bwd<<<blocks, 128, 0, st>>>(F, S, g2d, g_alpha_ext, dmg, P);
+    if (S.n > 0) {
+        switch (S.sh_degree) {
+        case 0: k_preprocess_bwd<0><<<blocks, 128, 0, st>>>(F, S, g2d, g_alpha_ext, dmg, P); break;
+        case 1: k_preprocess_bwd<1><<<blocks, 128, 0, st>>>(F, S, g2d, g_alpha_ext, dmg, P); break;
+        case 2: k_preprocess_bwd<2><<<blocks, 128, 0, st>>>(F, S, g2d, g_alpha_ext, dmg, P); break;
+        default: k_preprocess_bwd<3><<<blocks, 128, 0, st>>>(F, S, g2d, g_alpha_ext, dmg, P); break;
+        }
+    }
     k_dmax_bwd<<<1, 64, 0, st>>>(F, S, dmg, dmeans);
 }
 

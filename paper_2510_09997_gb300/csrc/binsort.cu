@@ -59,7 +59,7 @@ __device__ __forceinline__ void rs_warp_counts(const uint32_t* __restrict__ keys
 
 __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const FrameHeader* __restrict__ hdr,
                                                         const uint32_t* __restrict__ keys, int64_t n, int nb, int shift,
-                                                        uint32_t* __restrict__ hist)
+                                                        uint32_t* __restrict__ hist, uint32_t* __restrict__ totals)
 {
     __shared__ uint32_t h[RS_THREADS / 32][256];
     const int b = blockIdx.x, v = b / nb, lb = b % nb;
@@ -71,50 +71,29 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const FrameHeader* __res
     uint32_t s = 0;
     for (int w = 0; w < RS_THREADS / 32; ++w) s += h[w][threadIdx.x];
     hist[((size_t)v * 256 + threadIdx.x) * nb + lb] = s;
+    if (s) atomicAdd(&totals[v * 256 + threadIdx.x], s);
 }
 
-// Exclusive scan of one view's 256 * nb counts (digit-major) by one block:
-// one warp per digit scans that digit's block counts, then the 256 digit
-// totals are scanned and added back.
+// Exclusive scan, per (view, digit), of the block counts over the blocks:
+// one warp per (view, digit), 32 warps per block.
 __global__ void __launch_bounds__(1024) k_rs_scan(const FrameHeader* __restrict__ hdr, uint32_t* __restrict__ hist, int nb)
 {
-    __shared__ uint32_t tot[256];
-    __shared__ uint32_t dbase[256];
-    if (blockIdx.x >= hdr->n_views) return;
-    uint32_t* h = hist + (size_t)blockIdx.x * 256 * nb;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int d = wid; d < 256; d += nw) {
-        uint32_t* hd = h + (size_t)d * nb;
-        uint32_t carry = 0;
-        for (int k0 = 0; k0 < nb; k0 += 32) {
-            const int k = k0 + lane;
-            const uint32_t c = k < nb ? hd[k] : 0u;
-            uint32_t x = c;
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += y;
-            }
-            if (k < nb) hd[k] = carry + x - c;
-            carry += __shfl_sync(0xffffffffu, x, 31);
+    const int lane = threadIdx.x & 31;
+    const uint32_t vd = blockIdx.x * 32 + (threadIdx.x >> 5);     // view * 256 + digit
+    if (vd >= hdr->n_views * 256u) return;
+    uint32_t* hd = hist + (size_t)vd * nb;
+    uint32_t carry = 0;
+    for (int k0 = 0; k0 < nb; k0 += 32) {
+        const int k = k0 + lane;
+        const uint32_t c = k < nb ? hd[k] : 0u;
+        uint32_t x = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
         }
-        if (lane == 0) tot[d] = carry;
+        if (k < nb) hd[k] = carry + x - c;
+        carry += __shfl_sync(0xffffffffu, x, 31);
     }
-    __syncthreads();
-    if (wid == 0) {
-        uint32_t run = 0;
-        for (int d0 = 0; d0 < 256; d0 += 32) {
-            const uint32_t c = tot[d0 + lane];
-            uint32_t x = c;
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += y;
-            }
-            dbase[d0 + lane] = run + x - c;
-            run += __shfl_sync(0xffffffffu, x, 31);
-        }
-    }
-    __syncthreads();
-    for (int k = threadIdx.x; k < 256 * nb; k += blockDim.x) h[k] += dbase[k / nb];
 }
 
 // Stable scatter of one digit pass; on the last pass also gathers the tile
@@ -123,19 +102,37 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const FrameHeader* __
                                                            const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                            uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                            int64_t n, int nb, int shift, const uint32_t* __restrict__ hist,
+                                                           const uint32_t* __restrict__ totals,
                                                            const uint2* __restrict__ rect, uint2* __restrict__ srect)
 {
     __shared__ uint32_t h[RS_THREADS / 32][256];
     __shared__ uint32_t wb[RS_THREADS / 32][256];
+    __shared__ uint32_t dbase[256];
+    __shared__ uint32_t wsum[RS_THREADS / 32];
     const int b = blockIdx.x, v = b / nb, lb = b % nb;
     if ((uint32_t)v >= hdr->n_views) return;
     const int64_t vbase = (int64_t)v * n;
     const int64_t base = vbase + (int64_t)lb * RS_ITEMS;
     const int cnt = (int)min((int64_t)RS_ITEMS, n - (int64_t)lb * RS_ITEMS);
     rs_warp_counts(kin, base, cnt, shift, h);
+    {
+        // exclusive scan of the view's 256 digit totals (RS_THREADS == 256)
+        const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+        const uint32_t c = totals[v * 256 + threadIdx.x];
+        uint32_t x = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[wi] = x;
+        __syncthreads();
+        uint32_t off = 0;
+        for (int w = 0; w < wi; ++w) off += wsum[w];
+        dbase[threadIdx.x] = off + x - c;
+    }
     __syncthreads();
     {
-        uint32_t run = hist[((size_t)v * 256 + threadIdx.x) * nb + lb];
+        uint32_t run = dbase[threadIdx.x] + hist[((size_t)v * 256 + threadIdx.x) * nb + lb];
         for (int w = 0; w < RS_THREADS / 32; ++w) {
             wb[w][threadIdx.x] = run;
             run += h[w][threadIdx.x];
@@ -179,7 +176,8 @@ __device__ __forceinline__ int find_view_rb(const ViewDev* views, uint32_t V, ui
 // Walk of one warp over the chunk's rectangles for one tile row, in rank
 // order.  A group of 32 consecutive ranks is handled at once: the spans
 // [x0, x1) of the members that cover the row are laid end to end (prefix sum
-// of their widths) and processed 32 slots at a time; slots that fall on the
+// of their widths) and processed 32 slots at a time, each slot finding its
+// member by binary search over the span starts; slots that fall on the
 // same tile are ordered by __match_any_sync, lower slot = lower rank.
 //   EMIT = false: ctr[x] counts the chunk's pairs of tile x.
 //   EMIT = true:  ctr[x] starts at the tile's offset plus the chunk's offset
@@ -195,7 +193,6 @@ __global__ void __launch_bounds__(ROWS_PER_BLOCK * 32) k_rows(Frame F, uint32_t*
     __shared__ uint32_t s_key[STAGE];
     __shared__ uint32_t s_st[ROWS_PER_BLOCK][33];
     __shared__ uint32_t s_x0[ROWS_PER_BLOCK][32];
-    __shared__ uint32_t s_gi[ROWS_PER_BLOCK][32];
     const FrameHeader* hdr = F.hdr;
     if (EMIT && (hdr->status & STATUS_OVERFLOW)) return;
     const uint32_t V = hdr->n_views;
@@ -252,11 +249,11 @@ __global__ void __launch_bounds__(ROWS_PER_BLOCK * 32) k_rows(Frame F, uint32_t*
             if (total == 0) continue;
             s_st[w][lane] = end - wdt;
             s_x0[w][lane] = x0;
-            s_gi[w][lane] = (uint32_t)g;
             __syncwarp();
             for (uint32_t q0 = 0; q0 < total; q0 += 32) {
                 const uint32_t q = q0 + lane;
                 const bool valid = q < total;
+                // owner of slot q: the last member (in rank order) whose span starts at or before q
                 int o = 0;
 #pragma unroll
                 for (int step = 16; step > 0; step >>= 1)
@@ -266,14 +263,14 @@ __global__ void __launch_bounds__(ROWS_PER_BLOCK * 32) k_rows(Frame F, uint32_t*
                 if (valid) {
                     const uint32_t p = ctr[x] + __popc(peers & lt);
                     if (EMIT) {
-                        const uint32_t gi = s_gi[w][o];
+                        const uint32_t gi = (uint32_t)(g0 + o);
                         vals[p] = s_id[gi];
                         if (keys)
                             keys[p] = ((unsigned long long)(W.tile_base + (uint32_t)row * TX + x) << 32) | s_key[gi];
                     }
+                    // the highest peer holds the last slot of this tile: advance the counter past it
+                    if ((31 - __clz(peers)) == lane) ctr[x] = p + 1u;
                 }
-                __syncwarp();
-                if (valid && (__ffs(peers) - 1) == lane) ctr[x] += __popc(peers);
                 __syncwarp();
             }
         }
@@ -421,10 +418,13 @@ void launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long long ca
     const uint32_t V = L.n_views;
     if (n > 0) {
         uint32_t *ki = F.key0, *vi = F.val0, *ko = F.key1, *vo = F.val1;
+        uint32_t* totals = F.rs_hist + (size_t)V * 256 * nb;   // [4 passes][V][256]
+        cudaMemsetAsync(totals, 0, sizeof(uint32_t) * 4 * V * 256, st);
         for (int pass = 0; pass < 4; ++pass) {
-            k_rs_hist<<<V * nb, RS_THREADS, 0, st>>>(F.hdr, ki, n, nb, 8 * pass, F.rs_hist);
-            k_rs_scan<<<V, 1024, 0, st>>>(F.hdr, F.rs_hist, nb);
-            k_rs_scatter<<<V * nb, RS_THREADS, 0, st>>>(F.hdr, ki, vi, ko, vo, n, nb, 8 * pass, F.rs_hist, F.rect,
+            uint32_t* tot = totals + (size_t)pass * V * 256;
+            k_rs_hist<<<V * nb, RS_THREADS, 0, st>>>(F.hdr, ki, n, nb, 8 * pass, F.rs_hist, tot);
+            k_rs_scan<<<(V * 256 + 31) / 32, 1024, 0, st>>>(F.hdr, F.rs_hist, nb);
+            k_rs_scatter<<<V * nb, RS_THREADS, 0, st>>>(F.hdr, ki, vi, ko, vo, n, nb, 8 * pass, F.rs_hist, tot, F.rect,
                                                         pass == 3 ? F.srect : nullptr);
             std::swap(ki, ko);
             std::swap(vi, vo);

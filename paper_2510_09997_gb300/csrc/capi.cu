@@ -88,7 +88,7 @@ FrameLayout frame_layout(uint64_t n, uint32_t V, uint32_t TT, uint32_t rb_total,
     L.key1 = take(sizeof(uint32_t) * vn);
     L.val1 = take(sizeof(uint32_t) * vn);
     L.srect = take(sizeof(uint2) * vn);
-    L.rs_hist = take(sizeof(uint32_t) * 256 * (size_t)V * L.n_rs_blocks);
+    L.rs_hist = take(sizeof(uint32_t) * 256 * (size_t)V * (L.n_rs_blocks + 4));   // counts + 4 passes of totals
     L.cnt = take(sizeof(uint32_t) * (size_t)L.n_chunks * TT);
     L.total = o;
     L.total_tiles = TT;

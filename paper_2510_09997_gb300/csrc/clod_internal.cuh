@@ -21,7 +21,7 @@ constexpr int MAX_VIEWS = 64;
 
 // Depth-rank sort and emission geometry.
 constexpr int RS_THREADS = 256;
-constexpr int RS_ITEMS = 4096;          // keys per radix-sort block (16 per thread)
+constexpr int RS_ITEMS = 2048;          // keys per radix-sort block (8 per thread)
 constexpr int ROWS_PER_BLOCK = 8;       // tile rows per emission block (one warp each)
 constexpr int MAX_CHUNKS = 256;         // rank chunks per view
 constexpr int STAGE = 1024;             // rectangles staged in shared memory at a time

@@ -1,14 +1,13 @@
 // render.cu -- front-to-back alpha blending of every tile (Sec. 3.1, Eq. 1).
 //
-// Persistent blocks of 256 threads (one 16x16 tile, one pixel per thread;
-// each warp an 8x4 patch) take tiles from an atomic queue.  For its tile a
-// block walks the sorted list in batches of 256: each thread gathers one
-// Gaussian's record (u, v, -A/2, -B | -C/2, alpha'', r, g | b) into shared
-// memory and derives a box that holds every pixel the Gaussian can reach with
-// opacity >= 1/255; then every thread blends the batch for its pixel in list
-// order.  A warp whose patch misses a Gaussian's box skips it as a whole --
-// every one of its pixels would skip it anyway, so no result changes.  The
-// block stops once all its pixels are saturated (__syncthreads_count).
+// Persistent blocks of 128 threads take 16x16 tiles from an atomic queue; each
+// warp owns an 8x8 patch (two vertically adjacent pixels per thread) and
+// walks the tile's sorted list independently, 32 entries at a time: every
+// lane gathers one record (u, v, -A/2, -B | -C/2, alpha'', r, g | b) and
+// derives a box that holds every pixel the Gaussian can reach with opacity
+// >= 1/255; the warp blends, in list order, only the entries whose box meets
+// its patch -- every pixel of the patch would skip the others anyway, so no
+// result changes.  A warp stops once its 64 pixels are saturated.
 // Plain FP32/ALU work with one exponential per evaluated pair: no tensor
 // cores.
 #include <algorithm>
@@ -22,11 +21,11 @@ namespace clod {
 // ellipse d^T Q d <= 2|P*| (Q the conic), whose half-extents are
 // sqrt(2|P*| Sigma_xx), sqrt(2|P*| Sigma_yy) with Sigma = Q^-1.  Widened by
 // 0.1% (+0.01 px) so FP32 rounding of the power can never put a reached pixel
-// outside, and by the half-size of the 8x4 patch (3.5, 1.5), so the warp test
-// is |u - patch centre| > extent.  alpha'' < 1/255 reaches no pixel.  For a
+// outside, and by the half-size (hx, hy) of a patch of pixel centres, so the
+// warp test is |u - patch centre| > extent.  alpha'' < 1/255 reaches no pixel.  For a
 // conic so elongated that A C - B^2 loses more than 0.1% of A C to
 // cancellation the box is not trusted: such a Gaussian is never skipped.
-__device__ __forceinline__ float4 reach_box(float4 a, float4 c, float b)
+__device__ __forceinline__ float4 reach_box(float4 a, float4 c, float b, float hx, float hy)
 {
     const float A = -2.0f * a.z, B = -a.w, C = -2.0f * c.x;
     const float det = A * C - B * B;
@@ -38,30 +37,85 @@ __device__ __forceinline__ float4 reach_box(float4 a, float4 c, float b)
     const float r2 = 2.0f * P * 1.001f + 1e-3f;
     const float xe = sqrtf(r2 * (C / det)) * 1.001f + 0.01f;
     const float ye = sqrtf(r2 * (A / det)) * 1.001f + 0.01f;
-    return make_float4(b, xe + 3.5f, ye + 1.5f, 0.0f);
+    return make_float4(b, xe + hx, ye + hy, 0.0f);
 }
 
+// Blend of one pixel against one staged Gaussian (the decision arithmetic of
+// the spec).  Updates T, colour, contributor position; sets done on the stop.
+struct Px {
+    float T, C0, C1, C2;
+    uint32_t last;
+    bool done;
+};
+
 template <bool COUNT>
-__global__ void __launch_bounds__(BLOCK_PIX) k_blend_fwd(Frame F, const uint32_t* __restrict__ vals,
-                                                         const uint32_t* __restrict__ ranges,
-                                                         float* __restrict__ image, float* __restrict__ Tout,
-                                                         uint32_t* __restrict__ ncout,
-                                                         unsigned long long* __restrict__ evaluated)
+__device__ __forceinline__ void blend_one(Px& q, float fpx, float fpy, const float4& a, const float4& c, float cb,
+                                          uint32_t pos, unsigned long long& n_exp, unsigned long long& n_con)
 {
-    __shared__ float4 s0[BLOCK_PIX];
-    __shared__ float4 s1[BLOCK_PIX];
-    __shared__ float4 s2[BLOCK_PIX];   // b, half-extents of the reach box (+ patch half-size)
+    const float ddx = __fsub_rn(a.x, fpx), ddy = __fsub_rn(a.y, fpy);
+    if (COUNT) {
+        const float pw = __fmaf_rn(ddx, __fmaf_rn(a.z, ddx, __fmul_rn(a.w, ddy)), __fmul_rn(__fmul_rn(c.x, ddy), ddy));
+        if (!(pw > 0.0f || pw < -5.6f)) ++n_exp;
+    }
+    const float al = blend_alpha(ddx, ddy, a.z, a.w, c.x, c.y);
+    if (al < 0.0f) return;
+    const float tt = __fmul_rn(q.T, __fsub_rn(1.0f, al));
+    if (tt < 1e-4f) {
+        q.done = true;
+        return;
+    }
+    const float w = __fmul_rn(al, q.T);
+    q.C0 = __fmaf_rn(c.z, w, q.C0);
+    q.C1 = __fmaf_rn(c.w, w, q.C1);
+    q.C2 = __fmaf_rn(cb, w, q.C2);
+    q.T = tt;
+    q.last = pos;
+    if (COUNT) ++n_con;
+}
+
+__device__ __forceinline__ void store_px(const ViewDev& W, const Px& q, int px, int py, float* image, float* Tout,
+                                         uint32_t* ncout)
+{
+    if (px >= W.W || py >= W.H) return;
+    const size_t plane = (size_t)W.W * W.H;
+    const size_t p = (size_t)py * W.W + px;
+    float* img = W.out_img ? W.out_img : image + 3 * W.pix_base;
+    img[p] = __fmaf_rn(q.T, W.bg[0], q.C0);
+    img[plane + p] = __fmaf_rn(q.T, W.bg[1], q.C1);
+    img[2 * plane + p] = __fmaf_rn(q.T, W.bg[2], q.C2);
+    if (W.out_T) W.out_T[p] = q.T;
+    else if (Tout) Tout[W.pix_base + p] = q.T;
+    if (W.out_nc) W.out_nc[p] = q.last;
+    else if (ncout) ncout[W.pix_base + p] = q.last;
+}
+
+constexpr int BLEND_THREADS = 128;   // 4 warps per 16x16 tile, 8x8 pixels per warp, 2 per thread
+
+// Each warp walks the tile's list on its own, 32 entries at a time: every
+// lane gathers one record and tests its reach box against the warp's 8x8
+// patch; the ballot of hits is then blended in list order from per-warp
+// shared slots.  A warp leaves the tile when all its 64 pixels are
+// saturated; the block waits only between tiles.
+template <bool COUNT>
+__global__ void __launch_bounds__(BLEND_THREADS) k_blend_fwd(Frame F, const uint32_t* __restrict__ vals,
+                                                             const uint32_t* __restrict__ ranges,
+                                                             float* __restrict__ image, float* __restrict__ Tout,
+                                                             uint32_t* __restrict__ ncout,
+                                                             unsigned long long* __restrict__ evaluated)
+{
+    __shared__ float4 s0[4][32];
+    __shared__ float4 s1[4][32];
+    __shared__ float s2[4][32];
     __shared__ uint32_t s_tile;
     __shared__ int s_view;
     const FrameHeader* hdr = F.hdr;
     if (hdr->status & STATUS_OVERFLOW) return;
-    // 8x4 patch of this warp inside the tile, lane -> pixel
-    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ox = (wid & 1) * 8 + (lane & 7), oy = (wid >> 1) * 4 + (lane >> 3);
-    const float pcx = (float)((wid & 1) * 8) + 4.0f, pcy = (float)((wid >> 1) * 4) + 2.0f;
     const uint32_t TT = hdr->total_tiles;
     const uint32_t V = hdr->n_views;
     const int64_t n = static_cast<int64_t>(hdr->n);
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ox = (wid & 1) * 8 + (lane & 7), oy = (wid >> 1) * 8 + (lane >> 3) * 2;
+    const float pcx = (float)((wid & 1) * 8) + 4.0f, pcy = (float)((wid >> 1) * 8) + 4.0f;
     unsigned long long evals = 0, n_exp = 0, n_con = 0;
     for (;;) {
         if (threadIdx.x == 0) {
@@ -84,73 +138,55 @@ __global__ void __launch_bounds__(BLOCK_PIX) k_blend_fwd(Frame F, const uint32_t
         const ViewDev& W = F.views[s_view];
         const uint32_t local = t - W.tile_base;
         const int tx = (int)(local % (uint32_t)W.TX), ty = (int)(local / (uint32_t)W.TX);
-        const int px = tx * TILE + ox, py = ty * TILE + oy;
-        const bool inside = px < W.W && py < W.H;
+        const int px = tx * TILE + ox, py0 = ty * TILE + oy, py1 = py0 + 1;
         const float fpx = __fadd_rn(static_cast<float>(px), 0.5f);
-        const float fpy = __fadd_rn(static_cast<float>(py), 0.5f);
+        const float fpy0 = __fadd_rn(static_cast<float>(py0), 0.5f);
+        const float fpy1 = __fadd_rn(static_cast<float>(py1), 0.5f);
         const float wcx = (float)(tx * TILE) + pcx, wcy = (float)(ty * TILE) + pcy;
         const uint32_t start = ranges[2 * t], end = ranges[2 * t + 1];
         const int64_t vn = (int64_t)s_view * n;
-        float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
-        uint32_t last = 0;
-        bool done = !inside;
-        for (uint32_t b = start; b < end; b += BLOCK_PIX) {
-            if (__syncthreads_count(done) == BLOCK_PIX) break;
-            const uint32_t j = b + threadIdx.x;
+        Px q0{1.0f, 0.0f, 0.0f, 0.0f, 0u, !(px < W.W && py0 < W.H)};
+        Px q1{1.0f, 0.0f, 0.0f, 0.0f, 0u, !(px < W.W && py1 < W.H)};
+        for (uint32_t b = start; b < end; b += 32) {
+            if (__all_sync(0xffffffffu, q0.done && q1.done)) break;
+            const uint32_t j = b + lane;
+            bool hit = false;
             if (j < end) {
                 const int64_t g = vn + vals[j];
                 const float4 a = F.rec0[g];
                 const float4 c = F.rec1[g];
-                s0[threadIdx.x] = a;
-                s1[threadIdx.x] = c;
-                s2[threadIdx.x] = reach_box(a, c, F.rec2[g]);
-            }
-            __syncthreads();
-            const int cnt = (int)min((uint32_t)BLOCK_PIX, end - b);
-            if (!done) {
-                for (int k = 0; k < cnt; ++k) {
-                    const float4 a = s0[k];
-                    if (COUNT) ++evals;
-                    else {
-                        const float4 q = s2[k];
-                        if (fabsf(a.x - wcx) > q.y || fabsf(a.y - wcy) > q.z) continue;   // warp-uniform
-                    }
-                    const float4 c = s1[k];
-                    const float ddx = __fsub_rn(a.x, fpx), ddy = __fsub_rn(a.y, fpy);
-                    if (COUNT) {
-                        const float pw = __fmaf_rn(ddx, __fmaf_rn(a.z, ddx, __fmul_rn(a.w, ddy)),
-                                                   __fmul_rn(__fmul_rn(c.x, ddy), ddy));
-                        if (!(pw > 0.0f || pw < -5.6f)) ++n_exp;
-                    }
-                    const float al = blend_alpha(ddx, ddy, a.z, a.w, c.x, c.y);
-                    if (al < 0.0f) continue;
-                    const float tt = __fmul_rn(T, __fsub_rn(1.0f, al));
-                    if (tt < 1e-4f) {
-                        done = true;
-                        break;
-                    }
-                    const float w = __fmul_rn(al, T);
-                    C0 = __fmaf_rn(c.z, w, C0);
-                    C1 = __fmaf_rn(c.w, w, C1);
-                    C2 = __fmaf_rn(s2[k].x, w, C2);
-                    T = tt;
-                    last = b - start + (uint32_t)k + 1u;
-                    if (COUNT) ++n_con;
+                const float cb = F.rec2[g];
+                s0[wid][lane] = a;
+                s1[wid][lane] = c;
+                s2[wid][lane] = cb;
+                if (COUNT) hit = true;
+                else {
+                    const float4 box = reach_box(a, c, cb, 3.5f, 3.5f);
+                    hit = !(fabsf(a.x - wcx) > box.y || fabsf(a.y - wcy) > box.z);
                 }
             }
+            unsigned m = __ballot_sync(0xffffffffu, hit);
+            __syncwarp();
+            while (m) {
+                const int k = __ffs(m) - 1;
+                m &= m - 1;
+                const float4 a = s0[wid][k];
+                const float4 c = s1[wid][k];
+                const float cb = s2[wid][k];
+                const uint32_t pos = b - start + (uint32_t)k + 1u;
+                if (!q0.done) {
+                    if (COUNT) ++evals;
+                    blend_one<COUNT>(q0, fpx, fpy0, a, c, cb, pos, n_exp, n_con);
+                }
+                if (!q1.done) {
+                    if (COUNT) ++evals;
+                    blend_one<COUNT>(q1, fpx, fpy1, a, c, cb, pos, n_exp, n_con);
+                }
+            }
+            __syncwarp();
         }
-        if (inside) {
-            const size_t plane = (size_t)W.W * W.H;
-            const size_t p = (size_t)py * W.W + px;
-            float* img = W.out_img ? W.out_img : image + 3 * W.pix_base;
-            img[p] = __fmaf_rn(T, W.bg[0], C0);
-            img[plane + p] = __fmaf_rn(T, W.bg[1], C1);
-            img[2 * plane + p] = __fmaf_rn(T, W.bg[2], C2);
-            if (W.out_T) W.out_T[p] = T;
-            else if (Tout) Tout[W.pix_base + p] = T;
-            if (W.out_nc) W.out_nc[p] = last;
-            else if (ncout) ncout[W.pix_base + p] = last;
-        }
+        store_px(W, q0, px, py0, image, Tout, ncout);
+        store_px(W, q1, px, py1, image, Tout, ncout);
         __syncthreads();
     }
     if (COUNT) {
@@ -159,7 +195,7 @@ __global__ void __launch_bounds__(BLOCK_PIX) k_blend_fwd(Frame F, const uint32_t
             n_exp += __shfl_xor_sync(0xffffffffu, n_exp, o);
             n_con += __shfl_xor_sync(0xffffffffu, n_con, o);
         }
-        if ((threadIdx.x & 31) == 0) {
+        if (lane == 0) {
             atomicAdd(evaluated, evals);
             atomicAdd(evaluated + 1, n_exp);
             atomicAdd(evaluated + 2, n_con);
@@ -172,7 +208,7 @@ static int g_blend_blocks_per_sm = 0;
 cudaError_t render_setup()
 {
     int b = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_blend_fwd<false>, BLOCK_PIX, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_blend_fwd<false>, BLEND_THREADS, 0);
     if (e != cudaSuccess) return e;
     g_blend_blocks_per_sm = b > 0 ? b : 1;
     return cudaSuccess;
@@ -184,9 +220,9 @@ void launch_blend_fwd(const Frame& F, const uint32_t* vals, const uint32_t* rang
     const int blocks = n_sm * std::max(1, g_blend_blocks_per_sm);
     cudaMemsetAsync(&F.hdr->work[0], 0, sizeof(uint32_t), st);
     if (evaluated)
-        k_blend_fwd<true><<<blocks, BLOCK_PIX, 0, st>>>(F, vals, ranges, image, Tout, ncout, evaluated);
+        k_blend_fwd<true><<<blocks, BLEND_THREADS, 0, st>>>(F, vals, ranges, image, Tout, ncout, evaluated);
     else
-        k_blend_fwd<false><<<blocks, BLOCK_PIX, 0, st>>>(F, vals, ranges, image, Tout, ncout, nullptr);
+        k_blend_fwd<false><<<blocks, BLEND_THREADS, 0, st>>>(F, vals, ranges, image, Tout, ncout, nullptr);
 }
 
 }  // namespace clod

@@ -10,7 +10,8 @@ s_v, and the objective is
     eta_target = s_v^-1.5                                            (Eq. 3)
     eta_actual = sum_i M_i / N_total
 
-L_render is the L1 term (computed by the clod_l1_loss kernel).  eta_actual is a
+L_render = (1 - w) L1 + w D-SSIM (the clod_render_loss kernel; w = 0.2 as in
+the 3DGS training the paper builds on; w = 0 gives L1 alone).  eta_actual is a
 count of the binary mask; its gradient is taken straight through,
 dM_i/dalpha''_i := 1, so every alpha'' receives 2 w_s lambda (s_v - 1)^2
 ReLU(eta_a - eta_t) / N and the rasterizer's backward carries it on to alpha,
@@ -66,15 +67,16 @@ class GaussianModel(torch.nn.Module):
             {"params": [self.sh], "lr": 2.5e-3},
             {"params": [self.decay], "lr": 1e-2},
         ]
-        return torch.optim.Adam(groups, eps=1e-15)
+        return torch.optim.Adam(groups, eps=1e-15, fused=True)
 
 
 class TrainStep:
     """One optimisation step over a batch of views."""
 
     def __init__(self, model: GaussianModel, s_max: float = 16.0, lam_reg: float = 1.0, sampler: str = "log",
-                 seed: int = 0, extent: float = 1.0):
+                 seed: int = 0, extent: float = 1.0, dssim_weight: float = 0.2):
         self.model = model
+        self.dssim = float(dssim_weight)
         self.s_max = float(s_max)
         self.lam = float(lam_reg)
         self.sampler = sampler
@@ -102,7 +104,8 @@ class TrainStep:
         info = []
         cnt = counts.detach().cpu().numpy()
         for k, (v, s) in enumerate(zip(views, scales)):
-            l1 = A.L1Loss.apply(imgs[k], targets[k])
+            l1 = (A.RenderLoss.apply(imgs[k], targets[k], self.dssim) if self.dssim > 0
+                  else A.L1Loss.apply(imgs[k], targets[k]))
             eta_a_count = float(cnt[k, 0]) / N
             # straight-through estimator: value of the count, gradient of sum alpha'' / N
             a_sum = alpha[k].sum()
@@ -111,7 +114,7 @@ class TrainStep:
             l_reg = (s - 1.0) ** 2 * relu * relu
             ws = w_s(s, self.s_max)
             total = total + ws * (l1 + self.lam * l_reg)
-            info.append(dict(s_v=s, l1=float(l1.detach()), l_reg=float(l_reg.detach()), eta_actual=eta_a_count,
+            info.append(dict(s_v=s, l_render=float(l1.detach()), l1=float(l1.detach()), l_reg=float(l_reg.detach()), eta_actual=eta_a_count,
                              eta_target=eta_target(s), w_s=ws, rendered=int(cnt[k, 1])))
         return total / len(views), info
 

@@ -26,7 +26,7 @@ def setup(T, s_max=8.0):
              S.look_at((2.2, 1.0, 1.2), (0, 0, 0), 80, 64)]
     targets = [S.target_image(v.height, v.width, seed=k) for k, v in enumerate(views)]
     model = T.GaussianModel(sc)
-    step = T.TrainStep(model, s_max=s_max, lam_reg=1.0)
+    step = T.TrainStep(model, s_max=s_max, lam_reg=1.0, dssim_weight=0.0)
     return sc, views, targets, model, step
 
 
@@ -74,3 +74,31 @@ def test_short_run_lowers_loss(T):
         total, info = step.step(views, tg, [1.0, 1.0])
         first = total if first is None else first
     assert total < 0.8 * first
+
+
+def test_render_loss_kernel_matches_oracle(T):
+    """L_render = 0.8 L1 + 0.2 D-SSIM (value and gradient) against the FP64
+    oracle, on a ragged image size (tiles and halo borders)."""
+    from oracle import ssim as SS
+    from paper_2510_09997_gb300 import autograd as A
+    rng = np.random.default_rng(70)
+    x = rng.uniform(size=(3, 37, 53)).astype(np.float32)
+    y = rng.uniform(size=(3, 37, 53)).astype(np.float32)
+    xt = torch.tensor(x, device="cuda", requires_grad=True)
+    loss = A.RenderLoss.apply(xt, torch.tensor(y, device="cuda"), 0.2)
+    loss.backward()
+    v, g = SS.render_loss_grad(x.astype(np.float64), y.astype(np.float64), 0.2)
+    assert abs(float(loss) - v) < 1e-5 * abs(v)
+    gg = xt.grad.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(gg - g) / np.linalg.norm(g) < 1e-4
+
+
+def test_training_step_with_dssim(T):
+    sc, views, targets, model, step = setup(T)
+    step.dssim = 0.2
+    tg = [torch.tensor(t, device="cuda") for t in targets]
+    first = None
+    for it in range(20):
+        total, info = step.step(views, tg, [1.0, 1.0])
+        first = total if first is None else first
+    assert total < first

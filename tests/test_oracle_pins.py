@@ -486,3 +486,46 @@ def test_oracle_regression_fixture():
         assert int(len(fr["keys"])) == w["pairs"]
         assert hashlib.sha256(fr["keys"].tobytes()).hexdigest() == w["keys"]
         assert hashlib.sha256(fr["img"][0]["img32"].tobytes()).hexdigest() == w["img32"]
+
+
+# ---------------------------------------------------------------------------
+# D-SSIM term of L_render (Sec. 3.3)
+# ---------------------------------------------------------------------------
+def test_ssim_window_matches_scipy_gaussian_filter():
+    """The 11x11 window (sigma 1.5, zero outside) is SciPy's Gaussian filter
+    truncated at radius 5 with constant padding."""
+    import scipy.ndimage
+    from oracle import ssim as SS
+    img = np.random.default_rng(60).uniform(size=(2, 23, 31))
+    ref = np.stack([scipy.ndimage.gaussian_filter(c, SS.SIGMA, mode="constant", cval=0.0,
+                                                  truncate=SS.RADIUS / SS.SIGMA) for c in img])
+    assert np.abs(SS.blur(img) - ref).max() < 1e-14
+
+
+def test_ssim_closed_forms():
+    from oracle import ssim as SS
+    rng = np.random.default_rng(61)
+    x = rng.uniform(size=(3, 40, 40))
+    assert abs(SS.ssim(x, x) - 1.0) < 1e-12
+    # constant images: zero variance, so S = (2ab + C1) / (a^2 + b^2 + C1) away from the border
+    a, b = 0.3, 0.7
+    S = SS.ssim_map(np.full((1, 40, 40), a), np.full((1, 40, 40), b))
+    assert abs(S[0, 20, 20] - (2 * a * b + SS.C1) / (a * a + b * b + SS.C1)) < 1e-12
+    # SSIM is symmetric and below 1 for different images
+    y = rng.uniform(size=(3, 40, 40))
+    assert abs(SS.ssim(x, y) - SS.ssim(y, x)) < 1e-12 and SS.ssim(x, y) < 0.5
+
+
+def test_render_loss_gradient_central_differences():
+    from oracle import ssim as SS
+    rng = np.random.default_rng(62)
+    x = rng.uniform(size=(2, 14, 17))
+    y = rng.uniform(size=(2, 14, 17))
+    v, g = SS.render_loss_grad(x, y)
+    assert abs(v - SS.render_loss(x, y)) < 1e-12
+    for idx in [(0, 0, 0), (1, 7, 8), (0, 13, 16), (1, 3, 12)]:
+        h = 1e-6
+        xp = x.copy(); xp[idx] += h
+        xm = x.copy(); xm[idx] -= h
+        fd = (SS.render_loss(xp, y) - SS.render_loss(xm, y)) / (2 * h)
+        assert abs(fd - g[idx]) < 1e-6, (idx, fd, g[idx])
