@@ -56,6 +56,9 @@ def parse():
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--train-steps", type=int, default=10)
     p.add_argument("--serve-seconds", type=float, default=2.0)
+    p.add_argument("--no-city", action="store_true")
+    p.add_argument("--leg", default="all", choices=["all", "train", "serve", "city"],
+                   help="train / serve: run only that leg and print its JSON object (for profiling)")
     return p.parse_args()
 
 
@@ -162,6 +165,7 @@ def run_ours(args):
     for k in range(args.warmup):
         step(k)
     torch.cuda.synchronize()
+    fma = fma_peak(C)
     # stage events for the per-kernel roofline
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     L = C.lib()
@@ -232,7 +236,8 @@ def run_ours(args):
     peaks = measured_peaks()
     sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     n_sm = torch.cuda.get_device_properties(0).multi_processor_count
-    fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12          # TFLOP/s at the sampled clock
+    nominal = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12            # TFLOP/s at the sampled clock
+    fp32_peak = fma["tflops"] if fma else nominal
     blend_tflops = flop_per_frame / (st_ms[2] / 1e3) / 1e12
     hbm = measured_peaks().get("hbm_gbs", 6772.2)
     T_pre = stage[:, 0].sum() / 1e3
@@ -259,7 +264,9 @@ def run_ours(args):
                      "peak": round(fp32_peak, 2), "unit": "TFLOP/s", "frac": round(blend_tflops / fp32_peak, 4),
                      "traffic": None, "flop_model": "9 per visited pair + 33 per exp + 9 per contributor",
                      "pairs_per_frame": {"visited": round(cnt3[0]), "exp": round(cnt3[1]), "contrib": round(cnt3[2])},
-                     "peak_basis": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (sampled clock)" % (n_sm, sm_mhz)},
+                     "peak_basis": ("measured: own FMA microbenchmark (clod_probe_fma), %.2f TFLOP/s; nominal %d SMs x "
+                                    "128 lanes x 2 x %.0f MHz = %.2f" % (fp32_peak, n_sm, sm_mhz, nominal))
+                     if fma else "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (sampled clock)" % (n_sm, sm_mhz)},
         "gpu_launches": LAUNCHES_PER_FRAME * args.steps,
         "clocks": clk,
     }
@@ -273,11 +280,34 @@ def run_ours(args):
             torch.cuda.empty_cache()
         if not args.no_serve:
             out["serving"] = serve_leg(args)
+            torch.cuda.empty_cache()
+        if not args.no_city:
+            out["city"] = city_leg(args)
+            out["city"]["blend_fp32_frac"] = round(out["city"]["blend_tflops"] / fp32_peak, 4)
     if rank == 0:
         print(json.dumps(out))
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def fma_peak(C, iters=20000, reps=5):
+    """FP32 peak of this GPU from the library's FMA probe (best of reps)."""
+    import torch
+    sink = torch.zeros(1, dtype=torch.float32, device="cuda")
+    flops = C.ctypes.c_uint64()
+    L = C.lib()
+    best = 0.0
+    for r in range(reps + 1):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        C.check("clod_probe_fma", L.clod_probe_fma(iters, C._ptr(sink), C.ctypes.byref(flops), C._stream(None)))
+        e1.record()
+        torch.cuda.synchronize()
+        if r > 0:
+            best = max(best, flops.value / (e0.elapsed_time(e1) / 1e3) / 1e12)
+    return {"tflops": best, "iters": iters}
 
 
 def e2e_leg(C, ds, R, views, args, stream):
@@ -342,7 +372,7 @@ def train_leg(args):
     cams = S.orbit_cameras(16, WIDTH, HEIGHT, d_min=9.0, d_max=16.0, elev_deg=25.0, seed=2)
     targets = [torch.tensor(S.target_image(HEIGHT, WIDTH, seed=k), device="cuda") for k in range(4)]
     model = T.GaussianModel(sc)
-    step = T.TrainStep(model, s_max=16.0, lam_reg=1.0, seed=0, extent=5.0)
+    step = T.TrainStep(model, s_max=16.0, lam_reg=1.0, seed=0, extent=5.0, dssim_weight=0.0)
 
     def batch(k):
         return [cams[(4 * k + j) % len(cams)] for j in range(4)]
@@ -362,11 +392,84 @@ def train_leg(args):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.train_steps
     rendered = float(np.mean([i["rendered"] for inf in infos for i in inf]))
+    # the same step with the full rendering loss of Sec. 3.3 (0.8 L1 + 0.2 D-SSIM)
+    step.dssim = 0.2
+    for k in range(2):
+        step.step(batch(k), targets)
+    torch.cuda.synchronize()
+    e0.record()
+    for k in range(args.train_steps):
+        step.step(batch(k + 3), targets)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_dssim = e0.elapsed_time(e1) / args.train_steps
     return {"metric": "fwd+bwd training steps/s at 3M Gaussians", "value": round(1e3 / ms, 3), "unit": "steps/s",
             "ms_per_step": round(ms, 3), "steps": args.train_steps, "warmup": 3,
             "workload": "outdoor scene 3M Gaussians SH3 (10x10x4 box), 4 views/step 1920x1080, "
                         "s_v log-uniform [1,16], L1 + L_reg (lambda 1), Adam",
-            "mean_rendered_per_view": round(rendered, 1), "last_loss": round(float(loss), 6)}
+            "mean_rendered_per_view": round(rendered, 1), "last_loss": round(float(loss), 6),
+            "with_dssim": {"value": round(1e3 / ms_dssim, 3), "unit": "steps/s", "ms_per_step": round(ms_dssim, 3),
+                           "loss": "0.8 L1 + 0.2 D-SSIM + L_reg"}}
+
+
+def city_leg(args, steps=5):
+    """Large scene: 6M Gaussians (64 city-block planes + volume noise, SH3),
+    8 views per launch at 3840x2160, s_v in {1, 4, 16, 64} twice.  Culled
+    fraction, per-stage times, sort bytes and blend FP32 rate."""
+    import torch
+    from paper_2510_09997_gb300 import clod as C
+    from paper_2510_09997_gb300 import synth as S
+    sc = S.city_scene()
+    views = S.city_views()
+    V, n = len(views), sc.n
+    ds = C.DeviceScene.from_scene(sc)
+    probe = C.Renderer(ds, views, pair_capacity=1)
+    counts = torch.zeros((V, 2), dtype=torch.int32, device="cuda")
+    C.clod_preprocess(ds, views, probe.ws, counts=counts, n_pairs=probe.npairs)
+    K = int(probe.npairs.item())
+    cnt = counts.cpu().numpy().astype(np.float64)
+    del probe
+    R = C.Renderer(ds, views, pair_capacity=int(K * 1.02) + 1024)
+    for _ in range(2):
+        R.run()
+    torch.cuda.synchronize()
+    L = C.lib()
+    st = C._stream(None)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    for k in range(steps):
+        e = ev[k]
+        e[0].record()
+        C.check("clod_preprocess", L.clod_preprocess(C.ctypes.byref(ds.c), R.carr, V, C._ptr(R.ws), R.ws.numel(),
+                                                     None, None, None, C._ptr(R.npairs), st))
+        e[1].record()
+        C.check("clod_bin_sort", L.clod_bin_sort(C._ptr(R.ws), R.cap, None, C._ptr(R.vals), C._ptr(R.ranges), st))
+        e[2].record()
+        C.check("clod_render_fwd", L.clod_render_fwd(C._ptr(R.ws), C._ptr(R.vals), C._ptr(R.ranges),
+                                                     C._ptr(R.image), C._ptr(R.T), C._ptr(R.nc), st))
+        e[3].record()
+    torch.cuda.synchronize()
+    R.check()
+    stage = np.array([[ev[k][j].elapsed_time(ev[k][j + 1]) for j in range(3)] for k in range(steps)]).mean(0)
+    evals = torch.zeros(3, dtype=torch.int64, device="cuda")
+    C.clod_preprocess(ds, views, R.ws, n_pairs=R.npairs)
+    C.clod_bin_sort(R.ws, R.cap, None, R.vals, R.ranges)
+    C.clod_render_fwd(R.ws, R.vals, R.ranges, R.image, R.T, R.nc, evaluated=evals)
+    e3 = evals.cpu().numpy().astype(np.float64)
+    flop = FLOP_VISIT * e3[0] + FLOP_EXP * e3[1] + FLOP_CONTRIB * e3[2]
+    surv = cnt[:, 1].sum()
+    sort_bytes = 80 * n * V + 24 * surv + 4 * K
+    ms = float(stage.sum())
+    del R, ds
+    torch.cuda.empty_cache()
+    return {"workload": "city block 6M Gaussians SH3, 8 views/launch 3840x2160, s_v in {1,4,16,64} x2",
+            "views_per_s": round(V / (ms / 1e3), 2), "ms_per_launch": round(ms, 3),
+            "stage_ms": {"preprocess": round(float(stage[0]), 3), "bin_sort": round(float(stage[1]), 3),
+                         "blend": round(float(stage[2]), 3)},
+            "culled_fraction": round(1.0 - cnt[:, 0].sum() / (V * n), 4),
+            "culled_fraction_per_view": [round(1.0 - c / n, 4) for c in cnt[:, 0]],
+            "pairs": K, "sort_GB_s": round(sort_bytes / (stage[1] / 1e3) / 1e9, 1),
+            "sort_radix_equivalent_GB_s": round(152 * K / (stage[1] / 1e3) / 1e9, 1),
+            "blend_tflops": round(flop / (stage[2] / 1e3) / 1e12, 3)}
 
 
 def serve_leg(args):
@@ -527,5 +630,11 @@ if __name__ == "__main__":
     a = parse()
     if a.impl == "reference":
         run_reference(a)
+    elif a.leg == "train":
+        print(json.dumps(train_leg(a)))
+    elif a.leg == "serve":
+        print(json.dumps(serve_leg(a)))
+    elif a.leg == "city":
+        print(json.dumps(city_leg(a)))
     else:
         run_ours(a)

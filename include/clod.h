@@ -80,6 +80,24 @@ typedef struct clod_view {
     float eps;              /* epsilon of Eq. 2                                 */
     float bg[3];            /* background colour                                */
     uint32_t flags;         /* CLOD_LOD_OFF | CLOD_NO_NORMALIZE                 */
+    /* Region of a larger frame (regional level of detail, Sec. 4.4: one image
+     * whose vertical bands are rendered at different s_v).  With
+     * full_width > 0 the view is the width x height window at pixel
+     * (region_x, region_y) of a full_width x full_height frame: viewmat,
+     * fx, fy, cx, cy describe the FULL frame; the frustum of Sec. 3.2
+     * (d_max) and the projection are the full frame's, and every output
+     * pixel equals, bit for bit, the same pixel of the full-frame render at
+     * this view's s_v.  region_x and region_y must be multiples of 16 (tile
+     * aligned) and the window must lie inside the frame.  full_width = 0:
+     * the view is a whole frame (region_x, region_y, full_height ignored). */
+    int32_t region_x, region_y;
+    int32_t full_width, full_height;
+    /* Primitive budget (Sec. 4.2: models compared at equal Gaussian counts by
+     * applying the attenuation of Eq. 2 and keeping the primitives of highest
+     * attenuated opacity).  budget > 0 replaces the threshold test: M_i = 1
+     * for the min(budget, n) Gaussians of highest alpha'' (equal alpha'' in
+     * increasing index order), 0 for the rest.  0: M_i = alpha'' > tau s_v. */
+    uint32_t budget;
 } clod_view;
 
 /* Byte offsets of the arrays inside a frame workspace (for inspection). */
@@ -90,7 +108,7 @@ typedef struct clod_frame_layout {
     uint64_t n_survivors;   /* u32 [2 * n_views]: sum M_i, rendered (per view)  */
     uint64_t rec0;          /* float4 [n_views * n]: u, v, -A/2, -B             */
     uint64_t rec1;          /* float4 [n_views * n]: -C/2, alpha'', r, g        */
-    uint64_t rec2;          /* float  [n_views * n]: b                          */
+    uint64_t rec2;          /* float4 [n_views * n]: b, reach half-extents x, y (pixels; -inf: reaches no pixel), 0 */
     uint64_t depth;         /* float  [n_views * n]: camera-space z             */
     uint64_t rect;          /* uint2  [n_views * n]: (x0 | y0 << 16, x1 | y1 << 16), tiles [x0,x1)x[y0,y1) */
     uint64_t tile_count;    /* u32 [total_tiles]                                */
@@ -117,7 +135,9 @@ clod_status clod_frame_workspace_size(int64_t n, const clod_view* views, int32_t
 /* Per-Gaussian preprocessing of every view (Sec. 3.2 and Sec. 3.1):
  *   d_i = |mu_i - c|; d_max = max of d over the view frustum (t_z > near and
  *   projected centre in [0,W]x[0,H]); alpha'' of Eq. 2 with d' = d / d_max;
- *   mask M_i = alpha'' > tau s_v; for survivors (M_i, t_z > near, det > 0,
+ *   mask M_i = alpha'' > tau s_v (or the top-budget selection, see
+ *   clod_view.budget: a radix select of the keys (bits(alpha'') << 32 | ~i)
+ *   over all n Gaussians, six 11/10-bit digit passes); for survivors (M_i, t_z > near, det > 0,
  *   non-empty tile rectangle) the EWA projection (2D covariance + 0.3 I,
  *   its inverse, 3-sigma radius, 16x16-pixel tile rectangle), depth and the
  *   SH colour; per-tile pair counts and their exclusive scan.
@@ -226,6 +246,13 @@ clod_status clod_render_loss_workspace_size(int32_t channels, int32_t height, in
 clod_status clod_render_loss(const float* image, const float* target, int32_t channels, int32_t height,
                              int32_t width, float dssim_weight, void* ws, size_t ws_bytes,
                              float* loss, float* dL_dimage, clod_stream stream);
+
+/* Measurement aid (no counterpart in the paper): launches one full wave of
+ * threads that each run 8 independent chains of `iters` FP32 fused
+ * multiply-adds, so that timing the launch gives this GPU's FP32 peak (the
+ * roofline of the FP32-bound blend).  sink: device f32 [1] (never written in
+ * practice); *flops (host) = the launch's floating-point operations. */
+clod_status clod_probe_fma(int32_t iters, float* sink, uint64_t* flops, clod_stream stream);
 
 /* ------------------------------------------------------------------------ */
 /* Serving: continuous batching over a resident scene                         */

@@ -50,6 +50,7 @@ enum {
     OV_BG = 23,     /* 3: background colour                              */
     OV_W = 26, OV_H = 27,
     OV_FLAGS = 28,  /* bit 0: level of detail off; bit 1: no normalisation */
+    OV_BUDGET = 29, /* primitive budget, the bits of a uint32 (0: threshold mask) */
     OV_SIZE = 32
 };
 #define ORACLE_LOD_OFF 1
@@ -209,6 +210,16 @@ static void cam_point(const float* V, float x, float y, float z, float* t)
         t[k] = fmaf(V[OV_R + 3 * k], x, fmaf(V[OV_R + 3 * k + 1], y, fmaf(V[OV_R + 3 * k + 2], z, V[OV_T + k])));
 }
 
+/* Order of the primitive budget: alpha'' descending, then index ascending. */
+static const float* g_sort_alpha;
+static int budget_cmp(const void* pa, const void* pb)
+{
+    const int64_t a = *(const int64_t*)pa, b = *(const int64_t*)pb;
+    const float xa = g_sort_alpha[a], xb = g_sort_alpha[b];
+    if (xa != xb) return xa > xb ? -1 : 1;
+    return a < b ? -1 : (a > b ? 1 : 0);
+}
+
 /* Stage I for one view.  Inputs are the activated parameters.
  * Outputs (length n unless noted):
  *   dist      camera distance d_i
@@ -217,7 +228,8 @@ static void cam_point(const float* V, float x, float y, float z, float* t)
  *   dmax[0]   max of d over in_view (0 if none); argmax[0] lowest index
  *             attaining it (-1 if none)
  *   alpha_eff attenuated opacity alpha'' (Eq. 2)
- *   mask      M_i = alpha'' > tau * s_v (Sec. 3.2)
+ *   mask      M_i = alpha'' > tau * s_v (Sec. 3.2), or with a primitive
+ *             budget B the B Gaussians of highest alpha'' (Sec. 4.2)
  *   survive   1 if the Gaussian is rasterized: M_i, t_z > near, finite
  *             projection, det > 0, non-empty tile rectangle
  *   rec       REC floats (above) for survivors, zeros otherwise
@@ -264,14 +276,8 @@ void oracle_stage1(int64_t n, int deg, const float* means, const float* scales, 
     const float tany = (0.5f * Hf) / V[OV_FY];
     const float limx = 1.3f * tanx, limy = 1.3f * tany;
 
+    /* --- attenuated opacity, Eq. 2, and the mask M_i ------------------ */
     for (int64_t i = 0; i < n; ++i) {
-        float* R = rec + REC * i;
-        memset(R, 0, sizeof(float) * REC);
-        rect[4 * i] = rect[4 * i + 1] = rect[4 * i + 2] = rect[4 * i + 3] = 0;
-        tiles[i] = 0;
-        survive[i] = 0;
-
-        /* --- attenuated opacity, Eq. 2, and the mask M_i -------------- */
         float a2;
         int M;
         if (flags & ORACLE_LOD_OFF) {
@@ -290,7 +296,32 @@ void oracle_stage1(int64_t n, int deg, const float* means, const float* scales, 
         }
         alpha_eff[i] = a2;
         mask[i] = (uint8_t)M;
-        if (!M) continue;
+    }
+    /* Primitive budget (Sec. 4.2: primitives of highest attenuated opacity):
+     * the mask becomes the first min(budget, n) Gaussians in the order
+     * (alpha'' descending, index ascending). */
+    uint32_t budget;
+    memcpy(&budget, &V[OV_BUDGET], sizeof(budget));
+    if (budget > 0 && n > 0) {
+        int64_t* order = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+        if (order) {
+            for (int64_t i = 0; i < n; ++i) order[i] = i;
+            g_sort_alpha = alpha_eff;
+            qsort(order, (size_t)n, sizeof(int64_t), budget_cmp);
+            for (int64_t i = 0; i < n; ++i) mask[i] = 0;
+            for (int64_t r = 0; r < n && r < (int64_t)budget; ++r) mask[order[r]] = 1;
+            free(order);
+        }
+    }
+
+    for (int64_t i = 0; i < n; ++i) {
+        float* R = rec + REC * i;
+        memset(R, 0, sizeof(float) * REC);
+        rect[4 * i] = rect[4 * i + 1] = rect[4 * i + 2] = rect[4 * i + 3] = 0;
+        tiles[i] = 0;
+        survive[i] = 0;
+        if (!mask[i]) continue;
+        const float a2 = alpha_eff[i];
 
         const float* m = means + 3 * i;
         float t[3];

@@ -110,6 +110,9 @@ def pack_view(v) -> np.ndarray:
     a[23:26] = np.asarray(v.bg, np.float32)
     a[26], a[27] = v.width, v.height
     a[28] = v.flags
+    a[29:30] = np.array([int(getattr(v, "budget", 0))], np.uint32).view(np.float32)
+    if int(getattr(v, "full_width", 0)) > 0:
+        raise ValueError("the oracle renders whole frames; compare a region with the crop of its frame")
     return a
 
 

@@ -32,7 +32,8 @@ class clod_view(ctypes.Structure):
                 ("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
                 ("near_z", ctypes.c_float), ("campos", ctypes.c_float * 3), ("s_v", ctypes.c_float),
                 ("tau", ctypes.c_float), ("eps", ctypes.c_float), ("bg", ctypes.c_float * 3),
-                ("flags", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32), ("region_x", ctypes.c_int32), ("region_y", ctypes.c_int32),
+                ("full_width", ctypes.c_int32), ("full_height", ctypes.c_int32), ("budget", ctypes.c_uint32)]
 
 
 class clod_frame_layout(ctypes.Structure):
@@ -68,6 +69,7 @@ SIGNATURES = {
     "clod_backward_workspace_size": ([ctypes.c_int64, ctypes.c_int32, P], c_status),
     "clod_render_bwd": ([P, P, P, P, P, P, P, P, P, ctypes.c_size_t, P, P, P, P, P, P, P], c_status),
     "clod_l1_loss": ([P, P, ctypes.c_int64, ctypes.c_float, P, P, P], c_status),
+    "clod_probe_fma": ([ctypes.c_int32, P, P, P], c_status),
     "clod_render_loss_workspace_size": ([ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P], c_status),
     "clod_render_loss": ([P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, P, ctypes.c_size_t,
                           P, P, P], c_status),

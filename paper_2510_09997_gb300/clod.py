@@ -89,7 +89,26 @@ def cview(v) -> abi.clod_view:
         c.bg[i] = float(v.bg[i])
     c.s_v, c.tau, c.eps = float(v.s_v), float(v.tau), float(v.eps)
     c.flags = int(v.flags)
+    c.region_x, c.region_y = int(getattr(v, "region_x", 0)), int(getattr(v, "region_y", 0))
+    c.full_width, c.full_height = int(getattr(v, "full_width", 0)), int(getattr(v, "full_height", 0))
+    c.budget = int(getattr(v, "budget", 0))
     return c
+
+
+def band_views(view, x_bounds: Sequence[int], s_values: Sequence[float]) -> list:
+    """Split a full-frame view into vertical bands [x_bounds[k], x_bounds[k+1])
+    rendered at s_values[k] (regional level of detail, Sec. 4.4).  Inner bounds
+    must be multiples of 16; the bands share the full frame's camera, frustum and
+    d_max."""
+    xb = [int(x) for x in x_bounds]
+    if len(xb) != len(s_values) + 1 or xb[0] != 0 or xb[-1] != view.width or any(
+            b <= a for a, b in zip(xb, xb[1:])):
+        raise ValueError("x_bounds must rise from 0 to the view width, one band per s value")
+    out = []
+    for k, s in enumerate(s_values):
+        out.append(view.replace(width=xb[k + 1] - xb[k], region_x=xb[k], region_y=0,
+                                full_width=view.width, full_height=view.height, s_v=float(s)))
+    return out
 
 
 def view_array(views: Sequence) -> ctypes.Array:

@@ -76,22 +76,6 @@ __device__ __forceinline__ float warp_reduce16(float (&v)[16])
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
-// Reach box of a staged Gaussian (same construction as the forward blend's):
-// every pixel centre where the opacity can reach 1/255 lies within
-// (xe, ye) of (u, v); returned widened by the patch half-size.
-__device__ __forceinline__ float2 reach_extent(float4 a, float4 c, float hx, float hy)
-{
-    const float A = -2.0f * a.z, B = -a.w, C = -2.0f * c.x;
-    const float det = A * C - B * B;
-    const float a255 = 255.0f * c.y;
-    if (!(a255 >= 1.0f)) return make_float2(-1.0f, -1.0f);
-    if (!(det > 1e-3f * (A * C)) || !(A > 0.0f) || !(C > 0.0f))
-        return make_float2(__int_as_float(0x7f800000), __int_as_float(0x7f800000));
-    const float P = fminf(5.6f, logf(a255));
-    const float r2 = 2.0f * P * 1.001f + 1e-3f;
-    return make_float2(sqrtf(r2 * (C / det)) * 1.001f + 0.01f + hx, sqrtf(r2 * (A / det)) * 1.001f + 0.01f + hy);
-}
-
 struct BPx {
     float T, d0, d1, d2, S0, S1, S2;
     uint32_t last;
@@ -180,15 +164,15 @@ __global__ void __launch_bounds__(BWD_THREADS) k_blend_bwd(Frame F, const uint32
         const uint32_t local = t - W.tile_base;
         const int tx = (int)(local % (uint32_t)W.TX), ty = (int)(local / (uint32_t)W.TX);
         const int px = tx * TILE + ox;
-        const float fpx = __fadd_rn(static_cast<float>(px), 0.5f);
-        const float wcx = (float)(tx * TILE) + pcx, wcy = (float)(ty * TILE) + pcy;
+        const float fpx = __fadd_rn(static_cast<float>(px + W.ox), 0.5f);
+        const float wcx = (float)(tx * TILE + W.ox) + pcx, wcy = (float)(ty * TILE + W.oy) + pcy;
         const uint32_t start = ranges[2 * t];
         const int64_t vn = (int64_t)s_view * n;
         BPx q[2];
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             const int py = ty * TILE + oy + r;
-            q[r].fy = __fadd_rn(static_cast<float>(py), 0.5f);
+            q[r].fy = __fadd_rn(static_cast<float>(py + W.oy), 0.5f);
             q[r].T = 1.0f;
             q[r].d0 = q[r].d1 = q[r].d2 = q[r].S0 = q[r].S1 = q[r].S2 = 0.0f;
             q[r].last = 0;
@@ -218,10 +202,10 @@ __global__ void __launch_bounds__(BWD_THREADS) k_blend_bwd(Frame F, const uint32
                 const float4 c = F.rec1[g];
                 s0[wid][lane] = a;
                 s1[wid][lane] = c;
-                s2[wid][lane] = F.rec2[g];
+                const float4 e = F.rec2[g];
+                s2[wid][lane] = e.x;
                 sg[wid][lane] = g;
-                const float2 e = reach_extent(a, c, 3.5f, 3.5f);
-                hit = !(fabsf(a.x - wcx) > e.x || fabsf(a.y - wcy) > e.y);
+                hit = !(fabsf(a.x - wcx) > e.y + 3.5f || fabsf(a.y - wcy) > e.z + 3.5f);
             }
             unsigned bm = __ballot_sync(0xffffffffu, hit);
             __syncwarp();
@@ -402,7 +386,7 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(Frame F, clod_scene S, c
                 for (int a_ = 0; a_ < 3; ++a_)
                     for (int b_ = 0; b_ < 3; ++b_)
                         Sg[3 * a_ + b_] = Mm[3 * a_] * Mm[3 * b_] + Mm[3 * a_ + 1] * Mm[3 * b_ + 1] + Mm[3 * a_ + 2] * Mm[3 * b_ + 2];
-                const float limx = 1.3f * (0.5f * (float)W.W / W.fx), limy = 1.3f * (0.5f * (float)W.H / W.fy);
+                const float limx = 1.3f * (0.5f * (float)W.FW / W.fx), limy = 1.3f * (0.5f * (float)W.FH / W.fy);
                 const float txz = tx / tz, tyz = ty / tz;
                 const bool clx = txz < -limx || txz > limx, cly = tyz < -limy || tyz > limy;
                 const float txc = fminf(limx, fmaxf(-limx, txz)) * tz;

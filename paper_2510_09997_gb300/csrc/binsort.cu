@@ -184,15 +184,19 @@ __device__ __forceinline__ int find_view_rb(const ViewDev* views, uint32_t V, ui
 //                 and every slot writes its Gaussian at ctr[x] + (rank among
 //                 the slots of the same tile).
 template <bool EMIT>
-__global__ void __launch_bounds__(ROWS_PER_BLOCK * 32) k_rows(Frame F, uint32_t* __restrict__ vals,
+__global__ void __launch_bounds__(ROWS_PER_BLOCK * 32, 4) k_rows(Frame F, uint32_t* __restrict__ vals,
                                                              unsigned long long* __restrict__ keys)
 {
     extern __shared__ uint32_t sm[];
     __shared__ uint2 s_rect[STAGE];
     __shared__ uint32_t s_id[STAGE];
     __shared__ uint32_t s_key[STAGE];
+    __shared__ uint16_t s_list[STAGE];
+    __shared__ uint32_t s_wc[ROWS_PER_BLOCK];
     __shared__ uint32_t s_st[ROWS_PER_BLOCK][33];
     __shared__ uint32_t s_x0[ROWS_PER_BLOCK][32];
+    __shared__ uint32_t s_gi[ROWS_PER_BLOCK][32];
+    __shared__ uint16_t s_buf[ROWS_PER_BLOCK][64];
     const FrameHeader* hdr = F.hdr;
     if (EMIT && (hdr->status & STATUS_OVERFLOW)) return;
     const uint32_t V = hdr->n_views;
@@ -231,25 +235,86 @@ __global__ void __launch_bounds__(ROWS_PER_BLOCK * 32) k_rows(Frame F, uint32_t*
             }
         }
         __syncthreads();
+        // Order-preserving compaction of the staged rectangles that meet this
+        // block's rows: thread t tests entries [t * per, (t + 1) * per), and
+        // an exclusive scan of the hit counts over the threads places them.
+        int nl;
+        {
+            const int band0 = (int)rb * ROWS_PER_BLOCK, band1 = band0 + ROWS_PER_BLOCK;
+            const int per = (m + (int)blockDim.x - 1) / (int)blockDim.x;
+            const int k0 = (int)threadIdx.x * per;
+            uint32_t hm = 0u;
+            int c = 0;
+            for (int j = 0; j < per; ++j) {
+                const int k = k0 + j;
+                if (k < m) {
+                    const uint2 rc = s_rect[k];
+                    if ((int)(rc.x >> 16) < band1 && (int)(rc.y >> 16) > band0) {
+                        hm |= 1u << j;
+                        ++c;
+                    }
+                }
+            }
+            int x = c;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (lane == 31) s_wc[w] = (uint32_t)x;
+            __syncthreads();
+            int pos = x - c;
+            nl = 0;
+            for (int q = 0; q < ROWS_PER_BLOCK; ++q) {
+                if (q < w) pos += (int)s_wc[q];
+                nl += (int)s_wc[q];
+            }
+            for (int j = 0; hm; ++j, hm >>= 1)
+                if (hm & 1u) s_list[pos++] = (uint16_t)(k0 + j);
+            __syncthreads();
+        }
         if (!row_ok) continue;
-        for (int g0 = 0; g0 < m; g0 += 32) {
-            const int g = g0 + lane;
-            uint2 rc = make_uint2(0u, 0u);
-            if (g < m) rc = s_rect[g];
-            const int y0 = (int)(rc.x >> 16), y1 = (int)(rc.y >> 16);
-            const bool hit = g < m && row >= y0 && row < y1;
+        // Members of this row, in rank order, are gathered 32 at a time in the
+        // warp's buffer; each full group is laid out and emitted.
+        int nb = 0;
+        for (int g0 = 0;; g0 += 32) {
+            if (g0 < nl) {
+                const int g = g0 + lane;
+                uint32_t gi_l = 0u;
+                bool hit = false;
+                if (g < nl) {
+                    gi_l = s_list[g];
+                    const uint2 rc = s_rect[gi_l];
+                    hit = row >= (int)(rc.x >> 16) && row < (int)(rc.y >> 16);
+                }
+                const unsigned hb = __ballot_sync(0xffffffffu, hit);
+                if (hit) s_buf[w][nb + __popc(hb & lt)] = (uint16_t)gi_l;
+                nb += __popc(hb);
+                __syncwarp();
+                if (nb < 32) continue;
+            } else if (nb == 0) {
+                break;   // list done and buffer flushed
+            }
+            // one group: the first min(nb, 32) buffered members (nb < 32 only
+            // for the last group, once the list is done)
+            const int gsz = nb < 32 ? nb : 32;
+            const uint32_t gi_l = lane < gsz ? (uint32_t)s_buf[w][lane] : 0u;
+            const uint2 rc = lane < gsz ? s_rect[gi_l] : make_uint2(0u, 0u);
             const uint32_t x0 = rc.x & 0xFFFFu;
-            const uint32_t wdt = hit ? (rc.y & 0xFFFFu) - x0 : 0u;
+            const uint32_t wdt = lane < gsz ? (rc.y & 0xFFFFu) - x0 : 0u;
             uint32_t end = wdt;
             for (int o = 1; o < 32; o <<= 1) {
                 const uint32_t y = __shfl_up_sync(0xffffffffu, end, o);
                 if (lane >= o) end += y;
             }
             const uint32_t total = __shfl_sync(0xffffffffu, end, 31);
-            if (total == 0) continue;
             s_st[w][lane] = end - wdt;
             s_x0[w][lane] = x0;
+            s_gi[w][lane] = gi_l;
+            // the members beyond the group move to the front of the buffer
+            const uint32_t carry = lane + 32 < nb ? (uint32_t)s_buf[w][lane + 32] : 0u;
             __syncwarp();
+            if (lane + 32 < nb) s_buf[w][lane] = (uint16_t)carry;
+            nb -= gsz;
             for (uint32_t q0 = 0; q0 < total; q0 += 32) {
                 const uint32_t q = q0 + lane;
                 const bool valid = q < total;
@@ -263,7 +328,7 @@ __global__ void __launch_bounds__(ROWS_PER_BLOCK * 32) k_rows(Frame F, uint32_t*
                 if (valid) {
                     const uint32_t p = ctr[x] + __popc(peers & lt);
                     if (EMIT) {
-                        const uint32_t gi = (uint32_t)(g0 + o);
+                        const uint32_t gi = s_gi[w][o];
                         vals[p] = s_id[gi];
                         if (keys)
                             keys[p] = ((unsigned long long)(W.tile_base + (uint32_t)row * TX + x) << 32) | s_key[gi];
@@ -273,6 +338,7 @@ __global__ void __launch_bounds__(ROWS_PER_BLOCK * 32) k_rows(Frame F, uint32_t*
                 }
                 __syncwarp();
             }
+            __syncwarp();
         }
     }
     if (!EMIT && row_ok)

@@ -13,7 +13,7 @@
 namespace clod {
 
 void launch_preprocess(const Frame& F, const clod_scene& S, uint32_t V, uint8_t* mask_out, float* alpha_out,
-                       unsigned long long* n_pairs_out, int n_sm, cudaStream_t st);
+                       unsigned long long* n_pairs_out, int n_sm, cudaStream_t st, bool select);
 void launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long long cap, uint64_t* keys, uint32_t* vals,
                      uint32_t* ranges, cudaStream_t st);
 void launch_blend_fwd(const Frame& F, const uint32_t* vals, const uint32_t* ranges, float* image, float* Tout,
@@ -80,7 +80,7 @@ FrameLayout frame_layout(uint64_t n, uint32_t V, uint32_t TT, uint32_t rb_total,
     const size_t vn = (size_t)V * n;
     L.rec0 = take(sizeof(float4) * vn);
     L.rec1 = take(sizeof(float4) * vn);
-    L.rec2 = take(sizeof(float) * vn);
+    L.rec2 = take(sizeof(float4) * vn);
     L.depth = take(sizeof(float) * vn);
     L.rect = take(sizeof(uint2) * vn);
     L.key0 = take(sizeof(uint32_t) * vn);
@@ -90,6 +90,8 @@ FrameLayout frame_layout(uint64_t n, uint32_t V, uint32_t TT, uint32_t rb_total,
     L.srect = take(sizeof(uint2) * vn);
     L.rs_hist = take(sizeof(uint32_t) * 256 * (size_t)V * (L.n_rs_blocks + 4));   // counts + 4 passes of totals
     L.cnt = take(sizeof(uint32_t) * (size_t)L.n_chunks * TT);
+    L.sel = take(sizeof(SelState) * V);
+    L.sel_hist = take(sizeof(uint32_t) * SEL_BINS * (size_t)V);
     L.total = o;
     L.total_tiles = TT;
     L.n_views = V;
@@ -107,7 +109,7 @@ Frame frame_ptrs(void* ws, const FrameLayout& L)
     F.n_surv = reinterpret_cast<uint32_t*>(b + L.n_surv);
     F.rec0 = reinterpret_cast<float4*>(b + L.rec0);
     F.rec1 = reinterpret_cast<float4*>(b + L.rec1);
-    F.rec2 = reinterpret_cast<float*>(b + L.rec2);
+    F.rec2 = reinterpret_cast<float4*>(b + L.rec2);
     F.depth = reinterpret_cast<float*>(b + L.depth);
     F.rect = reinterpret_cast<uint2*>(b + L.rect);
     F.tile_count = reinterpret_cast<uint32_t*>(b + L.tile_count);
@@ -119,6 +121,8 @@ Frame frame_ptrs(void* ws, const FrameLayout& L)
     F.srect = reinterpret_cast<uint2*>(b + L.srect);
     F.rs_hist = reinterpret_cast<uint32_t*>(b + L.rs_hist);
     F.cnt = reinterpret_cast<uint32_t*>(b + L.cnt);
+    F.sel = reinterpret_cast<SelState*>(b + L.sel);
+    F.sel_hist = reinterpret_cast<uint32_t*>(b + L.sel_hist);
     return F;
 }
 
@@ -160,6 +164,61 @@ struct ViewGeom {
     size_t diff_max;
 };
 
+clod_status check_view(const clod_view& w, int v)
+{
+    if (w.width < 1 || w.height < 1 || w.width > 16384 || w.height > 16384)
+        return fail(CLOD_ERR_ARG, "view %d: size %dx%d outside [1, 16384]", v, w.width, w.height);
+    if (!(w.fx > 0.0f) || !(w.fy > 0.0f)) return fail(CLOD_ERR_ARG, "view %d: focal lengths must be > 0", v);
+    if (!std::isfinite(w.s_v) || !std::isfinite(w.tau) || !(w.eps >= 0.0f))
+        return fail(CLOD_ERR_ARG, "view %d: s_v, tau must be finite and eps >= 0", v);
+    if (w.full_width < 0) return fail(CLOD_ERR_ARG, "view %d: full_width < 0", v);
+    if (w.full_width > 0) {
+        if (w.full_width > 16384 || w.full_height < 1 || w.full_height > 16384)
+            return fail(CLOD_ERR_ARG, "view %d: full frame %dx%d outside [1, 16384]", v, w.full_width, w.full_height);
+        if (w.region_x < 0 || w.region_y < 0 || w.region_x % TILE || w.region_y % TILE)
+            return fail(CLOD_ERR_ARG, "view %d: region origin (%d, %d) must be non-negative multiples of %d", v,
+                        w.region_x, w.region_y, TILE);
+        if ((int64_t)w.region_x + w.width > w.full_width || (int64_t)w.region_y + w.height > w.full_height)
+            return fail(CLOD_ERR_ARG, "view %d: region %dx%d at (%d, %d) leaves the %dx%d frame", v, w.width,
+                        w.height, w.region_x, w.region_y, w.full_width, w.full_height);
+    }
+    return CLOD_OK;
+}
+
+void view_record(const clod_view& w, ViewDev& d)
+{
+    std::memset(&d, 0, sizeof(d));
+    for (int r = 0; r < 3; ++r) {
+        for (int c = 0; c < 3; ++c) d.R[3 * r + c] = w.viewmat[4 * r + c];
+        d.t[r] = w.viewmat[4 * r + 3];
+        d.c[r] = w.campos[r];
+        d.bg[r] = w.bg[r];
+    }
+    d.fx = w.fx;
+    d.fy = w.fy;
+    d.cx = w.cx;
+    d.cy = w.cy;
+    d.near_z = w.near_z;
+    d.s_v = w.s_v;
+    d.tau = w.tau;
+    d.eps = w.eps;
+    d.W = w.width;
+    d.H = w.height;
+    d.TX = (w.width + TILE - 1) / TILE;
+    d.TY = (w.height + TILE - 1) / TILE;
+    if (w.full_width > 0) {
+        d.ox = w.region_x;
+        d.oy = w.region_y;
+        d.FW = w.full_width;
+        d.FH = w.full_height;
+    } else {
+        d.FW = w.width;
+        d.FH = w.height;
+    }
+    d.flags = w.flags;
+    d.budget = w.budget;
+}
+
 static clod_status check_views(const clod_view* views, int32_t V, uint64_t n, ViewGeom* G)
 {
     if (!views) return fail(CLOD_ERR_ARG, "views is NULL");
@@ -167,11 +226,8 @@ static clod_status check_views(const clod_view* views, int32_t V, uint64_t n, Vi
     uint64_t tt = 0, px = 0;
     for (int v = 0; v < V; ++v) {
         const clod_view& w = views[v];
-        if (w.width < 1 || w.height < 1 || w.width > 16384 || w.height > 16384)
-            return fail(CLOD_ERR_ARG, "view %d: size %dx%d outside [1, 16384]", v, w.width, w.height);
-        if (!(w.fx > 0.0f) || !(w.fy > 0.0f)) return fail(CLOD_ERR_ARG, "view %d: focal lengths must be > 0", v);
-        if (!std::isfinite(w.s_v) || !std::isfinite(w.tau) || !(w.eps >= 0.0f))
-            return fail(CLOD_ERR_ARG, "view %d: s_v, tau must be finite and eps >= 0", v);
+        clod_status s = check_view(w, v);
+        if (s) return s;
         tt += (uint64_t)((w.width + TILE - 1) / TILE) * ((w.height + TILE - 1) / TILE);
         px += (uint64_t)w.width * w.height;
     }
@@ -203,26 +259,7 @@ static void make_view_table(const clod_view* views, int32_t V, uint64_t n, std::
     for (int v = 0; v < V; ++v) {
         const clod_view& w = views[v];
         ViewDev& d = out[v];
-        std::memset(&d, 0, sizeof(d));
-        for (int r = 0; r < 3; ++r) {
-            for (int c = 0; c < 3; ++c) d.R[3 * r + c] = w.viewmat[4 * r + c];
-            d.t[r] = w.viewmat[4 * r + 3];
-            d.c[r] = w.campos[r];
-            d.bg[r] = w.bg[r];
-        }
-        d.fx = w.fx;
-        d.fy = w.fy;
-        d.cx = w.cx;
-        d.cy = w.cy;
-        d.near_z = w.near_z;
-        d.s_v = w.s_v;
-        d.tau = w.tau;
-        d.eps = w.eps;
-        d.W = w.width;
-        d.H = w.height;
-        d.TX = (w.width + TILE - 1) / TILE;
-        d.TY = (w.height + TILE - 1) / TILE;
-        d.flags = w.flags;
+        view_record(w, d);
         d.tile_base = tile_base;
         d.pix_base = pix_base;
         d.rb_base = rb_base;
@@ -349,8 +386,10 @@ clod_status clod_preprocess(const clod_scene* scene, const clod_view* views, int
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(F.views, table.data(), sizeof(ViewDev) * n_views, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "clod_preprocess upload");
+    bool select = false;
+    for (int v = 0; v < n_views; ++v) select = select || views[v].budget > 0;
     launch_preprocess(F, *scene, (uint32_t)n_views, mask_out, alpha_eff_out,
-                      reinterpret_cast<unsigned long long*>(n_pairs_out), n_sm, st);
+                      reinterpret_cast<unsigned long long*>(n_pairs_out), n_sm, st, select);
     if (counts_out) {
         e = cudaMemcpyAsync(counts_out, F.n_surv, sizeof(uint32_t) * 2 * n_views, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) return cuda_fail(e, "clod_preprocess counts");

@@ -50,20 +50,33 @@ struct ViewDev {
     float c[3];
     float s_v, tau, eps;
     float bg[3];
-    int32_t W, H, TX, TY;
+    int32_t W, H, TX, TY;   // this view's pixels and tiles (the window of a region view)
+    int32_t ox, oy;         // window origin in the full frame, pixels (multiples of 16)
+    int32_t FW, FH;         // full frame (W, H for a whole-frame view)
     uint32_t flags;
+    uint32_t budget;        // > 0: top-budget mask by alpha''
     uint32_t tile_base;     // global id of this view's first tile
-    uint64_t pix_base;      // first pixel of this view in packed outputs
     uint32_t rb_base;       // first block of this view in the emission grids
-    uint32_t pad;
+    uint64_t pix_base;      // first pixel of this view in packed outputs
     float* out_img;         // optional per-view outputs (else packed at pix_base)
     float* out_T;
     uint32_t* out_nc;
 };
 
+// Radix select of the primitive budget: per-view state and digit counts.
+constexpr int SEL_BINS = 2048;          // 11-bit digits
+constexpr int SEL_PASSES = 6;           // 64-bit keys: 11 + 11 + 10 + 11 + 11 + 10 bits
+struct SelState {
+    unsigned long long T;       // smallest selected key (valid once done)
+    unsigned long long prefix;  // high digits fixed so far
+    uint32_t remaining;         // selections still to make below the prefix
+    uint32_t done;
+    uint32_t pad[2];
+};
+
 struct FrameLayout {
     size_t header, views, dmax_key, n_surv, rec0, rec1, rec2, depth, rect, tile_count, tile_offset,
-        key0, val0, key1, val1, srect, rs_hist, cnt, total;
+        key0, val0, key1, val1, srect, rs_hist, cnt, sel, sel_hist, total;
     uint32_t total_tiles, n_views, n_chunks, n_rs_blocks, rb_total, max_tx;
     uint64_t n;
     size_t diff_grid_max;   // max over views of (TX + 1) (TY + 1)
@@ -77,7 +90,7 @@ struct Frame {
     uint32_t* n_surv;
     float4* rec0;
     float4* rec1;
-    float* rec2;
+    float4* rec2;           // (b, reach half-extents x, y, 0)
     float* depth;
     uint2* rect;
     uint32_t* tile_count;
@@ -89,7 +102,17 @@ struct Frame {
     uint2* srect;           // tile rectangles in depth-rank order
     uint32_t* rs_hist;      // radix-sort digit counts [view][256][block]
     uint32_t* cnt;          // per (view, chunk, tile) pair counts, then offsets
+    SelState* sel;          // primitive-budget select state [view]
+    uint32_t* sel_hist;     // its digit counts [view][SEL_BINS]
 };
+
+// Key of the primitive-budget order: larger key = kept first (alpha''
+// descending, then index ascending).  alpha'' >= 0, so its bits order like
+// its value.
+__device__ __forceinline__ unsigned long long budget_key(float a2, uint32_t i)
+{
+    return (static_cast<unsigned long long>(__float_as_uint(a2)) << 32) | (0xFFFFFFFFu - i);
+}
 
 // ---------------------------------------------------------------------------
 // exp_spec: x = k ln2 + r, k = floor(x * L2E) with L2E = 1/ln2 rounded up to
@@ -150,13 +173,14 @@ __device__ __forceinline__ void project(const ViewDev& V, float tx, float ty, fl
     v = __fmaf_rn(V.fy, __fdiv_rn(ty, tz), V.cy);
 }
 
-// Centre inside the view frustum: t_z > near and (u, v) in [0,W]x[0,H].
+// Centre inside the view frustum: t_z > near and (u, v) in [0,W]x[0,H] of the
+// full frame.
 __device__ __forceinline__ bool in_frustum(const ViewDev& V, float tx, float ty, float tz)
 {
     if (!(tz > V.near_z)) return false;
     float u, v;
     project(V, tx, ty, tz, u, v);
-    return (u >= 0.0f) && (u <= static_cast<float>(V.W)) && (v >= 0.0f) && (v <= static_cast<float>(V.H));
+    return (u >= 0.0f) && (u <= static_cast<float>(V.FW)) && (v >= 0.0f) && (v <= static_cast<float>(V.FH));
 }
 
 // Attenuated opacity of Eq. 2 (dmax = 0 means no Gaussian in the frustum).
@@ -233,6 +257,35 @@ __device__ __forceinline__ float blend_alpha(float dx, float dy, float nA, float
     if (power > 0.0f || power < -5.6f) return -1.0f;
     const float a = fminf(0.99f, __fmul_rn(a2, exp_spec(power)));
     return a < (1.0f / 255.0f) ? -1.0f : a;
+}
+
+// Host: device record of one view (camera, level of detail, region, budget;
+// the packing fields tile_base, rb_base, pix_base and outputs are left 0) and
+// its validation.
+void view_record(const clod_view& w, ViewDev& d);
+clod_status check_view(const clod_view& w, int index);
+
+// Half-extents (x, y) of a box around (u, v) that holds every pixel centre
+// where the blend's opacity can reach 1/255, from the stored record values
+// nA = -A/2, nB = -B, nC = -C/2 and alpha''.  There power >= P* =
+// max(-5.6, -ln(255 alpha'')), i.e. the ellipse d^T Q d <= 2|P*| (Q the
+// conic), whose half-extents are sqrt(2|P*| Sigma_xx), sqrt(2|P*| Sigma_yy)
+// with Sigma = Q^-1; widened by 0.1% (+0.01 px) so FP32 rounding of the power
+// can never put a reached pixel outside.  -inf: reaches no pixel (alpha'' <
+// 1/255).  +inf: a conic so elongated that A C - B^2 loses more than 0.1% of
+// A C to cancellation is not trusted (never skipped).  Only a cull: no
+// decision depends on its rounding.
+__device__ __forceinline__ float2 reach_half_extents(float nA, float nB, float nC, float a2)
+{
+    const float A = -2.0f * nA, B = -nB, C = -2.0f * nC;
+    const float det = A * C - B * B;
+    const float a255 = 255.0f * a2;
+    const float inf = __int_as_float(0x7f800000);
+    if (!(a255 >= 1.0f)) return make_float2(-inf, -inf);
+    if (!(det > 1e-3f * (A * C)) || !(A > 0.0f) || !(C > 0.0f)) return make_float2(inf, inf);
+    const float P = fminf(5.6f, logf(a255));
+    const float r2 = 2.0f * P * 1.001f + 1e-3f;
+    return make_float2(sqrtf(r2 * (C / det)) * 1.001f + 0.01f, sqrtf(r2 * (A / det)) * 1.001f + 0.01f);
 }
 
 // Frame workspace layout (256-byte aligned arrays).

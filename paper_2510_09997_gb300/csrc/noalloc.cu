@@ -24,7 +24,7 @@
 namespace clod {
 
 void launch_preprocess(const Frame& F, const clod_scene& S, uint32_t V, uint8_t* mask_out, float* alpha_out,
-                       unsigned long long* n_pairs_out, int n_sm, cudaStream_t st);
+                       unsigned long long* n_pairs_out, int n_sm, cudaStream_t st, bool select);
 void launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long long cap, uint64_t* keys, uint32_t* vals,
                      uint32_t* ranges, cudaStream_t st);
 void launch_blend_fwd(const Frame& F, const uint32_t* vals, const uint32_t* ranges, float* image, float* Tout,
@@ -86,7 +86,7 @@ extern "C" clod_status clod_render_noalloc(const clod_scene* scene, const clod_v
     if (w.width < 1 || w.height < 1 || w.width > NA_MAX_SIDE || w.height > NA_MAX_SIDE)
         return fail(CLOD_ERR_ARG, "clod_render_noalloc takes views up to %dx%d, got %dx%d", NA_MAX_SIDE, NA_MAX_SIDE,
                     w.width, w.height);
-    if (!(w.fx > 0.0f) || !(w.fy > 0.0f)) return fail(CLOD_ERR_ARG, "focal lengths must be > 0");
+    if (clod_status sv = check_view(w, 0)) return sv;
 
     int n_sm = 0;
     clod_status s = device_ready(&n_sm);
@@ -107,26 +107,7 @@ extern "C" clod_status clod_render_noalloc(const clod_scene* scene, const clod_v
     uint32_t* ranges = reinterpret_cast<uint32_t*>(b + NA_RANGES_OFFSET);
 
     ViewDev vd;
-    std::memset(&vd, 0, sizeof(vd));
-    for (int r = 0; r < 3; ++r) {
-        for (int c = 0; c < 3; ++c) vd.R[3 * r + c] = w.viewmat[4 * r + c];
-        vd.t[r] = w.viewmat[4 * r + 3];
-        vd.c[r] = w.campos[r];
-        vd.bg[r] = w.bg[r];
-    }
-    vd.fx = w.fx;
-    vd.fy = w.fy;
-    vd.cx = w.cx;
-    vd.cy = w.cy;
-    vd.near_z = w.near_z;
-    vd.s_v = w.s_v;
-    vd.tau = w.tau;
-    vd.eps = w.eps;
-    vd.W = w.width;
-    vd.H = w.height;
-    vd.TX = TX;
-    vd.TY = TY;
-    vd.flags = w.flags;
+    view_record(w, vd);
     FrameHeader h;
     std::memset(&h, 0, sizeof(h));
     h.n = n;
@@ -143,7 +124,7 @@ extern "C" clod_status clod_render_noalloc(const clod_scene* scene, const clod_v
     if (e == cudaSuccess) e = cudaMemcpyAsync(F.hdr, &h, sizeof(h), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(F.views, &vd, sizeof(vd), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "clod_render_noalloc upload");
-    launch_preprocess(F, *scene, 1, nullptr, nullptr, nullptr, n_sm, st);
+    launch_preprocess(F, *scene, 1, nullptr, nullptr, nullptr, n_sm, st, w.budget > 0);
     launch_bin_sort(F, L, NA_MAX_PAIRS, nullptr, vals, ranges, st);
     launch_blend_fwd(F, vals, ranges, image, T_final, n_contrib, nullptr, n_sm, st);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "clod_render_noalloc launch");

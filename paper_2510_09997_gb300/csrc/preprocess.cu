@@ -74,18 +74,21 @@ __global__ void __launch_bounds__(256) k_dist_max(Frame F, const float* __restri
     }
 }
 
-// Pass B.
-__global__ void __launch_bounds__(256) k_preprocess(Frame F, clod_scene S, uint8_t* __restrict__ mask_out,
+// Pass B (DEG: the scene's SH degree, so the basis stays in registers).
+template <int DEG>
+__global__ void __launch_bounds__(256, 4) k_preprocess(Frame F, clod_scene S, uint8_t* __restrict__ mask_out,
                                                     float* __restrict__ alpha_out)
 {
     const uint32_t V = F.hdr->n_views;
     __shared__ ViewDev sv[MAX_VIEWS];
     __shared__ float sdmax[MAX_VIEWS];
+    __shared__ unsigned long long sT[MAX_VIEWS];
     __shared__ uint32_t cnt_mask[MAX_VIEWS], cnt_surv[MAX_VIEWS];
     __shared__ unsigned long long s_pairs;
     load_views(sv, F.views, V);
     for (uint32_t v = threadIdx.x; v < V; v += blockDim.x) {
         sdmax[v] = decode_dmax(F.dmax_key[v]);
+        sT[v] = F.sel[v].T;
         cnt_mask[v] = 0;
         cnt_surv[v] = 0;
     }
@@ -93,8 +96,7 @@ __global__ void __launch_bounds__(256) k_preprocess(Frame F, clod_scene S, uint8
     __syncthreads();
     unsigned long long my_pairs = 0ull;
     const int64_t n = S.n;
-    const int deg = S.sh_degree;
-    const int K = (deg + 1) * (deg + 1);
+    constexpr int K = (DEG + 1) * (DEG + 1);
     // block-uniform trip count: every lane reaches the ballots below
     for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = base + threadIdx.x;
@@ -113,11 +115,14 @@ __global__ void __launch_bounds__(256) k_preprocess(Frame F, clod_scene S, uint8
             float e0, e1, e2;
             const float d = cam_dist(W, mx, my, mz, e0, e1, e2);
             const float a2 = attenuated_opacity(W, alpha, sigma, d, sdmax[v]);
-            const bool M = active && ((W.flags & CLOD_LOD_OFF) ? true : (a2 > __fmul_rn(W.s_v, W.tau)));
+            bool M;
+            if (W.budget) M = active && budget_key(a2, static_cast<uint32_t>(i)) >= sT[v];   // top-budget by alpha''
+            else M = active && ((W.flags & CLOD_LOD_OFF) ? true : (a2 > __fmul_rn(W.s_v, W.tau)));
             if (active && alpha_out) alpha_out[o] = a2;
             if (active && mask_out) mask_out[o] = M ? 1 : 0;
             uint2 rect = make_uint2(0u, 0u);
             bool surv = false;
+            uint32_t dkey = 0xFFFFFFFFu;
             if (M) {
                 float tx, ty, tz;
                 cam_point(W, mx, my, mz, tx, ty, tz);
@@ -171,7 +176,7 @@ __global__ void __launch_bounds__(256) k_preprocess(Frame F, clod_scene S, uint8
                             Sg[3 * b + a] = val;
                         }
                     // EWA: cov2D = J W Sigma W^T J^T + 0.3 I
-                    const float Wf = static_cast<float>(W.W), Hf = static_cast<float>(W.H);
+                    const float Wf = static_cast<float>(W.FW), Hf = static_cast<float>(W.FH);
                     const float limx = __fmul_rn(1.3f, __fdiv_rn(__fmul_rn(0.5f, Wf), W.fx));
                     const float limy = __fmul_rn(1.3f, __fdiv_rn(__fmul_rn(0.5f, Hf), W.fy));
                     const float txc = __fmul_rn(fminf(limx, fmaxf(-limx, __fdiv_rn(tx, tz))), tz);
@@ -207,21 +212,27 @@ __global__ void __launch_bounds__(256) k_preprocess(Frame F, clod_scene S, uint8
                         const float fx1 = floorf(__fmul_rn(__fadd_rn(u, rad), 0.0625f));
                         const float fy0 = floorf(__fmul_rn(__fsub_rn(vv, rad), 0.0625f));
                         const float fy1 = floorf(__fmul_rn(__fadd_rn(vv, rad), 0.0625f));
-                        const float TXm = static_cast<float>(W.TX) - 1.0f, TYm = static_cast<float>(W.TY) - 1.0f;
+                        // tile rectangle in the full frame, then within this view's window
+                        const int FTX = (W.FW + TILE - 1) / TILE, FTY = (W.FH + TILE - 1) / TILE;
+                        const float TXm = static_cast<float>(FTX) - 1.0f, TYm = static_cast<float>(FTY) - 1.0f;
+                        const int wx = W.ox / TILE, wy = W.oy / TILE;
+                        int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
                         if (!(fx1 < 0.0f || fx0 > TXm || fy1 < 0.0f || fy0 > TYm)) {
-                            const int x0 = fx0 < 0.0f ? 0 : static_cast<int>(fx0);
-                            const int x1 = fx1 > TXm ? W.TX : static_cast<int>(fx1) + 1;
-                            const int y0 = fy0 < 0.0f ? 0 : static_cast<int>(fy0);
-                            const int y1 = fy1 > TYm ? W.TY : static_cast<int>(fy1) + 1;
+                            x0 = max(fx0 < 0.0f ? 0 : static_cast<int>(fx0), wx) - wx;
+                            x1 = min(fx1 > TXm ? FTX : static_cast<int>(fx1) + 1, wx + W.TX) - wx;
+                            y0 = max(fy0 < 0.0f ? 0 : static_cast<int>(fy0), wy) - wy;
+                            y1 = min(fy1 > TYm ? FTY : static_cast<int>(fy1) + 1, wy + W.TY) - wy;
+                        }
+                        if (x0 < x1 && y0 < y1) {
                             // colour from SH at direction (mu - c) / d
                             const float dx = __fdiv_rn(e0, d), dy = __fdiv_rn(e1, d), dz = __fdiv_rn(e2, d);
                             float bsh[16];
-                            sh_basis(dx, dy, dz, deg, bsh);
+                            sh_basis(dx, dy, dz, DEG, bsh);
                             const float* shp = S.sh + (size_t)i * K * 3;
                             float c0 = __fmul_rn(bsh[0], shp[0]);
                             float c1 = __fmul_rn(bsh[0], shp[1]);
                             float c2 = __fmul_rn(bsh[0], shp[2]);
-                            if (deg == 3) {
+                            if (DEG == 3) {
                                 const float4* s4 = reinterpret_cast<const float4*>(shp);
                                 float sh_r[48];
 #pragma unroll
@@ -239,6 +250,7 @@ __global__ void __launch_bounds__(256) k_preprocess(Frame F, clod_scene S, uint8
                                     c2 = __fmaf_rn(bsh[k], sh_r[3 * k + 2], c2);
                                 }
                             } else {
+#pragma unroll
                                 for (int k = 1; k < K; ++k) {
                                     c0 = __fmaf_rn(bsh[k], shp[3 * k], c0);
                                     c1 = __fmaf_rn(bsh[k], shp[3 * k + 1], c1);
@@ -248,10 +260,13 @@ __global__ void __launch_bounds__(256) k_preprocess(Frame F, clod_scene S, uint8
                             c0 = fmaxf(__fadd_rn(c0, 0.5f), 0.0f);
                             c1 = fmaxf(__fadd_rn(c1, 0.5f), 0.0f);
                             c2 = fmaxf(__fadd_rn(c2, 0.5f), 0.0f);
-                            F.rec0[o] = make_float4(u, vv, __fmul_rn(-0.5f, A), -B);
-                            F.rec1[o] = make_float4(__fmul_rn(-0.5f, C), a2, c0, c1);
-                            F.rec2[o] = c2;
+                            const float nA = __fmul_rn(-0.5f, A), nC = __fmul_rn(-0.5f, C);
+                            const float2 ext = reach_half_extents(nA, -B, nC, a2);
+                            F.rec0[o] = make_float4(u, vv, nA, -B);
+                            F.rec1[o] = make_float4(nC, a2, c0, c1);
+                            F.rec2[o] = make_float4(c2, ext.x, ext.y, 0.0f);
                             F.depth[o] = tz;
+                            dkey = __float_as_uint(tz);
                             rect = make_uint2(static_cast<uint32_t>(x0) | (static_cast<uint32_t>(y0) << 16),
                                               static_cast<uint32_t>(x1) | (static_cast<uint32_t>(y1) << 16));
                             surv = true;
@@ -262,7 +277,7 @@ __global__ void __launch_bounds__(256) k_preprocess(Frame F, clod_scene S, uint8
             }
             if (active) {
                 F.rect[o] = rect;
-                F.key0[o] = surv ? __float_as_uint(F.depth[o]) : 0xFFFFFFFFu;
+                F.key0[o] = dkey;
                 F.val0[o] = static_cast<uint32_t>(i);
             }
             // per-view counts: warp-aggregated, then one shared atomic per warp
@@ -284,15 +299,25 @@ __global__ void __launch_bounds__(256) k_preprocess(Frame F, clod_scene S, uint8
     if (threadIdx.x == 0 && s_pairs) atomicAdd(&F.hdr->n_pairs, s_pairs);
 }
 
+void launch_budget_select(const Frame& F, const clod_scene& S, uint32_t V, int n_sm, cudaStream_t st);
+
+// select: run the primitive-budget select (needed when a view has budget > 0).
 void launch_preprocess(const Frame& F, const clod_scene& S, uint32_t V, uint8_t* mask_out, float* alpha_out,
-                       unsigned long long* n_pairs_out, int n_sm, cudaStream_t st)
+                       unsigned long long* n_pairs_out, int n_sm, cudaStream_t st, bool select)
 {
     const int64_t n = S.n;
     int blocks = static_cast<int>(std::min<int64_t>((n + 255) / 256, (int64_t)n_sm * 8));
     if (blocks < 1) blocks = 1;
-    (void)V;
     if (n > 0) k_dist_max<<<blocks, 256, 0, st>>>(F, S.means, n);
-    if (n > 0) k_preprocess<<<blocks, 256, 0, st>>>(F, S, mask_out, alpha_out);
+    if (n > 0 && select) launch_budget_select(F, S, V, n_sm, st);
+    if (n > 0) {
+        switch (S.sh_degree) {
+        case 0: k_preprocess<0><<<blocks, 256, 0, st>>>(F, S, mask_out, alpha_out); break;
+        case 1: k_preprocess<1><<<blocks, 256, 0, st>>>(F, S, mask_out, alpha_out); break;
+        case 2: k_preprocess<2><<<blocks, 256, 0, st>>>(F, S, mask_out, alpha_out); break;
+        default: k_preprocess<3><<<blocks, 256, 0, st>>>(F, S, mask_out, alpha_out); break;
+        }
+    }
     if (n_pairs_out)
         cudaMemcpyAsync(n_pairs_out, &F.hdr->n_pairs, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st);
 }

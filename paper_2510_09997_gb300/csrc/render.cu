@@ -3,9 +3,10 @@
 // Persistent blocks of 128 threads take 16x16 tiles from an atomic queue; each
 // warp owns an 8x8 patch (two vertically adjacent pixels per thread) and
 // walks the tile's sorted list independently, 32 entries at a time: every
-// lane gathers one record (u, v, -A/2, -B | -C/2, alpha'', r, g | b) and
-// derives a box that holds every pixel the Gaussian can reach with opacity
-// >= 1/255; the warp blends, in list order, only the entries whose box meets
+// lane gathers one record (u, v, -A/2, -B | -C/2, alpha'', r, g | b, reach
+// half-extents) and tests the box that holds every pixel the Gaussian can
+// reach with opacity >= 1/255 (computed once per Gaussian by the
+// preprocessing); the warp blends, in list order, only the entries whose box meets
 // its patch -- every pixel of the patch would skip the others anyway, so no
 // result changes.  A warp stops once its 64 pixels are saturated.
 // Plain FP32/ALU work with one exponential per evaluated pair: no tensor
@@ -15,30 +16,6 @@
 #include "clod_internal.cuh"
 
 namespace clod {
-
-// Box around (u, v) holding every pixel centre where the blend's opacity can
-// reach 1/255: there power >= P* = max(-5.6, -ln(255 alpha'')), i.e. the
-// ellipse d^T Q d <= 2|P*| (Q the conic), whose half-extents are
-// sqrt(2|P*| Sigma_xx), sqrt(2|P*| Sigma_yy) with Sigma = Q^-1.  Widened by
-// 0.1% (+0.01 px) so FP32 rounding of the power can never put a reached pixel
-// outside, and by the half-size (hx, hy) of a patch of pixel centres, so the
-// warp test is |u - patch centre| > extent.  alpha'' < 1/255 reaches no pixel.  For a
-// conic so elongated that A C - B^2 loses more than 0.1% of A C to
-// cancellation the box is not trusted: such a Gaussian is never skipped.
-__device__ __forceinline__ float4 reach_box(float4 a, float4 c, float b, float hx, float hy)
-{
-    const float A = -2.0f * a.z, B = -a.w, C = -2.0f * c.x;
-    const float det = A * C - B * B;
-    const float a255 = 255.0f * c.y;
-    if (!(a255 >= 1.0f)) return make_float4(b, -1.0f, -1.0f, 0.0f);
-    if (!(det > 1e-3f * (A * C)) || !(A > 0.0f) || !(C > 0.0f))
-        return make_float4(b, __int_as_float(0x7f800000), __int_as_float(0x7f800000), 0.0f);
-    const float P = fminf(5.6f, logf(a255));
-    const float r2 = 2.0f * P * 1.001f + 1e-3f;
-    const float xe = sqrtf(r2 * (C / det)) * 1.001f + 0.01f;
-    const float ye = sqrtf(r2 * (A / det)) * 1.001f + 0.01f;
-    return make_float4(b, xe + hx, ye + hy, 0.0f);
-}
 
 // Blend of one pixel against one staged Gaussian (the decision arithmetic of
 // the spec).  Updates T, colour, contributor position; sets done on the stop.
@@ -139,10 +116,11 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_fwd(Frame F, const uint
         const uint32_t local = t - W.tile_base;
         const int tx = (int)(local % (uint32_t)W.TX), ty = (int)(local / (uint32_t)W.TX);
         const int px = tx * TILE + ox, py0 = ty * TILE + oy, py1 = py0 + 1;
-        const float fpx = __fadd_rn(static_cast<float>(px), 0.5f);
-        const float fpy0 = __fadd_rn(static_cast<float>(py0), 0.5f);
-        const float fpy1 = __fadd_rn(static_cast<float>(py1), 0.5f);
-        const float wcx = (float)(tx * TILE) + pcx, wcy = (float)(ty * TILE) + pcy;
+        // pixel centres in full-frame coordinates (a region view is offset by ox, oy)
+        const float fpx = __fadd_rn(static_cast<float>(px + W.ox), 0.5f);
+        const float fpy0 = __fadd_rn(static_cast<float>(py0 + W.oy), 0.5f);
+        const float fpy1 = __fadd_rn(static_cast<float>(py1 + W.oy), 0.5f);
+        const float wcx = (float)(tx * TILE + W.ox) + pcx, wcy = (float)(ty * TILE + W.oy) + pcy;
         const uint32_t start = ranges[2 * t], end = ranges[2 * t + 1];
         const int64_t vn = (int64_t)s_view * n;
         Px q0{1.0f, 0.0f, 0.0f, 0.0f, 0u, !(px < W.W && py0 < W.H)};
@@ -155,15 +133,13 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_fwd(Frame F, const uint
                 const int64_t g = vn + vals[j];
                 const float4 a = F.rec0[g];
                 const float4 c = F.rec1[g];
-                const float cb = F.rec2[g];
+                const float4 e = F.rec2[g];
                 s0[wid][lane] = a;
                 s1[wid][lane] = c;
-                s2[wid][lane] = cb;
+                s2[wid][lane] = e.x;
+                // the reach box (stored by the preprocessing) against the warp's 8x8 patch
                 if (COUNT) hit = true;
-                else {
-                    const float4 box = reach_box(a, c, cb, 3.5f, 3.5f);
-                    hit = !(fabsf(a.x - wcx) > box.y || fabsf(a.y - wcy) > box.z);
-                }
+                else hit = !(fabsf(a.x - wcx) > e.y + 3.5f || fabsf(a.y - wcy) > e.z + 3.5f);
             }
             unsigned m = __ballot_sync(0xffffffffu, hit);
             __syncwarp();

@@ -33,7 +33,7 @@
 namespace clod {
 
 void launch_preprocess(const Frame& F, const clod_scene& S, uint32_t V, uint8_t* mask_out, float* alpha_out,
-                       unsigned long long* n_pairs_out, int n_sm, cudaStream_t st);
+                       unsigned long long* n_pairs_out, int n_sm, cudaStream_t st, bool select);
 void launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long long cap, uint64_t* keys, uint32_t* vals,
                      uint32_t* ranges, cudaStream_t st);
 void launch_blend_fwd(const Frame& F, const uint32_t* vals, const uint32_t* ranges, float* image, float* Tout,
@@ -76,7 +76,8 @@ struct Slot {
     FrameHeader* h_hdr_up = nullptr; // pinned staging
     FrameHeader* h_hdr_down = nullptr;
     uint32_t* h_counts = nullptr;    // pinned: per view sum M, rendered
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph = nullptr;      // batches without a primitive budget
+    cudaGraphExec_t graph_sel = nullptr;  // batches with one (adds the budget select)
     bool busy = false;
     std::vector<uint64_t> tickets;
 };
@@ -112,26 +113,7 @@ static void fill_views(clod_server* S, const std::vector<const Request*>& batch,
     for (size_t v = 0; v < batch.size(); ++v) {
         const clod_view& w = batch[v]->view;
         ViewDev& d = sl.h_views[v];
-        std::memset(&d, 0, sizeof(d));
-        for (int r = 0; r < 3; ++r) {
-            for (int c = 0; c < 3; ++c) d.R[3 * r + c] = w.viewmat[4 * r + c];
-            d.t[r] = w.viewmat[4 * r + 3];
-            d.c[r] = w.campos[r];
-            d.bg[r] = w.bg[r];
-        }
-        d.fx = w.fx;
-        d.fy = w.fy;
-        d.cx = w.cx;
-        d.cy = w.cy;
-        d.near_z = w.near_z;
-        d.s_v = w.s_v;
-        d.tau = w.tau;
-        d.eps = w.eps;
-        d.W = w.width;
-        d.H = w.height;
-        d.TX = (w.width + TILE - 1) / TILE;
-        d.TY = (w.height + TILE - 1) / TILE;
-        d.flags = w.flags;
+        view_record(w, d);
         d.tile_base = tile_base;
         d.rb_base = rb_base;
         d.out_img = batch[v]->out;
@@ -150,14 +132,14 @@ static void fill_views(clod_server* S, const std::vector<const Request*>& batch,
 }
 
 // The launch sequence of one batch on a slot (captured once when graphs are on).
-static void enqueue_batch(clod_server* S, Slot& sl, cudaStream_t st)
+static void enqueue_batch(clod_server* S, Slot& sl, cudaStream_t st, bool select)
 {
     const Frame F = frame_ptrs(sl.ws, sl.L);
     const int V = (int)S->cfg.max_views_per_batch;
     cudaMemsetAsync(sl.ws, 0, sl.L.views, st);
     cudaMemcpyAsync(F.hdr, sl.h_hdr_up, sizeof(FrameHeader), cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(F.views, sl.h_views, sizeof(ViewDev) * V, cudaMemcpyHostToDevice, st);
-    launch_preprocess(F, S->scene, (uint32_t)V, nullptr, nullptr, nullptr, S->n_sm, st);
+    launch_preprocess(F, S->scene, (uint32_t)V, nullptr, nullptr, nullptr, S->n_sm, st, select);
     launch_bin_sort(F, sl.L, S->cfg.pair_capacity, nullptr, sl.vals, sl.ranges, st);
     launch_blend_fwd(F, sl.vals, sl.ranges, nullptr, nullptr, nullptr, nullptr, S->n_sm, st);
     cudaMemcpyAsync(sl.h_hdr_down, F.hdr, sizeof(FrameHeader), cudaMemcpyDeviceToHost, st);
@@ -182,16 +164,18 @@ static clod_status slot_init(clod_server* S, Slot& sl)
     if ((e = cudaMallocHost(&sl.h_counts, sizeof(uint32_t) * 2 * V)) != cudaSuccess) return cuda_fail(e, "pinned counts");
     std::memset(sl.h_views, 0, sizeof(ViewDev) * V);
     if (S->cfg.use_graphs) {
-        // capture the slot's launch sequence once; sizes come from the header at run time
-        cudaGraph_t g = nullptr;
-        e = cudaStreamBeginCapture(sl.stream, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) return cuda_fail(e, "begin capture");
-        enqueue_batch(S, sl, sl.stream);
-        e = cudaStreamEndCapture(sl.stream, &g);
-        if (e != cudaSuccess) return cuda_fail(e, "end capture");
-        e = cudaGraphInstantiate(&sl.graph, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+        // capture the slot's launch sequences once; sizes come from the header at run time
+        for (int sel = 0; sel < 2; ++sel) {
+            cudaGraph_t g = nullptr;
+            e = cudaStreamBeginCapture(sl.stream, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return cuda_fail(e, "begin capture");
+            enqueue_batch(S, sl, sl.stream, sel != 0);
+            e = cudaStreamEndCapture(sl.stream, &g);
+            if (e != cudaSuccess) return cuda_fail(e, "end capture");
+            e = cudaGraphInstantiate(sel ? &sl.graph_sel : &sl.graph, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+        }
     }
     return CLOD_OK;
 }
@@ -199,6 +183,7 @@ static clod_status slot_init(clod_server* S, Slot& sl)
 static void slot_free(Slot& sl)
 {
     if (sl.graph) cudaGraphExecDestroy(sl.graph);
+    if (sl.graph_sel) cudaGraphExecDestroy(sl.graph_sel);
     if (sl.stream) cudaStreamSynchronize(sl.stream);
     cudaFree(sl.ws);
     cudaFree(sl.vals);
@@ -229,7 +214,7 @@ static clod_status render_alone(clod_server* S, Slot& sl, Request& r)
     cudaMemsetAsync(sl.ws, 0, L.views, st);
     cudaMemcpyAsync(F.hdr, &h, sizeof(h), cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(F.views, sl.h_views, sizeof(ViewDev), cudaMemcpyHostToDevice, st);
-    launch_preprocess(F, S->scene, 1, nullptr, nullptr, nullptr, S->n_sm, st);
+    launch_preprocess(F, S->scene, 1, nullptr, nullptr, nullptr, S->n_sm, st, one[0]->view.budget > 0);
     unsigned long long K = 0;
     cudaMemcpyAsync(&K, &F.hdr->n_pairs, sizeof(K), cudaMemcpyDeviceToHost, st);
     cudaError_t e = cudaStreamSynchronize(st);
@@ -332,10 +317,12 @@ static void worker_main(clod_server* S)
                 rw->t_launch = t;
                 rw->batch = (int32_t)batch.size();
             }
+            bool select = false;
+            for (const Request* r : batch) select = select || r->view.budget > 0;
             cudaError_t e;
-            if (sl.graph) e = cudaGraphLaunch(sl.graph, sl.stream);
+            if (sl.graph) e = cudaGraphLaunch(select ? sl.graph_sel : sl.graph, sl.stream);
             else {
-                enqueue_batch(S, sl, sl.stream);
+                enqueue_batch(S, sl, sl.stream, select);
                 e = cudaGetLastError();
             }
             if (e == cudaSuccess) e = cudaEventRecord(sl.ev, sl.stream);
@@ -415,7 +402,7 @@ clod_status clod_serve_submit(clod_server* S, const clod_view* view, float* imag
     if (w.width < 1 || w.height < 1 || w.width > S->cfg.max_width || w.height > S->cfg.max_height)
         return fail(CLOD_ERR_ARG, "view %dx%d outside the server's %dx%d", w.width, w.height, S->cfg.max_width,
                     S->cfg.max_height);
-    if (!(w.fx > 0.0f) || !(w.fy > 0.0f)) return fail(CLOD_ERR_ARG, "focal lengths must be > 0");
+    if (clod_status s = check_view(w, 0)) return s;
     std::lock_guard<std::mutex> lk(S->mu);
     if (S->fatal) return fail(S->fatal, "server stopped after a CUDA error");
     if ((int)S->pending.size() >= S->cfg.queue_capacity) return fail(CLOD_ERR_QUEUE_FULL, "queue full");

@@ -78,6 +78,12 @@ class View:
     near: float = 0.2
     bg: Sequence[float] = (0.0, 0.0, 0.0)
     flags: int = 0
+    # window of a larger frame (full_width > 0): the camera fields describe the full frame
+    region_x: int = 0
+    region_y: int = 0
+    full_width: int = 0
+    full_height: int = 0
+    budget: int = 0        # > 0: keep the `budget` Gaussians of highest alpha'' instead of the tau s_v test
 
     def replace(self, **kw) -> "View":
         return dataclasses.replace(self, **kw)
@@ -211,6 +217,20 @@ def city_scene(n: int = 6_000_000, seed: int = 5, sh_degree: int = 3, n_planes: 
     rng.shuffle(pts)
     means = pts.astype(np.float32)
     return Scene(means, *_attributes(rng, n, sh_degree))
+
+
+def city_views(width: int = 3840, height: int = 2160, scales=(1.0, 4.0, 16.0, 64.0, 1.0, 4.0, 16.0, 64.0),
+               seed: int = 55) -> List[View]:
+    """Cameras around the city block: azimuth uniform, distance U[40, 90],
+    height U[15, 45], looking at a jittered point 10 up; one view per scale."""
+    rng = np.random.default_rng(seed)
+    views = []
+    for s in scales:
+        ang = rng.uniform(0, 2 * np.pi)
+        d = rng.uniform(40.0, 90.0)
+        eye = (d * np.cos(ang), d * np.sin(ang), rng.uniform(15.0, 45.0))
+        views.append(look_at(eye, (rng.normal(0, 5), rng.normal(0, 5), 10.0), width, height, s_v=float(s)))
+    return views
 
 
 def small_scene(n: int = 200, seed: int = 3, sh_degree: int = 3, extent: float = 0.6,

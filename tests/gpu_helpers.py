@@ -15,7 +15,7 @@ def frame_stage1(fr, n):
     V = len(fr.views)
     rec0 = fr.ws_array("rec0", torch.float32, 4 * V * n).view(V, n, 4).cpu().numpy()
     rec1 = fr.ws_array("rec1", torch.float32, 4 * V * n).view(V, n, 4).cpu().numpy()
-    rec2 = fr.ws_array("rec2", torch.float32, V * n).view(V, n).cpu().numpy()
+    rec2 = fr.ws_array("rec2", torch.float32, 4 * V * n).view(V, n, 4)[:, :, 0].cpu().numpy()
     depth = fr.ws_array("depth", torch.float32, V * n).view(V, n).cpu().numpy()
     rect = fr.ws_array("rect", torch.int32, 2 * V * n).view(V, n, 2).cpu().numpy().view(np.uint32)
     key = fr.ws_array("dmax_key", torch.int64, V).cpu().numpy().view(np.uint64)
@@ -77,3 +77,23 @@ def assert_image_matches(fr, v, ref, tiles=None, tol64=2e-4):
         assert err <= tol64, err
         return err
     return 0.0
+
+
+def run_and_compare(C, scene, views, tiles=None, with64=True):
+    """Render ``views`` through the C ABI and compare Stage I, the sorted pairs,
+    the ranges and the images with the oracle."""
+    ds = C.DeviceScene.from_scene(scene)
+    fr = C.render(ds, views)
+    torch.cuda.synchronize()
+    ref = O.frame(scene, views, with64=with64, tiles=tiles)
+    g = frame_stage1(fr, scene.n)
+    for v in range(len(views)):
+        assert_stage1_equal(g[v], ref["s1"][v])
+    assert fr.n_pairs == len(ref["keys"])
+    assert np.array_equal(fr.keys.cpu().numpy().view(np.uint64), ref["keys"])
+    assert np.array_equal(fr.vals.cpu().numpy().view(np.uint32), ref["vals"])
+    assert np.array_equal(fr.ranges.cpu().numpy().view(np.uint32), ref["ranges"])
+    errs = []
+    for v in range(len(views)):
+        errs.append(assert_image_matches(fr, v, ref["img"][v], None if tiles is None else tiles[v]))
+    return fr, ref, errs

@@ -49,3 +49,23 @@ def test_validation_without_gpu(L):
     assert L.clod_preprocess(None, views, 1, None, 0, None, None, None, None, None) == abi.CLOD_ERR_ARG
     assert L.clod_bin_sort(None, 0, None, None, None, None) == abi.CLOD_ERR_ARG
     assert L.clod_backward_workspace_size(5, 0, ctypes.byref(nbytes)) == abi.CLOD_ERR_ARG
+
+
+def test_region_view_validation_without_gpu(L):
+    """Regional views: tile-aligned origins inside the full frame only."""
+    from paper_2510_09997_gb300 import abi, clod, synth as S
+    nbytes = ctypes.c_size_t()
+    full = S.look_at((2.5, -1.0, 1.0), (0, 0, 0), 250, 130)
+    good = clod.band_views(full, [0, 64, 128, 176, 250], [8.0, 4.0, 2.0, 1.0])
+    assert [b.width for b in good] == [64, 64, 48, 74]
+    assert L.clod_frame_workspace_size(100, clod.view_array(good), 4, ctypes.byref(nbytes), None) == abi.CLOD_OK
+    for bad in (good[1].replace(region_x=40),                  # not a multiple of 16
+                good[3].replace(width=90),                      # leaves the frame
+                good[0].replace(region_y=-16),
+                good[0].replace(full_height=0)):
+        assert L.clod_frame_workspace_size(100, clod.view_array([bad]), 1, ctypes.byref(nbytes),
+                                           None) == abi.CLOD_ERR_ARG
+        assert b"view 0" in L.clod_last_error()
+    with pytest.raises(ValueError):
+        clod.band_views(full, [0, 64, 250], [1.0])
+    assert ctypes.sizeof(abi.clod_view) == 136

@@ -12,7 +12,7 @@ import torch
 from oracle import oracle as O
 from paper_2510_09997_gb300 import synth as S
 
-from gpu_helpers import assert_image_matches, assert_stage1_equal, frame_stage1
+from gpu_helpers import assert_image_matches, assert_stage1_equal, frame_stage1, run_and_compare
 
 pytestmark = pytest.mark.gpu
 
@@ -22,24 +22,6 @@ def C():
     from paper_2510_09997_gb300 import clod
     clod.require_cuda()
     return clod
-
-
-def run_and_compare(C, scene, views, tiles=None, with64=True):
-    ds = C.DeviceScene.from_scene(scene)
-    fr = C.render(ds, views)
-    torch.cuda.synchronize()
-    ref = O.frame(scene, views, with64=with64, tiles=tiles)
-    g = frame_stage1(fr, scene.n)
-    for v in range(len(views)):
-        assert_stage1_equal(g[v], ref["s1"][v])
-    assert fr.n_pairs == len(ref["keys"])
-    assert np.array_equal(fr.keys.cpu().numpy().view(np.uint64), ref["keys"])
-    assert np.array_equal(fr.vals.cpu().numpy().view(np.uint32), ref["vals"])
-    assert np.array_equal(fr.ranges.cpu().numpy().view(np.uint32), ref["ranges"])
-    errs = []
-    for v in range(len(views)):
-        errs.append(assert_image_matches(fr, v, ref["img"][v], None if tiles is None else tiles[v]))
-    return fr, ref, errs
 
 
 @pytest.mark.parametrize("s", [1.0, 4.0])

@@ -25,13 +25,7 @@ def city():
     from paper_2510_09997_gb300 import clod as C
     C.require_cuda()
     sc = S.city_scene()
-    rng = np.random.default_rng(55)
-    views = []
-    for k, s in enumerate((1.0, 4.0, 16.0, 64.0, 1.0, 4.0, 16.0, 64.0)):
-        ang = rng.uniform(0, 2 * np.pi)
-        d = rng.uniform(40.0, 90.0)
-        eye = (d * np.cos(ang), d * np.sin(ang), rng.uniform(15.0, 45.0))
-        views.append(S.look_at(eye, (rng.normal(0, 5), rng.normal(0, 5), 10.0), 3840, 2160, s_v=s))
+    views = S.city_views()
     ds = C.DeviceScene.from_scene(sc)
     fr = C.render(ds, views, want_keys=False)
     torch.cuda.synchronize()

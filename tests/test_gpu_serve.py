@@ -1,5 +1,6 @@
 """Continuous-batching server (clod_server_*): every request's image equals the
-same view rendered alone, whatever batch it lands in; graphs on and off agree;
+same view rendered alone, whatever batch it lands in (requests include
+primitive budgets and windows of a frame); graphs on and off agree;
 batches that overflow the slot's pair buffer are re-run and still correct;
 requests arriving while batches are in flight are admitted."""
 import time
@@ -29,7 +30,12 @@ def env():
         dirv = rng.normal(size=3)
         dirv /= np.linalg.norm(dirv)
         s = float(np.float32(np.exp(rng.uniform(0, np.log(8)))))
-        views.append(S.look_at(d * dirv, (0, 0, 0), w, h, s_v=s, bg=(0.1, 0.2, 0.3)))
+        v = S.look_at(d * dirv, (0, 0, 0), w, h, s_v=s, bg=(0.1, 0.2, 0.3))
+        if k % 5 == 4:      # primitive budget
+            v = v.replace(budget=1500 + 300 * k)
+        if k % 7 == 3:      # a window of the frame
+            v = v.replace(width=w - 16, height=h - 32, region_x=16, region_y=16, full_width=w, full_height=h)
+        views.append(v)
     solo = []
     for v in views:
         fr = C.render(ds, [v], want_keys=False)

@@ -529,3 +529,49 @@ def test_render_loss_gradient_central_differences():
         xm = x.copy(); xm[idx] -= h
         fd = (SS.render_loss(xp, y) - SS.render_loss(xm, y)) / (2 * h)
         assert abs(fd - g[idx]) < 1e-6, (idx, fd, g[idx])
+
+
+# ---------------------------------------------------------------------------
+# Primitive budget (Sec. 4.2: keep the primitives of highest alpha'')
+# ---------------------------------------------------------------------------
+def test_budget_threshold_equivalence():
+    """The threshold mask alpha'' > tau s_v keeps exactly the top-|M| set by
+    alpha'' (every kept alpha'' exceeds every dropped one), so a budget equal
+    to |M| reproduces Stage I bit for bit."""
+    sc = S.tiny_scene(n=5000, seed=70)
+    for s in (2.0, 6.0):
+        thr = O.stage1(sc, S.tiny_view(s))
+        B = int(thr["mask"].sum())
+        assert 0 < B < sc.n
+        bud = O.stage1(sc, S.tiny_view(s, budget=B))
+        for k in ("alpha_eff", "mask", "survive", "rec", "rect", "tiles"):
+            assert np.array_equal(thr[k], bud[k]), k
+
+
+def test_budget_selects_top_alpha_by_brute_force():
+    """Exactly min(B, n) Gaussians kept: the first B of (alpha'' descending,
+    index ascending), checked against a NumPy lexicographic order."""
+    sc = S.tiny_scene(n=3000, seed=71)
+    for B in (1, 17, 1000, 2999, 3000, 5000):
+        s1 = O.stage1(sc, S.tiny_view(3.0, budget=B))
+        order = np.lexsort((np.arange(sc.n), -s1["alpha_eff"].astype(np.float64)))
+        ref = np.zeros(sc.n, np.uint8)
+        ref[order[:B]] = 1
+        assert np.array_equal(s1["mask"], ref), B
+        assert int(s1["mask"].sum()) == min(B, sc.n)
+
+
+def test_budget_ties_go_to_lower_indices():
+    """Equal alpha'' (level of detail off, one opacity for all): the budget keeps
+    the lowest indices."""
+    sc = S.tiny_scene(n=2000, seed=72)
+    sc = S.Scene(sc.means, sc.scales, sc.quats, np.full(sc.n, 0.5, np.float32), sc.sh, sc.decay)
+    s1 = O.stage1(sc, S.tiny_view(4.0, flags=O.LOD_OFF, budget=123))
+    assert np.array_equal(np.flatnonzero(s1["mask"]), np.arange(123))
+    # mixed: two opacity levels, ties inside each level by index
+    op = np.where(np.arange(sc.n) % 3 == 0, 0.9, 0.5).astype(np.float32)
+    sc2 = S.Scene(sc.means, sc.scales, sc.quats, op, sc.sh, sc.decay)
+    s2 = O.stage1(sc2, S.tiny_view(4.0, flags=O.LOD_OFF, budget=800))
+    hi = np.flatnonzero(op == np.float32(0.9))
+    lo = np.flatnonzero(op == np.float32(0.5))
+    assert np.array_equal(np.flatnonzero(s2["mask"]), np.sort(np.concatenate([hi, lo[:800 - hi.size]])))
