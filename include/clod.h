@@ -217,12 +217,15 @@ clod_status clod_backward_workspace_size(int64_t n, int32_t n_views, size_t* byt
  * through d_i and through d_max = d_{j*}, j* the lowest-index farthest
  * Gaussian in the view frustum).
  * T_final, n_contrib: the forward's packed outputs.  dL_dimage: packed like
- * the image.  dL_dalpha_eff: f32 [n_views * n] or NULL.
+ * the image.  dL_dalpha_eff: f32 [n_views * n] or NULL.  dL_dalpha_view:
+ * f32 [n_views] or NULL, one external dL/d(alpha'') shared by every Gaussian
+ * of a view (the straight-through gradient is such a constant; added to
+ * dL_dalpha_eff when both are given).
  * Outputs are ACCUMULATED (+=): dmeans n x 3, dscales n x 3, dquats n x 4,
  * dopacity n, dsh n x (deg+1)^2 x 3, ddecay n. */
 clod_status clod_render_bwd(const clod_scene* scene, const void* ws, const uint32_t* vals,
                             const uint32_t* ranges, const float* T_final, const uint32_t* n_contrib,
-                            const float* dL_dimage, const float* dL_dalpha_eff,
+                            const float* dL_dimage, const float* dL_dalpha_eff, const float* dL_dalpha_view,
                             void* bwd_ws, size_t bwd_ws_bytes,
                             float* dmeans, float* dscales, float* dquats, float* dopacity,
                             float* dsh, float* ddecay, clod_stream stream);
@@ -240,12 +243,51 @@ clod_status clod_render_loss_workspace_size(int32_t channels, int32_t height, in
  * w = dssim_weight in [0, 1] (0.2 in the 3DGS training the paper builds on).
  * SSIM: 11x11 Gaussian window (sigma 1.5, zero outside the image),
  * C1 = 0.01^2, C2 = 0.03^2, mean over pixels and channels.  image, target:
- * device f32 channels x height x width.  *loss (device f32) += L_render;
- * dL_dimage (may be NULL) = dL_render/dimage, which needs ws (device, size
- * from clod_render_loss_workspace_size). */
+ * device f32 channels x height x width.  *loss (device f32, may be NULL) +=
+ * L_render; dL_dimage (may be NULL) = grad_scale * dL_render/dimage (the
+ * factor of this term in the caller's total), which for w > 0 needs ws
+ * (device, size from clod_render_loss_workspace_size; w = 0 needs none). */
 clod_status clod_render_loss(const float* image, const float* target, int32_t channels, int32_t height,
-                             int32_t width, float dssim_weight, void* ws, size_t ws_bytes,
+                             int32_t width, float dssim_weight, float grad_scale, void* ws, size_t ws_bytes,
                              float* loss, float* dL_dimage, clod_stream stream);
+
+/* Point-count regulariser and total objective of the training step
+ * (Sec. 3.3, Eq. 3-5), on the device, for n_views views of one step:
+ *   eta_actual_v = counts[2v] / n (the mask counts of clod_preprocess),
+ *   L_reg_v = (s_v - 1)^2 ReLU(eta_actual_v - s_v^-1.5)^2,
+ *   *total = sum_v weight_v (lrender_v + lambda_reg L_reg_v)   (written),
+ *   dL_dalpha_view[v] = weight_v lambda_reg 2 (s_v - 1)^2 ReLU(.) / n,
+ * the straight-through gradient (dM_i/dalpha''_i := 1) for clod_render_bwd.
+ * weight_v = w_s(s_v) / n_views for Eq. 5 averaged over the step's views.
+ * counts: device u32 [2 n_views].  s_v, weight: host f32 [n_views].
+ * lrender: device f32 [n_views] or NULL (0).  dL_dalpha_view, total,
+ * lreg_out (device f32 [n_views]): each may be NULL. */
+clod_status clod_lreg_grad(const uint32_t* counts, int64_t n, int32_t n_views, const float* s_v,
+                           const float* weight, float lambda_reg, const float* lrender,
+                           float* dL_dalpha_view, float* total, float* lreg_out, clod_stream stream);
+
+/* Adam (beta1, beta2, eps; bias-corrected, no weight decay) over the six
+ * parameter groups, learning rate per group: means, log-scales, quaternions,
+ * opacity logits, SH, sigma_d (Sec. 4.1 gives sigma_d 1e-2). */
+typedef struct clod_adam_cfg {
+    float lr[6];
+    float beta1, beta2, eps;
+    int32_t step;           /* t >= 1 */
+} clod_adam_cfg;
+
+/* One Adam step fused with the activations.  raw: host array of 6 device
+ * pointers, the raw parameters (means n x 3, log-scales n x 3, quats n x 4,
+ * opacity logits n, sh n x (deg+1)^2 x 3, sigma_d n), updated in place.
+ * grads: host array of 6 device pointers, the gradients with respect to the
+ * ACTIVATED parameters (clod_render_bwd's outputs); the log-scale and logit
+ * gradients are formed inside (times scale, times a (1 - a)); all six are
+ * zeroed afterwards.  scales, opacity: the activated copies the rasterizer
+ * reads (exp(log-scale), sigmoid(logit)), read for the chain rule and
+ * rewritten from the updated raw values.  m, v: device f32 moments of
+ * n (14 + 3 (deg+1)^2) elements each, the six groups in the order above. */
+clod_status clod_adam_step(const clod_adam_cfg* cfg, int64_t n, int32_t sh_degree, float* const* raw,
+                           float* const* grads, float* scales, float* opacity, float* m, float* v,
+                           clod_stream stream);
 
 /* Measurement aid (no counterpart in the paper): launches one full wave of
  * threads that each run 8 independent chains of `iters` FP32 fused

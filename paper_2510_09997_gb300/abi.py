@@ -50,6 +50,11 @@ class clod_server_cfg(ctypes.Structure):
                 ("max_height", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class clod_adam_cfg(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float * 6), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("step", ctypes.c_int32)]
+
+
 class clod_req_stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("batch_size", ctypes.c_int32), ("submit_us", ctypes.c_double),
                 ("launch_us", ctypes.c_double), ("done_us", ctypes.c_double), ("n_rendered", ctypes.c_uint32),
@@ -67,12 +72,14 @@ SIGNATURES = {
     "clod_frame_check": ([P, ctypes.c_uint64, P, P], c_status),
     # backward
     "clod_backward_workspace_size": ([ctypes.c_int64, ctypes.c_int32, P], c_status),
-    "clod_render_bwd": ([P, P, P, P, P, P, P, P, P, ctypes.c_size_t, P, P, P, P, P, P, P], c_status),
+    "clod_render_bwd": ([P, P, P, P, P, P, P, P, P, P, ctypes.c_size_t, P, P, P, P, P, P, P], c_status),
     "clod_l1_loss": ([P, P, ctypes.c_int64, ctypes.c_float, P, P, P], c_status),
     "clod_probe_fma": ([ctypes.c_int32, P, P, P], c_status),
     "clod_render_loss_workspace_size": ([ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P], c_status),
-    "clod_render_loss": ([P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, P, ctypes.c_size_t,
-                          P, P, P], c_status),
+    "clod_render_loss": ([P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_float, P,
+                          ctypes.c_size_t, P, P, P], c_status),
+    "clod_lreg_grad": ([P, ctypes.c_int64, ctypes.c_int32, P, P, ctypes.c_float, P, P, P, P, P], c_status),
+    "clod_adam_step": ([P, ctypes.c_int64, ctypes.c_int32, P, P, P, P, P, P, P], c_status),
     "clod_render_noalloc": ([P, P, P, P, P, P], c_status),
     # serving
     "clod_server_create": ([P, P, P], c_status),

@@ -58,7 +58,7 @@ class CLoDRender(torch.autograd.Function):
         ga = g_alpha.contiguous() if g_alpha is not None else None
         C.check("clod_render_bwd", C.lib().clod_render_bwd(
             ctypes.byref(sc.c), C._ptr(fr.ws), C._ptr(fr.vals), C._ptr(fr.ranges), C._ptr(fr.T_final),
-            C._ptr(fr.n_contrib), C._ptr(gi), C._ptr(ga), C._ptr(bws), bws.numel(),
+            C._ptr(fr.n_contrib), C._ptr(gi), C._ptr(ga), None, C._ptr(bws), bws.numel(),
             *[C._ptr(g) for g in grads], C._stream(None)))
         return (*grads, None)
 
@@ -109,7 +109,7 @@ class RenderLoss(torch.autograd.Function):
         C.check("clod_render_loss_workspace_size", C.lib().clod_render_loss_workspace_size(Cc, H, W, ctypes.byref(nb)))
         ws = torch.empty(int(nb.value), dtype=torch.uint8, device=image.device)
         C.check("clod_render_loss", C.lib().clod_render_loss(C._ptr(image), C._ptr(target), Cc, H, W,
-                                                             float(dssim_weight), C._ptr(ws), ws.numel(),
+                                                             float(dssim_weight), 1.0, C._ptr(ws), ws.numel(),
                                                              C._ptr(loss), C._ptr(grad), C._stream(None)))
         ctx.save_for_backward(grad)
         return loss[0]

@@ -15,6 +15,7 @@ from . import abi
 from ._lib import load
 
 _FIELDS = ("means", "scales", "quats", "opacity", "sh", "decay")
+MAX_VIEWS = 64          # views per launch
 
 
 class ClodError(RuntimeError):
@@ -69,6 +70,12 @@ class DeviceScene:
     @classmethod
     def from_scene(cls, scene) -> "DeviceScene":
         return cls(*(getattr(scene, k) for k in _FIELDS))
+
+    @classmethod
+    def from_tensors(cls, *tensors) -> "DeviceScene":
+        """A scene over existing contiguous float32 CUDA tensors (aliased, not
+        copied: later writes to them are seen by the next render)."""
+        return cls(*tensors)
 
     def __getattr__(self, k):
         if k in _FIELDS:

@@ -284,11 +284,13 @@ struct ParamGrads {
 template <int DEG>
 __global__ void __launch_bounds__(128) k_preprocess_bwd(Frame F, clod_scene S, const float4* __restrict__ g2d,
                                                         const float* __restrict__ g_alpha_ext,
+                                                        const float* __restrict__ g_alpha_view,
                                                         float* __restrict__ dmax_grad, ParamGrads P)
 {
     __shared__ ViewDev sv[MAX_VIEWS];
     __shared__ float sdmax[MAX_VIEWS];
     __shared__ float sdmg[MAX_VIEWS];
+    __shared__ float sgav[MAX_VIEWS];
     const uint32_t V = F.hdr->n_views;
     {
         const int words = static_cast<int>(V * sizeof(ViewDev) / 4);
@@ -298,6 +300,7 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(Frame F, clod_scene S, c
         for (uint32_t v = threadIdx.x; v < V; v += blockDim.x) {
             sdmax[v] = decode_dmax(F.dmax_key[v]);
             sdmg[v] = 0.f;
+            sgav[v] = g_alpha_view ? g_alpha_view[v] : 0.f;
         }
     }
     __syncthreads();
@@ -323,7 +326,7 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(Frame F, clod_scene S, c
             const int64_t o = (int64_t)v * n + i;
             const uint2 rc = F.rect[o];
             const bool surv = (rc.y & 0xFFFFu) > (rc.x & 0xFFFFu);
-            float g_a2 = g_alpha_ext ? g_alpha_ext[o] : 0.f;
+            float g_a2 = (g_alpha_ext ? g_alpha_ext[o] : 0.f) + sgav[v];
             float e0, e1, e2;
             const float d = cam_dist(W, mx, my, mz, e0, e1, e2);
             if (surv) {
@@ -583,7 +586,7 @@ cudaError_t backward_setup()
 
 void launch_backward(const Frame& F, const clod_scene& S, uint32_t V, const uint32_t* vals, const uint32_t* ranges,
                      const float* Tfin, const uint32_t* ncon, const float* dimg, const float* g_alpha_ext,
-                     void* bwd_ws, float* dmeans, float* dscales, float* dquats, float* dopacity, float* dsh,
+                     const float* g_alpha_view, void* bwd_ws, float* dmeans, float* dscales, float* dquats, float* dopacity, float* dsh,
                      float* ddecay, int n_sm, cudaStream_t st)
 {
     const BwdLayout L = bwd_layout((uint64_t)S.n, V);
@@ -599,10 +602,10 @@ void launch_backward(const Frame& F, const clod_scene& S, uint32_t V, const uint
     if (blocks < 1) blocks = 1;
     if (S.n > 0) {
         switch (S.sh_degree) {
-        case 0: k_preprocess_bwd<0><<<blocks, 128, 0, st>>>(F, S, g2d, g_alpha_ext, dmg, P); break;
-        case 1: k_preprocess_bwd<1><<<blocks, 128, 0, st>>>(F, S, g2d, g_alpha_ext, dmg, P); break;
-        case 2: k_preprocess_bwd<2><<<blocks, 128, 0, st>>>(F, S, g2d, g_alpha_ext, dmg, P); break;
-        default: k_preprocess_bwd<3><<<blocks, 128, 0, st>>>(F, S, g2d, g_alpha_ext, dmg, P); break;
+        case 0: k_preprocess_bwd<0><<<blocks, 128, 0, st>>>(F, S, g2d, g_alpha_ext, g_alpha_view, dmg, P); break;
+        case 1: k_preprocess_bwd<1><<<blocks, 128, 0, st>>>(F, S, g2d, g_alpha_ext, g_alpha_view, dmg, P); break;
+        case 2: k_preprocess_bwd<2><<<blocks, 128, 0, st>>>(F, S, g2d, g_alpha_ext, g_alpha_view, dmg, P); break;
+        default: k_preprocess_bwd<3><<<blocks, 128, 0, st>>>(F, S, g2d, g_alpha_ext, g_alpha_view, dmg, P); break;
         }
     }
     k_dmax_bwd<<<1, 64, 0, st>>>(F, S, dmg, dmeans);

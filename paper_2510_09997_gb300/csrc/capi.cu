@@ -23,7 +23,7 @@ cudaError_t render_setup();
 cudaError_t backward_setup();
 void launch_backward(const Frame& F, const clod_scene& S, uint32_t V, const uint32_t* vals, const uint32_t* ranges,
                      const float* Tfin, const uint32_t* ncon, const float* dimg, const float* g_alpha_ext,
-                     void* bwd_ws, float* dmeans, float* dscales, float* dquats, float* dopacity, float* dsh,
+                     const float* g_alpha_view, void* bwd_ws, float* dmeans, float* dscales, float* dquats, float* dopacity, float* dsh,
                      float* ddecay, int n_sm, cudaStream_t st);
 size_t backward_ws_bytes(uint64_t n, uint32_t V);
 void launch_l1(const float* img, const float* tgt, int64_t count, float scale, float* loss, float* grad, int n_sm,
@@ -476,7 +476,8 @@ clod_status clod_backward_workspace_size(int64_t n, int32_t n_views, size_t* byt
 
 clod_status clod_render_bwd(const clod_scene* scene, const void* ws, const uint32_t* vals, const uint32_t* ranges,
                             const float* T_final, const uint32_t* n_contrib, const float* dL_dimage,
-                            const float* dL_dalpha_eff, void* bwd_ws, size_t bwd_ws_bytes, float* dmeans,
+                            const float* dL_dalpha_eff, const float* dL_dalpha_view, void* bwd_ws,
+                            size_t bwd_ws_bytes, float* dmeans,
                             float* dscales, float* dquats, float* dopacity, float* dsh, float* ddecay,
                             clod_stream stream)
 {
@@ -496,7 +497,8 @@ clod_status clod_render_bwd(const clod_scene* scene, const void* ws, const uint3
     int n_sm = 0;
     if ((s = device_ready(&n_sm))) return s;
     const Frame F = frame_ptrs(const_cast<void*>(ws), L);
-    launch_backward(F, *scene, L.n_views, vals, ranges, T_final, n_contrib, dL_dimage, dL_dalpha_eff, bwd_ws, dmeans,
+    launch_backward(F, *scene, L.n_views, vals, ranges, T_final, n_contrib, dL_dimage, dL_dalpha_eff, dL_dalpha_view,
+                    bwd_ws, dmeans,
                     dscales, dquats, dopacity, dsh, ddecay, n_sm, static_cast<cudaStream_t>(stream));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "clod_render_bwd launch");

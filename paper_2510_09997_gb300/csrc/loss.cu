@@ -11,6 +11,8 @@
 //                 M2 = dS/ds_xx, M3 = dS/ds_xy;
 //   k_ssim_bwd  per tile: blurs of M1, M2, M3 (the window is symmetric) and
 //               dSSIM/dx = (w * M1 + 2 x (w * M2) + y (w * M3)) / N.
+//   k_l1_term   lambda = 0: the L1 term alone (no maps).
+// The gradient is scaled by the caller's factor of this term in its total.
 #include <algorithm>
 #include <cmath>
 
@@ -123,7 +125,7 @@ __global__ void __launch_bounds__(SS_T * SS_T) k_ssim_fwd(const float* __restric
 }
 
 __global__ void __launch_bounds__(SS_T * SS_T) k_ssim_bwd(const float* __restrict__ img, const float* __restrict__ tgt,
-                                                          int W, int H, float lam, float inv_n,
+                                                          int W, int H, float lam, float ginv_n,
                                                           const float* __restrict__ maps, float* __restrict__ grad)
 {
     __shared__ float sm[3][SS_H][SS_H];
@@ -164,7 +166,22 @@ __global__ void __launch_bounds__(SS_T * SS_T) k_ssim_bwd(const float* __restric
     const float xv = img[p], yv = tgt[p];
     const float dssim = b[0] + 2.f * xv * b[1] + yv * b[2];
     const float dl1 = xv > yv ? 1.f : (xv < yv ? -1.f : 0.f);
-    grad[p] = inv_n * ((1.0f - lam) * dl1 - lam * dssim);
+    grad[p] = ginv_n * ((1.0f - lam) * dl1 - lam * dssim);
+}
+
+// w = 0: L1 alone.  loss += mean |x - y|; grad = grad_scale sign(x - y) / count.
+__global__ void __launch_bounds__(256) k_l1_term(const float* __restrict__ img, const float* __restrict__ tgt,
+                                                 int64_t count, float inv_n, float ginv_n, float* __restrict__ loss,
+                                                 float* __restrict__ grad)
+{
+    float acc = 0.0f;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x) {
+        const float d = img[k] - tgt[k];
+        acc += fabsf(d);
+        if (grad) grad[k] = d > 0.0f ? ginv_n : (d < 0.0f ? -ginv_n : 0.0f);
+    }
+    const float tot = block_sum(acc);
+    if (threadIdx.x == 0 && loss) atomicAdd(loss, tot * inv_n);
 }
 
 static bool g_win_ready[64];
@@ -202,8 +219,8 @@ clod_status clod_render_loss_workspace_size(int32_t channels, int32_t height, in
 }
 
 clod_status clod_render_loss(const float* image, const float* target, int32_t channels, int32_t height, int32_t width,
-                             float dssim_weight, void* ws, size_t ws_bytes, float* loss, float* dL_dimage,
-                             clod_stream stream)
+                             float dssim_weight, float grad_scale, void* ws, size_t ws_bytes, float* loss,
+                             float* dL_dimage, clod_stream stream)
 {
     if (!image || !target || channels < 1 || height < 1 || width < 1)
         return fail(CLOD_ERR_ARG, "bad argument to clod_render_loss");
@@ -211,18 +228,26 @@ clod_status clod_render_loss(const float* image, const float* target, int32_t ch
     size_t need = 0;
     clod_status s = clod_render_loss_workspace_size(channels, height, width, &need);
     if (s) return s;
-    if (dL_dimage && (!ws || ws_bytes < need))
-        return fail(CLOD_ERR_CAPACITY, "render-loss workspace needs %zu bytes, got %zu", need, ws_bytes);
+    if (!std::isfinite(grad_scale)) return fail(CLOD_ERR_ARG, "grad_scale must be finite");
     int n_sm = 0;
     if ((s = device_ready(&n_sm))) return s;
-    if ((s = window_ready())) return s;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const dim3 grid((width + SS_T - 1) / SS_T, (height + SS_T - 1) / SS_T, channels);
-    const float inv_n = 1.0f / ((float)channels * height * width);
-    float* maps = dL_dimage ? static_cast<float*>(ws) : nullptr;
-    k_ssim_fwd<<<grid, SS_T * SS_T, 0, st>>>(image, target, width, height, dssim_weight, inv_n, loss, maps);
-    if (dL_dimage)
-        k_ssim_bwd<<<grid, SS_T * SS_T, 0, st>>>(image, target, width, height, dssim_weight, inv_n, maps, dL_dimage);
+    const int64_t count = (int64_t)channels * height * width;
+    const float inv_n = 1.0f / (float)count;
+    if (dssim_weight == 0.0f) {
+        const int blocks = static_cast<int>(std::min<int64_t>((count + 255) / 256, (int64_t)n_sm * 4));
+        k_l1_term<<<blocks, 256, 0, st>>>(image, target, count, inv_n, grad_scale * inv_n, loss, dL_dimage);
+    } else {
+        if (dL_dimage && (!ws || ws_bytes < need))
+            return fail(CLOD_ERR_CAPACITY, "render-loss workspace needs %zu bytes, got %zu", need, ws_bytes);
+        if ((s = window_ready())) return s;
+        const dim3 grid((width + SS_T - 1) / SS_T, (height + SS_T - 1) / SS_T, channels);
+        float* maps = dL_dimage ? static_cast<float*>(ws) : nullptr;
+        k_ssim_fwd<<<grid, SS_T * SS_T, 0, st>>>(image, target, width, height, dssim_weight, inv_n, loss, maps);
+        if (dL_dimage)
+            k_ssim_bwd<<<grid, SS_T * SS_T, 0, st>>>(image, target, width, height, dssim_weight, grad_scale * inv_n,
+                                                     maps, dL_dimage);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "clod_render_loss launch");
     return CLOD_OK;

@@ -1,0 +1,162 @@
+// train.cu -- the training step around the rasterizer (Sec. 3.3).
+//
+//   k_lreg   per view: eta_actual = sum M_i / N (the mask counts the
+//            preprocessing wrote), L_reg = (s_v - 1)^2 ReLU(eta_actual -
+//            s_v^-1.5)^2 (Eq. 3-4), the total L_total = sum_v w_v (L_render_v
+//            + lambda L_reg_v) (Eq. 5 with w_v = w_s / V), and the
+//            straight-through gradient dL/dalpha''_i = w_v lambda 2 (s_v -
+//            1)^2 ReLU(.) / N, one scalar per view (dM_i/dalpha''_i := 1).
+//   k_adam   one Adam step over the six parameter groups, fused with the
+//            activations: the rasterizer's gradients are taken back to the
+//            raw parameters (scales = exp(log-scales), opacity =
+//            sigmoid(logit)), the moments and raw values are updated, the
+//            activated scales and opacities are rewritten from the new raw
+//            values and the gradients are cleared for the next step.
+#include <algorithm>
+#include <cmath>
+
+#include "clod_internal.cuh"
+
+namespace clod {
+
+clod_status fail(clod_status s, const char* fmt, ...);
+clod_status cuda_fail(cudaError_t e, const char* what);
+clod_status device_ready(int* n_sm);
+
+struct LregArgs {
+    float s_v[MAX_VIEWS];
+    float w[MAX_VIEWS];
+};
+
+__global__ void k_lreg(const uint32_t* __restrict__ counts, double inv_n, float lam, int V, LregArgs a,
+                       const float* __restrict__ lrender, float* __restrict__ dalpha, float* __restrict__ total,
+                       float* __restrict__ lreg_out)
+{
+    __shared__ float part[MAX_VIEWS];
+    const int v = threadIdx.x;
+    float t = 0.0f;
+    if (v < V) {
+        const float s = a.s_v[v];
+        const float eta_a = static_cast<float>(static_cast<double>(counts[2 * v]) * inv_n);
+        const float eta_t = powf(s, -1.5f);
+        const float relu = fmaxf(eta_a - eta_t, 0.0f);
+        const float s1 = (s - 1.0f) * (s - 1.0f);
+        const float lreg = s1 * relu * relu;
+        if (lreg_out) lreg_out[v] = lreg;
+        if (dalpha) dalpha[v] = a.w[v] * lam * 2.0f * s1 * relu * static_cast<float>(inv_n);
+        t = a.w[v] * ((lrender ? lrender[v] : 0.0f) + lam * lreg);
+    }
+    if (v < MAX_VIEWS) part[v] = t;
+    __syncthreads();
+    if (v == 0 && total) {
+        float sum = 0.0f;
+        for (int k = 0; k < V; ++k) sum += part[k];
+        *total = sum;
+    }
+}
+
+struct AdamArgs {
+    float* p[6];            // raw parameters
+    float* g[6];            // gradients with respect to the activated parameters
+    float* act[6];          // activated copies (scales, opacity), else null
+    int64_t off[7];         // element offsets of the groups in m, v
+    float step_size[6];     // lr / (1 - beta1^t)
+    float b1, b2, inv_bc2_sqrt, eps;
+};
+
+__global__ void __launch_bounds__(256) k_adam(AdamArgs A, float* __restrict__ m, float* __restrict__ v)
+{
+    const int64_t E = A.off[6];
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+        int gi = 0;
+#pragma unroll
+        for (int k = 1; k < 6; ++k) gi += e >= A.off[k] ? 1 : 0;
+        const int64_t j = e - A.off[gi];
+        float* gp = A.g[gi] + j;
+        float g = *gp;
+        *gp = 0.0f;
+        float* ap = A.act[gi];
+        float a = 0.0f;
+        if (ap) {
+            a = ap[j];
+            g = gi == 1 ? g * a : g * a * (1.0f - a);   // d exp / d log = exp; d sigmoid = a (1 - a)
+        }
+        const float mm = A.b1 * m[e] + (1.0f - A.b1) * g;
+        const float vv = A.b2 * v[e] + (1.0f - A.b2) * g * g;
+        m[e] = mm;
+        v[e] = vv;
+        const float denom = sqrtf(vv) * A.inv_bc2_sqrt + A.eps;
+        float* pp = A.p[gi] + j;
+        const float p = *pp - A.step_size[gi] * (mm / denom);
+        *pp = p;
+        if (ap) ap[j] = gi == 1 ? expf(p) : 1.0f / (1.0f + expf(-p));
+    }
+}
+
+}  // namespace clod
+
+using namespace clod;
+
+extern "C" {
+
+clod_status clod_lreg_grad(const uint32_t* counts, int64_t n, int32_t n_views, const float* s_v, const float* weight,
+                           float lambda_reg, const float* lrender, float* dL_dalpha_view, float* total, float* lreg_out,
+                           clod_stream stream)
+{
+    if (!counts || n < 1 || n_views < 1 || n_views > MAX_VIEWS || !s_v || !weight)
+        return fail(CLOD_ERR_ARG, "bad argument to clod_lreg_grad");
+    LregArgs a{};
+    for (int v = 0; v < n_views; ++v) {
+        if (!(s_v[v] > 0.0f) || !std::isfinite(s_v[v])) return fail(CLOD_ERR_ARG, "view %d: s_v must be > 0", v);
+        a.s_v[v] = s_v[v];
+        a.w[v] = weight[v];
+    }
+    int n_sm = 0;
+    clod_status s = device_ready(&n_sm);
+    if (s) return s;
+    k_lreg<<<1, MAX_VIEWS, 0, static_cast<cudaStream_t>(stream)>>>(counts, 1.0 / (double)n, lambda_reg, n_views, a,
+                                                                    lrender, dL_dalpha_view, total, lreg_out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "clod_lreg_grad launch");
+    return CLOD_OK;
+}
+
+clod_status clod_adam_step(const clod_adam_cfg* cfg, int64_t n, int32_t sh_degree, float* const* raw,
+                           float* const* grads, float* scales, float* opacity, float* m, float* v, clod_stream stream)
+{
+    if (!cfg || !raw || !grads || !scales || !opacity || !m || !v || n < 0 || sh_degree < 0 || sh_degree > 3)
+        return fail(CLOD_ERR_ARG, "bad argument to clod_adam_step");
+    if (cfg->step < 1) return fail(CLOD_ERR_ARG, "Adam step counts from 1");
+    if (n == 0) return CLOD_OK;
+    const int64_t K = (int64_t)(sh_degree + 1) * (sh_degree + 1);
+    const int64_t cnt[6] = {3 * n, 3 * n, 4 * n, n, 3 * K * n, n};
+    AdamArgs A{};
+    A.off[0] = 0;
+    for (int k = 0; k < 6; ++k) {
+        if (!raw[k] || !grads[k]) return fail(CLOD_ERR_ARG, "parameter group %d is NULL", k);
+        A.p[k] = raw[k];
+        A.g[k] = grads[k];
+        A.act[k] = nullptr;
+        A.off[k + 1] = A.off[k] + cnt[k];
+    }
+    A.act[1] = scales;
+    A.act[3] = opacity;
+    const double bc1 = 1.0 - std::pow((double)cfg->beta1, (double)cfg->step);
+    const double bc2 = 1.0 - std::pow((double)cfg->beta2, (double)cfg->step);
+    for (int k = 0; k < 6; ++k) A.step_size[k] = (float)(cfg->lr[k] / bc1);
+    A.b1 = cfg->beta1;
+    A.b2 = cfg->beta2;
+    A.inv_bc2_sqrt = (float)(1.0 / std::sqrt(bc2));
+    A.eps = cfg->eps;
+    int n_sm = 0;
+    clod_status s = device_ready(&n_sm);
+    if (s) return s;
+    const int64_t E = A.off[6];
+    const int blocks = static_cast<int>(std::min<int64_t>((E + 255) / 256, (int64_t)n_sm * 16));
+    k_adam<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(A, m, v);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "clod_adam_step launch");
+    return CLOD_OK;
+}
+
+}  // extern "C"

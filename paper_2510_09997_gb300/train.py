@@ -10,24 +10,35 @@ s_v, and the objective is
     eta_target = s_v^-1.5                                            (Eq. 3)
     eta_actual = sum_i M_i / N_total
 
-L_render = (1 - w) L1 + w D-SSIM (the clod_render_loss kernel; w = 0.2 as in
-the 3DGS training the paper builds on; w = 0 gives L1 alone).  eta_actual is a
-count of the binary mask; its gradient is taken straight through,
-dM_i/dalpha''_i := 1, so every alpha'' receives 2 w_s lambda (s_v - 1)^2
-ReLU(eta_a - eta_t) / N and the rasterizer's backward carries it on to alpha,
-sigma_d and the means.  Parameters are kept raw (log-scales, opacity logits)
-and activated with exp / sigmoid before the rasterizer; Adam updates them,
-sigma_d with learning rate 1e-2 and lambda_reg = 1 (Sec. 4.1).
+averaged over the step's views.  L_render = (1 - w) L1 + w D-SSIM (w = 0.2
+as in the 3DGS training the paper builds on; w = 0 gives L1 alone).
+eta_actual is a count of the binary mask; its gradient is taken straight
+through, dM_i/dalpha''_i := 1, so every alpha'' of view v receives
+2 w_v lambda (s_v - 1)^2 ReLU(eta_a - eta_t) / N, one scalar per view that the
+rasterizer's backward carries on to alpha, sigma_d and the means.
+
+Every step runs in libclod's kernels: the forward (clod_preprocess,
+clod_bin_sort, clod_render_fwd), the loss and its image gradient
+(clod_render_loss, written straight into the packed gradient), L_reg, the
+total and the per-view straight-through scalars (clod_lreg_grad), the
+backward (clod_render_bwd) and Adam fused with the parameter activations
+(clod_adam_step: raw log-scales and opacity logits, exp / sigmoid).  Python
+only allocates the buffers once and passes pointers.  sigma_d has learning
+rate 1e-2 and lambda_reg = 1 (Sec. 4.1).
 """
 from __future__ import annotations
 
+import ctypes
 import math
 from typing import List, Optional, Sequence
 
 import numpy as np
 import torch
 
-from . import autograd as A
+from . import abi
+from . import clod as C
+
+LR_NAMES = ("means", "log_scales", "quats", "opacity_logit", "sh", "decay")
 
 
 def eta_target(s_v: float) -> float:
@@ -38,50 +49,66 @@ def w_s(s_v: float, s_max: float) -> float:
     return (1.0 - 0.5 * s_v / s_max) ** 2
 
 
-class GaussianModel(torch.nn.Module):
+class GaussianModel:
+    """Raw parameters (what Adam updates) and the activated scales and
+    opacities the rasterizer reads.  At construction the activated copies are
+    the scene's values themselves; afterwards clod_adam_step rewrites them."""
+
     def __init__(self, scene, device="cuda"):
-        super().__init__()
-        f = lambda a: torch.nn.Parameter(torch.tensor(np.asarray(a, np.float32), device=device))
-        self.means = f(scene.means)
-        self.log_scales = f(np.log(scene.scales))
-        self.quats = f(scene.quats)
-        op = np.clip(scene.opacity, 1e-6, 1 - 1e-6)
-        self.opacity_logit = f(np.log(op / (1 - op)))
-        self.sh = f(scene.sh)
-        self.decay = f(scene.decay)
+        t = lambda a: torch.tensor(np.ascontiguousarray(a, np.float32), device=device)
+        self.means = t(scene.means)
+        self.log_scales = t(np.log(np.asarray(scene.scales, np.float64)))
+        self.quats = t(scene.quats)
+        op = np.clip(np.asarray(scene.opacity, np.float64), 1e-6, 1 - 1e-6)
+        self.opacity_logit = t(np.log(op / (1 - op)))
+        self.sh = t(scene.sh)
+        self.decay = t(scene.decay)
+        self.scales = t(scene.scales)
+        self.opacity = t(scene.opacity)
+        self.sh_degree = int(round(self.sh.shape[1] ** 0.5)) - 1
 
     @property
     def n(self) -> int:
         return int(self.means.shape[0])
 
     def activated(self):
-        return (self.means, torch.exp(self.log_scales), self.quats, torch.sigmoid(self.opacity_logit),
-                self.sh, self.decay)
+        return (self.means, self.scales, self.quats, self.opacity, self.sh, self.decay)
 
-    def optimizer(self, extent: float = 1.0):
-        groups = [
-            {"params": [self.means], "lr": 1.6e-4 * extent},
-            {"params": [self.log_scales], "lr": 5e-3},
-            {"params": [self.quats], "lr": 1e-3},
-            {"params": [self.opacity_logit], "lr": 5e-2},
-            {"params": [self.sh], "lr": 2.5e-3},
-            {"params": [self.decay], "lr": 1e-2},
-        ]
-        return torch.optim.Adam(groups, eps=1e-15, fused=True)
+    def raw(self):
+        return (self.means, self.log_scales, self.quats, self.opacity_logit, self.sh, self.decay)
+
+    def scene(self) -> C.DeviceScene:
+        return C.DeviceScene.from_tensors(*self.activated())
 
 
 class TrainStep:
     """One optimisation step over a batch of views."""
 
     def __init__(self, model: GaussianModel, s_max: float = 16.0, lam_reg: float = 1.0, sampler: str = "log",
-                 seed: int = 0, extent: float = 1.0, dssim_weight: float = 0.2):
+                 seed: int = 0, extent: float = 1.0, dssim_weight: float = 0.2, betas=(0.9, 0.999),
+                 eps: float = 1e-15):
         self.model = model
         self.dssim = float(dssim_weight)
         self.s_max = float(s_max)
         self.lam = float(lam_reg)
         self.sampler = sampler
         self.rng = np.random.default_rng(seed)
-        self.opt = model.optimizer(extent)
+        self.lr = [1.6e-4 * extent, 5e-3, 1e-3, 5e-2, 2.5e-3, 1e-2]
+        self.betas = (float(betas[0]), float(betas[1]))
+        self.eps = float(eps)
+        self.t = 0
+        dev = model.means.device
+        n_el = sum(p.numel() for p in model.raw())
+        self.m = torch.zeros(n_el, dtype=torch.float32, device=dev)
+        self.v = torch.zeros(n_el, dtype=torch.float32, device=dev)
+        self.grads = [torch.zeros_like(p) for p in model.activated()]
+        self.total = torch.zeros(1, dtype=torch.float32, device=dev)
+        self.lrender = torch.zeros(C.MAX_VIEWS, dtype=torch.float32, device=dev)
+        self.lreg = torch.zeros(C.MAX_VIEWS, dtype=torch.float32, device=dev)
+        self.dalpha = torch.zeros(C.MAX_VIEWS, dtype=torch.float32, device=dev)
+        self._bws = None
+        self._lws = None
+        self.scene = model.scene()
 
     def sample_scale(self) -> float:
         if self.s_max <= 1.0:
@@ -92,35 +119,91 @@ class TrainStep:
             s = math.exp(self.rng.uniform(0.0, math.log(self.s_max)))
         return float(np.float32(s))
 
-    def loss(self, views: Sequence, targets: Sequence[torch.Tensor], scales: Optional[List[float]] = None):
-        """Returns (L_total, per-view diagnostics)."""
+    def _workspace(self, attr, nbytes):
+        buf = getattr(self, attr)
+        if buf is None or buf.numel() < nbytes:
+            buf = torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=self.model.means.device)
+            setattr(self, attr, buf)
+        return buf
+
+    def forward_backward(self, views: Sequence, targets: Sequence[torch.Tensor], scales: Optional[List[float]] = None):
+        """Forward, loss, L_reg, backward: the six activated-parameter
+        gradients accumulate into self.grads.  Returns (frame, per-view info)."""
         if scales is None:
             scales = [self.sample_scale() for _ in views]
         views = [v.replace(s_v=s) for v, s in zip(views, scales)]
-        imgs, alpha, mask, counts = A.render(*self.model.activated(), views)
-        self.last = dict(images=imgs, alpha=alpha, views=views)
-        N = self.model.n
-        total = 0.0
-        info = []
-        cnt = counts.detach().cpu().numpy()
-        for k, (v, s) in enumerate(zip(views, scales)):
-            l1 = (A.RenderLoss.apply(imgs[k], targets[k], self.dssim) if self.dssim > 0
-                  else A.L1Loss.apply(imgs[k], targets[k]))
-            eta_a_count = float(cnt[k, 0]) / N
-            # straight-through estimator: value of the count, gradient of sum alpha'' / N
-            a_sum = alpha[k].sum()
-            eta_a = eta_a_count + (a_sum - a_sum.detach()) / N
-            relu = torch.relu(eta_a - eta_target(s))
-            l_reg = (s - 1.0) ** 2 * relu * relu
-            ws = w_s(s, self.s_max)
-            total = total + ws * (l1 + self.lam * l_reg)
-            info.append(dict(s_v=s, l_render=float(l1.detach()), l1=float(l1.detach()), l_reg=float(l_reg.detach()), eta_actual=eta_a_count,
-                             eta_target=eta_target(s), w_s=ws, rendered=int(cnt[k, 1])))
-        return total / len(views), info
+        V = len(views)
+        L = C.lib()
+        st = C._stream(None)
+        fr = C.render(self.scene, views, want_keys=False)
+        dimg = torch.empty_like(fr.image)
+        weights = [w_s(s, self.s_max) / V for s in scales]
+        self.lrender[:V].zero_()
+        for k, v in enumerate(views):
+            b = 3 * fr.pix_base[k]
+            img = fr.image[b:b + 3 * v.width * v.height]
+            ws = None
+            nbytes = 0
+            if self.dssim > 0:
+                nb = ctypes.c_size_t()
+                C.check("clod_render_loss_workspace_size",
+                        L.clod_render_loss_workspace_size(3, v.height, v.width, ctypes.byref(nb)))
+                ws = self._workspace("_lws", nb.value)
+                nbytes = ws.numel()
+            C.check("clod_render_loss", L.clod_render_loss(
+                C._ptr(img), C._ptr(targets[k]), 3, v.height, v.width, self.dssim, weights[k],
+                C._ptr(ws) if ws is not None else None, nbytes, C._ptr(self.lrender[k:]),
+                C._ptr(dimg[b:]), st))
+        s_arr = (ctypes.c_float * V)(*scales)
+        w_arr = (ctypes.c_float * V)(*weights)
+        C.check("clod_lreg_grad", L.clod_lreg_grad(C._ptr(fr.counts), self.model.n, V, s_arr, w_arr, self.lam,
+                                                   C._ptr(self.lrender), C._ptr(self.dalpha), C._ptr(self.total),
+                                                   C._ptr(self.lreg), st))
+        nb = ctypes.c_size_t()
+        C.check("clod_backward_workspace_size", L.clod_backward_workspace_size(self.model.n, V, ctypes.byref(nb)))
+        bws = self._workspace("_bws", nb.value)
+        C.check("clod_render_bwd", L.clod_render_bwd(
+            ctypes.byref(self.scene.c), C._ptr(fr.ws), C._ptr(fr.vals), C._ptr(fr.ranges), C._ptr(fr.T_final),
+            C._ptr(fr.n_contrib), C._ptr(dimg), None, C._ptr(self.dalpha), C._ptr(bws), bws.numel(),
+            *[C._ptr(g) for g in self.grads], st))
+        info = dict(views=views, n=self.model.n, scales=list(scales), w_s=[w_s(s, self.s_max) for s in scales],
+                    eta_target=[eta_target(s) for s in scales], counts=fr.counts, l_render=self.lrender[:V],
+                    l_reg=self.lreg[:V])
+        self.last = dict(frame=fr, dimage=dimg, **info)
+        return fr, info
+
+    def loss(self, views, targets, scales=None):
+        """L_total (device scalar) and per-view diagnostics, without the update
+        (the gradients are left accumulated in self.grads)."""
+        fr, info = self.forward_backward(views, targets, scales)
+        return self.total, info
 
     def step(self, views: Sequence, targets: Sequence[torch.Tensor], scales: Optional[List[float]] = None):
-        self.opt.zero_grad(set_to_none=True)
-        total, info = self.loss(views, targets, scales)
-        total.backward()
-        self.opt.step()
-        return float(total.detach()), info
+        """Forward + backward + Adam.  Returns (L_total as a device scalar
+        tensor, per-view diagnostics as device tensors)."""
+        fr, info = self.forward_backward(views, targets, scales)
+        self.t += 1
+        cfg = abi.clod_adam_cfg()
+        for k in range(6):
+            cfg.lr[k] = self.lr[k]
+        cfg.beta1, cfg.beta2, cfg.eps, cfg.step = self.betas[0], self.betas[1], self.eps, self.t
+        P = ctypes.c_void_p * 6
+        raw = P(*[C._ptr(p) for p in self.model.raw()])
+        grads = P(*[C._ptr(g) for g in self.grads])
+        C.check("clod_adam_step", C.lib().clod_adam_step(ctypes.byref(cfg), self.model.n, self.model.sh_degree, raw,
+                                                         grads, C._ptr(self.model.scales),
+                                                         C._ptr(self.model.opacity), C._ptr(self.m), C._ptr(self.v),
+                                                         C._stream(None)))
+        return self.total, info
+
+
+def per_view_info(info) -> List[dict]:
+    """Host copy of a step's diagnostics (synchronises)."""
+    cnt = info["counts"].cpu().numpy()
+    lr = info["l_render"].cpu().numpy()
+    lg = info["l_reg"].cpu().numpy()
+    out = []
+    for k, s in enumerate(info["scales"]):
+        out.append(dict(s_v=s, l_render=float(lr[k]), l_reg=float(lg[k]), eta_actual=float(cnt[k, 0]) / info["n"],
+                        eta_target=info["eta_target"][k], w_s=info["w_s"][k], rendered=int(cnt[k, 1])))
+    return out
