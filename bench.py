@@ -41,7 +41,12 @@ FLOP_VISIT, FLOP_EXP, FLOP_CONTRIB = 9, 33, 9
 LAUNCHES_PER_FRAME = 19
 
 
-def frames_list():
+def frames_list(only=None):
+    """The sweep's (camera, s_v) frames; ``only`` = "CAM:S" keeps one frame
+    (for profiling a single frame; not the benchmark workload)."""
+    if only:
+        c, s = only.split(":")
+        return [(int(c), float(s))]
     return [(c, s) for c in range(N_CAMS) for s in SCALES]
 
 
@@ -57,6 +62,7 @@ def parse():
     p.add_argument("--train-steps", type=int, default=10)
     p.add_argument("--serve-seconds", type=float, default=2.0)
     p.add_argument("--no-city", action="store_true")
+    p.add_argument("--frame", default=None, help="CAM:S -- time only that frame of the sweep (profiling)")
     p.add_argument("--leg", default="all", choices=["all", "train", "serve", "city"],
                    help="train / serve: run only that leg and print its JSON object (for profiling)")
     return p.parse_args()
@@ -141,7 +147,7 @@ def run_ours(args):
     C.require_cuda()
     sc = S.object_scene(N_GAUSS)
     cams = S.orbit_cameras(N_CAMS, WIDTH, HEIGHT)
-    allf = frames_list()
+    allf = frames_list(args.frame)
     # this rank's frames (replicas: rank r takes frames r, r+N, ...)
     mine = allf[rank::world] if world > 1 else allf
     views = [cams[c].replace(s_v=s) for c, s in mine]
@@ -270,6 +276,8 @@ def run_ours(args):
         "gpu_launches": LAUNCHES_PER_FRAME * args.steps,
         "clocks": clk,
     }
+    if args.frame:
+        out["config"]["single_frame"] = args.frame     # profiling run, not the sweep
     if rank == 0 and not args.no_extras:
         out["e2e"] = e2e_leg(C, ds, R, views, args, stream)
         out["cpu_baseline"] = cpu_baseline(sc, views)

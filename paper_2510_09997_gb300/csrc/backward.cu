@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(BWD_THREADS) k_blend_bwd(Frame F, const uint32
 {
     __shared__ float4 s0[4][32];
     __shared__ float4 s1[4][32];
-    __shared__ float s2[4][32];
+    __shared__ float4 s2[4][32];
     __shared__ int64_t sg[4][32];
     __shared__ uint32_t s_tile;
     __shared__ int s_view;
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(BWD_THREADS) k_blend_bwd(Frame F, const uint32
                 s0[wid][lane] = a;
                 s1[wid][lane] = c;
                 const float4 e = F.rec2[g];
-                s2[wid][lane] = e.x;
+                s2[wid][lane] = e;
                 sg[wid][lane] = g;
                 hit = !(fabsf(a.x - wcx) > e.y + 3.5f || fabsf(a.y - wcy) > e.z + 3.5f);
             }
@@ -214,13 +214,16 @@ __global__ void __launch_bounds__(BWD_THREADS) k_blend_bwd(Frame F, const uint32
                 bm &= ~(1u << k);
                 const float4 a = s0[wid][k];
                 const float4 c = s1[wid][k];
-                const float cb = s2[wid][k];
+                const float4 e = s2[wid][k];
                 const uint32_t pos = lo + (uint32_t)k + 1u;
                 float g[16];
 #pragma unroll
                 for (int i = 0; i < 16; ++i) g[i] = 0.0f;
-                bool any = bwd_one(q[0], fpx, a, c, cb, pos, g);
-                any |= bwd_one(q[1], fpx, a, c, cb, pos, g);
+                // per-pixel reach box: outside it the forward skipped this Gaussian
+                const bool ix = fabsf(a.x - fpx) <= e.y;
+                bool any = false;
+                if (ix && fabsf(a.y - q[0].fy) <= e.z) any = bwd_one(q[0], fpx, a, c, e.x, pos, g);
+                if (ix && fabsf(a.y - q[1].fy) <= e.z) any |= bwd_one(q[1], fpx, a, c, e.x, pos, g);
                 if (__any_sync(0xffffffffu, any)) {
                     const float tot = warp_reduce16(g);
                     if (!(lane & 1) && lane < 18) atomicAdd(g2d + 12 * sg[wid][k] + (lane >> 1), tot);

@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_fwd(Frame F, const uint
 {
     __shared__ float4 s0[4][32];
     __shared__ float4 s1[4][32];
-    __shared__ float s2[4][32];
+    __shared__ float4 s2[4][32];
     __shared__ uint32_t s_tile;
     __shared__ int s_view;
     const FrameHeader* hdr = F.hdr;
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_fwd(Frame F, const uint
                 const float4 e = F.rec2[g];
                 s0[wid][lane] = a;
                 s1[wid][lane] = c;
-                s2[wid][lane] = e.x;
+                s2[wid][lane] = e;
                 // the reach box (stored by the preprocessing) against the warp's 8x8 patch
                 if (COUNT) hit = true;
                 else hit = !(fabsf(a.x - wcx) > e.y + 3.5f || fabsf(a.y - wcy) > e.z + 3.5f);
@@ -148,15 +148,18 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_fwd(Frame F, const uint
                 m &= m - 1;
                 const float4 a = s0[wid][k];
                 const float4 c = s1[wid][k];
-                const float cb = s2[wid][k];
+                const float4 e = s2[wid][k];
                 const uint32_t pos = b - start + (uint32_t)k + 1u;
-                if (!q0.done) {
+                // the same reach box per pixel: outside it the pixel would skip
+                // this Gaussian (opacity < 1/255), so the test changes nothing
+                const bool ix = COUNT || fabsf(a.x - fpx) <= e.y;
+                if (!q0.done && ix && (COUNT || fabsf(a.y - fpy0) <= e.z)) {
                     if (COUNT) ++evals;
-                    blend_one<COUNT>(q0, fpx, fpy0, a, c, cb, pos, n_exp, n_con);
+                    blend_one<COUNT>(q0, fpx, fpy0, a, c, e.x, pos, n_exp, n_con);
                 }
-                if (!q1.done) {
+                if (!q1.done && ix && (COUNT || fabsf(a.y - fpy1) <= e.z)) {
                     if (COUNT) ++evals;
-                    blend_one<COUNT>(q1, fpx, fpy1, a, c, cb, pos, n_exp, n_con);
+                    blend_one<COUNT>(q1, fpx, fpy1, a, c, e.x, pos, n_exp, n_con);
                 }
             }
             __syncwarp();

@@ -64,32 +64,52 @@ struct AdamArgs {
     float b1, b2, inv_bc2_sqrt, eps;
 };
 
+constexpr int ADAM_UNROLL = 4;
+
+// Group by group; each thread takes ADAM_UNROLL elements per round and issues
+// all their loads before any store, so that many loads are in flight.
 __global__ void __launch_bounds__(256) k_adam(AdamArgs A, float* __restrict__ m, float* __restrict__ v)
 {
-    const int64_t E = A.off[6];
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
-        int gi = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int gi = 0; gi < 6; ++gi) {
+        const int64_t cnt = A.off[gi + 1] - A.off[gi];
+        float* __restrict__ P = A.p[gi];
+        float* __restrict__ G = A.g[gi];
+        float* __restrict__ Act = A.act[gi];
+        float* __restrict__ M = m + A.off[gi];
+        float* __restrict__ Vv = v + A.off[gi];
+        const float ss = A.step_size[gi];
+        for (int64_t j0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j0 < cnt; j0 += ADAM_UNROLL * stride) {
+            float p[ADAM_UNROLL], g[ADAM_UNROLL], mm[ADAM_UNROLL], vv[ADAM_UNROLL], a[ADAM_UNROLL];
 #pragma unroll
-        for (int k = 1; k < 6; ++k) gi += e >= A.off[k] ? 1 : 0;
-        const int64_t j = e - A.off[gi];
-        float* gp = A.g[gi] + j;
-        float g = *gp;
-        *gp = 0.0f;
-        float* ap = A.act[gi];
-        float a = 0.0f;
-        if (ap) {
-            a = ap[j];
-            g = gi == 1 ? g * a : g * a * (1.0f - a);   // d exp / d log = exp; d sigmoid = a (1 - a)
+            for (int u = 0; u < ADAM_UNROLL; ++u) {
+                const int64_t j = j0 + u * stride;
+                if (j < cnt) {
+                    p[u] = P[j];
+                    g[u] = G[j];
+                    mm[u] = M[j];
+                    vv[u] = Vv[j];
+                    a[u] = Act ? Act[j] : 0.0f;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < ADAM_UNROLL; ++u) {
+                const int64_t j = j0 + u * stride;
+                if (j < cnt) {
+                    float gr = g[u];
+                    if (Act) gr = gi == 1 ? gr * a[u] : gr * a[u] * (1.0f - a[u]);   // d exp = exp; d sigmoid = a (1 - a)
+                    const float m1 = A.b1 * mm[u] + (1.0f - A.b1) * gr;
+                    const float v1 = A.b2 * vv[u] + (1.0f - A.b2) * gr * gr;
+                    const float denom = sqrtf(v1) * A.inv_bc2_sqrt + A.eps;
+                    const float pn = p[u] - ss * (m1 / denom);
+                    M[j] = m1;
+                    Vv[j] = v1;
+                    P[j] = pn;
+                    G[j] = 0.0f;
+                    if (Act) Act[j] = gi == 1 ? expf(pn) : 1.0f / (1.0f + expf(-pn));
+                }
+            }
         }
-        const float mm = A.b1 * m[e] + (1.0f - A.b1) * g;
-        const float vv = A.b2 * v[e] + (1.0f - A.b2) * g * g;
-        m[e] = mm;
-        v[e] = vv;
-        const float denom = sqrtf(vv) * A.inv_bc2_sqrt + A.eps;
-        float* pp = A.p[gi] + j;
-        const float p = *pp - A.step_size[gi] * (mm / denom);
-        *pp = p;
-        if (ap) ap[j] = gi == 1 ? expf(p) : 1.0f / (1.0f + expf(-p));
     }
 }
 
@@ -152,7 +172,8 @@ clod_status clod_adam_step(const clod_adam_cfg* cfg, int64_t n, int32_t sh_degre
     clod_status s = device_ready(&n_sm);
     if (s) return s;
     const int64_t E = A.off[6];
-    const int blocks = static_cast<int>(std::min<int64_t>((E + 255) / 256, (int64_t)n_sm * 16));
+    // one resident wave (the kernel is register-heavy: 2 blocks of 256 per SM)
+    const int blocks = static_cast<int>(std::min<int64_t>((E + 255) / 256, (int64_t)n_sm * 2));
     k_adam<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(A, m, v);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "clod_adam_step launch");
