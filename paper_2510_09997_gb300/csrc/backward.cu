@@ -92,8 +92,8 @@ __device__ __forceinline__ bool bwd_one(BPx& q, float fpx, const float4& a, cons
     // never fused): same power, same exponential, same skip
     const float dx = __fsub_rn(a.x, fpx), dy = __fsub_rn(a.y, q.fy);
     const float power = __fmaf_rn(dx, __fmaf_rn(a.z, dx, __fmul_rn(a.w, dy)), __fmul_rn(__fmul_rn(c.x, dy), dy));
-    if (power > 0.0f || power < -5.6f) return false;
-    const float G = exp_spec(power);
+    if (!(power <= 0.0f && power >= -5.6f)) return false;
+    const float G = exp_spec_core(power);   // power in [-5.6, 0]
     const float raw = __fmul_rn(c.y, G);
     const float al = fminf(0.99f, raw);
     if (al < (1.0f / 255.0f)) return false;
@@ -338,6 +338,10 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(Frame F, clod_scene S, c
                 const float g_u = G0.x, g_v = G0.y, g_A = G0.z, g_B = G0.w, g_C = G1.x;
                 g_a2 += G1.y;
                 const float g_col[3] = {G1.z, G1.w, Gb};
+                // the forward's clamped colours: max(SH + 0.5, 0) > 0 is the
+                // forward's own decision of whether the clamp was inactive
+                const float4 R1 = F.rec1[o];
+                const float col[3] = {R1.z, R1.w, F.rec2[o].x};
                 // ---- colour (SH) -------------------------------------------------
                 const float inv_d = 1.0f / d;
                 const float dx = e0 * inv_d, dy = e1 * inv_d, dz = e2 * inv_d;
@@ -348,10 +352,7 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(Frame F, clod_scene S, c
                 float gdx = 0.f, gdy = 0.f, gdz = 0.f;
 #pragma unroll
                 for (int ch = 0; ch < 3; ++ch) {
-                    float acc = 0.f;
-#pragma unroll
-                    for (int k = 0; k < K; ++k) acc += b[k] * shp[3 * k + ch];
-                    if (acc + 0.5f > 0.0f && g_col[ch] != 0.0f) {
+                    if (col[ch] > 0.0f && g_col[ch] != 0.0f) {
                         const float gc = g_col[ch];
 #pragma unroll
                         for (int k = 0; k < K; ++k) {

@@ -7,8 +7,10 @@
 //
 //   1. depth-rank sort: a stable LSD radix sort (8-bit digits, four passes)
 //      of the survivors' depth bits per view, values = Gaussian index in
-//      index order, culled Gaussians keyed all-ones (sorted last).  The last
-//      pass also gathers each survivor's tile rectangle into rank order.
+//      index order.  Culled Gaussians (keyed all-ones by the preprocessing)
+//      are dropped by the first pass, so the later passes move only the
+//      survivors.  The last pass also gathers each survivor's tile
+//      rectangle into rank order.
 //   2. the survivors of a view are cut into chunks of consecutive ranks; one
 //      warp per (chunk, tile row) walks the chunk's rectangles in rank order
 //      and counts, per tile of its row, the pairs the chunk contributes
@@ -41,7 +43,7 @@ __device__ __forceinline__ uint32_t lanemask_lt()
 // Per-warp digit counts of the block's items: warp w owns items
 // [w * 512, w * 512 + 512) of the block, in order.
 __device__ __forceinline__ void rs_warp_counts(const uint32_t* __restrict__ keys, int64_t base, int cnt, int shift,
-                                               uint32_t (*h)[256])
+                                               uint32_t (*h)[256], bool drop)
 {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int k = lane; k < 256; k += 32) h[w][k] = 0;
@@ -49,15 +51,27 @@ __device__ __forceinline__ void rs_warp_counts(const uint32_t* __restrict__ keys
     constexpr int PER_WARP = RS_ITEMS / (RS_THREADS / 32);
     for (int r = 0; r < PER_WARP; r += 32) {
         const int idx = w * PER_WARP + r + lane;
-        const bool valid = idx < cnt;
-        const uint32_t d = valid ? ((keys[base + idx] >> shift) & 255u) : 256u;
+        uint32_t key = 0u;
+        bool valid = idx < cnt;
+        if (valid) key = keys[base + idx];
+        if (drop && key == 0xFFFFFFFFu) valid = false;
+        const uint32_t d = valid ? ((key >> shift) & 255u) : 256u;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
         if (valid && (__ffs(peers) - 1) == lane) h[w][d] += __popc(peers);
         __syncwarp();
     }
 }
 
+// Items of radix block lb of view v: the first pass reads all n keys of the
+// view (and drops the culled); later passes read the view's survivors.
+__device__ __forceinline__ int rs_block_count(const uint32_t* n_surv, int v, int64_t n, int lb, bool first)
+{
+    const int64_t nv = first ? n : (int64_t)n_surv[2 * v + 1];
+    return (int)max((int64_t)0, min((int64_t)RS_ITEMS, nv - (int64_t)lb * RS_ITEMS));
+}
+
 __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const FrameHeader* __restrict__ hdr,
+                                                        const uint32_t* __restrict__ n_surv,
                                                         const uint32_t* __restrict__ keys, int64_t n, int nb, int shift,
                                                         uint32_t* __restrict__ hist, uint32_t* __restrict__ totals)
 {
@@ -65,8 +79,12 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const FrameHeader* __res
     const int b = blockIdx.x, v = b / nb, lb = b % nb;
     if ((uint32_t)v >= hdr->n_views) return;
     const int64_t base = (int64_t)v * n + (int64_t)lb * RS_ITEMS;
-    const int cnt = (int)min((int64_t)RS_ITEMS, n - (int64_t)lb * RS_ITEMS);
-    rs_warp_counts(keys, base, cnt, shift, h);
+    const int cnt = rs_block_count(n_surv, v, n, lb, shift == 0);
+    if (cnt == 0) {     // no items: zero counts for the scan
+        hist[((size_t)v * 256 + threadIdx.x) * nb + lb] = 0u;
+        return;
+    }
+    rs_warp_counts(keys, base, cnt, shift, h, shift == 0);
     __syncthreads();
     uint32_t s = 0;
     for (int w = 0; w < RS_THREADS / 32; ++w) s += h[w][threadIdx.x];
@@ -99,6 +117,7 @@ __global__ void __launch_bounds__(1024) k_rs_scan(const FrameHeader* __restrict_
 // Stable scatter of one digit pass; on the last pass also gathers the tile
 // rectangle of every survivor into rank order.
 __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const FrameHeader* __restrict__ hdr,
+                                                           const uint32_t* __restrict__ n_surv,
                                                            const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                            uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                            int64_t n, int nb, int shift, const uint32_t* __restrict__ hist,
@@ -113,8 +132,10 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const FrameHeader* __
     if ((uint32_t)v >= hdr->n_views) return;
     const int64_t vbase = (int64_t)v * n;
     const int64_t base = vbase + (int64_t)lb * RS_ITEMS;
-    const int cnt = (int)min((int64_t)RS_ITEMS, n - (int64_t)lb * RS_ITEMS);
-    rs_warp_counts(kin, base, cnt, shift, h);
+    const bool first = shift == 0;
+    const int cnt = rs_block_count(n_surv, v, n, lb, first);
+    if (cnt == 0) return;
+    rs_warp_counts(kin, base, cnt, shift, h, first);
     {
         // exclusive scan of the view's 256 digit totals (RS_THREADS == 256)
         const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
@@ -144,8 +165,9 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const FrameHeader* __
     constexpr int PER_WARP = RS_ITEMS / (RS_THREADS / 32);
     for (int r = 0; r < PER_WARP; r += 32) {
         const int idx = w * PER_WARP + r + lane;
-        const bool valid = idx < cnt;
+        bool valid = idx < cnt;
         const uint32_t key = valid ? kin[base + idx] : 0u;
+        if (first && key == 0xFFFFFFFFu) valid = false;     // culled: dropped
         const uint32_t d = valid ? ((key >> shift) & 255u) : 256u;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
         if (valid) {
@@ -153,7 +175,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const FrameHeader* __
             const uint32_t val = vin[base + idx];
             kout[vbase + pos] = key;
             vout[vbase + pos] = val;
-            if (srect && key != 0xFFFFFFFFu) srect[vbase + pos] = rect[vbase + val];
+            if (srect) srect[vbase + pos] = rect[vbase + val];
         }
         __syncwarp();
         if (valid && (__ffs(peers) - 1) == lane) wb[w][d] += __popc(peers);
@@ -488,10 +510,10 @@ void launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long long ca
         cudaMemsetAsync(totals, 0, sizeof(uint32_t) * 4 * V * 256, st);
         for (int pass = 0; pass < 4; ++pass) {
             uint32_t* tot = totals + (size_t)pass * V * 256;
-            k_rs_hist<<<V * nb, RS_THREADS, 0, st>>>(F.hdr, ki, n, nb, 8 * pass, F.rs_hist, tot);
+            k_rs_hist<<<V * nb, RS_THREADS, 0, st>>>(F.hdr, F.n_surv, ki, n, nb, 8 * pass, F.rs_hist, tot);
             k_rs_scan<<<(V * 256 + 31) / 32, 1024, 0, st>>>(F.hdr, F.rs_hist, nb);
-            k_rs_scatter<<<V * nb, RS_THREADS, 0, st>>>(F.hdr, ki, vi, ko, vo, n, nb, 8 * pass, F.rs_hist, tot, F.rect,
-                                                        pass == 3 ? F.srect : nullptr);
+            k_rs_scatter<<<V * nb, RS_THREADS, 0, st>>>(F.hdr, F.n_surv, ki, vi, ko, vo, n, nb, 8 * pass, F.rs_hist,
+                                                        tot, F.rect, pass == 3 ? F.srect : nullptr);
             std::swap(ki, ko);
             std::swap(vi, vo);
         }

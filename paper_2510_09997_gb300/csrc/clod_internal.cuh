@@ -119,10 +119,10 @@ __device__ __forceinline__ unsigned long long budget_key(float a2, uint32_t i)
 // float (so r >= 0), e^r by a degree-9 Taylor polynomial (Horner), capped at
 // 2, scaled by 2^k.  Monotone non-decreasing; 0 below -80 and for NaN.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float exp_spec(float x)
+// exp_spec for x already known to lie in [-80, 0] (the blends call it after
+// their power range test); exp_spec below adds the range handling.
+__device__ __forceinline__ float exp_spec_core(float x)
 {
-    if (!(x >= -80.0f)) return 0.0f;
-    if (x > 0.0f) x = 0.0f;
     const float L2E = __int_as_float(0x3FB8AA3C);
     const float MAGIC = 12582912.0f;
     const float LN2HI = __int_as_float(0x3F317218);
@@ -145,6 +145,13 @@ __device__ __forceinline__ float exp_spec(float x)
     p = fminf(p, 2.0f);
     // p in [1, 2], k >= -116: the scaled value is a normal float
     return __int_as_float(__float_as_int(p) + (static_cast<int>(kf) << 23));
+}
+
+__device__ __forceinline__ float exp_spec(float x)
+{
+    if (!(x >= -80.0f)) return 0.0f;
+    if (x > 0.0f) x = 0.0f;
+    return exp_spec_core(x);
 }
 
 // Camera-frame point: t_k = R_k0 x + (R_k1 y + (R_k2 z + t_k)), fused.
@@ -254,8 +261,8 @@ __device__ __forceinline__ void sh_basis(float x, float y, float z, int deg, flo
 __device__ __forceinline__ float blend_alpha(float dx, float dy, float nA, float nB, float nC, float a2)
 {
     const float power = __fmaf_rn(dx, __fmaf_rn(nA, dx, __fmul_rn(nB, dy)), __fmul_rn(__fmul_rn(nC, dy), dy));
-    if (power > 0.0f || power < -5.6f) return -1.0f;
-    const float a = fminf(0.99f, __fmul_rn(a2, exp_spec(power)));
+    if (!(power <= 0.0f && power >= -5.6f)) return -1.0f;   // also skips a NaN power (exp_spec(NaN) = 0)
+    const float a = fminf(0.99f, __fmul_rn(a2, exp_spec_core(power)));   // power in [-5.6, 0]
     return a < (1.0f / 255.0f) ? -1.0f : a;
 }
 

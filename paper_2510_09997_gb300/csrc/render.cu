@@ -32,7 +32,7 @@ __device__ __forceinline__ void blend_one(Px& q, float fpx, float fpy, const flo
     const float ddx = __fsub_rn(a.x, fpx), ddy = __fsub_rn(a.y, fpy);
     if (COUNT) {
         const float pw = __fmaf_rn(ddx, __fmaf_rn(a.z, ddx, __fmul_rn(a.w, ddy)), __fmul_rn(__fmul_rn(c.x, ddy), ddy));
-        if (!(pw > 0.0f || pw < -5.6f)) ++n_exp;
+        if (pw <= 0.0f && pw >= -5.6f) ++n_exp;
     }
     const float al = blend_alpha(ddx, ddy, a.z, a.w, c.x, c.y);
     if (al < 0.0f) return;
