@@ -97,7 +97,7 @@ __device__ __forceinline__ bool bwd_one(BPx& q, float fpx, const float4& a, cons
     const float raw = __fmul_rn(c.y, G);
     const float al = fminf(0.99f, raw);
     if (al < (1.0f / 255.0f)) return false;
-    const float iom = __frcp_rn(1.0f - al);
+    const float iom = __fdividef(1.0f, 1.0f - al);   // fast reciprocal: 1 - al >= 0.01
     const float Tb = q.T * iom;
     const float w = al * Tb;
     g[6] += w * q.d0;
@@ -236,43 +236,58 @@ __global__ void __launch_bounds__(BWD_THREADS) k_blend_bwd(Frame F, const uint32
     }
 }
 
-// SH basis and its derivative with respect to the direction (x, y, z).
-__device__ __forceinline__ void sh_basis_grad(float x, float y, float z, int deg, float* b, float* bx, float* by,
-                                              float* bz)
+// Real SH basis function k (colour-model signs) at unit direction (x, y, z)
+// and its partial derivatives; xx, yy, zz are the squares.
+__device__ __forceinline__ void sh_term(int k, float x, float y, float z, float xx, float yy, float zz, float& b,
+                                        float& bx, float& by, float& bz)
 {
     const float C1 = CLOD_SH_C1;
-    b[0] = CLOD_SH_C0;
-    bx[0] = by[0] = bz[0] = 0.f;
-    if (deg < 1) return;
-    b[1] = -C1 * y; bx[1] = 0.f; by[1] = -C1; bz[1] = 0.f;
-    b[2] = C1 * z;  bx[2] = 0.f; by[2] = 0.f; bz[2] = C1;
-    b[3] = -C1 * x; bx[3] = -C1; by[3] = 0.f; bz[3] = 0.f;
-    if (deg < 2) return;
-    const float xx = x * x, yy = y * y, zz = z * z;
-    b[4] = CLOD_SH_C2_0 * x * y; bx[4] = CLOD_SH_C2_0 * y; by[4] = CLOD_SH_C2_0 * x; bz[4] = 0.f;
-    b[5] = CLOD_SH_C2_1 * y * z; bx[5] = 0.f; by[5] = CLOD_SH_C2_1 * z; bz[5] = CLOD_SH_C2_1 * y;
-    b[6] = CLOD_SH_C2_2 * (2.f * zz - xx - yy);
-    bx[6] = -2.f * CLOD_SH_C2_2 * x; by[6] = -2.f * CLOD_SH_C2_2 * y; bz[6] = 4.f * CLOD_SH_C2_2 * z;
-    b[7] = CLOD_SH_C2_3 * x * z; bx[7] = CLOD_SH_C2_3 * z; by[7] = 0.f; bz[7] = CLOD_SH_C2_3 * x;
-    b[8] = CLOD_SH_C2_4 * (xx - yy); bx[8] = 2.f * CLOD_SH_C2_4 * x; by[8] = -2.f * CLOD_SH_C2_4 * y; bz[8] = 0.f;
-    if (deg < 3) return;
-    b[9] = CLOD_SH_C3_0 * y * (3.f * xx - yy);
-    bx[9] = 6.f * CLOD_SH_C3_0 * x * y; by[9] = CLOD_SH_C3_0 * (3.f * xx - 3.f * yy); bz[9] = 0.f;
-    b[10] = CLOD_SH_C3_1 * x * y * z;
-    bx[10] = CLOD_SH_C3_1 * y * z; by[10] = CLOD_SH_C3_1 * x * z; bz[10] = CLOD_SH_C3_1 * x * y;
-    b[11] = CLOD_SH_C3_2 * y * (4.f * zz - xx - yy);
-    bx[11] = -2.f * CLOD_SH_C3_2 * x * y; by[11] = CLOD_SH_C3_2 * (4.f * zz - xx - 3.f * yy);
-    bz[11] = 8.f * CLOD_SH_C3_2 * y * z;
-    b[12] = CLOD_SH_C3_3 * z * (2.f * zz - 3.f * xx - 3.f * yy);
-    bx[12] = -6.f * CLOD_SH_C3_3 * x * z; by[12] = -6.f * CLOD_SH_C3_3 * y * z;
-    bz[12] = CLOD_SH_C3_3 * (6.f * zz - 3.f * xx - 3.f * yy);
-    b[13] = CLOD_SH_C3_4 * x * (4.f * zz - xx - yy);
-    bx[13] = CLOD_SH_C3_4 * (4.f * zz - 3.f * xx - yy); by[13] = -2.f * CLOD_SH_C3_4 * x * y;
-    bz[13] = 8.f * CLOD_SH_C3_4 * x * z;
-    b[14] = CLOD_SH_C3_5 * z * (xx - yy);
-    bx[14] = 2.f * CLOD_SH_C3_5 * x * z; by[14] = -2.f * CLOD_SH_C3_5 * y * z; bz[14] = CLOD_SH_C3_5 * (xx - yy);
-    b[15] = CLOD_SH_C3_6 * x * (xx - 3.f * yy);
-    bx[15] = CLOD_SH_C3_6 * (3.f * xx - 3.f * yy); by[15] = -6.f * CLOD_SH_C3_6 * x * y; bz[15] = 0.f;
+    bx = by = bz = 0.f;
+    switch (k) {
+    case 0: b = CLOD_SH_C0; break;
+    case 1: b = -C1 * y; by = -C1; break;
+    case 2: b = C1 * z; bz = C1; break;
+    case 3: b = -C1 * x; bx = -C1; break;
+    case 4: b = CLOD_SH_C2_0 * x * y; bx = CLOD_SH_C2_0 * y; by = CLOD_SH_C2_0 * x; break;
+    case 5: b = CLOD_SH_C2_1 * y * z; by = CLOD_SH_C2_1 * z; bz = CLOD_SH_C2_1 * y; break;
+    case 6:
+        b = CLOD_SH_C2_2 * (2.f * zz - xx - yy);
+        bx = -2.f * CLOD_SH_C2_2 * x; by = -2.f * CLOD_SH_C2_2 * y; bz = 4.f * CLOD_SH_C2_2 * z;
+        break;
+    case 7: b = CLOD_SH_C2_3 * x * z; bx = CLOD_SH_C2_3 * z; bz = CLOD_SH_C2_3 * x; break;
+    case 8: b = CLOD_SH_C2_4 * (xx - yy); bx = 2.f * CLOD_SH_C2_4 * x; by = -2.f * CLOD_SH_C2_4 * y; break;
+    case 9:
+        b = CLOD_SH_C3_0 * y * (3.f * xx - yy);
+        bx = 6.f * CLOD_SH_C3_0 * x * y; by = CLOD_SH_C3_0 * (3.f * xx - 3.f * yy);
+        break;
+    case 10:
+        b = CLOD_SH_C3_1 * x * y * z;
+        bx = CLOD_SH_C3_1 * y * z; by = CLOD_SH_C3_1 * x * z; bz = CLOD_SH_C3_1 * x * y;
+        break;
+    case 11:
+        b = CLOD_SH_C3_2 * y * (4.f * zz - xx - yy);
+        bx = -2.f * CLOD_SH_C3_2 * x * y; by = CLOD_SH_C3_2 * (4.f * zz - xx - 3.f * yy);
+        bz = 8.f * CLOD_SH_C3_2 * y * z;
+        break;
+    case 12:
+        b = CLOD_SH_C3_3 * z * (2.f * zz - 3.f * xx - 3.f * yy);
+        bx = -6.f * CLOD_SH_C3_3 * x * z; by = -6.f * CLOD_SH_C3_3 * y * z;
+        bz = CLOD_SH_C3_3 * (6.f * zz - 3.f * xx - 3.f * yy);
+        break;
+    case 13:
+        b = CLOD_SH_C3_4 * x * (4.f * zz - xx - yy);
+        bx = CLOD_SH_C3_4 * (4.f * zz - 3.f * xx - yy); by = -2.f * CLOD_SH_C3_4 * x * y;
+        bz = 8.f * CLOD_SH_C3_4 * x * z;
+        break;
+    case 14:
+        b = CLOD_SH_C3_5 * z * (xx - yy);
+        bx = 2.f * CLOD_SH_C3_5 * x * z; by = -2.f * CLOD_SH_C3_5 * y * z; bz = CLOD_SH_C3_5 * (xx - yy);
+        break;
+    default:
+        b = CLOD_SH_C3_6 * x * (xx - 3.f * yy);
+        bx = CLOD_SH_C3_6 * (3.f * xx - 3.f * yy); by = -6.f * CLOD_SH_C3_6 * x * y;
+        break;
+    }
 }
 
 struct ParamGrads {
@@ -285,7 +300,7 @@ struct ParamGrads {
 };
 
 template <int DEG>
-__global__ void __launch_bounds__(128) k_preprocess_bwd(Frame F, clod_scene S, const float4* __restrict__ g2d,
+__global__ void __launch_bounds__(128, 6) k_preprocess_bwd(Frame F, clod_scene S, const float4* __restrict__ g2d,
                                                         const float* __restrict__ g_alpha_ext,
                                                         const float* __restrict__ g_alpha_view,
                                                         float* __restrict__ dmax_grad, ParamGrads P)
@@ -345,23 +360,28 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(Frame F, clod_scene S, c
                 // ---- colour (SH) -------------------------------------------------
                 const float inv_d = 1.0f / d;
                 const float dx = e0 * inv_d, dy = e1 * inv_d, dz = e2 * inv_d;
-                float b[16], bx[16], by[16], bz[16];
-                sh_basis_grad(dx, dy, dz, deg, b, bx, by, bz);
                 const float* shp = S.sh + (size_t)i * K * 3;
                 float* dshp = P.dsh + (size_t)i * K * 3;
+                // gradient reaching each channel's SH sum (0 where the clamp held)
+                const float gc0 = col[0] > 0.0f ? g_col[0] : 0.0f;
+                const float gc1 = col[1] > 0.0f ? g_col[1] : 0.0f;
+                const float gc2 = col[2] > 0.0f ? g_col[2] : 0.0f;
                 float gdx = 0.f, gdy = 0.f, gdz = 0.f;
+                if (gc0 != 0.0f || gc1 != 0.0f || gc2 != 0.0f) {
+                    const float xx = dx * dx, yy = dy * dy, zz = dz * dz;
+                    // one basis function and its direction derivatives at a
+                    // time (k is a compile-time constant after unrolling)
 #pragma unroll
-                for (int ch = 0; ch < 3; ++ch) {
-                    if (col[ch] > 0.0f && g_col[ch] != 0.0f) {
-                        const float gc = g_col[ch];
-#pragma unroll
-                        for (int k = 0; k < K; ++k) {
-                            dshp[3 * k + ch] += b[k] * gc;
-                            const float s = shp[3 * k + ch] * gc;
-                            gdx += bx[k] * s;
-                            gdy += by[k] * s;
-                            gdz += bz[k] * s;
-                        }
+                    for (int k = 0; k < K; ++k) {
+                        float bk, bxk, byk, bzk;
+                        sh_term(k, dx, dy, dz, xx, yy, zz, bk, bxk, byk, bzk);
+                        const float s = shp[3 * k] * gc0 + shp[3 * k + 1] * gc1 + shp[3 * k + 2] * gc2;
+                        gdx += bxk * s;
+                        gdy += byk * s;
+                        gdz += bzk * s;
+                        if (gc0 != 0.0f) dshp[3 * k] += bk * gc0;
+                        if (gc1 != 0.0f) dshp[3 * k + 1] += bk * gc1;
+                        if (gc2 != 0.0f) dshp[3 * k + 2] += bk * gc2;
                     }
                 }
                 // direction = e / |e|
