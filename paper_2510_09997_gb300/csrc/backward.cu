@@ -300,7 +300,7 @@ struct ParamGrads {
 };
 
 template <int DEG>
-__global__ void __launch_bounds__(128, 6) k_preprocess_bwd(Frame F, clod_scene S, const float4* __restrict__ g2d,
+__global__ void __launch_bounds__(128) k_preprocess_bwd(Frame F, clod_scene S, const float4* __restrict__ g2d,
                                                         const float* __restrict__ g_alpha_ext,
                                                         const float* __restrict__ g_alpha_view,
                                                         float* __restrict__ dmax_grad, ParamGrads P)
