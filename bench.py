@@ -364,9 +364,54 @@ def cpu_baseline(sc, views, budget_s=20.0):
         tsum += time.perf_counter() - a
         done += len(chunk)
     frame_s = (t1 - t0) + tsum * ntiles / max(done, 1)
-    return {"value": round(1.0 / frame_s, 5), "unit": "frames/s", "cores": 1, "kind": "oracle",
-            "sample": "camera 0, s_v=1: full Stage I + pairs + sort, blend of %d/%d random tiles scaled to the frame"
-                      % (done, ntiles), "seconds": round((t1 - t0) + tsum, 2)}
+    out = {"value": round(1.0 / frame_s, 5), "unit": "frames/s", "cores": 1, "kind": "oracle",
+           "sample": "camera 0, s_v=1: full Stage I + pairs + sort, blend of %d/%d random tiles scaled to the frame"
+                     % (done, ntiles), "seconds": round((t1 - t0) + tsum, 2)}
+    try:
+        out["parallel"] = cpu_baseline_parallel(t1 - t0, order, ntiles, budget_s)
+    except Exception as e:           # the single-core figure stands on its own
+        out["parallel"] = {"unavailable": str(e)[:200]}
+    return out
+
+
+def _oracle_worker_init():
+    global _W
+    from oracle import oracle as O
+    from paper_2510_09997_gb300 import synth as S
+    sc = S.object_scene(N_GAUSS)
+    v = S.orbit_cameras(N_CAMS, WIDTH, HEIGHT)[0].replace(s_v=1.0)
+    _W = (O, sc, v, O.stage1(sc, v))
+
+
+def _oracle_worker_tiles(chunk):
+    O, sc, v, s1 = _W
+    a = time.perf_counter()
+    O.render(sc, v, s1, None, tiles=np.asarray(chunk))
+    return time.perf_counter() - a
+
+
+def cpu_baseline_parallel(t_stage1, order, ntiles, budget_s):
+    """The same oracle on every host core: Stage I, pairs and sort once (the
+    single-thread time above), the sampled tiles split over worker processes
+    (spawned, each rebuilding the scene and Stage I untimed)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    with cf.ProcessPoolExecutor(max_workers=cores, mp_context=mp.get_context("spawn"),
+                                initializer=_oracle_worker_init) as ex:
+        list(ex.map(_oracle_worker_tiles, [order[:1]] * cores))       # workers ready
+        done, wall = 0, 0.0
+        while done < ntiles and wall < budget_s / 2:
+            chunks = [order[done + 32 * k: done + 32 * (k + 1)] for k in range(cores)]
+            chunks = [c for c in chunks if len(c)]
+            a = time.perf_counter()
+            list(ex.map(_oracle_worker_tiles, chunks))
+            wall += time.perf_counter() - a
+            done += sum(len(c) for c in chunks)
+    frame_s = t_stage1 + wall * ntiles / max(done, 1)
+    return {"value": round(1.0 / frame_s, 5), "unit": "frames/s", "cores": cores, "kind": "oracle",
+            "sample": "as the single-core figure; blend of %d/%d tiles over %d processes, Stage I single-threaded"
+                      % (done, ntiles, cores)}
 
 
 def train_leg(args):

@@ -122,7 +122,7 @@ __device__ __forceinline__ bool bwd_one(BPx& q, float fpx, const float4& a, cons
 
 constexpr int BWD_THREADS = 128;   // 4 warps per tile, 8x8 pixels per warp, 2 per thread
 
-__global__ void __launch_bounds__(BWD_THREADS) k_blend_bwd(Frame F, const uint32_t* __restrict__ vals,
+__global__ void __launch_bounds__(BWD_THREADS, 8) k_blend_bwd(Frame F, const uint32_t* __restrict__ vals,
                                                            const uint32_t* __restrict__ ranges,
                                                            const float* __restrict__ Tfin,
                                                            const uint32_t* __restrict__ ncon,

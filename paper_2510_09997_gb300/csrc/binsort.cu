@@ -420,38 +420,50 @@ __global__ void __launch_bounds__(512) k_chunk_count(Frame F)
 }
 
 // 3a. per tile: exclusive scan of the chunk counts; tile_count = total.
-__global__ void __launch_bounds__(256) k_chunk_scan(Frame F)
+// A block takes 32 tiles (one per lane, so every load of a chunk's counts is
+// coalesced) and cuts the chunks into 8 segments, one per warp: segment
+// sums, their scan across the warps, then each segment rescanned.
+constexpr int CS_TILES = 32, CS_SEG = 8;
+__global__ void __launch_bounds__(CS_TILES * CS_SEG) k_chunk_scan(Frame F)
 {
+    __shared__ uint32_t part[CS_SEG][CS_TILES];
     const uint32_t TT = F.hdr->total_tiles;
     const uint32_t V = F.hdr->n_views;
     const uint32_t CH = F.hdr->n_chunks;
-    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= TT) return;
-    int v = 0;
-    for (uint32_t u = 1; u < V; ++u)
-        if (t >= F.views[u].tile_base) v = (int)u;
-    const ViewDev& W = F.views[v];
-    const uint32_t T = (uint32_t)(W.TX * W.TY);
-    uint32_t* col = F.cnt + (size_t)CH * W.tile_base + (t - W.tile_base);
-    uint32_t acc = 0;
-    constexpr int B = 8;
-    uint32_t c = 0;
-    for (; c + B <= CH; c += B) {
-        uint32_t x[B];
-#pragma unroll
-        for (int k = 0; k < B; ++k) x[k] = col[(size_t)(c + k) * T];
-#pragma unroll
-        for (int k = 0; k < B; ++k) {
-            col[(size_t)(c + k) * T] = acc;
-            acc += x[k];
-        }
+    const int tx = threadIdx.x % CS_TILES, sg = threadIdx.x / CS_TILES;
+    const uint32_t t = blockIdx.x * CS_TILES + tx;
+    const bool ok = t < TT;
+    uint32_t* col = nullptr;
+    uint32_t T = 0;
+    if (ok) {
+        int v = 0;
+        for (uint32_t u = 1; u < V; ++u)
+            if (t >= F.views[u].tile_base) v = (int)u;
+        const ViewDev& W = F.views[v];
+        T = (uint32_t)(W.TX * W.TY);
+        col = F.cnt + (size_t)CH * W.tile_base + (t - W.tile_base);
     }
-    for (; c < CH; ++c) {
+    const uint32_t per = (CH + CS_SEG - 1) / CS_SEG;
+    const uint32_t c0 = min(CH, sg * per), c1 = min(CH, c0 + per);
+    uint32_t sum = 0;
+    if (ok)
+        for (uint32_t c = c0; c < c1; ++c) sum += col[(size_t)c * T];
+    part[sg][tx] = sum;
+    __syncthreads();
+    uint32_t off = 0, tot = 0;
+#pragma unroll
+    for (int q = 0; q < CS_SEG; ++q) {
+        const uint32_t x = part[q][tx];
+        if (q < sg) off += x;
+        tot += x;
+    }
+    if (!ok) return;
+    for (uint32_t c = c0; c < c1; ++c) {
         const uint32_t x = col[(size_t)c * T];
-        col[(size_t)c * T] = acc;
-        acc += x;
+        col[(size_t)c * T] = off;
+        off += x;
     }
-    F.tile_count[t] = acc;
+    if (sg == 0) F.tile_count[t] = tot;
 }
 
 // 3b. exclusive scan of the tile counts by one block of 1024 threads; writes
@@ -523,7 +535,7 @@ void launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long long ca
         k_chunk_count<<<V * L.n_chunks, 512, L.diff_grid_max * sizeof(uint32_t), st>>>(F);
     else
         k_rows<false><<<L.rb_total, ROWS_PER_BLOCK * 32, smem, st>>>(F, nullptr, nullptr);
-    k_chunk_scan<<<(L.total_tiles + 255) / 256, 256, 0, st>>>(F);
+    k_chunk_scan<<<(L.total_tiles + CS_TILES - 1) / CS_TILES, CS_TILES * CS_SEG, 0, st>>>(F);
     k_scan_tiles<<<1, 1024, 0, st>>>(F, ranges, cap);
     k_rows<true><<<L.rb_total, ROWS_PER_BLOCK * 32, smem, st>>>(F, vals, reinterpret_cast<unsigned long long*>(keys));
 }

@@ -129,7 +129,13 @@ __device__ __forceinline__ float exp_spec_core(float x)
     const float LN2LO = __int_as_float(0xB102E308);
     float t = __fmaf_rn(x, L2E, MAGIC);
     float kf = __fsub_rn(t, MAGIC);
-    if (__fmaf_rn(x, L2E, -kf) < 0.0f) kf = __fsub_rn(kf, 1.0f);
+    // t lies in [MAGIC - 116, MAGIC], where floats are spaced by 1: its bits
+    // minus MAGIC's are the same integer as kf (no float-to-int conversion)
+    int ki = __float_as_int(t) - 0x4B400000;
+    if (__fmaf_rn(x, L2E, -kf) < 0.0f) {
+        kf = __fsub_rn(kf, 1.0f);
+        ki -= 1;
+    }
     float r = __fmaf_rn(kf, -LN2HI, x);
     r = __fmaf_rn(kf, -LN2LO, r);
     float p = __int_as_float(0x3638EF1D);            // 1/9!
@@ -144,7 +150,7 @@ __device__ __forceinline__ float exp_spec_core(float x)
     p = __fmaf_rn(p, r, 1.0f);
     p = fminf(p, 2.0f);
     // p in [1, 2], k >= -116: the scaled value is a normal float
-    return __int_as_float(__float_as_int(p) + (static_cast<int>(kf) << 23));
+    return __int_as_float(__float_as_int(p) + (ki << 23));
 }
 
 __device__ __forceinline__ float exp_spec(float x)
