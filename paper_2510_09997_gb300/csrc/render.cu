@@ -36,18 +36,18 @@ __device__ __forceinline__ void blend_one(Px& q, float fpx, float fpy, const flo
     }
     const float al = blend_alpha(ddx, ddy, a.z, a.w, c.x, c.y);
     if (al < 0.0f) return;
+    // contributor or stop, without a second branch: a stopping pixel adds
+    // 0 * colour (exact: C + 0 = C) and keeps T and last
     const float tt = __fmul_rn(q.T, __fsub_rn(1.0f, al));
-    if (tt < 1e-4f) {
-        q.done = true;
-        return;
-    }
-    const float w = __fmul_rn(al, q.T);
+    const bool con = !(tt < 1e-4f);
+    const float w = con ? __fmul_rn(al, q.T) : 0.0f;
     q.C0 = __fmaf_rn(c.z, w, q.C0);
     q.C1 = __fmaf_rn(c.w, w, q.C1);
     q.C2 = __fmaf_rn(cb, w, q.C2);
-    q.T = tt;
-    q.last = pos;
-    if (COUNT) ++n_con;
+    q.T = con ? tt : q.T;
+    q.last = con ? pos : q.last;
+    q.done = !con;
+    if (COUNT && con) ++n_con;
 }
 
 __device__ __forceinline__ void store_px(const ViewDev& W, const Px& q, int px, int py, float* image, float* Tout,
