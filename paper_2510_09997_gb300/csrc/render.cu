@@ -50,6 +50,43 @@ __device__ __forceinline__ void blend_one(Px& q, float fpx, float fpy, const flo
     if (COUNT && con) ++n_con;
 }
 
+// The contributor/stop update of one pixel once its opacity al (< 0: skip)
+// is known: same operations as blend_one.
+__device__ __forceinline__ void blend_finish(Px& q, float al, const float4& c, float cb, uint32_t pos)
+{
+    if (al < 0.0f) return;
+    const float tt = __fmul_rn(q.T, __fsub_rn(1.0f, al));
+    const bool con = !(tt < 1e-4f);
+    const float w = con ? __fmul_rn(al, q.T) : 0.0f;
+    q.C0 = __fmaf_rn(c.z, w, q.C0);
+    q.C1 = __fmaf_rn(c.w, w, q.C1);
+    q.C2 = __fmaf_rn(cb, w, q.C2);
+    q.T = con ? tt : q.T;
+    q.last = con ? pos : q.last;
+    q.done = !con;
+}
+
+// Both pixels of a thread against one Gaussian: the two powers, then (if
+// either lies in [-5.6, 0]) the two exponentials side by side, so that their
+// dependency chains interleave.  Every pixel's result is that of blend_one.
+__device__ __forceinline__ void blend_pair(Px& q0, Px& q1, bool t0, bool t1, float fpx, float fpy0, float fpy1,
+                                           const float4& a, const float4& c, float cb, uint32_t pos)
+{
+    const float ddx = __fsub_rn(a.x, fpx);
+    const float dy0 = __fsub_rn(a.y, fpy0), dy1 = __fsub_rn(a.y, fpy1);
+    const float p0 = __fmaf_rn(ddx, __fmaf_rn(a.z, ddx, __fmul_rn(a.w, dy0)), __fmul_rn(__fmul_rn(c.x, dy0), dy0));
+    const float p1 = __fmaf_rn(ddx, __fmaf_rn(a.z, ddx, __fmul_rn(a.w, dy1)), __fmul_rn(__fmul_rn(c.x, dy1), dy1));
+    const bool r0 = t0 && p0 <= 0.0f && p0 >= -5.6f;
+    const bool r1 = t1 && p1 <= 0.0f && p1 >= -5.6f;
+    if (!(r0 || r1)) return;
+    const float g0 = exp_spec_core(r0 ? p0 : 0.0f), g1 = exp_spec_core(r1 ? p1 : 0.0f);
+    float a0 = fminf(0.99f, __fmul_rn(c.y, g0)), a1 = fminf(0.99f, __fmul_rn(c.y, g1));
+    a0 = (r0 && !(a0 < (1.0f / 255.0f))) ? a0 : -1.0f;
+    a1 = (r1 && !(a1 < (1.0f / 255.0f))) ? a1 : -1.0f;
+    blend_finish(q0, a0, c, cb, pos);
+    blend_finish(q1, a1, c, cb, pos);
+}
+
 __device__ __forceinline__ void store_px(const ViewDev& W, const Px& q, int px, int py, float* image, float* Tout,
                                          uint32_t* ncout)
 {
@@ -152,14 +189,20 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_fwd(Frame F, const uint
                 const uint32_t pos = b - start + (uint32_t)k + 1u;
                 // the same reach box per pixel: outside it the pixel would skip
                 // this Gaussian (opacity < 1/255), so the test changes nothing
-                const bool ix = COUNT || fabsf(a.x - fpx) <= e.y;
-                if (!q0.done && ix && (COUNT || fabsf(a.y - fpy0) <= e.z)) {
-                    if (COUNT) ++evals;
-                    blend_one<COUNT>(q0, fpx, fpy0, a, c, e.x, pos, n_exp, n_con);
-                }
-                if (!q1.done && ix && (COUNT || fabsf(a.y - fpy1) <= e.z)) {
-                    if (COUNT) ++evals;
-                    blend_one<COUNT>(q1, fpx, fpy1, a, c, e.x, pos, n_exp, n_con);
+                if (COUNT) {
+                    if (!q0.done) {
+                        ++evals;
+                        blend_one<COUNT>(q0, fpx, fpy0, a, c, e.x, pos, n_exp, n_con);
+                    }
+                    if (!q1.done) {
+                        ++evals;
+                        blend_one<COUNT>(q1, fpx, fpy1, a, c, e.x, pos, n_exp, n_con);
+                    }
+                } else {
+                    const bool ix = fabsf(a.x - fpx) <= e.y;
+                    const bool t0 = !q0.done && ix && fabsf(a.y - fpy0) <= e.z;
+                    const bool t1 = !q1.done && ix && fabsf(a.y - fpy1) <= e.z;
+                    if (t0 || t1) blend_pair(q0, q1, t0, t1, fpx, fpy0, fpy1, a, c, e.x, pos);
                 }
             }
             __syncwarp();
