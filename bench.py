@@ -50,6 +50,28 @@ def frames_list(only=None):
     return [(c, s) for c in range(N_CAMS) for s in SCALES]
 
 
+def shard_frames(frames, rank, world):
+    """Replicas: rank r renders frames r, r + world, ... (disjoint shards that
+    together cover the sweep); no data-path collective."""
+    return list(frames[rank::world]) if world > 1 else list(frames)
+
+
+def max_over_ranks(x, device="cpu"):
+    """The slowest rank's time (all ranks take part when world > 1)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, elapsed_max):
+    """Units all ranks processed divided by the slowest rank's time."""
+    return units_per_rank * world / elapsed_max
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -149,7 +171,7 @@ def run_ours(args):
     cams = S.orbit_cameras(N_CAMS, WIDTH, HEIGHT)
     allf = frames_list(args.frame)
     # this rank's frames (replicas: rank r takes frames r, r+N, ...)
-    mine = allf[rank::world] if world > 1 else allf
+    mine = shard_frames(allf, rank, world)
     views = [cams[c].replace(s_v=s) for c, s in mine]
     ds = C.DeviceScene.from_scene(sc)
 
@@ -198,11 +220,7 @@ def run_ours(args):
     t1.record()
     torch.cuda.synchronize()
     clk = clocks.stop()
-    elapsed = t0.elapsed_time(t1) / 1e3
-    if world > 1:
-        tt = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed = float(tt.item())
+    elapsed = max_over_ranks(t0.elapsed_time(t1) / 1e3, device="cuda")
     R.check()   # every frame fitted the pair capacity (the last one is checked; all used K <= kmax)
     stage = np.array([[ev[k][j].elapsed_time(ev[k][j + 1]) for j in range(3)] for k in range(args.steps)])
     st_ms = stage.mean(0)
@@ -237,8 +255,7 @@ def run_ours(args):
     ev_per_frame = float(cnt3[0])
     flop_per_frame = FLOP_VISIT * cnt3[0] + FLOP_EXP * cnt3[1] + FLOP_CONTRIB * cnt3[2]
 
-    frames_total = args.steps * world
-    value = frames_total / elapsed
+    value = whole_job_rate(args.steps, world, elapsed)
     peaks = measured_peaks()
     sm_mhz = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     n_sm = torch.cuda.get_device_properties(0).multi_processor_count

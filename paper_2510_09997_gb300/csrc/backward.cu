@@ -83,17 +83,16 @@ struct BPx {
 };
 
 // Reverse blend of one pixel against one staged Gaussian at list position
-// pos (1-based); adds this pixel's 9 gradients into g.
-__device__ __forceinline__ bool bwd_one(BPx& q, float fpx, const float4& a, const float4& c, float cb, uint32_t pos,
-                                        float (&g)[16])
+// pos (1-based), split in two: the forward's decision arithmetic (explicit
+// round-to-nearest intrinsics, never fused: same power, same exponential,
+// same skip) in bwd_pair, the gradients in bwd_tail, which adds the pixel's
+// 9 gradients into g.
+// The gradient part for a pixel whose power is in range (r) and whose
+// exponential is G.
+__device__ __forceinline__ bool bwd_tail(BPx& q, bool r, float G, float dx, float dy, const float4& a,
+                                         const float4& c, float cb, float (&g)[16])
 {
-    if (pos > q.last) return false;
-    // the forward's decision arithmetic (explicit round-to-nearest intrinsics,
-    // never fused): same power, same exponential, same skip
-    const float dx = __fsub_rn(a.x, fpx), dy = __fsub_rn(a.y, q.fy);
-    const float power = __fmaf_rn(dx, __fmaf_rn(a.z, dx, __fmul_rn(a.w, dy)), __fmul_rn(__fmul_rn(c.x, dy), dy));
-    if (!(power <= 0.0f && power >= -5.6f)) return false;
-    const float G = exp_spec_core(power);   // power in [-5.6, 0]
+    if (!r) return false;
     const float raw = __fmul_rn(c.y, G);
     const float al = fminf(0.99f, raw);
     if (al < (1.0f / 255.0f)) return false;
@@ -118,6 +117,27 @@ __device__ __forceinline__ bool bwd_one(BPx& q, float fpx, const float4& a, cons
         g[4] += gp * (-0.5f * dy * dy);
     }
     return true;
+}
+
+// Both pixels of a thread against one Gaussian (only if not past their last
+// contributor), the two exponentials side by side.
+__device__ __forceinline__ bool bwd_pair(BPx& q0, BPx& q1, bool t0, bool t1, float fpx, const float4& a,
+                                         const float4& c, float cb, uint32_t pos, float (&g)[16])
+{
+    t0 = t0 && pos <= q0.last;
+    t1 = t1 && pos <= q1.last;
+    if (!(t0 || t1)) return false;
+    const float dx = __fsub_rn(a.x, fpx);
+    const float dy0 = __fsub_rn(a.y, q0.fy), dy1 = __fsub_rn(a.y, q1.fy);
+    const float p0 = __fmaf_rn(dx, __fmaf_rn(a.z, dx, __fmul_rn(a.w, dy0)), __fmul_rn(__fmul_rn(c.x, dy0), dy0));
+    const float p1 = __fmaf_rn(dx, __fmaf_rn(a.z, dx, __fmul_rn(a.w, dy1)), __fmul_rn(__fmul_rn(c.x, dy1), dy1));
+    const bool r0 = t0 && p0 <= 0.0f && p0 >= -5.6f;
+    const bool r1 = t1 && p1 <= 0.0f && p1 >= -5.6f;
+    if (!(r0 || r1)) return false;
+    const float G0 = exp_spec_core(r0 ? p0 : 0.0f), G1 = exp_spec_core(r1 ? p1 : 0.0f);
+    bool any = bwd_tail(q0, r0, G0, dx, dy0, a, c, cb, g);
+    any |= bwd_tail(q1, r1, G1, dx, dy1, a, c, cb, g);
+    return any;
 }
 
 constexpr int BWD_THREADS = 128;   // 4 warps per tile, 8x8 pixels per warp, 2 per thread
@@ -221,9 +241,9 @@ __global__ void __launch_bounds__(BWD_THREADS, 8) k_blend_bwd(Frame F, const uin
                 for (int i = 0; i < 16; ++i) g[i] = 0.0f;
                 // per-pixel reach box: outside it the forward skipped this Gaussian
                 const bool ix = fabsf(a.x - fpx) <= e.y;
-                bool any = false;
-                if (ix && fabsf(a.y - q[0].fy) <= e.z) any = bwd_one(q[0], fpx, a, c, e.x, pos, g);
-                if (ix && fabsf(a.y - q[1].fy) <= e.z) any |= bwd_one(q[1], fpx, a, c, e.x, pos, g);
+                const bool t0 = ix && fabsf(a.y - q[0].fy) <= e.z;
+                const bool t1 = ix && fabsf(a.y - q[1].fy) <= e.z;
+                const bool any = (t0 || t1) && bwd_pair(q[0], q[1], t0, t1, fpx, a, c, e.x, pos, g);
                 if (__any_sync(0xffffffffu, any)) {
                     const float tot = warp_reduce16(g);
                     if (!(lane & 1) && lane < 18) atomicAdd(g2d + 12 * sg[wid][k] + (lane >> 1), tot);
