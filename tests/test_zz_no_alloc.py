@@ -1,8 +1,9 @@
 """clod_render_noalloc: the forward render for callers that cannot allocate
 device memory (its scratch is a fixed array inside the library).  Checked
 through the C ABI against the allocating path (clod_preprocess /
-clod_bin_sort / clod_render_fwd), bit for bit, on two calls in a row: the
-second call must not see anything the first left in the shared array.
+clod_bin_sort / clod_render_fwd), bit for bit, on several calls in a row
+(including a primitive budget and a window of a frame): no call may see
+anything an earlier one left in the shared array.
 """
 import ctypes
 
@@ -21,8 +22,10 @@ def test_noalloc_matches_allocating_path_two_calls():
     L = C.lib()
     sc = S.tiny_scene(n=20000, seed=0, sh_degree=1)
     ds = C.DeviceScene.from_scene(sc)
-    views = [S.tiny_view(1.0, bg=(0.1, 0.2, 0.3)),
-             S.look_at((2.0, 1.0, 1.5), (0, 0, 0), 200, 150, s_v=4.0, bg=(0.0, 0.0, 0.0))]
+    full = S.look_at((2.0, 1.0, 1.5), (0, 0, 0), 200, 150, s_v=4.0, bg=(0.0, 0.0, 0.0))
+    views = [S.tiny_view(1.0, bg=(0.1, 0.2, 0.3)), full,
+             S.tiny_view(2.0, budget=3000),                                      # primitive budget
+             full.replace(width=96, height=80, region_x=64, region_y=48, full_width=200, full_height=150)]
     for v in views:
         fr = C.render(ds, [v], want_keys=False)
         img = torch.full((3, v.height, v.width), -1.0, device="cuda")
