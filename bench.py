@@ -551,6 +551,25 @@ def city_leg(args, steps=5):
     e3 = evals.cpu().numpy().astype(np.float64)
     flop = FLOP_VISIT * e3[0] + FLOP_EXP * e3[1] + FLOP_CONTRIB * e3[2]
     surv = cnt[:, 1].sum()
+    # backward of the same launch (dL/dimage = a fixed random image gradient)
+    nb = C.ctypes.c_size_t()
+    C.check("clod_backward_workspace_size", L.clod_backward_workspace_size(n, V, C.ctypes.byref(nb)))
+    bws = torch.empty(nb.value, dtype=torch.uint8, device="cuda")
+    grads = [torch.zeros_like(t) for t in (ds.means, ds.scales, ds.quats, ds.opacity, ds.sh, ds.decay)]
+    dimg = torch.randn(R.image.numel(), device="cuda", generator=torch.Generator(device="cuda").manual_seed(0))
+    bt = []
+    for k in range(4):
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record()
+        C.check("clod_render_bwd", L.clod_render_bwd(C.ctypes.byref(ds.c), C._ptr(R.ws), C._ptr(R.vals),
+                                                     C._ptr(R.ranges), C._ptr(R.T), C._ptr(R.nc), C._ptr(dimg),
+                                                     None, None, C._ptr(bws), bws.numel(),
+                                                     *[C._ptr(g) for g in grads], st))
+        b1.record()
+        torch.cuda.synchronize()
+        if k:
+            bt.append(b0.elapsed_time(b1))
+    del bws, grads, dimg
     sort_bytes = 80 * n * V + 24 * surv + 4 * K
     ms = float(stage.sum())
     del R, ds
@@ -563,7 +582,8 @@ def city_leg(args, steps=5):
             "culled_fraction_per_view": [round(1.0 - c / n, 4) for c in cnt[:, 0]],
             "pairs": K, "sort_GB_s": round(sort_bytes / (stage[1] / 1e3) / 1e9, 1),
             "sort_radix_equivalent_GB_s": round(152 * K / (stage[1] / 1e3) / 1e9, 1),
-            "blend_tflops": round(flop / (stage[2] / 1e3) / 1e12, 3)}
+            "blend_tflops": round(flop / (stage[2] / 1e3) / 1e12, 3),
+            "backward_ms_per_launch": round(float(np.mean(bt)), 3)}
 
 
 def serve_leg(args):

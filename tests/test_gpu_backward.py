@@ -92,3 +92,45 @@ def test_l1_loss_kernel(A):
     ref = (a.detach() - b).abs().mean()
     assert abs(float(loss) - float(ref)) < 1e-5 * float(ref)
     assert torch.allclose(a.grad, torch.sign(a.detach() - b) / a.numel())
+
+
+def test_gpu_gradients_match_central_differences_200_32x32(A):
+    """The 200-Gaussian 32x32 finite-difference subcase of the training
+    workload: GPU gradients (with an external dL/dalpha'') against central
+    FP64 differences of the oracle's forward statement with its decisions
+    frozen, on sampled entries of all six groups."""
+    sc = S.small_scene(n=200, seed=3, sh_degree=3)
+    v = S.look_at((0.4, -1.8, 1.2), (0, 0, 0), 32, 32, s_v=2.0, bg=(0.2, 0.1, 0.0))
+    fr, s1, _ = G.frozen_from_oracle(sc, v)
+    rng = np.random.default_rng(5)
+    gimg = rng.normal(size=(3, 32, 32))
+    galpha = rng.normal(size=sc.n) * 0.1
+    g = gpu_grads(A, sc, [v], [gimg], [galpha])
+
+    def loss(P):
+        out = G.view_forward(P, v, fr)
+        return float((out["image"].detach().numpy() * gimg).sum() + (out["alpha_eff"].detach().numpy() * galpha).sum())
+
+    P0 = G.params_f64(sc, requires_grad=False)
+    live = np.nonzero(s1["survive"])[0]
+    assert live.size > 20
+    pick = rng.choice(live, size=10, replace=False)
+    for name in NAMES:
+        flat = P0[name].reshape(-1)
+        per = flat.numel() // sc.n
+        fd, gg = [], []
+        for i in pick:
+            for j in range(min(per, 4)):
+                k = int(i) * per + j
+                x0 = float(flat[k])
+                h = 1e-6 * max(1.0, abs(x0))
+                flat[k] = x0 + h
+                lp = loss(P0)
+                flat[k] = x0 - h
+                lm = loss(P0)
+                flat[k] = x0
+                fd.append((lp - lm) / (2 * h))
+                gg.append(g[name].reshape(-1)[k])
+        fd, gg = np.array(fd), np.array(gg)
+        assert np.linalg.norm(fd) > 0, name
+        assert np.linalg.norm(gg - fd) <= 2e-3 * np.linalg.norm(fd), (name, np.linalg.norm(gg - fd) / np.linalg.norm(fd))
