@@ -284,7 +284,10 @@ typedef struct clod_adam_cfg {
  * zeroed afterwards.  scales, opacity: the activated copies the rasterizer
  * reads (exp(log-scale), sigmoid(logit)), read for the chain rule and
  * rewritten from the updated raw values.  m, v: device f32 moments of
- * n (14 + 3 (deg+1)^2) elements each, the six groups in the order above. */
+ * clod_adam_state_size() elements each (zero before the first step), the six
+ * groups in the order above, each starting at a multiple of 4 elements.
+ * Every array must be 16-byte aligned (CLOD_ERR_ARG otherwise). */
+clod_status clod_adam_state_size(int64_t n, int32_t sh_degree, int64_t* elements);
 clod_status clod_adam_step(const clod_adam_cfg* cfg, int64_t n, int32_t sh_degree, float* const* raw,
                            float* const* grads, float* scales, float* opacity, float* m, float* v,
                            clod_stream stream);

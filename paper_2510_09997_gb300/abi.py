@@ -79,6 +79,7 @@ SIGNATURES = {
     "clod_render_loss": ([P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_float, P,
                           ctypes.c_size_t, P, P, P], c_status),
     "clod_lreg_grad": ([P, ctypes.c_int64, ctypes.c_int32, P, P, ctypes.c_float, P, P, P, P, P], c_status),
+    "clod_adam_state_size": ([ctypes.c_int64, ctypes.c_int32, P], c_status),
     "clod_adam_step": ([P, ctypes.c_int64, ctypes.c_int32, P, P, P, P, P, P, P], c_status),
     "clod_render_noalloc": ([P, P, P, P, P, P], c_status),
     # serving

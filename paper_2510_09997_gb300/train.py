@@ -98,9 +98,10 @@ class TrainStep:
         self.eps = float(eps)
         self.t = 0
         dev = model.means.device
-        n_el = sum(p.numel() for p in model.raw())
-        self.m = torch.zeros(n_el, dtype=torch.float32, device=dev)
-        self.v = torch.zeros(n_el, dtype=torch.float32, device=dev)
+        ne = ctypes.c_int64()
+        C.check("clod_adam_state_size", C.lib().clod_adam_state_size(model.n, model.sh_degree, ctypes.byref(ne)))
+        self.m = torch.zeros(ne.value, dtype=torch.float32, device=dev)
+        self.v = torch.zeros(ne.value, dtype=torch.float32, device=dev)
         self.grads = [torch.zeros_like(p) for p in model.activated()]
         self.total = torch.zeros(1, dtype=torch.float32, device=dev)
         self.lrender = torch.zeros(C.MAX_VIEWS, dtype=torch.float32, device=dev)

@@ -108,7 +108,10 @@ def test_fused_adam_matches_torch_adam(T):
     lr = [1e-3, 2e-3, 3e-3, 4e-2, 5e-3, 1e-2]
     ref = [torch.tensor(t.cpu().numpy().astype(np.float64), requires_grad=True) for t in model.raw()]
     opt = torch.optim.Adam([{"params": [p], "lr": l} for p, l in zip(ref, lr)], betas=(0.9, 0.999), eps=1e-15)
-    m = torch.zeros(sum(t.numel() for t in model.raw()), device="cuda")
+    ne = ctypes.c_int64()
+    C.check("size", C.lib().clod_adam_state_size(model.n, model.sh_degree, ctypes.byref(ne)))
+    assert ne.value >= sum(t.numel() for t in model.raw())
+    m = torch.zeros(ne.value, device="cuda")
     v = torch.zeros_like(m)
     grads = [torch.zeros_like(t) for t in model.activated()]
     P = ctypes.c_void_p * 6
