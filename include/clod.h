@@ -169,7 +169,10 @@ clod_status clod_preprocess(const clod_scene* scene, const clod_view* views, int
  *             tiles without pairs get [0, 0).
  * If K > pair_capacity nothing is written to keys_out/vals_out and the frame
  * is marked overflowed: clod_render_fwd then writes nothing and
- * clod_frame_check() returns CLOD_ERR_CAPACITY with the required K. */
+ * clod_frame_check() returns CLOD_ERR_CAPACITY with the required K.
+ * The sort consumes the depth keys and digit counts clod_preprocess left in
+ * ws: call it once per clod_preprocess (to retry with a larger capacity, run
+ * clod_preprocess again). */
 clod_status clod_bin_sort(void* ws, uint64_t pair_capacity,
                           uint64_t* keys_out, uint32_t* vals_out, uint32_t* ranges_out,
                           clod_stream stream);
