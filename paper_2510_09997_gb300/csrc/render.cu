@@ -105,11 +105,12 @@ __device__ __forceinline__ void store_px(const ViewDev& W, const Px& q, int px, 
 
 constexpr int BLEND_THREADS = 128;   // 4 warps per 16x16 tile, 8x8 pixels per warp, 2 per thread
 
-// Each warp walks the tile's list on its own, 32 entries at a time: every
-// lane gathers one record and tests its reach box against the warp's 8x8
-// patch; the ballot of hits is then blended in list order from per-warp
-// shared slots.  A warp leaves the tile when all its 64 pixels are
-// saturated; the block waits only between tiles.
+// Each warp takes (tile, 8x8 quarter) work items from an atomic queue and
+// walks the tile's list on its own, 32 entries at a time: every lane gathers
+// one record and tests its reach box against the warp's patch; the ballot of
+// hits is then blended in list order from per-warp shared slots.  A warp
+// leaves its patch when all 64 pixels are saturated and takes the next item;
+// nothing waits for the other warps of the block.
 template <bool COUNT>
 __global__ void __launch_bounds__(BLEND_THREADS) k_blend_fwd(Frame F, const uint32_t* __restrict__ vals,
                                                              const uint32_t* __restrict__ ranges,
@@ -120,36 +121,27 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_fwd(Frame F, const uint
     __shared__ float4 s0[4][32];
     __shared__ float4 s1[4][32];
     __shared__ float4 s2[4][32];
-    __shared__ uint32_t s_tile;
-    __shared__ int s_view;
     const FrameHeader* hdr = F.hdr;
     if (hdr->status & STATUS_OVERFLOW) return;
     const uint32_t TT = hdr->total_tiles;
     const uint32_t V = hdr->n_views;
     const int64_t n = static_cast<int64_t>(hdr->n);
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ox = (wid & 1) * 8 + (lane & 7), oy = (wid >> 1) * 8 + (lane >> 3) * 2;
-    const float pcx = (float)((wid & 1) * 8) + 4.0f, pcy = (float)((wid >> 1) * 8) + 4.0f;
     unsigned long long evals = 0, n_exp = 0, n_con = 0;
     for (;;) {
-        if (threadIdx.x == 0) {
-            const uint32_t t = atomicAdd(&F.hdr->work[0], 1u);
-            s_tile = t;
-            int v = 0;
-            if (t < TT)
-                for (uint32_t u = 0; u < V; ++u) {
-                    const ViewDev& W = F.views[u];
-                    if (t >= W.tile_base && t < W.tile_base + (uint32_t)(W.TX * W.TY)) {
-                        v = (int)u;
-                        break;
-                    }
-                }
-            s_view = v;
-        }
-        __syncthreads();
-        const uint32_t t = s_tile;
+        // work item = (tile, quarter): this warp's 8x8 patch of a tile
+        uint32_t unit = 0;
+        if (lane == 0) unit = atomicAdd(&F.hdr->work[0], 1u);
+        unit = __shfl_sync(0xffffffffu, unit, 0);
+        const uint32_t t = unit >> 2;
         if (t >= TT) break;
-        const ViewDev& W = F.views[s_view];
+        const int qd = (int)(unit & 3u);
+        int view = 0;
+        for (uint32_t u = 1; u < V; ++u)
+            if (t >= F.views[u].tile_base) view = (int)u;
+        const ViewDev& W = F.views[view];
+        const int ox = (qd & 1) * 8 + (lane & 7), oy = (qd >> 1) * 8 + (lane >> 3) * 2;
+        const float pcx = (float)((qd & 1) * 8) + 4.0f, pcy = (float)((qd >> 1) * 8) + 4.0f;
         const uint32_t local = t - W.tile_base;
         const int tx = (int)(local % (uint32_t)W.TX), ty = (int)(local / (uint32_t)W.TX);
         const int px = tx * TILE + ox, py0 = ty * TILE + oy, py1 = py0 + 1;
@@ -159,7 +151,7 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_fwd(Frame F, const uint
         const float fpy1 = __fadd_rn(static_cast<float>(py1 + W.oy), 0.5f);
         const float wcx = (float)(tx * TILE + W.ox) + pcx, wcy = (float)(ty * TILE + W.oy) + pcy;
         const uint32_t start = ranges[2 * t], end = ranges[2 * t + 1];
-        const int64_t vn = (int64_t)s_view * n;
+        const int64_t vn = (int64_t)view * n;
         Px q0{1.0f, 0.0f, 0.0f, 0.0f, 0u, !(px < W.W && py0 < W.H)};
         Px q1{1.0f, 0.0f, 0.0f, 0.0f, 0u, !(px < W.W && py1 < W.H)};
         for (uint32_t b = start; b < end; b += 32) {
@@ -209,7 +201,6 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_fwd(Frame F, const uint
         }
         store_px(W, q0, px, py0, image, Tout, ncout);
         store_px(W, q1, px, py1, image, Tout, ncout);
-        __syncthreads();
     }
     if (COUNT) {
         for (int o = 16; o > 0; o >>= 1) {
