@@ -152,42 +152,33 @@ __global__ void __launch_bounds__(BWD_THREADS, 8) k_blend_bwd(Frame F, const uin
     __shared__ float4 s1[4][32];
     __shared__ float4 s2[4][32];
     __shared__ int64_t sg[4][32];
-    __shared__ uint32_t s_tile;
-    __shared__ int s_view;
     const FrameHeader* hdr = F.hdr;
     if (hdr->status & STATUS_OVERFLOW) return;
     const uint32_t TT = hdr->total_tiles;
     const uint32_t V = hdr->n_views;
     const int64_t n = static_cast<int64_t>(hdr->n);
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ox = (wid & 1) * 8 + (lane & 7), oy = (wid >> 1) * 8 + (lane >> 3) * 2;
-    const float pcx = (float)((wid & 1) * 8) + 4.0f, pcy = (float)((wid >> 1) * 8) + 4.0f;
     for (;;) {
-        if (threadIdx.x == 0) {
-            const uint32_t t = atomicAdd(&F.hdr->work[1], 1u);
-            s_tile = t;
-            int v = 0;
-            if (t < TT)
-                for (uint32_t u = 0; u < V; ++u) {
-                    const ViewDev& W = F.views[u];
-                    if (t >= W.tile_base && t < W.tile_base + (uint32_t)(W.TX * W.TY)) {
-                        v = (int)u;
-                        break;
-                    }
-                }
-            s_view = v;
-        }
-        __syncthreads();
-        const uint32_t t = s_tile;
+        // work item = (tile, quarter): this warp's 8x8 patch of a tile
+        uint32_t unit = 0;
+        if (lane == 0) unit = atomicAdd(&F.hdr->work[1], 1u);
+        unit = __shfl_sync(0xffffffffu, unit, 0);
+        const uint32_t t = unit >> 2;
         if (t >= TT) break;
-        const ViewDev& W = F.views[s_view];
+        const int qd = (int)(unit & 3u);
+        int view = 0;
+        for (uint32_t u = 1; u < V; ++u)
+            if (t >= F.views[u].tile_base) view = (int)u;
+        const ViewDev& W = F.views[view];
+        const int ox = (qd & 1) * 8 + (lane & 7), oy = (qd >> 1) * 8 + (lane >> 3) * 2;
+        const float pcx = (float)((qd & 1) * 8) + 4.0f, pcy = (float)((qd >> 1) * 8) + 4.0f;
         const uint32_t local = t - W.tile_base;
         const int tx = (int)(local % (uint32_t)W.TX), ty = (int)(local / (uint32_t)W.TX);
         const int px = tx * TILE + ox;
         const float fpx = __fadd_rn(static_cast<float>(px + W.ox), 0.5f);
         const float wcx = (float)(tx * TILE + W.ox) + pcx, wcy = (float)(ty * TILE + W.oy) + pcy;
         const uint32_t start = ranges[2 * t];
-        const int64_t vn = (int64_t)s_view * n;
+        const int64_t vn = (int64_t)view * n;
         BPx q[2];
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
@@ -252,7 +243,6 @@ __global__ void __launch_bounds__(BWD_THREADS, 8) k_blend_bwd(Frame F, const uin
             __syncwarp();
             hi = lo;
         }
-        __syncthreads();
     }
 }
 
