@@ -37,6 +37,21 @@ __device__ __forceinline__ uint32_t lanemask_lt()
     return m;
 }
 
+// Lanes of the warp holding the same value as this lane, for values below
+// 2^BITS: one ballot per bit (the same mask as __match_any_sync).
+template <int BITS>
+__device__ __forceinline__ uint32_t match_bits(uint32_t d)
+{
+    uint32_t m = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b < BITS; ++b) {
+        const bool bit = (d >> b) & 1u;
+        const uint32_t bb = __ballot_sync(0xffffffffu, bit);
+        m &= bit ? bb : ~bb;
+    }
+    return m;
+}
+
 // ---------------------------------------------------------------------------
 // 1. depth-rank sort
 // ---------------------------------------------------------------------------
@@ -56,7 +71,7 @@ __device__ __forceinline__ void rs_warp_counts(const uint32_t* __restrict__ keys
         if (valid) key = keys[base + idx];
         if (drop && key == 0xFFFFFFFFu) valid = false;
         const uint32_t d = valid ? ((key >> shift) & 255u) : 256u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t peers = match_bits<9>(d);     // d <= 256
         if (valid && (__ffs(peers) - 1) == lane) h[w][d] += __popc(peers);
         __syncwarp();
     }
@@ -169,7 +184,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const FrameHeader* __
         const uint32_t key = valid ? kin[base + idx] : 0u;
         if (first && key == 0xFFFFFFFFu) valid = false;     // culled: dropped
         const uint32_t d = valid ? ((key >> shift) & 255u) : 256u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t peers = match_bits<9>(d);     // d <= 256
         if (valid) {
             const uint32_t pos = wb[w][d] + __popc(peers & lt);
             const uint32_t val = vin[base + idx];
