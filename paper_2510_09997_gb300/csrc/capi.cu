@@ -12,6 +12,8 @@
 
 namespace clod {
 
+void launch_frame_setup(const Frame& F, void* ws, const FrameHeader& h, const ViewDev* views, size_t zero_begin,
+                        size_t zero_end, int n_sm, cudaStream_t st);
 void launch_preprocess(const Frame& F, const clod_scene& S, uint32_t V, uint8_t* mask_out, float* alpha_out,
                        unsigned long long* n_pairs_out, int n_sm, cudaStream_t st, bool select);
 void launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long long cap, uint64_t* keys, uint32_t* vals,
@@ -381,11 +383,10 @@ clod_status clod_preprocess(const clod_scene* scene, const clod_view* views, int
     h.n_rs_blocks = L.n_rs_blocks;
     h.max_tx = L.max_tx;
     h.rb_total = L.rb_total;
-    cudaError_t e = cudaMemsetAsync(ws, 0, L.views, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(F.hdr, &h, sizeof(h), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(F.views, table.data(), sizeof(ViewDev) * n_views, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(e, "clod_preprocess upload");
+    // header and view table as kernel parameters; the block after the header cleared
+    launch_frame_setup(F, ws, h, table.data(), L.dmax_key, L.views, n_sm, st);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "clod_preprocess set-up");
     bool select = false;
     for (int v = 0; v < n_views; ++v) select = select || views[v].budget > 0;
     launch_preprocess(F, *scene, (uint32_t)n_views, mask_out, alpha_eff_out,

@@ -299,6 +299,53 @@ __global__ void __launch_bounds__(256, 4) k_preprocess(Frame F, clod_scene S, ui
     if (threadIdx.x == 0 && s_pairs) atomicAdd(&F.hdr->n_pairs, s_pairs);
 }
 
+// Frame set-up in one launch: the header and the view table arrive as the
+// kernel's parameters (no host-to-device copies), and the zero-initialised
+// block after the header ([zero_begin, zero_end) bytes of the workspace:
+// d_max keys, counts, tile counts) is cleared.
+template <int MAXV>
+struct SetupArgs {
+    FrameHeader h;
+    ViewDev views[MAXV];
+};
+
+template <int MAXV>
+__global__ void __launch_bounds__(256) k_frame_setup(const SetupArgs<MAXV> a, Frame F, char* base, size_t zero_begin,
+                                                     size_t zero_end)
+{
+    uint32_t* z = reinterpret_cast<uint32_t*>(base + zero_begin);
+    const size_t words = (zero_end - zero_begin) / 4;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < words; k += (size_t)gridDim.x * blockDim.x)
+        z[k] = 0u;
+    if (blockIdx.x == 0) {
+        if (threadIdx.x == 0) *F.hdr = a.h;
+        const int vw = static_cast<int>(a.h.n_views * sizeof(ViewDev) / 4);
+        const int* src = reinterpret_cast<const int*>(a.views);
+        int* dst = reinterpret_cast<int*>(F.views);
+        for (int k = threadIdx.x; k < vw; k += blockDim.x) dst[k] = src[k];
+    }
+}
+
+template <int MAXV>
+static void setup_launch(const Frame& F, void* ws, const FrameHeader& h, const ViewDev* views, size_t zero_begin,
+                         size_t zero_end, int n_sm, cudaStream_t st)
+{
+    SetupArgs<MAXV> a;
+    a.h = h;
+    for (uint32_t v = 0; v < h.n_views; ++v) a.views[v] = views[v];
+    const size_t words = (zero_end - zero_begin) / 4;
+    const int blocks = static_cast<int>(std::max<size_t>(1, std::min<size_t>((words + 255) / 256, (size_t)n_sm * 2)));
+    k_frame_setup<MAXV><<<blocks, 256, 0, st>>>(a, F, static_cast<char*>(ws), zero_begin, zero_end);
+}
+
+void launch_frame_setup(const Frame& F, void* ws, const FrameHeader& h, const ViewDev* views, size_t zero_begin,
+                        size_t zero_end, int n_sm, cudaStream_t st)
+{
+    if (h.n_views <= 1) setup_launch<1>(F, ws, h, views, zero_begin, zero_end, n_sm, st);
+    else if (h.n_views <= 8) setup_launch<8>(F, ws, h, views, zero_begin, zero_end, n_sm, st);
+    else setup_launch<MAX_VIEWS>(F, ws, h, views, zero_begin, zero_end, n_sm, st);
+}
+
 void launch_budget_select(const Frame& F, const clod_scene& S, uint32_t V, int n_sm, cudaStream_t st);
 
 // select: run the primitive-budget select (needed when a view has budget > 0).
