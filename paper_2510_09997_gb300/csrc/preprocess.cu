@@ -77,7 +77,8 @@ __global__ void __launch_bounds__(256) k_dist_max(Frame F, const float* __restri
 // Pass B (DEG: the scene's SH degree, so the basis stays in registers).
 template <int DEG>
 __global__ void __launch_bounds__(256, 4) k_preprocess(Frame F, clod_scene S, uint8_t* __restrict__ mask_out,
-                                                    float* __restrict__ alpha_out)
+                                                    float* __restrict__ alpha_out,
+                                                    unsigned long long* __restrict__ n_pairs_out)
 {
     const uint32_t V = F.hdr->n_views;
     __shared__ ViewDev sv[MAX_VIEWS];
@@ -297,6 +298,17 @@ __global__ void __launch_bounds__(256, 4) k_preprocess(Frame F, clod_scene S, ui
         if (cnt_surv[v]) atomicAdd(&F.n_surv[2 * v + 1], cnt_surv[v]);
     }
     if (threadIdx.x == 0 && s_pairs) atomicAdd(&F.hdr->n_pairs, s_pairs);
+    if (n_pairs_out) {
+        // the last block to finish copies K out (work[2] counts finished blocks)
+        __shared__ bool last;
+        __threadfence();
+        if (threadIdx.x == 0) last = atomicAdd(&F.hdr->work[2], 1u) == gridDim.x - 1;
+        __syncthreads();
+        if (last && threadIdx.x == 0) {
+            __threadfence();
+            *n_pairs_out = atomicAdd(&F.hdr->n_pairs, 0ull);
+        }
+    }
 }
 
 // Frame set-up in one launch: the header and the view table arrive as the
@@ -359,13 +371,13 @@ void launch_preprocess(const Frame& F, const clod_scene& S, uint32_t V, uint8_t*
     if (n > 0 && select) launch_budget_select(F, S, V, n_sm, st);
     if (n > 0) {
         switch (S.sh_degree) {
-        case 0: k_preprocess<0><<<blocks, 256, 0, st>>>(F, S, mask_out, alpha_out); break;
-        case 1: k_preprocess<1><<<blocks, 256, 0, st>>>(F, S, mask_out, alpha_out); break;
-        case 2: k_preprocess<2><<<blocks, 256, 0, st>>>(F, S, mask_out, alpha_out); break;
-        default: k_preprocess<3><<<blocks, 256, 0, st>>>(F, S, mask_out, alpha_out); break;
+        case 0: k_preprocess<0><<<blocks, 256, 0, st>>>(F, S, mask_out, alpha_out, n_pairs_out); break;
+        case 1: k_preprocess<1><<<blocks, 256, 0, st>>>(F, S, mask_out, alpha_out, n_pairs_out); break;
+        case 2: k_preprocess<2><<<blocks, 256, 0, st>>>(F, S, mask_out, alpha_out, n_pairs_out); break;
+        default: k_preprocess<3><<<blocks, 256, 0, st>>>(F, S, mask_out, alpha_out, n_pairs_out); break;
         }
     }
-    if (n_pairs_out)
+    if (n_pairs_out && n <= 0)   // otherwise k_preprocess's last block writes it
         cudaMemcpyAsync(n_pairs_out, &F.hdr->n_pairs, sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st);
 }
 
