@@ -202,6 +202,14 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_fwd(Frame F, const uint
         store_px(W, q0, px, py0, image, Tout, ncout);
         store_px(W, q1, px, py1, image, Tout, ncout);
     }
+    // the last warp out resets the tile queue for the next call on this frame
+    if (lane == 0) {
+        const uint32_t total = gridDim.x * (blockDim.x >> 5);
+        if (atomicAdd(&F.hdr->work[3], 1u) == total - 1) {
+            F.hdr->work[0] = 0u;
+            F.hdr->work[3] = 0u;
+        }
+    }
     if (COUNT) {
         for (int o = 16; o > 0; o >>= 1) {
             evals += __shfl_xor_sync(0xffffffffu, evals, o);
@@ -231,7 +239,6 @@ void launch_blend_fwd(const Frame& F, const uint32_t* vals, const uint32_t* rang
                       uint32_t* ncout, unsigned long long* evaluated, int n_sm, cudaStream_t st)
 {
     const int blocks = n_sm * std::max(1, g_blend_blocks_per_sm);
-    cudaMemsetAsync(&F.hdr->work[0], 0, sizeof(uint32_t), st);
     if (evaluated)
         k_blend_fwd<true><<<blocks, BLEND_THREADS, 0, st>>>(F, vals, ranges, image, Tout, ncout, evaluated);
     else
