@@ -534,7 +534,7 @@ void launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long long ca
     if (n > 0) {
         uint32_t *ki = F.key0, *vi = F.val0, *ko = F.key1, *vo = F.val1;
         uint32_t* totals = F.rs_hist + (size_t)V * 256 * nb;   // [4 passes][V][256]
-        // totals were cleared by k_dist_max
+        cudaMemsetAsync(totals, 0, sizeof(uint32_t) * 4 * V * 256, st);
         for (int pass = 0; pass < 4; ++pass) {
             uint32_t* tot = totals + (size_t)pass * V * 256;
             k_rs_hist<<<V * nb, RS_THREADS, 0, st>>>(F.hdr, F.n_surv, ki, n, nb, 8 * pass, F.rs_hist, tot);

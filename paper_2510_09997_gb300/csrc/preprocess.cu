@@ -45,13 +45,6 @@ __global__ void __launch_bounds__(256) k_dist_max(Frame F, const float* __restri
     __shared__ ViewDev sv[MAX_VIEWS];
     __shared__ unsigned long long wmax[8];
     load_views(sv, F.views, V);
-    {
-        // the depth-rank sort's digit totals (4 passes), which it accumulates
-        uint32_t* tot = F.rs_hist + (size_t)V * 256 * F.hdr->n_rs_blocks;
-        const size_t words = (size_t)4 * V * 256;
-        for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < words; k += (size_t)gridDim.x * blockDim.x)
-            tot[k] = 0u;
-    }
     __syncthreads();
     for (uint32_t v = 0; v < V; ++v) {
         const ViewDev& W = sv[v];

@@ -96,3 +96,25 @@ def test_arrivals_while_busy_and_wait_timeout(env):
     st = srv.wait(t, 30.0)
     assert st.status == 0
     srv.close()
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+def test_partial_batches_reuse_one_slot(env, graphs):
+    """Groups of 1, 3, 5, 2 and 4 requests, each waited for before the next is
+    submitted, on one slot of 6 views: every batch is smaller than the slot's
+    layout and reuses workspace a previous batch wrote, and every image still
+    equals the solo render."""
+    C, serve, ds, views, solo = env
+    srv = serve.Server(ds, max_width=320, max_height=256, max_views_per_batch=6, n_slots=1, use_graphs=graphs)
+    k = 0
+    for g in (1, 3, 5, 2, 4):
+        idx = list(range(k, k + g))
+        k += g
+        outs = [torch.full((3, views[i].height, views[i].width), -7.0, device="cuda") for i in idx]
+        tickets = [srv.submit(views[i], o) for i, o in zip(idx, outs)]
+        stats = [srv.wait(t, 30.0) for t in tickets]
+        torch.cuda.synchronize()
+        assert all(st.status == 0 for st in stats)
+        for i, o in zip(idx, outs):
+            assert torch.equal(o, solo[i]), i
+    srv.close()
