@@ -244,8 +244,8 @@ def run_ours(args):
     sh_bytes = 12 * 16
     # preprocess: means twice (distance pass + main pass), opacity, decay, and per
     # Gaussian rect + sort key/value written; per survivor scales, quats, SH read
-    # and the 40 B of records written
-    pre_bytes = (12 + 12 + 8 + 16) * n * len(n_surv) + (28 + sh_bytes + 40) * n_surv.sum()
+    # and the 52 B of records written (three float4 and the depth)
+    pre_bytes = (12 + 12 + 8 + 16) * n * len(n_surv) + (28 + sh_bytes + 52) * n_surv.sum()
     # sort as built: 4 radix passes over n keys (4 B read for counts, 8 B read,
     # 8 B written), rectangles gathered into rank order (16 B per survivor),
     # chunk counting (8 B per survivor), emission (4 B per pair written)

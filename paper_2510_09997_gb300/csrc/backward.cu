@@ -120,9 +120,11 @@ __device__ __forceinline__ bool bwd_tail(BPx& q, bool r, float G, float dx, floa
 }
 
 // Both pixels of a thread against one Gaussian (only if not past their last
-// contributor), the two exponentials side by side.
+// contributor), the two exponentials side by side.  Powers below the
+// Gaussian's floor pf (>= -5.6) give opacity < 1/255, skipped as in the
+// forward pass.
 __device__ __forceinline__ bool bwd_pair(BPx& q0, BPx& q1, bool t0, bool t1, float fpx, const float4& a,
-                                         const float4& c, float cb, uint32_t pos, float (&g)[16])
+                                         const float4& c, float cb, float pf, uint32_t pos, float (&g)[16])
 {
     t0 = t0 && pos <= q0.last;
     t1 = t1 && pos <= q1.last;
@@ -131,8 +133,8 @@ __device__ __forceinline__ bool bwd_pair(BPx& q0, BPx& q1, bool t0, bool t1, flo
     const float dy0 = __fsub_rn(a.y, q0.fy), dy1 = __fsub_rn(a.y, q1.fy);
     const float p0 = __fmaf_rn(dx, __fmaf_rn(a.z, dx, __fmul_rn(a.w, dy0)), __fmul_rn(__fmul_rn(c.x, dy0), dy0));
     const float p1 = __fmaf_rn(dx, __fmaf_rn(a.z, dx, __fmul_rn(a.w, dy1)), __fmul_rn(__fmul_rn(c.x, dy1), dy1));
-    const bool r0 = t0 && p0 <= 0.0f && p0 >= -5.6f;
-    const bool r1 = t1 && p1 <= 0.0f && p1 >= -5.6f;
+    const bool r0 = t0 && p0 <= 0.0f && p0 >= pf;
+    const bool r1 = t1 && p1 <= 0.0f && p1 >= pf;
     if (!(r0 || r1)) return false;
     const float G0 = exp_spec_core(r0 ? p0 : 0.0f), G1 = exp_spec_core(r1 ? p1 : 0.0f);
     bool any = bwd_tail(q0, r0, G0, dx, dy0, a, c, cb, g);
@@ -230,11 +232,8 @@ __global__ void __launch_bounds__(BWD_THREADS, 8) k_blend_bwd(Frame F, const uin
                 float g[16];
 #pragma unroll
                 for (int i = 0; i < 16; ++i) g[i] = 0.0f;
-                // per-pixel reach box: outside it the forward skipped this Gaussian
-                const bool ix = fabsf(a.x - fpx) <= e.y;
-                const bool t0 = ix && fabsf(a.y - q[0].fy) <= e.z;
-                const bool t1 = ix && fabsf(a.y - q[1].fy) <= e.z;
-                const bool any = (t0 || t1) && bwd_pair(q[0], q[1], t0, t1, fpx, a, c, e.x, pos, g);
+                // per pixel, the power floor e.w decides, as in the forward pass
+                const bool any = bwd_pair(q[0], q[1], true, true, fpx, a, c, e.x, e.w, pos, g);
                 if (__any_sync(0xffffffffu, any)) {
                     const float tot = warp_reduce16(g);
                     if (!(lane & 1) && lane < 18) atomicAdd(g2d + 12 * sg[wid][k] + (lane >> 1), tot);

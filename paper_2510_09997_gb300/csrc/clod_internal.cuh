@@ -301,6 +301,21 @@ __device__ __forceinline__ float2 reach_half_extents(float nA, float nB, float n
     return make_float2(sqrtf(r2 * (C / det)) * 1.001f + 0.01f, sqrtf(r2 * (A / det)) * 1.001f + 0.01f);
 }
 
+// Lowest power at which the blend's opacity can still reach 1/255 (stored
+// with the record; the blend skips lower powers without the exponential).
+// a = alpha'' exp_spec(power) >= 1/255 needs power >= -ln(255 alpha'') up to
+// the relative errors of exp_spec, the product and logf (each a few 1e-7);
+// the floor sits 0.1% + 1e-3 below -logf(255 alpha''), so every skipped
+// power has a < 1/255 and would be skipped by the exact test as well.  Never
+// below -5.6 (the exponential's range); +inf when alpha'' < 1/255 (no power
+// reaches 1/255, since exp_spec <= 1 on powers <= 0).  Only a cull.
+__device__ __forceinline__ float power_floor(float a2)
+{
+    const float a255 = 255.0f * a2;
+    if (!(a255 >= 1.0f)) return __int_as_float(0x7f800000);
+    return fmaxf(-5.6f, -(logf(a255) * 1.001f + 1e-3f));
+}
+
 // Frame workspace layout (256-byte aligned arrays).
 FrameLayout frame_layout(uint64_t n, uint32_t n_views, uint32_t total_tiles, uint32_t rb_total, uint32_t max_tx,
                          size_t diff_grid_max);

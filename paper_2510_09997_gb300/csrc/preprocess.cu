@@ -49,17 +49,33 @@ __global__ void __launch_bounds__(256) k_dist_max(Frame F, const float* __restri
     for (uint32_t v = 0; v < V; ++v) {
         const ViewDev& W = sv[v];
         unsigned long long best = 0ull;
-        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-             i += (int64_t)gridDim.x * blockDim.x) {
-            const float x = means[3 * i], y = means[3 * i + 1], z = means[3 * i + 2];
-            float tx, ty, tz, e0, e1, e2;
-            cam_point(W, x, y, z, tx, ty, tz);
-            const float d = cam_dist(W, x, y, z, e0, e1, e2);
-            if (in_frustum(W, tx, ty, tz)) {
-                const unsigned long long key =
-                    (static_cast<unsigned long long>(__float_as_uint(d)) << 32) |
-                    static_cast<unsigned long long>(0xFFFFFFFFu - static_cast<uint32_t>(i));
-                best = key > best ? key : best;
+        // DM Gaussians per thread and round, their loads issued together
+        constexpr int DM = 4;
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < n; i0 += DM * stride) {
+            float x[DM], y[DM], z[DM];
+#pragma unroll
+            for (int u = 0; u < DM; ++u) {
+                const int64_t i = i0 + u * stride;
+                x[u] = y[u] = z[u] = 0.0f;
+                if (i < n) {
+                    x[u] = means[3 * i];
+                    y[u] = means[3 * i + 1];
+                    z[u] = means[3 * i + 2];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < DM; ++u) {
+                const int64_t i = i0 + u * stride;
+                float tx, ty, tz, e0, e1, e2;
+                cam_point(W, x[u], y[u], z[u], tx, ty, tz);
+                const float d = cam_dist(W, x[u], y[u], z[u], e0, e1, e2);
+                if (i < n && in_frustum(W, tx, ty, tz)) {
+                    const unsigned long long key =
+                        (static_cast<unsigned long long>(__float_as_uint(d)) << 32) |
+                        static_cast<unsigned long long>(0xFFFFFFFFu - static_cast<uint32_t>(i));
+                    best = key > best ? key : best;
+                }
             }
         }
         best = warp_max_u64(best);
@@ -98,17 +114,32 @@ __global__ void __launch_bounds__(256, 4) k_preprocess(Frame F, clod_scene S, ui
     unsigned long long my_pairs = 0ull;
     const int64_t n = S.n;
     constexpr int K = (DEG + 1) * (DEG + 1);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // the next Gaussian's centre, opacity and decay are loaded one iteration
+    // ahead, so that their latency overlaps the current Gaussian's work
+    float nmx = 0.f, nmy = 0.f, nmz = 0.f, nalpha = 0.f, nsigma = 0.f;
+    {
+        const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+        if (i < n) {
+            nmx = S.means[3 * i];
+            nmy = S.means[3 * i + 1];
+            nmz = S.means[3 * i + 2];
+            nalpha = S.opacity[i];
+            nsigma = S.decay[i];
+        }
+    }
     // block-uniform trip count: every lane reaches the ballots below
-    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += stride) {
         const int64_t i = base + threadIdx.x;
         const bool active = i < n;
-        float mx = 0.f, my = 0.f, mz = 0.f, alpha = 0.f, sigma = 0.f;
-        if (active) {
-            mx = S.means[3 * i];
-            my = S.means[3 * i + 1];
-            mz = S.means[3 * i + 2];
-            alpha = S.opacity[i];
-            sigma = S.decay[i];
+        const float mx = nmx, my = nmy, mz = nmz, alpha = nalpha, sigma = nsigma;
+        if (i + stride < n) {
+            const int64_t j = i + stride;
+            nmx = S.means[3 * j];
+            nmy = S.means[3 * j + 1];
+            nmz = S.means[3 * j + 2];
+            nalpha = S.opacity[j];
+            nsigma = S.decay[j];
         }
         for (uint32_t v = 0; v < V; ++v) {
             const ViewDev& W = sv[v];
@@ -125,6 +156,9 @@ __global__ void __launch_bounds__(256, 4) k_preprocess(Frame F, clod_scene S, ui
             bool surv = false;
             uint32_t dkey = 0xFFFFFFFFu;
             if (M) {
+                // rotation and scales in one round trip, before they are needed
+                const float4 q = reinterpret_cast<const float4*>(S.quats)[i];
+                const float s0 = S.scales[3 * i], s1 = S.scales[3 * i + 1], s2 = S.scales[3 * i + 2];
                 float tx, ty, tz;
                 cam_point(W, mx, my, mz, tx, ty, tz);
                 float u = 0.f, vv = 0.f;
@@ -134,7 +168,6 @@ __global__ void __launch_bounds__(256, 4) k_preprocess(Frame F, clod_scene S, ui
                 float qw = 0.f, qx = 0.f, qy = 0.f, qz = 0.f;
                 bool ok1 = false;
                 if (ok0) {
-                    const float4 q = reinterpret_cast<const float4*>(S.quats)[i];
                     const float n2 = __fmaf_rn(q.x, q.x, __fmaf_rn(q.y, q.y, __fmaf_rn(q.z, q.z, __fmul_rn(q.w, q.w))));
                     ok1 = n2 > 0.0f;
                     const float inv = __fdiv_rn(1.0f, __fsqrt_rn(n2));
@@ -157,7 +190,6 @@ __global__ void __launch_bounds__(256, 4) k_preprocess(Frame F, clod_scene S, ui
                     r[6] = __fmul_rn(2.0f, __fsub_rn(xz, wy));
                     r[7] = __fmul_rn(2.0f, __fadd_rn(yz, wx));
                     r[8] = __fmaf_rn(-2.0f, __fadd_rn(xx, yy), 1.0f);
-                    const float s0 = S.scales[3 * i], s1 = S.scales[3 * i + 1], s2 = S.scales[3 * i + 2];
                     float Mm[9];
 #pragma unroll
                     for (int a = 0; a < 3; ++a) {
@@ -265,7 +297,7 @@ __global__ void __launch_bounds__(256, 4) k_preprocess(Frame F, clod_scene S, ui
                             const float2 ext = reach_half_extents(nA, -B, nC, a2);
                             F.rec0[o] = make_float4(u, vv, nA, -B);
                             F.rec1[o] = make_float4(nC, a2, c0, c1);
-                            F.rec2[o] = make_float4(c2, ext.x, ext.y, 0.0f);
+                            F.rec2[o] = make_float4(c2, ext.x, ext.y, power_floor(a2));
                             F.depth[o] = tz;
                             dkey = __float_as_uint(tz);
                             rect = make_uint2(static_cast<uint32_t>(x0) | (static_cast<uint32_t>(y0) << 16),
@@ -365,9 +397,11 @@ void launch_preprocess(const Frame& F, const clod_scene& S, uint32_t V, uint8_t*
                        unsigned long long* n_pairs_out, int n_sm, cudaStream_t st, bool select)
 {
     const int64_t n = S.n;
-    int blocks = static_cast<int>(std::min<int64_t>((n + 255) / 256, (int64_t)n_sm * 8));
+    // one resident wave of each kernel (the loops stride over the rest)
+    int blocks = static_cast<int>(std::min<int64_t>((n + 255) / 256, (int64_t)n_sm * 4));
     if (blocks < 1) blocks = 1;
-    if (n > 0) k_dist_max<<<blocks, 256, 0, st>>>(F, S.means, n);
+    const int dm_blocks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((n + 1023) / 1024, (int64_t)n_sm * 4)));
+    if (n > 0) k_dist_max<<<dm_blocks, 256, 0, st>>>(F, S.means, n);
     if (n > 0 && select) launch_budget_select(F, S, V, n_sm, st);
     if (n > 0) {
         switch (S.sh_degree) {

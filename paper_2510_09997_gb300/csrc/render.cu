@@ -4,11 +4,13 @@
 // warp owns an 8x8 patch (two vertically adjacent pixels per thread) and
 // walks the tile's sorted list independently, 32 entries at a time: every
 // lane gathers one record (u, v, -A/2, -B | -C/2, alpha'', r, g | b, reach
-// half-extents) and tests the box that holds every pixel the Gaussian can
-// reach with opacity >= 1/255 (computed once per Gaussian by the
-// preprocessing); the warp blends, in list order, only the entries whose box meets
-// its patch -- every pixel of the patch would skip the others anyway, so no
-// result changes.  A warp stops once its 64 pixels are saturated.
+// half-extents, power floor) and tests the box that holds every pixel the
+// Gaussian can reach with opacity >= 1/255 (computed once per Gaussian by the
+// preprocessing); the warp blends, in list order, only the entries whose box
+// meets its patch -- every pixel of the patch would skip the others anyway, so
+// no result changes.  Per pixel, a power below the Gaussian's floor (opacity
+// < 1/255 for certain) skips the exponential.  A warp stops once its 64
+// pixels are saturated.
 // Plain FP32/ALU work with one exponential per evaluated pair: no tensor
 // cores.
 #include <algorithm>
@@ -67,17 +69,19 @@ __device__ __forceinline__ void blend_finish(Px& q, float al, const float4& c, f
 }
 
 // Both pixels of a thread against one Gaussian: the two powers, then (if
-// either lies in [-5.6, 0]) the two exponentials side by side, so that their
-// dependency chains interleave.  Every pixel's result is that of blend_one.
+// either lies in [pf, 0], pf >= -5.6 the Gaussian's power floor) the two
+// exponentials side by side, so that their dependency chains interleave.
+// Below pf the opacity is < 1/255 (skipped either way): every pixel's result
+// is that of blend_one.
 __device__ __forceinline__ void blend_pair(Px& q0, Px& q1, bool t0, bool t1, float fpx, float fpy0, float fpy1,
-                                           const float4& a, const float4& c, float cb, uint32_t pos)
+                                           const float4& a, const float4& c, float cb, float pf, uint32_t pos)
 {
     const float ddx = __fsub_rn(a.x, fpx);
     const float dy0 = __fsub_rn(a.y, fpy0), dy1 = __fsub_rn(a.y, fpy1);
     const float p0 = __fmaf_rn(ddx, __fmaf_rn(a.z, ddx, __fmul_rn(a.w, dy0)), __fmul_rn(__fmul_rn(c.x, dy0), dy0));
     const float p1 = __fmaf_rn(ddx, __fmaf_rn(a.z, ddx, __fmul_rn(a.w, dy1)), __fmul_rn(__fmul_rn(c.x, dy1), dy1));
-    const bool r0 = t0 && p0 <= 0.0f && p0 >= -5.6f;
-    const bool r1 = t1 && p1 <= 0.0f && p1 >= -5.6f;
+    const bool r0 = t0 && p0 <= 0.0f && p0 >= pf;
+    const bool r1 = t1 && p1 <= 0.0f && p1 >= pf;
     if (!(r0 || r1)) return;
     const float g0 = exp_spec_core(r0 ? p0 : 0.0f), g1 = exp_spec_core(r1 ? p1 : 0.0f);
     float a0 = fminf(0.99f, __fmul_rn(c.y, g0)), a1 = fminf(0.99f, __fmul_rn(c.y, g1));
@@ -179,8 +183,6 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_fwd(Frame F, const uint
                 const float4 c = s1[wid][k];
                 const float4 e = s2[wid][k];
                 const uint32_t pos = b - start + (uint32_t)k + 1u;
-                // the same reach box per pixel: outside it the pixel would skip
-                // this Gaussian (opacity < 1/255), so the test changes nothing
                 if (COUNT) {
                     if (!q0.done) {
                         ++evals;
@@ -191,10 +193,11 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_fwd(Frame F, const uint
                         blend_one<COUNT>(q1, fpx, fpy1, a, c, e.x, pos, n_exp, n_con);
                     }
                 } else {
-                    const bool ix = fabsf(a.x - fpx) <= e.y;
-                    const bool t0 = !q0.done && ix && fabsf(a.y - fpy0) <= e.z;
-                    const bool t1 = !q1.done && ix && fabsf(a.y - fpy1) <= e.z;
-                    if (t0 || t1) blend_pair(q0, q1, t0, t1, fpx, fpy0, fpy1, a, c, e.x, pos);
+                    // per pixel, the power floor e.w decides (no box test: the
+                    // warp's box test above already passed, and a pixel outside
+                    // the reach box has a power below the floor)
+                    const bool t0 = !q0.done, t1 = !q1.done;
+                    if (t0 || t1) blend_pair(q0, q1, t0, t1, fpx, fpy0, fpy1, a, c, e.x, e.w, pos);
                 }
             }
             __syncwarp();
