@@ -55,22 +55,35 @@ __device__ __forceinline__ uint32_t match_bits(uint32_t d)
 // ---------------------------------------------------------------------------
 // 1. depth-rank sort
 // ---------------------------------------------------------------------------
-// Per-warp digit counts of the block's items: warp w owns items
-// [w * 512, w * 512 + 512) of the block, in order.
-__device__ __forceinline__ void rs_warp_counts(const uint32_t* __restrict__ keys, int64_t base, int cnt, int shift,
-                                               uint32_t (*h)[256], bool drop)
+// Keys of the block's items held by this thread: warp w owns items
+// [w * PER_WARP, (w + 1) * PER_WARP) of the block, lane l the items
+// w * PER_WARP + 32 r + l.  All loads are issued before any is used (one
+// round trip).  0xFFFFFFFF marks "no item": beyond the block, or culled (the
+// first pass); the later passes never hold it, since a survivor's key is the
+// bit pattern of a positive depth.
+constexpr int RS_PER_WARP = RS_ITEMS / (RS_THREADS / 32);
+constexpr int RS_R = RS_PER_WARP / 32;
+__device__ __forceinline__ void rs_load_keys(const uint32_t* __restrict__ keys, int64_t base, int cnt,
+                                             uint32_t (&kk)[RS_R])
+{
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int r = 0; r < RS_R; ++r) {
+        const int idx = w * RS_PER_WARP + r * 32 + lane;
+        kk[r] = idx < cnt ? keys[base + idx] : 0xFFFFFFFFu;
+    }
+}
+
+// Per-warp digit counts of the held keys, in h[w][digit].
+__device__ __forceinline__ void rs_warp_counts(const uint32_t (&kk)[RS_R], int shift, uint32_t (*h)[256])
 {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int k = lane; k < 256; k += 32) h[w][k] = 0;
     __syncwarp();
-    constexpr int PER_WARP = RS_ITEMS / (RS_THREADS / 32);
-    for (int r = 0; r < PER_WARP; r += 32) {
-        const int idx = w * PER_WARP + r + lane;
-        uint32_t key = 0u;
-        bool valid = idx < cnt;
-        if (valid) key = keys[base + idx];
-        if (drop && key == 0xFFFFFFFFu) valid = false;
-        const uint32_t d = valid ? ((key >> shift) & 255u) : 256u;
+#pragma unroll
+    for (int r = 0; r < RS_R; ++r) {
+        const bool valid = kk[r] != 0xFFFFFFFFu;
+        const uint32_t d = valid ? ((kk[r] >> shift) & 255u) : 256u;
         const uint32_t peers = match_bits<9>(d);     // d <= 256
         if (valid && (__ffs(peers) - 1) == lane) h[w][d] += __popc(peers);
         __syncwarp();
@@ -99,7 +112,9 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const FrameHeader* __res
         hist[((size_t)v * 256 + threadIdx.x) * nb + lb] = 0u;
         return;
     }
-    rs_warp_counts(keys, base, cnt, shift, h, shift == 0);
+    uint32_t kk[RS_R];
+    rs_load_keys(keys, base, cnt, kk);
+    rs_warp_counts(kk, shift, h);
     __syncthreads();
     uint32_t s = 0;
     for (int w = 0; w < RS_THREADS / 32; ++w) s += h[w][threadIdx.x];
@@ -129,8 +144,10 @@ __global__ void __launch_bounds__(1024) k_rs_scan(const FrameHeader* __restrict_
     }
 }
 
-// Stable scatter of one digit pass; on the last pass also gathers the tile
-// rectangle of every survivor into rank order.
+// Stable scatter of one digit pass; on the last pass (GATHER) also gathers the
+// tile rectangle of every survivor into rank order.  Keys, values and
+// rectangles are loaded before the counting, so their latency overlaps it.
+template <bool GATHER>
 __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const FrameHeader* __restrict__ hdr,
                                                            const uint32_t* __restrict__ n_surv,
                                                            const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
@@ -150,7 +167,20 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const FrameHeader* __
     const bool first = shift == 0;
     const int cnt = rs_block_count(n_surv, v, n, lb, first);
     if (cnt == 0) return;
-    rs_warp_counts(kin, base, cnt, shift, h, first);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t kk[RS_R], vv[RS_R];
+    uint2 rr[RS_R];
+    rs_load_keys(kin, base, cnt, kk);
+#pragma unroll
+    for (int r = 0; r < RS_R; ++r) {
+        const int idx = w * RS_PER_WARP + r * 32 + lane;
+        vv[r] = idx < cnt ? vin[base + idx] : 0u;
+    }
+    if (GATHER) {
+#pragma unroll
+        for (int r = 0; r < RS_R; ++r) rr[r] = kk[r] != 0xFFFFFFFFu ? rect[vbase + vv[r]] : make_uint2(0u, 0u);
+    }
+    rs_warp_counts(kk, shift, h);
     {
         // exclusive scan of the view's 256 digit totals (RS_THREADS == 256)
         const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
@@ -175,22 +205,17 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const FrameHeader* __
         }
     }
     __syncthreads();
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t lt = lanemask_lt();
-    constexpr int PER_WARP = RS_ITEMS / (RS_THREADS / 32);
-    for (int r = 0; r < PER_WARP; r += 32) {
-        const int idx = w * PER_WARP + r + lane;
-        bool valid = idx < cnt;
-        const uint32_t key = valid ? kin[base + idx] : 0u;
-        if (first && key == 0xFFFFFFFFu) valid = false;     // culled: dropped
-        const uint32_t d = valid ? ((key >> shift) & 255u) : 256u;
+#pragma unroll
+    for (int r = 0; r < RS_R; ++r) {
+        const bool valid = kk[r] != 0xFFFFFFFFu;     // culled keys are dropped here
+        const uint32_t d = valid ? ((kk[r] >> shift) & 255u) : 256u;
         const uint32_t peers = match_bits<9>(d);     // d <= 256
         if (valid) {
             const uint32_t pos = wb[w][d] + __popc(peers & lt);
-            const uint32_t val = vin[base + idx];
-            kout[vbase + pos] = key;
-            vout[vbase + pos] = val;
-            if (srect) srect[vbase + pos] = rect[vbase + val];
+            kout[vbase + pos] = kk[r];
+            vout[vbase + pos] = vv[r];
+            if (GATHER) srect[vbase + pos] = rr[r];
         }
         __syncwarp();
         if (valid && (__ffs(peers) - 1) == lane) wb[w][d] += __popc(peers);
@@ -439,6 +464,7 @@ __global__ void __launch_bounds__(512) k_chunk_count(Frame F)
 // coalesced) and cuts the chunks into 8 segments, one per warp: segment
 // sums, their scan across the warps, then each segment rescanned.
 constexpr int CS_TILES = 32, CS_SEG = 8;
+constexpr int CS_MAXPER = (MAX_CHUNKS + CS_SEG - 1) / CS_SEG;
 __global__ void __launch_bounds__(CS_TILES * CS_SEG) k_chunk_scan(Frame F)
 {
     __shared__ uint32_t part[CS_SEG][CS_TILES];
@@ -458,11 +484,16 @@ __global__ void __launch_bounds__(CS_TILES * CS_SEG) k_chunk_scan(Frame F)
         T = (uint32_t)(W.TX * W.TY);
         col = F.cnt + (size_t)CH * W.tile_base + (t - W.tile_base);
     }
-    const uint32_t per = (CH + CS_SEG - 1) / CS_SEG;
+    const uint32_t per = (CH + CS_SEG - 1) / CS_SEG;     // <= CS_MAXPER
     const uint32_t c0 = min(CH, sg * per), c1 = min(CH, c0 + per);
+    // the segment's counts are held in registers: one round of loads
+    uint32_t xs[CS_MAXPER];
     uint32_t sum = 0;
-    if (ok)
-        for (uint32_t c = c0; c < c1; ++c) sum += col[(size_t)c * T];
+#pragma unroll
+    for (int k = 0; k < CS_MAXPER; ++k) {
+        xs[k] = (ok && c0 + k < c1) ? col[(size_t)(c0 + k) * T] : 0u;
+        sum += xs[k];
+    }
     part[sg][tx] = sum;
     __syncthreads();
     uint32_t off = 0, tot = 0;
@@ -473,53 +504,77 @@ __global__ void __launch_bounds__(CS_TILES * CS_SEG) k_chunk_scan(Frame F)
         tot += x;
     }
     if (!ok) return;
-    for (uint32_t c = c0; c < c1; ++c) {
-        const uint32_t x = col[(size_t)c * T];
-        col[(size_t)c * T] = off;
-        off += x;
+#pragma unroll
+    for (int k = 0; k < CS_MAXPER; ++k) {
+        if (c0 + k < c1) col[(size_t)(c0 + k) * T] = off;
+        off += xs[k];
     }
     if (sg == 0) F.tile_count[t] = tot;
 }
 
 // 3b. exclusive scan of the tile counts by one block of 1024 threads; writes
-// the tile offsets, the ranges ([0, 0) for empty tiles) and checks K.
+// the tile offsets, the ranges ([0, 0) for empty tiles) and checks K.  Rounds
+// of 4096 tiles: each thread loads 4 consecutive counts (one 16-byte load
+// from the 256-byte aligned array), the block scans, and the offsets go out
+// through shared memory in coalesced stores.
+constexpr int ST_PER = 4;
+constexpr int ST_ROUND = 1024 * ST_PER;
 __global__ void __launch_bounds__(1024) k_scan_tiles(Frame F, uint32_t* __restrict__ ranges, unsigned long long cap)
 {
     __shared__ unsigned long long wsum[32];
+    __shared__ uint32_t so[ST_ROUND];
+    __shared__ uint32_t sc[ST_ROUND];
     const uint32_t TT = F.hdr->total_tiles;
-    const uint32_t per = (TT + blockDim.x - 1) / blockDim.x;
-    const uint32_t b0 = min(TT, threadIdx.x * per), b1 = min(TT, b0 + per);
-    unsigned long long s = 0;
-    for (uint32_t t = b0; t < b1; ++t) s += F.tile_count[t];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    unsigned long long x = s;
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) wsum[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-        unsigned long long w = wsum[lane];
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
+    unsigned long long carry = 0;
+    for (uint32_t base = 0; base < TT; base += ST_ROUND) {
+        const uint32_t t0 = base + threadIdx.x * ST_PER;
+        uint32_t c[ST_PER] = {0u, 0u, 0u, 0u};
+        if (t0 + ST_PER <= TT) {
+            const uint4 c4 = *reinterpret_cast<const uint4*>(F.tile_count + t0);
+            c[0] = c4.x; c[1] = c4.y; c[2] = c4.z; c[3] = c4.w;
+        } else {
+            for (int u = 0; u < ST_PER; ++u)
+                if (t0 + u < TT) c[u] = F.tile_count[t0 + u];
         }
-        wsum[lane] = w;
-    }
-    __syncthreads();
-    unsigned long long run = x - s + (wid ? wsum[wid - 1] : 0ull);
-    const unsigned long long total = wsum[31];
-    for (uint32_t t = b0; t < b1; ++t) {
-        const uint32_t c = F.tile_count[t];
-        F.tile_offset[t] = static_cast<uint32_t>(run);
-        ranges[2 * t] = c ? static_cast<uint32_t>(run) : 0u;
-        ranges[2 * t + 1] = c ? static_cast<uint32_t>(run + c) : 0u;
-        run += c;
+        const unsigned long long s = (unsigned long long)c[0] + c[1] + c[2] + c[3];
+        unsigned long long x = s;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            unsigned long long w = wsum[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            wsum[lane] = w;
+        }
+        __syncthreads();
+        unsigned long long run = carry + x - s + (wid ? wsum[wid - 1] : 0ull);
+#pragma unroll
+        for (int u = 0; u < ST_PER; ++u) {
+            so[threadIdx.x * ST_PER + u] = static_cast<uint32_t>(run);
+            sc[threadIdx.x * ST_PER + u] = c[u];
+            run += c[u];
+        }
+        carry += wsum[31];
+        __syncthreads();
+        const uint32_t m = min((uint32_t)ST_ROUND, TT - base);
+        for (uint32_t k = threadIdx.x; k < m; k += blockDim.x) {
+            const uint32_t o = so[k], cc = sc[k];
+            F.tile_offset[base + k] = o;
+            ranges[2 * (size_t)(base + k)] = cc ? o : 0u;
+            ranges[2 * (size_t)(base + k) + 1] = cc ? o + cc : 0u;
+        }
+        __syncthreads();     // so, sc and wsum are reused by the next round
     }
     if (threadIdx.x == 0) {
-        F.tile_offset[TT] = static_cast<uint32_t>(total);
-        if (total != F.hdr->n_pairs || total > cap || total > 0xFFFFFFFFull) atomicOr(&F.hdr->status, STATUS_OVERFLOW);
+        F.tile_offset[TT] = static_cast<uint32_t>(carry);
+        if (carry != F.hdr->n_pairs || carry > cap || carry > 0xFFFFFFFFull) atomicOr(&F.hdr->status, STATUS_OVERFLOW);
     }
 }
 
@@ -539,8 +594,12 @@ void launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long long ca
             uint32_t* tot = totals + (size_t)pass * V * 256;
             k_rs_hist<<<V * nb, RS_THREADS, 0, st>>>(F.hdr, F.n_surv, ki, n, nb, 8 * pass, F.rs_hist, tot);
             k_rs_scan<<<(V * 256 + 31) / 32, 1024, 0, st>>>(F.hdr, F.rs_hist, nb);
-            k_rs_scatter<<<V * nb, RS_THREADS, 0, st>>>(F.hdr, F.n_surv, ki, vi, ko, vo, n, nb, 8 * pass, F.rs_hist,
-                                                        tot, F.rect, pass == 3 ? F.srect : nullptr);
+            if (pass == 3)
+                k_rs_scatter<true><<<V * nb, RS_THREADS, 0, st>>>(F.hdr, F.n_surv, ki, vi, ko, vo, n, nb, 8 * pass,
+                                                                  F.rs_hist, tot, F.rect, F.srect);
+            else
+                k_rs_scatter<false><<<V * nb, RS_THREADS, 0, st>>>(F.hdr, F.n_surv, ki, vi, ko, vo, n, nb, 8 * pass,
+                                                                   F.rs_hist, tot, nullptr, nullptr);
             std::swap(ki, ko);
             std::swap(vi, vo);
         }

@@ -164,6 +164,14 @@ __global__ void __launch_bounds__(256, 4) k_preprocess(Frame F, clod_scene S, ui
                 float u = 0.f, vv = 0.f;
                 if (tz > W.near_z) project(W, tx, ty, tz, u, vv);
                 const bool ok0 = (tz > W.near_z) && isfinite(u) && isfinite(vv);
+                // the SH row is fetched into L2 now, while the covariance is
+                // computed, for a centre within a frame-sized margin of the
+                // frame (a likely survivor); the loads below then hit L2
+                if (ok0 && fabsf(u - 0.5f * W.FW) < 1.5f * W.FW && fabsf(vv - 0.5f * W.FH) < 1.5f * W.FH) {
+                    const char* row = reinterpret_cast<const char*>(S.sh + (size_t)i * K * 3);
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(row));
+                    if (K * 12 > 64) asm volatile("prefetch.global.L2 [%0];" ::"l"(row + 128));
+                }
                 // 3D covariance Sigma = R S S^T R^T
                 float qw = 0.f, qx = 0.f, qy = 0.f, qz = 0.f;
                 bool ok1 = false;
