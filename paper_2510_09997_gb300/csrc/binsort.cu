@@ -10,7 +10,11 @@
 //      index order.  Culled Gaussians (keyed all-ones by the preprocessing)
 //      are dropped by the first pass, so the later passes move only the
 //      survivors.  The last pass also gathers each survivor's tile
-//      rectangle into rank order.
+//      rectangle into rank order.  Each pass is two launches: per-block
+//      digit counts (with per-view digit totals and sums over groups of
+//      RS_G1 and RS_G2 blocks, by atomics), then the scatter, where every
+//      block adds up its own offsets from the group sums and the counts of
+//      the blocks before it in its group (no separate scan).
 //   2. the survivors of a view are cut into chunks of consecutive ranks; one
 //      warp per (chunk, tile row) walks the chunk's rectangles in rank order
 //      and counts, per tile of its row, the pairs the chunk contributes
@@ -21,9 +25,10 @@
 //      tile_offset + chunk offset + (number of earlier-ranked Gaussians of the
 //      chunk in that tile) -- its final sorted position.
 //
-// Work is O(n) for the rank sort, O(K) writes for the emission; nothing is
-// atomic but per-block counters, so the result is deterministic and equals
-// the stable sort of the index-ordered emission by key.
+// Work is O(n) for the rank sort, O(K) writes for the emission; the only
+// atomics add integer counts (order-independent), so the result is
+// deterministic and equals the stable sort of the index-ordered emission by
+// key.
 #include <algorithm>
 
 #include "clod_internal.cuh"
@@ -58,20 +63,30 @@ __device__ __forceinline__ uint32_t match_bits(uint32_t d)
 // Keys of the block's items held by this thread: warp w owns items
 // [w * PER_WARP, (w + 1) * PER_WARP) of the block, lane l the items
 // w * PER_WARP + 32 r + l.  All loads are issued before any is used (one
-// round trip).  0xFFFFFFFF marks "no item": beyond the block, or culled (the
-// first pass); the later passes never hold it, since a survivor's key is the
-// bit pattern of a positive depth.
+// round trip), and before the block's item count is known (any key of the
+// view's n slots may be read); rs_mask_keys then applies the count.
+// 0xFFFFFFFF marks "no item": beyond the block, or culled (the first pass);
+// the later passes never hold it, since a survivor's key is the bit pattern
+// of a positive depth.
 constexpr int RS_PER_WARP = RS_ITEMS / (RS_THREADS / 32);
 constexpr int RS_R = RS_PER_WARP / 32;
-__device__ __forceinline__ void rs_load_keys(const uint32_t* __restrict__ keys, int64_t base, int cnt,
-                                             uint32_t (&kk)[RS_R])
+__device__ __forceinline__ void rs_load_keys_early(const uint32_t* __restrict__ keys, int64_t vbase, int lb,
+                                                   int64_t n, uint32_t (&kk)[RS_R])
 {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
     for (int r = 0; r < RS_R; ++r) {
-        const int idx = w * RS_PER_WARP + r * 32 + lane;
-        kk[r] = idx < cnt ? keys[base + idx] : 0xFFFFFFFFu;
+        const int64_t j = (int64_t)lb * RS_ITEMS + w * RS_PER_WARP + r * 32 + lane;
+        kk[r] = j < n ? keys[vbase + j] : 0xFFFFFFFFu;
     }
+}
+
+__device__ __forceinline__ void rs_mask_keys(int cnt, uint32_t (&kk)[RS_R])
+{
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int r = 0; r < RS_R; ++r)
+        if (w * RS_PER_WARP + r * 32 + lane >= cnt) kk[r] = 0xFFFFFFFFu;
 }
 
 // Per-warp digit counts of the held keys, in h[w][digit].
@@ -101,46 +116,26 @@ __device__ __forceinline__ int rs_block_count(const uint32_t* n_surv, int v, int
 __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const FrameHeader* __restrict__ hdr,
                                                         const uint32_t* __restrict__ n_surv,
                                                         const uint32_t* __restrict__ keys, int64_t n, int nb, int shift,
-                                                        uint32_t* __restrict__ hist, uint32_t* __restrict__ totals)
+                                                        uint32_t* __restrict__ hist, uint32_t* __restrict__ totals,
+                                                        uint32_t* __restrict__ sum1, uint32_t* __restrict__ sum2)
 {
     __shared__ uint32_t h[RS_THREADS / 32][256];
     const int b = blockIdx.x, v = b / nb, lb = b % nb;
-    if ((uint32_t)v >= hdr->n_views) return;
-    const int64_t base = (int64_t)v * n + (int64_t)lb * RS_ITEMS;
-    const int cnt = rs_block_count(n_surv, v, n, lb, shift == 0);
-    if (cnt == 0) {     // no items: zero counts for the scan
-        hist[((size_t)v * 256 + threadIdx.x) * nb + lb] = 0u;
-        return;
-    }
     uint32_t kk[RS_R];
-    rs_load_keys(keys, base, cnt, kk);
+    rs_load_keys_early(keys, (int64_t)v * n, lb, n, kk);
+    if ((uint32_t)v >= hdr->n_views) return;
+    const int cnt = rs_block_count(n_surv, v, n, lb, shift == 0);
+    if (cnt == 0) return;     // no items (and none in any later block)
+    rs_mask_keys(cnt, kk);
     rs_warp_counts(kk, shift, h);
     __syncthreads();
     uint32_t s = 0;
     for (int w = 0; w < RS_THREADS / 32; ++w) s += h[w][threadIdx.x];
-    hist[((size_t)v * 256 + threadIdx.x) * nb + lb] = s;
-    if (s) atomicAdd(&totals[v * 256 + threadIdx.x], s);
-}
-
-// Exclusive scan, per (view, digit), of the block counts over the blocks:
-// one warp per (view, digit), 32 warps per block.
-__global__ void __launch_bounds__(1024) k_rs_scan(const FrameHeader* __restrict__ hdr, uint32_t* __restrict__ hist, int nb)
-{
-    const int lane = threadIdx.x & 31;
-    const uint32_t vd = blockIdx.x * 32 + (threadIdx.x >> 5);     // view * 256 + digit
-    if (vd >= hdr->n_views * 256u) return;
-    uint32_t* hd = hist + (size_t)vd * nb;
-    uint32_t carry = 0;
-    for (int k0 = 0; k0 < nb; k0 += 32) {
-        const int k = k0 + lane;
-        const uint32_t c = k < nb ? hd[k] : 0u;
-        uint32_t x = c;
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (k < nb) hd[k] = carry + x - c;
-        carry += __shfl_sync(0xffffffffu, x, 31);
+    hist[((size_t)v * nb + lb) * 256 + threadIdx.x] = s;
+    if (s) {
+        atomicAdd(&totals[v * 256 + threadIdx.x], s);
+        atomicAdd(&sum1[((size_t)v * rs_groups(nb, RS_G1) + lb / RS_G1) * 256 + threadIdx.x], s);
+        atomicAdd(&sum2[((size_t)v * rs_groups(nb, RS_G2) + lb / RS_G2) * 256 + threadIdx.x], s);
     }
 }
 
@@ -154,6 +149,8 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const FrameHeader* __
                                                            uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                            int64_t n, int nb, int shift, const uint32_t* __restrict__ hist,
                                                            const uint32_t* __restrict__ totals,
+                                                           const uint32_t* __restrict__ sum1,
+                                                           const uint32_t* __restrict__ sum2,
                                                            const uint2* __restrict__ rect, uint2* __restrict__ srect)
 {
     __shared__ uint32_t h[RS_THREADS / 32][256];
@@ -161,21 +158,42 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const FrameHeader* __
     __shared__ uint32_t dbase[256];
     __shared__ uint32_t wsum[RS_THREADS / 32];
     const int b = blockIdx.x, v = b / nb, lb = b % nb;
-    if ((uint32_t)v >= hdr->n_views) return;
     const int64_t vbase = (int64_t)v * n;
     const int64_t base = vbase + (int64_t)lb * RS_ITEMS;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // keys, values, the view's digit total and this block's digit offset are
+    // loaded together, before the item count is known
+    uint32_t kk[RS_R], vv[RS_R];
+    uint2 rr[RS_R];
+    rs_load_keys_early(kin, vbase, lb, n, kk);
+#pragma unroll
+    for (int r = 0; r < RS_R; ++r) {
+        const int64_t j = (int64_t)lb * RS_ITEMS + w * RS_PER_WARP + r * 32 + lane;
+        vv[r] = j < n ? vin[vbase + j] : 0u;
+    }
+    const uint32_t c_tot = totals[v * 256 + threadIdx.x];
+    // this block's offset within the digit: the counts of the earlier blocks,
+    // as groups of RS_G2 blocks, then groups of RS_G1, then single blocks
+    uint32_t c_blk = 0;
+    {
+        const uint32_t* p2 = sum2 + (size_t)v * rs_groups(nb, RS_G2) * 256 + threadIdx.x;
+        const uint32_t* p1 = sum1 + (size_t)v * rs_groups(nb, RS_G1) * 256 + threadIdx.x;
+        const uint32_t* p0 = hist + (size_t)v * nb * 256 + threadIdx.x;
+        const int q2 = lb / RS_G2, q1 = lb / RS_G1;
+#pragma unroll 8
+        for (int k = 0; k < q2; ++k) c_blk += p2[(size_t)k * 256];
+#pragma unroll
+        for (int k = 0; k < RS_G2 / RS_G1 - 1; ++k)
+            if (q2 * (RS_G2 / RS_G1) + k < q1) c_blk += p1[(size_t)(q2 * (RS_G2 / RS_G1) + k) * 256];
+#pragma unroll
+        for (int k = 0; k < RS_G1 - 1; ++k)
+            if (q1 * RS_G1 + k < lb) c_blk += p0[(size_t)(q1 * RS_G1 + k) * 256];
+    }
+    if ((uint32_t)v >= hdr->n_views) return;
     const bool first = shift == 0;
     const int cnt = rs_block_count(n_surv, v, n, lb, first);
     if (cnt == 0) return;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint32_t kk[RS_R], vv[RS_R];
-    uint2 rr[RS_R];
-    rs_load_keys(kin, base, cnt, kk);
-#pragma unroll
-    for (int r = 0; r < RS_R; ++r) {
-        const int idx = w * RS_PER_WARP + r * 32 + lane;
-        vv[r] = idx < cnt ? vin[base + idx] : 0u;
-    }
+    rs_mask_keys(cnt, kk);
     if (GATHER) {
 #pragma unroll
         for (int r = 0; r < RS_R; ++r) rr[r] = kk[r] != 0xFFFFFFFFu ? rect[vbase + vv[r]] : make_uint2(0u, 0u);
@@ -183,8 +201,8 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const FrameHeader* __
     rs_warp_counts(kk, shift, h);
     {
         // exclusive scan of the view's 256 digit totals (RS_THREADS == 256)
-        const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-        const uint32_t c = totals[v * 256 + threadIdx.x];
+        const int wi = threadIdx.x >> 5;
+        const uint32_t c = c_tot;
         uint32_t x = c;
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
@@ -198,7 +216,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const FrameHeader* __
     }
     __syncthreads();
     {
-        uint32_t run = dbase[threadIdx.x] + hist[((size_t)v * 256 + threadIdx.x) * nb + lb];
+        uint32_t run = dbase[threadIdx.x] + c_blk;
         for (int w = 0; w < RS_THREADS / 32; ++w) {
             wb[w][threadIdx.x] = run;
             run += h[w][threadIdx.x];
@@ -255,9 +273,6 @@ __global__ void __launch_bounds__(ROWS_PER_BLOCK * 32, 4) k_rows(Frame F, uint32
     __shared__ uint32_t s_key[STAGE];
     __shared__ uint16_t s_list[STAGE];
     __shared__ uint32_t s_wc[ROWS_PER_BLOCK];
-    __shared__ uint32_t s_st[ROWS_PER_BLOCK][33];
-    __shared__ uint32_t s_x0[ROWS_PER_BLOCK][32];
-    __shared__ uint32_t s_gi[ROWS_PER_BLOCK][32];
     __shared__ uint16_t s_buf[ROWS_PER_BLOCK][64];
     const FrameHeader* hdr = F.hdr;
     if (EMIT && (hdr->status & STATUS_OVERFLOW)) return;
@@ -369,28 +384,33 @@ __global__ void __launch_bounds__(ROWS_PER_BLOCK * 32, 4) k_rows(Frame F, uint32
                 if (lane >= o) end += y;
             }
             const uint32_t total = __shfl_sync(0xffffffffu, end, 31);
-            s_st[w][lane] = end - wdt;
-            s_x0[w][lane] = x0;
-            s_gi[w][lane] = gi_l;
+            const uint32_t st = end - wdt;     // this member's first slot
             // the members beyond the group move to the front of the buffer
             const uint32_t carry = lane + 32 < nb ? (uint32_t)s_buf[w][lane + 32] : 0u;
             __syncwarp();
             if (lane + 32 < nb) s_buf[w][lane] = (uint16_t)carry;
             nb -= gsz;
+            uint32_t started = 0;     // members whose span starts before the window
             for (uint32_t q0 = 0; q0 < total; q0 += 32) {
                 const uint32_t q = q0 + lane;
                 const bool valid = q < total;
-                // owner of slot q: the last member (in rank order) whose span starts at or before q
-                int o = 0;
-#pragma unroll
-                for (int step = 16; step > 0; step >>= 1)
-                    if (s_st[w][o + step] <= q) o += step;
-                const uint32_t x = valid ? s_x0[w][o] + (q - s_st[w][o]) : 0xFFFFFFFFu;
+                // owner of slot q: the last member (in rank order) whose span
+                // starts at or before q.  Spans are non-empty and laid end to
+                // end, so the starts are distinct; S marks those in this window
+                // (lanes past the group add a start at total, past every valid slot).
+                const uint32_t rel = st - q0;
+                const uint32_t S = __reduce_or_sync(0xffffffffu, rel < 32u ? (1u << rel) : 0u);
+                const uint32_t o = (started + __popc(S & ((2u << lane) - 1u)) - 1u) & 31u;
+                started += __popc(S);
+                const uint32_t x_o = __shfl_sync(0xffffffffu, x0, o);
+                const uint32_t st_o = __shfl_sync(0xffffffffu, st, o);
+                const uint32_t gi_o = __shfl_sync(0xffffffffu, gi_l, o);
+                const uint32_t x = valid ? x_o + (q - st_o) : 0xFFFFFFFFu;
                 const uint32_t peers = __match_any_sync(0xffffffffu, x);
                 if (valid) {
                     const uint32_t p = ctr[x] + __popc(peers & lt);
                     if (EMIT) {
-                        const uint32_t gi = s_gi[w][o];
+                        const uint32_t gi = gi_o;
                         vals[p] = s_id[gi];
                         if (keys)
                             keys[p] = ((unsigned long long)(W.tile_base + (uint32_t)row * TX + x) << 32) | s_key[gi];
@@ -588,18 +608,23 @@ void launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long long ca
     const uint32_t V = L.n_views;
     if (n > 0) {
         uint32_t *ki = F.key0, *vi = F.val0, *ko = F.key1, *vo = F.val1;
-        uint32_t* totals = F.rs_hist + (size_t)V * 256 * nb;   // [4 passes][V][256]
-        cudaMemsetAsync(totals, 0, sizeof(uint32_t) * 4 * V * 256, st);
+        // after the block counts [V][nb][256]: per pass the digit totals
+        // [V][256] and the group sums [V][groups][256] of both levels
+        const size_t n1 = (size_t)V * 256 * rs_groups(nb, RS_G1), n2 = (size_t)V * 256 * rs_groups(nb, RS_G2);
+        const size_t per_pass = (size_t)V * 256 + n1 + n2;
+        uint32_t* sums = F.rs_hist + (size_t)V * 256 * nb;
+        cudaMemsetAsync(sums, 0, sizeof(uint32_t) * 4 * per_pass, st);
         for (int pass = 0; pass < 4; ++pass) {
-            uint32_t* tot = totals + (size_t)pass * V * 256;
-            k_rs_hist<<<V * nb, RS_THREADS, 0, st>>>(F.hdr, F.n_surv, ki, n, nb, 8 * pass, F.rs_hist, tot);
-            k_rs_scan<<<(V * 256 + 31) / 32, 1024, 0, st>>>(F.hdr, F.rs_hist, nb);
+            uint32_t* tot = sums + (size_t)pass * per_pass;
+            uint32_t* s1 = tot + (size_t)V * 256;
+            uint32_t* s2 = s1 + n1;
+            k_rs_hist<<<V * nb, RS_THREADS, 0, st>>>(F.hdr, F.n_surv, ki, n, nb, 8 * pass, F.rs_hist, tot, s1, s2);
             if (pass == 3)
                 k_rs_scatter<true><<<V * nb, RS_THREADS, 0, st>>>(F.hdr, F.n_surv, ki, vi, ko, vo, n, nb, 8 * pass,
-                                                                  F.rs_hist, tot, F.rect, F.srect);
+                                                                  F.rs_hist, tot, s1, s2, F.rect, F.srect);
             else
                 k_rs_scatter<false><<<V * nb, RS_THREADS, 0, st>>>(F.hdr, F.n_surv, ki, vi, ko, vo, n, nb, 8 * pass,
-                                                                   F.rs_hist, tot, nullptr, nullptr);
+                                                                   F.rs_hist, tot, s1, s2, nullptr, nullptr);
             std::swap(ki, ko);
             std::swap(vi, vo);
         }

@@ -90,7 +90,10 @@ FrameLayout frame_layout(uint64_t n, uint32_t V, uint32_t TT, uint32_t rb_total,
     L.key1 = take(sizeof(uint32_t) * vn);
     L.val1 = take(sizeof(uint32_t) * vn);
     L.srect = take(sizeof(uint2) * vn);
-    L.rs_hist = take(sizeof(uint32_t) * 256 * (size_t)V * (L.n_rs_blocks + 4));   // counts + 4 passes of totals
+    // block counts + 4 passes of digit totals and of the two levels of group sums
+    const int nbk = (int)L.n_rs_blocks;
+    L.rs_hist = take(sizeof(uint32_t) * 256 * (size_t)V *
+                     ((size_t)nbk + 4 * (1 + (size_t)rs_groups(nbk, RS_G1) + (size_t)rs_groups(nbk, RS_G2))));
     L.cnt = take(sizeof(uint32_t) * (size_t)L.n_chunks * TT);
     L.sel = take(sizeof(SelState) * V);
     L.sel_hist = take(sizeof(uint32_t) * SEL_BINS * (size_t)V);

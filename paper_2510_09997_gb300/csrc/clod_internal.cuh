@@ -22,6 +22,8 @@ constexpr int MAX_VIEWS = 64;
 // Depth-rank sort and emission geometry.
 constexpr int RS_THREADS = 256;
 constexpr int RS_ITEMS = 2048;          // keys per radix-sort block (8 per thread)
+constexpr int RS_G1 = 8, RS_G2 = 64;    // radix-sort blocks per group of the two offset-sum levels
+__host__ __device__ inline int rs_groups(int nb, int g) { return (nb + g - 1) / g; }
 constexpr int ROWS_PER_BLOCK = 8;       // tile rows per emission block (one warp each)
 constexpr int MAX_CHUNKS = 256;         // rank chunks per view
 constexpr int STAGE = 1024;             // rectangles staged in shared memory at a time
@@ -100,7 +102,7 @@ struct Frame {
     uint32_t* key1;
     uint32_t* val1;
     uint2* srect;           // tile rectangles in depth-rank order
-    uint32_t* rs_hist;      // radix-sort digit counts [view][256][block]
+    uint32_t* rs_hist;      // radix-sort digit counts [view][block][256], totals, superblock sums
     uint32_t* cnt;          // per (view, chunk, tile) pair counts, then offsets
     SelState* sel;          // primitive-budget select state [view]
     uint32_t* sel_hist;     // its digit counts [view][SEL_BINS]
