@@ -36,9 +36,10 @@ WORKLOAD = "object scene 1M Gaussians SH3, 1920x1080, 64-camera orbit d=2..20, s
 # [-5.6, 0]: + exp_spec 31 (13 FMA, 2 subtractions, cap) + opacity 2 = 33; a
 # contributing pair: + transmittance 2 + weight 1 + colour 6 = 9.
 FLOP_VISIT, FLOP_EXP, FLOP_CONTRIB = 9, 33, 9
-# kernels per frame: k_dist_max, k_preprocess; 4 x (k_rs_hist, k_rs_scan,
-# k_rs_scatter); k_chunk_count, k_chunk_scan, k_scan_tiles, k_rows<emit>; k_blend_fwd
-LAUNCHES_PER_FRAME = 19
+# kernels per frame: k_frame_setup, k_dist_max, k_preprocess; 4 x (k_rs_hist,
+# k_rs_scatter); k_chunk_count, k_chunk_scan, k_scan_tiles, k_rows<emit>;
+# k_blend_fwd
+LAUNCHES_PER_FRAME = 16
 
 
 def frames_list(only=None):
@@ -85,6 +86,7 @@ def parse():
     p.add_argument("--serve-seconds", type=float, default=2.0)
     p.add_argument("--no-city", action="store_true")
     p.add_argument("--frame", default=None, help="CAM:S -- time only that frame of the sweep (profiling)")
+    p.add_argument("--inflight", type=int, default=4, help="frames in flight (renderers and streams)")
     p.add_argument("--leg", default="all", choices=["all", "train", "serve", "city"],
                    help="train / serve: run only that leg and print its JSON object (for profiling)")
     return p.parse_args()
@@ -183,45 +185,81 @@ def run_ours(args):
         C.clod_preprocess(ds, [v], probe.ws, n_pairs=probe.npairs)
         kmax = max(kmax, int(probe.npairs.item()))
     del probe
-    R = C.Renderer(ds, [views[0]], pair_capacity=int(kmax * 1.02) + 1024)
+    # frames in flight: one renderer (workspace, pair list, image) and one
+    # stream per frame in flight; frame k goes to renderer k mod n_fl
+    n_fl = max(1, args.inflight)
+    Rs = [C.Renderer(ds, [views[0]], pair_capacity=int(kmax * 1.02) + 1024) for _ in range(n_fl)]
+    R = Rs[0]
     stream = torch.cuda.current_stream()
+    streams = [torch.cuda.Stream() for _ in range(n_fl)]
+    L = C.lib()
 
-    def step(k):
-        R.set_views([views[k % len(views)]])
-        R.run()
+    def launch(k, Rk, st, e=None, es=None):
+        Rk.set_views([views[k % len(views)]])
+        if e is not None:
+            e[0].record(es)
+        C.check("clod_preprocess", L.clod_preprocess(C.ctypes.byref(ds.c), Rk.carr, 1, C._ptr(Rk.ws),
+                                                     Rk.ws.numel(), None, None, None, C._ptr(Rk.npairs), st))
+        if e is not None:
+            e[1].record(es)
+        C.check("clod_bin_sort", L.clod_bin_sort(C._ptr(Rk.ws), Rk.cap, None, C._ptr(Rk.vals), C._ptr(Rk.ranges), st))
+        if e is not None:
+            e[2].record(es)
+        C.check("clod_render_fwd", L.clod_render_fwd(C._ptr(Rk.ws), C._ptr(Rk.vals), C._ptr(Rk.ranges),
+                                                     C._ptr(Rk.image), C._ptr(Rk.T), C._ptr(Rk.nc), st))
+        if e is not None:
+            e[3].record(es)
 
-    for k in range(args.warmup):
-        step(k)
+    def pipelined(n):
+        for k in range(n):
+            i = k % n_fl
+            launch(k, Rs[i], C._stream(streams[i]))
+
+    for s_ in streams:
+        s_.wait_stream(stream)
+    pipelined(max(args.warmup, n_fl))
     torch.cuda.synchronize()
     fma = fma_peak(C)
-    # stage events for the per-kernel roofline
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
-    L = C.lib()
-    st = C._stream(None)
     if world > 1:
         dist.barrier()
     clocks = ClockSampler(local)
     torch.cuda.synchronize()
+    # timed region 1 (the headline): the sweep with n_fl frames in flight
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
-    t0.record()
+    t0.record(stream)
+    for s_ in streams:
+        s_.wait_event(t0)
+    pipelined(args.steps)
+    for s_ in streams:
+        e_ = torch.cuda.Event()
+        e_.record(s_)
+        stream.wait_event(e_)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    elapsed = max_over_ranks(t0.elapsed_time(t1) / 1e3, device="cuda")
+    for r_ in Rs:
+        r_.check()   # every frame fitted the pair capacity (all used K <= kmax)
+    # timed region 2: the same frames one at a time on one stream, with events
+    # around each stage (each kernel runs alone: the per-stage times and the
+    # roofline come from here)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    st = C._stream(None)
+    for k in range(args.warmup):
+        launch(k, R, st)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
     for k in range(args.steps):
-        R.set_views([views[k % len(views)]])
-        e = ev[k]
-        e[0].record()
-        C.check("clod_preprocess", L.clod_preprocess(C.ctypes.byref(ds.c), R.carr, 1, C._ptr(R.ws), R.ws.numel(),
-                                                     None, None, None, C._ptr(R.npairs), st))
-        e[1].record()
-        C.check("clod_bin_sort", L.clod_bin_sort(C._ptr(R.ws), R.cap, None, C._ptr(R.vals), C._ptr(R.ranges), st))
-        e[2].record()
-        C.check("clod_render_fwd", L.clod_render_fwd(C._ptr(R.ws), C._ptr(R.vals), C._ptr(R.ranges),
-                                                     C._ptr(R.image), C._ptr(R.T), C._ptr(R.nc), st))
-        e[3].record()
-    t1.record()
+        launch(k, R, st, ev[k], stream)
+    s1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    elapsed = max_over_ranks(t0.elapsed_time(t1) / 1e3, device="cuda")
-    R.check()   # every frame fitted the pair capacity (the last one is checked; all used K <= kmax)
+    elapsed_seq = max_over_ranks(s0.elapsed_time(s1) / 1e3, device="cuda")
+    R.check()
     stage = np.array([[ev[k][j].elapsed_time(ev[k][j + 1]) for j in range(3)] for k in range(args.steps)])
     st_ms = stage.mean(0)
 
@@ -279,7 +317,10 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_gaussians": N_GAUSS, "width": WIDTH, "height": HEIGHT,
                    "frames_per_rank": len(views), "l2": "inputs larger than L2 (240 MB scene)",
-                   "parallelism": "replicas" if world > 1 else "single"},
+                   "parallelism": "replicas" if world > 1 else "single", "frames_in_flight": n_fl},
+        "sequential": {"value": round(whole_job_rate(args.steps, world, elapsed_seq), 3), "unit": "frames/s",
+                       "ms_per_step": round(elapsed_seq * 1e3 / args.steps, 4),
+                       "note": "one frame at a time on one stream; stage_ms and roofline are from this pass"},
         "stage_ms": {"preprocess": round(float(st_ms[0]), 4), "bin_sort": round(float(st_ms[1]), 4),
                      "blend": round(float(st_ms[2]), 4)},
         "stage_hbm": stage_bw,
@@ -296,9 +337,9 @@ def run_ours(args):
     if args.frame:
         out["config"]["single_frame"] = args.frame     # profiling run, not the sweep
     if rank == 0 and not args.no_extras:
-        out["e2e"] = e2e_leg(C, ds, R, views, args, stream)
+        out["e2e"] = e2e_leg(C, ds, Rs, views, args)
         out["cpu_baseline"] = cpu_baseline(sc, views)
-        del R, ds
+        del R, Rs, ds
         torch.cuda.empty_cache()
         if not args.no_train:
             out["train"] = train_leg(args)
@@ -335,37 +376,37 @@ def fma_peak(C, iters=20000, reps=5):
     return {"tflops": best, "iters": iters}
 
 
-def e2e_leg(C, ds, R, views, args, stream):
-    """Same frames through the C ABI with host buffers, pipelined: the frame
-    header and view record (248 B) go host->device inside clod_preprocess,
-    every image comes back to pinned host memory on a copy stream while the
-    next frame renders, and the host waits for each image before it reuses
-    that buffer.  Wall-clock time of the whole loop."""
+def e2e_leg(C, ds, Rs, views, args):
+    """Same frames through the C ABI with host buffers and len(Rs) frames in
+    flight (one renderer, render stream and copy stream each): the frame
+    header and view record (248 B) go host->device as launch parameters,
+    every image comes back to pinned host memory while other frames render,
+    and the host waits for each image before it reuses that buffer.
+    Wall-clock time of the whole loop."""
     import torch
-    R2 = C.Renderer(ds, [views[0]], pair_capacity=R.cap)
-    rs = [R, R2]
-    hosts = [torch.empty(R.image.numel(), dtype=torch.float32, pin_memory=True) for _ in range(2)]
-    copy_stream = torch.cuda.Stream()
-    render_stream = torch.cuda.Stream()
-    done = [None, None]
+    n_fl = len(Rs)
+    hosts = [torch.empty(Rs[0].image.numel(), dtype=torch.float32, pin_memory=True) for _ in range(n_fl)]
+    copy_streams = [torch.cuda.Stream() for _ in range(n_fl)]
+    render_streams = [torch.cuda.Stream() for _ in range(n_fl)]
+    done = [None] * n_fl
     steps = min(args.steps, 128)
 
     def frame(k):
-        i = k % 2
+        i = k % n_fl
         if done[i] is not None:
             done[i].synchronize()             # the host has this buffer's previous image
-        rr = rs[i]
+        rr = Rs[i]
         rr.set_views([views[k % len(views)]])
-        rr.run(render_stream)
+        rr.run(render_streams[i])
         ready = torch.cuda.Event()
-        ready.record(render_stream)
-        copy_stream.wait_event(ready)
-        with torch.cuda.stream(copy_stream):
+        ready.record(render_streams[i])
+        copy_streams[i].wait_event(ready)
+        with torch.cuda.stream(copy_streams[i]):
             hosts[i].copy_(rr.image, non_blocking=True)
             done[i] = torch.cuda.Event()
-            done[i].record(copy_stream)
+            done[i].record(copy_streams[i])
 
-    for k in range(4):
+    for k in range(2 * n_fl):
         frame(k)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -374,11 +415,12 @@ def e2e_leg(C, ds, R, views, args, stream):
     for d in done:
         d.synchronize()
     dt = time.perf_counter() - t0
-    rs[0].check()
-    rs[1].check()
+    for r in Rs:
+        r.check()
     return {"value": round(steps / dt, 3), "unit": "frames/s", "h2d_bytes_per_step": 248,
-            "d2h_bytes_per_step": int(R.image.numel() * 4), "steps": steps,
-            "pipeline": "two frame buffers; image copies overlap the next frame"}
+            "d2h_bytes_per_step": int(Rs[0].image.numel() * 4), "steps": steps,
+            "pipeline": "%d frames in flight (one render and one copy stream each); image copies overlap the "
+                        "other frames" % n_fl}
 
 
 def cpu_baseline(sc, views, budget_s=20.0):
