@@ -84,6 +84,7 @@ def parse():
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--train-steps", type=int, default=10)
     p.add_argument("--serve-seconds", type=float, default=2.0)
+    p.add_argument("--serve-slots", type=int, default=6, help="server slots (batches in flight)")
     p.add_argument("--no-city", action="store_true")
     p.add_argument("--frame", default=None, help="CAM:S -- time only that frame of the sweep (profiling)")
     p.add_argument("--inflight", type=int, default=4, help="frames in flight (renderers and streams)")
@@ -692,7 +693,7 @@ def serve_leg(args):
             lat[k] = done - arr[k]
         return lat, len(vs) / (done - arr[0])
 
-    def run_server(vs, arr, B=8, slots=3):
+    def run_server(vs, arr, B=8, slots=args.serve_slots):
         srv = SV.Server(ds, max_views_per_batch=B, n_slots=slots, use_graphs=True, pair_capacity=1 << 25,
                         max_pixels_per_batch=3840 * 2160 * 2, max_width=3840, max_height=2160)
         for v in warm:
@@ -731,7 +732,8 @@ def serve_leg(args):
 
     q = lambda a, p: round(float(np.percentile(a, p)) * 1e3, 3)
     res = {"workload": "object scene 2M Gaussians SH3 resident; Poisson arrivals; 512^2/720p/1080p/4K mixed; "
-                       "d in [1,50]; s_v log-uniform [1,32]; server: 8 views/batch, 3 slots, CUDA graphs",
+                       "d in [1,50]; s_v log-uniform [1,32]; server: 8 views/batch, %d slots, CUDA graphs"
+                       % args.serve_slots,
            "latency": "completion minus scheduled arrival"}
     for lam in (rate, 300.0):
         n = min(n_req, int(lam * args.serve_seconds))

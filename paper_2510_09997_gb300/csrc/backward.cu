@@ -165,8 +165,8 @@ __global__ void __launch_bounds__(BWD_THREADS, 8) k_blend_bwd(Frame F, const uin
         uint32_t unit = 0;
         if (lane == 0) unit = atomicAdd(&F.hdr->work[1], 1u);
         unit = __shfl_sync(0xffffffffu, unit, 0);
-        const uint32_t t = unit >> 2;
-        if (t >= TT) break;
+        if ((unit >> 2) >= TT) break;
+        const uint32_t t = F.torder[unit >> 2];     // longest tile lists first
         const int qd = (int)(unit & 3u);
         int view = 0;
         for (uint32_t u = 1; u < V; ++u)

@@ -546,6 +546,11 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Frame F, uint32_t* __restri
     __shared__ uint32_t sc[ST_ROUND];
     const uint32_t TT = F.hdr->total_tiles;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    // "long" tiles (for the work order below): lists longer than twice the mean
+    const unsigned long long thr = 2ull * F.hdr->n_pairs / (TT ? TT : 1u);
+    __shared__ uint32_t s_long;
+    if (threadIdx.x == 0) s_long = 0u;
+    __syncthreads();
     unsigned long long carry = 0;
     for (uint32_t base = 0; base < TT; base += ST_ROUND) {
         const uint32_t t0 = base + threadIdx.x * ST_PER;
@@ -558,6 +563,8 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Frame F, uint32_t* __restri
                 if (t0 + u < TT) c[u] = F.tile_count[t0 + u];
         }
         const unsigned long long s = (unsigned long long)c[0] + c[1] + c[2] + c[3];
+        const uint32_t nl = __reduce_add_sync(0xffffffffu, (c[0] > thr) + (c[1] > thr) + (c[2] > thr) + (c[3] > thr));
+        if (lane == 0 && nl) atomicAdd_block(&s_long, nl);
         unsigned long long x = s;
         for (int o = 1; o < 32; o <<= 1) {
             const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
@@ -591,6 +598,45 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Frame F, uint32_t* __restri
             ranges[2 * (size_t)(base + k) + 1] = cc ? o + cc : 0u;
         }
         __syncthreads();     // so, sc and wsum are reused by the next round
+    }
+    // the blends' work order: the long tiles first, then the others, each
+    // class in tile order -- so the longest items do not start last, and
+    // neighbouring tiles still run together.  Only the order in which warps
+    // take tiles: no result depends on it.  (If K exceeds the capacity the
+    // blends do not run; the order is still a permutation.)
+    __shared__ uint32_t hsum[32];
+    const uint32_t n_long = s_long;
+    uint32_t long_before = 0;
+    for (uint32_t base = 0; base < TT; base += ST_ROUND) {
+        const uint32_t t0 = base + threadIdx.x * ST_PER;
+        bool hv[ST_PER];
+        uint32_t h = 0;
+#pragma unroll
+        for (int u = 0; u < ST_PER; ++u) {
+            hv[u] = t0 + u < TT && F.tile_count[t0 + u] > thr;
+            h += hv[u] ? 1u : 0u;
+        }
+        uint32_t x = h;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) hsum[wid] = x;
+        __syncthreads();
+        uint32_t before = long_before + x - h, round_total = 0;
+        for (int w2 = 0; w2 < 32; ++w2) {
+            const uint32_t y = hsum[w2];
+            if (w2 < wid) before += y;
+            round_total += y;
+        }
+#pragma unroll
+        for (int u = 0; u < ST_PER; ++u) {
+            const uint32_t t = t0 + u;
+            if (t < TT) F.torder[hv[u] ? before : n_long + (t - before)] = t;
+            before += hv[u] ? 1u : 0u;
+        }
+        long_before += round_total;
+        __syncthreads();     // hsum is rewritten by the next round
     }
     if (threadIdx.x == 0) {
         F.tile_offset[TT] = static_cast<uint32_t>(carry);

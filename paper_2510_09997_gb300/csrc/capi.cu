@@ -79,6 +79,7 @@ FrameLayout frame_layout(uint64_t n, uint32_t V, uint32_t TT, uint32_t rb_total,
     L.tile_count = take(sizeof(uint32_t) * (size_t)TT);
     L.views = take(sizeof(ViewDev) * V);
     L.tile_offset = take(sizeof(uint32_t) * ((size_t)TT + 1));
+    L.torder = take(sizeof(uint32_t) * (size_t)TT);
     const size_t vn = (size_t)V * n;
     L.rec0 = take(sizeof(float4) * vn);
     L.rec1 = take(sizeof(float4) * vn);
@@ -119,6 +120,7 @@ Frame frame_ptrs(void* ws, const FrameLayout& L)
     F.rect = reinterpret_cast<uint2*>(b + L.rect);
     F.tile_count = reinterpret_cast<uint32_t*>(b + L.tile_count);
     F.tile_offset = reinterpret_cast<uint32_t*>(b + L.tile_offset);
+    F.torder = reinterpret_cast<uint32_t*>(b + L.torder);
     F.key0 = reinterpret_cast<uint32_t*>(b + L.key0);
     F.val0 = reinterpret_cast<uint32_t*>(b + L.val0);
     F.key1 = reinterpret_cast<uint32_t*>(b + L.key1);

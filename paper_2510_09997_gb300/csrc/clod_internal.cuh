@@ -77,7 +77,7 @@ struct SelState {
 };
 
 struct FrameLayout {
-    size_t header, views, dmax_key, n_surv, rec0, rec1, rec2, depth, rect, tile_count, tile_offset,
+    size_t header, views, dmax_key, n_surv, rec0, rec1, rec2, depth, rect, tile_count, tile_offset, torder,
         key0, val0, key1, val1, srect, rs_hist, cnt, sel, sel_hist, total;
     uint32_t total_tiles, n_views, n_chunks, n_rs_blocks, rb_total, max_tx;
     uint64_t n;
@@ -92,11 +92,12 @@ struct Frame {
     uint32_t* n_surv;
     float4* rec0;
     float4* rec1;
-    float4* rec2;           // (b, reach half-extents x, y, 0)
+    float4* rec2;           // (b, reach half-extents x, y, power floor)
     float* depth;
     uint2* rect;
     uint32_t* tile_count;
     uint32_t* tile_offset;
+    uint32_t* torder;       // the blends' work order: tiles by descending list length
     uint32_t* key0;         // depth-rank sort ping-pong: keys (depth bits) / values (index)
     uint32_t* val0;
     uint32_t* key1;
