@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const FrameHeader* __res
 // tile rectangle of every survivor into rank order.  Keys, values and
 // rectangles are loaded before the counting, so their latency overlaps it.
 template <bool GATHER>
-__global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const FrameHeader* __restrict__ hdr,
+__global__ void __launch_bounds__(RS_THREADS, 4) k_rs_scatter(const FrameHeader* __restrict__ hdr,
                                                            const uint32_t* __restrict__ n_surv,
                                                            const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                            uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
@@ -485,7 +485,7 @@ __global__ void __launch_bounds__(512) k_chunk_count(Frame F)
 // sums, their scan across the warps, then each segment rescanned.
 constexpr int CS_TILES = 32, CS_SEG = 8;
 constexpr int CS_MAXPER = (MAX_CHUNKS + CS_SEG - 1) / CS_SEG;
-__global__ void __launch_bounds__(CS_TILES * CS_SEG) k_chunk_scan(Frame F)
+__global__ void __launch_bounds__(CS_TILES * CS_SEG, 2) k_chunk_scan(Frame F)
 {
     __shared__ uint32_t part[CS_SEG][CS_TILES];
     const uint32_t TT = F.hdr->total_tiles;
