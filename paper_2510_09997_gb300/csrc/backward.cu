@@ -318,6 +318,9 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(Frame F, clod_scene S, c
     __shared__ float sdmax[MAX_VIEWS];
     __shared__ float sdmg[MAX_VIEWS];
     __shared__ float sgav[MAX_VIEWS];
+    // each thread's SH gradient summed over the views, element-major (no bank
+    // conflicts); added to the gradient buffer once per Gaussian
+    __shared__ float s_dsh[48][128];
     const uint32_t V = F.hdr->n_views;
     {
         const int words = static_cast<int>(V * sizeof(ViewDev) / 4);
@@ -340,6 +343,7 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(Frame F, clod_scene S, c
         float gm0 = 0.f, gm1 = 0.f, gm2 = 0.f, gs0 = 0.f, gs1 = 0.f, gs2 = 0.f;
         float gq0 = 0.f, gq1 = 0.f, gq2 = 0.f, gq3 = 0.f, gop = 0.f, gdec = 0.f;
         float mx = 0.f, my = 0.f, mz = 0.f, alpha = 0.f, sigma = 0.f;
+        bool sh_any = false;
         if (active) {
             mx = S.means[3 * i];
             my = S.means[3 * i + 1];
@@ -370,13 +374,17 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(Frame F, clod_scene S, c
                 const float inv_d = 1.0f / d;
                 const float dx = e0 * inv_d, dy = e1 * inv_d, dz = e2 * inv_d;
                 const float* shp = S.sh + (size_t)i * K * 3;
-                float* dshp = P.dsh + (size_t)i * K * 3;
                 // gradient reaching each channel's SH sum (0 where the clamp held)
                 const float gc0 = col[0] > 0.0f ? g_col[0] : 0.0f;
                 const float gc1 = col[1] > 0.0f ? g_col[1] : 0.0f;
                 const float gc2 = col[2] > 0.0f ? g_col[2] : 0.0f;
                 float gdx = 0.f, gdy = 0.f, gdz = 0.f;
                 if (gc0 != 0.0f || gc1 != 0.0f || gc2 != 0.0f) {
+                    if (!sh_any) {
+#pragma unroll
+                        for (int j = 0; j < 3 * K; ++j) s_dsh[j][threadIdx.x] = 0.0f;
+                        sh_any = true;
+                    }
                     const float xx = dx * dx, yy = dy * dy, zz = dz * dz;
                     // one basis function and its direction derivatives at a
                     // time (k is a compile-time constant after unrolling)
@@ -384,13 +392,14 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(Frame F, clod_scene S, c
                     for (int k = 0; k < K; ++k) {
                         float bk, bxk, byk, bzk;
                         sh_term(k, dx, dy, dz, xx, yy, zz, bk, bxk, byk, bzk);
-                        const float s = shp[3 * k] * gc0 + shp[3 * k + 1] * gc1 + shp[3 * k + 2] * gc2;
+                        const float s = __ldg(shp + 3 * k) * gc0 + __ldg(shp + 3 * k + 1) * gc1 +
+                                        __ldg(shp + 3 * k + 2) * gc2;
                         gdx += bxk * s;
                         gdy += byk * s;
                         gdz += bzk * s;
-                        if (gc0 != 0.0f) dshp[3 * k] += bk * gc0;
-                        if (gc1 != 0.0f) dshp[3 * k + 1] += bk * gc1;
-                        if (gc2 != 0.0f) dshp[3 * k + 2] += bk * gc2;
+                        s_dsh[3 * k][threadIdx.x] += bk * gc0;
+                        s_dsh[3 * k + 1][threadIdx.x] += bk * gc1;
+                        s_dsh[3 * k + 2][threadIdx.x] += bk * gc2;
                     }
                 }
                 // direction = e / |e|
@@ -543,6 +552,11 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(Frame F, clod_scene S, c
                     }
                 }
             }
+        }
+        if (sh_any) {
+            float* dshp = P.dsh + (size_t)i * K * 3;
+#pragma unroll
+            for (int j = 0; j < 3 * K; ++j) dshp[j] += s_dsh[j][threadIdx.x];
         }
         if (active) {
             P.dmeans[3 * i] += gm0;
