@@ -63,30 +63,33 @@ __device__ __forceinline__ uint32_t match_bits(uint32_t d)
 // Keys of the block's items held by this thread: warp w owns items
 // [w * PER_WARP, (w + 1) * PER_WARP) of the block, lane l the items
 // w * PER_WARP + 32 r + l.  All loads are issued before any is used (one
-// round trip), and before the block's item count is known (any key of the
-// view's n slots may be read); rs_mask_keys then applies the count.
+// round trip).
 // 0xFFFFFFFF marks "no item": beyond the block, or culled (the first pass);
 // the later passes never hold it, since a survivor's key is the bit pattern
 // of a positive depth.
 constexpr int RS_PER_WARP = RS_ITEMS / (RS_THREADS / 32);
 constexpr int RS_R = RS_PER_WARP / 32;
-__device__ __forceinline__ void rs_load_keys_early(const uint32_t* __restrict__ keys, int64_t vbase, int lb,
-                                                   int64_t n, uint32_t (&kk)[RS_R])
+__device__ __forceinline__ void rs_load_keys(const uint32_t* __restrict__ keys, int64_t base, int cnt,
+                                             uint32_t (&kk)[RS_R])
 {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
     for (int r = 0; r < RS_R; ++r) {
-        const int64_t j = (int64_t)lb * RS_ITEMS + w * RS_PER_WARP + r * 32 + lane;
-        kk[r] = j < n ? keys[vbase + j] : 0xFFFFFFFFu;
+        const int idx = w * RS_PER_WARP + r * 32 + lane;
+        kk[r] = idx < cnt ? keys[base + idx] : 0xFFFFFFFFu;
     }
 }
 
-__device__ __forceinline__ void rs_mask_keys(int cnt, uint32_t (&kk)[RS_R])
+// Items of radix block lb: the first pass reads all n keys of the view (and
+// drops the culled), a count known without a load; later passes read the
+// view's survivors, n_surv[2 v + 1].
+__device__ __forceinline__ int rs_first_count(int64_t n, int lb)
 {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-    for (int r = 0; r < RS_R; ++r)
-        if (w * RS_PER_WARP + r * 32 + lane >= cnt) kk[r] = 0xFFFFFFFFu;
+    return (int)max((int64_t)0, min((int64_t)RS_ITEMS, n - (int64_t)lb * RS_ITEMS));
+}
+__device__ __forceinline__ int rs_later_count(const uint32_t* n_surv, int v, int lb)
+{
+    return (int)max((int64_t)0, min((int64_t)RS_ITEMS, (int64_t)n_surv[2 * v + 1] - (int64_t)lb * RS_ITEMS));
 }
 
 // Per-warp digit counts of the held keys, in h[w][digit].
@@ -105,14 +108,6 @@ __device__ __forceinline__ void rs_warp_counts(const uint32_t (&kk)[RS_R], int s
     }
 }
 
-// Items of radix block lb of view v: the first pass reads all n keys of the
-// view (and drops the culled); later passes read the view's survivors.
-__device__ __forceinline__ int rs_block_count(const uint32_t* n_surv, int v, int64_t n, int lb, bool first)
-{
-    const int64_t nv = first ? n : (int64_t)n_surv[2 * v + 1];
-    return (int)max((int64_t)0, min((int64_t)RS_ITEMS, nv - (int64_t)lb * RS_ITEMS));
-}
-
 __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const FrameHeader* __restrict__ hdr,
                                                         const uint32_t* __restrict__ n_surv,
                                                         const uint32_t* __restrict__ keys, int64_t n, int nb, int shift,
@@ -121,12 +116,23 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const FrameHeader* __res
 {
     __shared__ uint32_t h[RS_THREADS / 32][256];
     const int b = blockIdx.x, v = b / nb, lb = b % nb;
+    const int64_t base = (int64_t)v * n + (int64_t)lb * RS_ITEMS;
+    // the first pass's keys are loaded before the view check (its count needs
+    // no load); a later pass reads its count first, so blocks past the
+    // survivors move no data
     uint32_t kk[RS_R];
-    rs_load_keys_early(keys, (int64_t)v * n, lb, n, kk);
-    if ((uint32_t)v >= hdr->n_views) return;
-    const int cnt = rs_block_count(n_surv, v, n, lb, shift == 0);
+    int cnt;
+    if (shift == 0) {
+        cnt = rs_first_count(n, lb);
+        rs_load_keys(keys, base, cnt, kk);
+        if ((uint32_t)v >= hdr->n_views) return;
+    } else {
+        if ((uint32_t)v >= hdr->n_views) return;
+        cnt = rs_later_count(n_surv, v, lb);
+        if (cnt == 0) return;
+        rs_load_keys(keys, base, cnt, kk);
+    }
     if (cnt == 0) return;     // no items (and none in any later block)
-    rs_mask_keys(cnt, kk);
     rs_warp_counts(kk, shift, h);
     __syncthreads();
     uint32_t s = 0;
@@ -161,15 +167,25 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_rs_scatter(const FrameHeader*
     const int64_t vbase = (int64_t)v * n;
     const int64_t base = vbase + (int64_t)lb * RS_ITEMS;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // keys, values, the view's digit total and this block's digit offset are
-    // loaded together, before the item count is known
+    // keys, values, the view's digit total and this block's digit offsets are
+    // loaded together (in the first pass before the view check; a later pass
+    // reads its item count first, so blocks past the survivors move no data)
+    const bool first = shift == 0;
+    int cnt;
+    if (first) {
+        cnt = rs_first_count(n, lb);
+    } else {
+        if ((uint32_t)v >= hdr->n_views) return;
+        cnt = rs_later_count(n_surv, v, lb);
+        if (cnt == 0) return;
+    }
     uint32_t kk[RS_R], vv[RS_R];
     uint2 rr[RS_R];
-    rs_load_keys_early(kin, vbase, lb, n, kk);
+    rs_load_keys(kin, base, cnt, kk);
 #pragma unroll
     for (int r = 0; r < RS_R; ++r) {
-        const int64_t j = (int64_t)lb * RS_ITEMS + w * RS_PER_WARP + r * 32 + lane;
-        vv[r] = j < n ? vin[vbase + j] : 0u;
+        const int idx = w * RS_PER_WARP + r * 32 + lane;
+        vv[r] = idx < cnt ? vin[base + idx] : 0u;
     }
     const uint32_t c_tot = totals[v * 256 + threadIdx.x];
     // this block's offset within the digit: the counts of the earlier blocks,
@@ -189,11 +205,8 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_rs_scatter(const FrameHeader*
         for (int k = 0; k < RS_G1 - 1; ++k)
             if (q1 * RS_G1 + k < lb) c_blk += p0[(size_t)(q1 * RS_G1 + k) * 256];
     }
-    if ((uint32_t)v >= hdr->n_views) return;
-    const bool first = shift == 0;
-    const int cnt = rs_block_count(n_surv, v, n, lb, first);
+    if (first && (uint32_t)v >= hdr->n_views) return;
     if (cnt == 0) return;
-    rs_mask_keys(cnt, kk);
     if (GATHER) {
 #pragma unroll
         for (int r = 0; r < RS_R; ++r) rr[r] = kk[r] != 0xFFFFFFFFu ? rect[vbase + vv[r]] : make_uint2(0u, 0u);
