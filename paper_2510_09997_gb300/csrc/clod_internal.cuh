@@ -26,7 +26,7 @@ constexpr int RS_G1 = 8, RS_G2 = 64;    // radix-sort blocks per group of the tw
 __host__ __device__ inline int rs_groups(int nb, int g) { return (nb + g - 1) / g; }
 constexpr int ROWS_PER_BLOCK = 8;       // tile rows per emission block (one warp each)
 constexpr int MAX_CHUNKS = 256;         // rank chunks per view
-constexpr int STAGE = 1024;             // rectangles staged in shared memory at a time
+constexpr int STAGE = 2048;             // rectangles staged in shared memory at a time
 
 // Frame header at offset 0 of a frame workspace.
 struct FrameHeader {
