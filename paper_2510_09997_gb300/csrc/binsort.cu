@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(ROWS_PER_BLOCK * 32, 4) k_rows(Frame F, uint32
             s_rect[k] = F.srect[vb + s0 + k];
             if (EMIT) {
                 s_id[k] = F.val0[vb + s0 + k];
-                s_key[k] = F.key0[vb + s0 + k];
+                if (keys) s_key[k] = F.key0[vb + s0 + k];
             }
         }
         __syncthreads();
@@ -398,6 +398,11 @@ __global__ void __launch_bounds__(ROWS_PER_BLOCK * 32, 4) k_rows(Frame F, uint32
             }
             const uint32_t total = __shfl_sync(0xffffffffu, end, 31);
             const uint32_t st = end - wdt;     // this member's first slot
+            // per member: first slot and first tile packed (widths are at most
+            // 1024 tiles, so total <= 32768), and the Gaussian index (and key)
+            const uint32_t xst = (st << 16) | x0;
+            const uint32_t gid = (EMIT && lane < gsz) ? s_id[gi_l] : 0u;
+            const uint32_t gkey = (EMIT && keys && lane < gsz) ? s_key[gi_l] : 0u;
             // the members beyond the group move to the front of the buffer
             const uint32_t carry = lane + 32 < nb ? (uint32_t)s_buf[w][lane + 32] : 0u;
             __syncwarp();
@@ -415,19 +420,20 @@ __global__ void __launch_bounds__(ROWS_PER_BLOCK * 32, 4) k_rows(Frame F, uint32
                 const uint32_t S = __reduce_or_sync(0xffffffffu, rel < 32u ? (1u << rel) : 0u);
                 const uint32_t o = (started + __popc(S & ((2u << lane) - 1u)) - 1u) & 31u;
                 started += __popc(S);
-                const uint32_t x_o = __shfl_sync(0xffffffffu, x0, o);
-                const uint32_t st_o = __shfl_sync(0xffffffffu, st, o);
-                const uint32_t gi_o = __shfl_sync(0xffffffffu, gi_l, o);
-                const uint32_t x = valid ? x_o + (q - st_o) : 0xFFFFFFFFu;
+                const uint32_t xst_o = __shfl_sync(0xffffffffu, xst, o);
+                const uint32_t gid_o = EMIT ? __shfl_sync(0xffffffffu, gid, o) : 0u;
+                const uint32_t x = valid ? (xst_o & 0xFFFFu) + (q - (xst_o >> 16)) : 0xFFFFFFFFu;
                 const uint32_t peers = __match_any_sync(0xffffffffu, x);
+                if (EMIT && keys) {
+                    const uint32_t key_o = __shfl_sync(0xffffffffu, gkey, o);
+                    if (valid) {
+                        const uint32_t p = ctr[x] + __popc(peers & lt);
+                        keys[p] = ((unsigned long long)(W.tile_base + (uint32_t)row * TX + x) << 32) | key_o;
+                    }
+                }
                 if (valid) {
                     const uint32_t p = ctr[x] + __popc(peers & lt);
-                    if (EMIT) {
-                        const uint32_t gi = gi_o;
-                        vals[p] = s_id[gi];
-                        if (keys)
-                            keys[p] = ((unsigned long long)(W.tile_base + (uint32_t)row * TX + x) << 32) | s_key[gi];
-                    }
+                    if (EMIT) vals[p] = gid_o;
                     // the highest peer holds the last slot of this tile: advance the counter past it
                     if ((31 - __clz(peers)) == lane) ctr[x] = p + 1u;
                 }
