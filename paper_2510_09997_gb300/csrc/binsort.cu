@@ -257,6 +257,15 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_rs_scatter(const FrameHeader*
 // ---------------------------------------------------------------------------
 // 2./4. per (chunk, tile row) walks
 // ---------------------------------------------------------------------------
+// Rank chunks a view actually uses: one per 1024 survivors (at least one), at
+// most CH (the layout's count).  Chunks at or past it hold no ranks; the
+// count, the chunk scan and the emission skip them, so a light frame does
+// not pay for CH chunks.
+__device__ __forceinline__ uint32_t chunks_used(uint32_t Ns, uint32_t CH)
+{
+    return max(1u, min(CH, (Ns + 1023u) / 1024u));
+}
+
 // Block -> (view, chunk, row block) through the views' rb_base.
 __device__ __forceinline__ int find_view_rb(const ViewDev* views, uint32_t V, uint32_t b)
 {
@@ -308,7 +317,9 @@ __global__ void __launch_bounds__(ROWS_PER_BLOCK * 32, 4) k_rows(Frame F, uint32
     uint32_t* ctr = sm + (size_t)w * hdr->max_tx;
     uint32_t* cnt_row = F.cnt + (size_t)CH * W.tile_base + (size_t)c * T + (size_t)row * TX;
     const uint32_t Ns = F.n_surv[2 * v + 1];
-    const uint32_t C = (Ns + CH - 1) / CH;
+    const uint32_t CHe = chunks_used(Ns, CH);
+    if (c >= CHe) return;
+    const uint32_t C = (Ns + CHe - 1) / CHe;
     const uint32_t r0 = min(Ns, c * C), r1 = min(Ns, r0 + C);
     if (row_ok)
         for (int x = lane; x < TX; x += 32)
@@ -460,12 +471,14 @@ __global__ void __launch_bounds__(512) k_chunk_count(Frame F)
     const uint32_t c = blockIdx.x % CH;
     if ((uint32_t)v >= hdr->n_views) return;
     const ViewDev& W = F.views[v];
+    const uint32_t Ns = F.n_surv[2 * v + 1];
+    const uint32_t CHe = chunks_used(Ns, CH);
+    if (c >= CHe) return;
     const int TX = W.TX, TY = W.TY, GX = TX + 1;
     const int G = GX * (TY + 1);
     for (int k = threadIdx.x; k < G; k += blockDim.x) g[k] = 0u;
     __syncthreads();
-    const uint32_t Ns = F.n_surv[2 * v + 1];
-    const uint32_t C = (Ns + CH - 1) / CH;
+    const uint32_t C = (Ns + CHe - 1) / CHe;
     const uint32_t r0 = min(Ns, c * C), r1 = min(Ns, r0 + C);
     const uint2* sr = F.srect + (int64_t)v * n;
     for (uint32_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
@@ -514,7 +527,7 @@ __global__ void __launch_bounds__(CS_TILES * CS_SEG, 2) k_chunk_scan(Frame F)
     const uint32_t t = blockIdx.x * CS_TILES + tx;
     const bool ok = t < TT;
     uint32_t* col = nullptr;
-    uint32_t T = 0;
+    uint32_t T = 0, CHe = 0;
     if (ok) {
         int v = 0;
         for (uint32_t u = 1; u < V; ++u)
@@ -522,9 +535,10 @@ __global__ void __launch_bounds__(CS_TILES * CS_SEG, 2) k_chunk_scan(Frame F)
         const ViewDev& W = F.views[v];
         T = (uint32_t)(W.TX * W.TY);
         col = F.cnt + (size_t)CH * W.tile_base + (t - W.tile_base);
+        CHe = chunks_used(F.n_surv[2 * v + 1], CH);
     }
-    const uint32_t per = (CH + CS_SEG - 1) / CS_SEG;     // <= CS_MAXPER
-    const uint32_t c0 = min(CH, sg * per), c1 = min(CH, c0 + per);
+    const uint32_t per = (CHe + CS_SEG - 1) / CS_SEG;     // <= CS_MAXPER
+    const uint32_t c0 = min(CHe, sg * per), c1 = min(CHe, c0 + per);
     // the segment's counts are held in registers: one round of loads
     uint32_t xs[CS_MAXPER];
     uint32_t sum = 0;
