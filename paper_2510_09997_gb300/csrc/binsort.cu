@@ -570,6 +570,13 @@ __global__ void __launch_bounds__(CS_TILES * CS_SEG, 2) k_chunk_scan(Frame F)
 // of 4096 tiles: each thread loads 4 consecutive counts (one 16-byte load
 // from the 256-byte aligned array), the block scans, and the offsets go out
 // through shared memory in coalesced stores.
+// Length class of a tile list for the blends' work order: 0 (longest) to 3.
+__device__ __forceinline__ uint32_t tile_class(uint32_t c, unsigned long long mean)
+{
+    const unsigned long long cc = c;
+    return cc > 2ull * mean ? 0u : (cc > mean ? 1u : (2ull * cc > mean ? 2u : 3u));
+}
+
 constexpr int ST_PER = 4;
 constexpr int ST_ROUND = 1024 * ST_PER;
 __global__ void __launch_bounds__(1024) k_scan_tiles(Frame F, uint32_t* __restrict__ ranges, unsigned long long cap)
@@ -579,10 +586,11 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Frame F, uint32_t* __restri
     __shared__ uint32_t sc[ST_ROUND];
     const uint32_t TT = F.hdr->total_tiles;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    // "long" tiles (for the work order below): lists longer than twice the mean
-    const unsigned long long thr = 2ull * F.hdr->n_pairs / (TT ? TT : 1u);
-    __shared__ uint32_t s_long;
-    if (threadIdx.x == 0) s_long = 0u;
+    // length classes of the tiles (for the work order below): lists longer
+    // than 2m, than m, than m/2 (m the mean list length), and the rest
+    const unsigned long long mean = F.hdr->n_pairs / (TT ? TT : 1u);
+    __shared__ uint32_t s_cls[4];
+    if (threadIdx.x < 4) s_cls[threadIdx.x] = 0u;
     __syncthreads();
     unsigned long long carry = 0;
     for (uint32_t base = 0; base < TT; base += ST_ROUND) {
@@ -596,8 +604,15 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Frame F, uint32_t* __restri
                 if (t0 + u < TT) c[u] = F.tile_count[t0 + u];
         }
         const unsigned long long s = (unsigned long long)c[0] + c[1] + c[2] + c[3];
-        const uint32_t nl = __reduce_add_sync(0xffffffffu, (c[0] > thr) + (c[1] > thr) + (c[2] > thr) + (c[3] > thr));
-        if (lane == 0 && nl) atomicAdd_block(&s_long, nl);
+        {
+            uint32_t k4 = 0;     // per-class counts of this thread's tiles, 8 bits each
+#pragma unroll
+            for (int u = 0; u < ST_PER; ++u)
+                if (t0 + u < TT) k4 += 1u << (8 * tile_class(c[u], mean));
+            // a warp holds at most 128 tiles, so the 8-bit fields never carry
+            const uint32_t w4 = __reduce_add_sync(0xffffffffu, k4);
+            if (lane < 4 && ((w4 >> (8 * lane)) & 0xFFu)) atomicAdd_block(&s_cls[lane], (w4 >> (8 * lane)) & 0xFFu);
+        }
         unsigned long long x = s;
         for (int o = 1; o < 32; o <<= 1) {
             const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
@@ -632,43 +647,59 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(Frame F, uint32_t* __restri
         }
         __syncthreads();     // so, sc and wsum are reused by the next round
     }
-    // the blends' work order: the long tiles first, then the others, each
-    // class in tile order -- so the longest items do not start last, and
-    // neighbouring tiles still run together.  Only the order in which warps
-    // take tiles: no result depends on it.  (If K exceeds the capacity the
-    // blends do not run; the order is still a permutation.)
-    __shared__ uint32_t hsum[32];
-    const uint32_t n_long = s_long;
-    uint32_t long_before = 0;
+    // the blends' work order: the length classes longest first, each class in
+    // tile order -- so the longest items do not start last, and neighbouring
+    // tiles still run together.  Only the order in which warps take tiles: no
+    // result depends on it.  (If K exceeds the capacity the blends do not
+    // run; the order is still a permutation.)
+    __shared__ unsigned long long hsum[32];
+    uint32_t cbase[4];
+    {
+        uint32_t run = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            cbase[k] = run;      // tiles of the longer classes come first
+            run += s_cls[k];
+        }
+    }
     for (uint32_t base = 0; base < TT; base += ST_ROUND) {
         const uint32_t t0 = base + threadIdx.x * ST_PER;
-        bool hv[ST_PER];
-        uint32_t h = 0;
+        uint32_t cls[ST_PER];
+        unsigned long long h = 0;     // per-class counts of this thread's tiles, 16 bits each
 #pragma unroll
         for (int u = 0; u < ST_PER; ++u) {
-            hv[u] = t0 + u < TT && F.tile_count[t0 + u] > thr;
-            h += hv[u] ? 1u : 0u;
+            cls[u] = t0 + u < TT ? tile_class(F.tile_count[t0 + u], mean) : 4u;
+            if (cls[u] < 4u) h += 1ull << (16 * cls[u]);
         }
-        uint32_t x = h;
+        // a round holds at most 4096 tiles: the 16-bit fields never carry
+        unsigned long long x = h;
         for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
         if (lane == 31) hsum[wid] = x;
         __syncthreads();
-        uint32_t before = long_before + x - h, round_total = 0;
+        unsigned long long before = x - h, round_total = 0;
         for (int w2 = 0; w2 < 32; ++w2) {
-            const uint32_t y = hsum[w2];
+            const unsigned long long y = hsum[w2];
             if (w2 < wid) before += y;
             round_total += y;
         }
+        uint32_t pos[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) pos[k] = cbase[k] + (uint32_t)((before >> (16 * k)) & 0xFFFFu);
 #pragma unroll
         for (int u = 0; u < ST_PER; ++u) {
-            const uint32_t t = t0 + u;
-            if (t < TT) F.torder[hv[u] ? before : n_long + (t - before)] = t;
-            before += hv[u] ? 1u : 0u;
+            if (cls[u] < 4u) {
+                uint32_t q = 0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (cls[u] == (uint32_t)k) q = pos[k]++;
+                F.torder[q] = t0 + u;
+            }
         }
-        long_before += round_total;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) cbase[k] += (uint32_t)((round_total >> (16 * k)) & 0xFFFFu);
         __syncthreads();     // hsum is rewritten by the next round
     }
     if (threadIdx.x == 0) {
