@@ -279,8 +279,9 @@ __device__ __forceinline__ int find_view_rb(const ViewDev* views, uint32_t V, ui
 // order.  A group of 32 consecutive ranks is handled at once: the spans
 // [x0, x1) of the members that cover the row are laid end to end (prefix sum
 // of their widths) and processed 32 slots at a time, each slot finding its
-// member by binary search over the span starts; slots that fall on the
-// same tile are ordered by __match_any_sync, lower slot = lower rank.
+// member from the window's bitmask of span starts (a warp OR-reduction and
+// a population count); slots that fall on the same tile are ordered by
+// __match_any_sync, lower slot = lower rank.
 //   EMIT = false: ctr[x] counts the chunk's pairs of tile x.
 //   EMIT = true:  ctr[x] starts at the tile's offset plus the chunk's offset
 //                 and every slot writes its Gaussian at ctr[x] + (rank among
