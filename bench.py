@@ -85,6 +85,7 @@ def parse():
     p.add_argument("--train-steps", type=int, default=10)
     p.add_argument("--serve-seconds", type=float, default=2.0)
     p.add_argument("--serve-slots", type=int, default=6, help="server slots (batches in flight)")
+    p.add_argument("--serve-pairs", type=int, default=1 << 28, help="pair capacity of a server slot")
     p.add_argument("--no-city", action="store_true")
     p.add_argument("--frame", default=None, help="CAM:S -- time only that frame of the sweep (profiling)")
     p.add_argument("--inflight", type=int, default=8, help="frames in flight (renderers and streams)")
@@ -691,7 +692,7 @@ def serve_leg(args):
         return lat, len(vs) / (done - arr[0])
 
     def run_server(vs, arr, B=8, slots=args.serve_slots):
-        srv = SV.Server(ds, max_views_per_batch=B, n_slots=slots, use_graphs=True, pair_capacity=1 << 25,
+        srv = SV.Server(ds, max_views_per_batch=B, n_slots=slots, use_graphs=True, pair_capacity=args.serve_pairs,
                         max_pixels_per_batch=3840 * 2160 * 2, max_width=3840, max_height=2160)
         for v in warm:
             srv.wait(srv.submit(v, bufs[(v.width, v.height)][0]), 60.0)
@@ -729,8 +730,8 @@ def serve_leg(args):
 
     q = lambda a, p: round(float(np.percentile(a, p)) * 1e3, 3)
     res = {"workload": "object scene 2M Gaussians SH3 resident; Poisson arrivals; 512^2/720p/1080p/4K mixed; "
-                       "d in [1,50]; s_v log-uniform [1,32]; server: 8 views/batch, %d slots, CUDA graphs"
-                       % args.serve_slots,
+                       "d in [1,50]; s_v log-uniform [1,32]; server: 8 views/batch, %d slots of %d pairs, "
+                       "CUDA graphs" % (args.serve_slots, args.serve_pairs),
            "latency": "completion minus scheduled arrival"}
     for lam in (rate, 300.0):
         n = min(n_req, int(lam * args.serve_seconds))
