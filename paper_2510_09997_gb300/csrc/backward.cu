@@ -335,7 +335,6 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(Frame F, clod_scene S, c
     }
     __syncthreads();
     const int64_t n = S.n;
-    constexpr int deg = DEG;
     constexpr int K = (DEG + 1) * (DEG + 1);
     for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = base + threadIdx.x;
