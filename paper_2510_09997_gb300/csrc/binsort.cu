@@ -286,6 +286,8 @@ __device__ __forceinline__ int find_view_rb(const ViewDev* views, uint32_t V, ui
 //   EMIT = true:  ctr[x] starts at the tile's offset plus the chunk's offset
 //                 and every slot writes its Gaussian at ctr[x] + (rank among
 //                 the slots of the same tile).
+static_assert(ROWS_PER_BLOCK <= 8, "a band's row mask is 8 bits");
+static_assert(STAGE <= 8 * ROWS_PER_BLOCK * 32, "the compaction holds at most 8 entries' row masks per thread");
 template <bool EMIT>
 __global__ void __launch_bounds__(ROWS_PER_BLOCK * 32, 4) k_rows(Frame F, uint32_t* __restrict__ vals,
                                                              unsigned long long* __restrict__ keys)
@@ -295,6 +297,7 @@ __global__ void __launch_bounds__(ROWS_PER_BLOCK * 32, 4) k_rows(Frame F, uint32
     __shared__ uint32_t s_id[STAGE];
     __shared__ uint32_t s_key[STAGE];
     __shared__ uint16_t s_list[STAGE];
+    __shared__ uint8_t s_rmask[STAGE];      // per listed rectangle: the band's rows it covers
     __shared__ uint32_t s_wc[ROWS_PER_BLOCK];
     __shared__ uint16_t s_buf[ROWS_PER_BLOCK][64];
     const FrameHeader* hdr = F.hdr;
@@ -346,14 +349,18 @@ __global__ void __launch_bounds__(ROWS_PER_BLOCK * 32, 4) k_rows(Frame F, uint32
             const int per = (m + (int)blockDim.x - 1) / (int)blockDim.x;
             const int k0 = (int)threadIdx.x * per;
             uint32_t hm = 0u;
+            unsigned long long rmasks = 0ull;     // 8 bits per tested entry (per <= 8)
             int c = 0;
             for (int j = 0; j < per; ++j) {
                 const int k = k0 + j;
                 if (k < m) {
                     const uint2 rc = s_rect[k];
-                    if ((int)(rc.x >> 16) < band1 && (int)(rc.y >> 16) > band0) {
+                    const int y0 = (int)(rc.x >> 16), y1 = (int)(rc.y >> 16);
+                    if (y0 < band1 && y1 > band0) {
                         hm |= 1u << j;
                         ++c;
+                        const int lo = max(y0, band0) - band0, hi = min(y1, band1) - band0;
+                        rmasks |= (unsigned long long)(((1u << hi) - 1u) & ~((1u << lo) - 1u)) << (8 * j);
                     }
                 }
             }
@@ -371,7 +378,10 @@ __global__ void __launch_bounds__(ROWS_PER_BLOCK * 32, 4) k_rows(Frame F, uint32
                 nl += (int)s_wc[q];
             }
             for (int j = 0; hm; ++j, hm >>= 1)
-                if (hm & 1u) s_list[pos++] = (uint16_t)(k0 + j);
+                if (hm & 1u) {
+                    s_rmask[pos] = (uint8_t)(rmasks >> (8 * j));
+                    s_list[pos++] = (uint16_t)(k0 + j);
+                }
             __syncthreads();
         }
         if (!row_ok) continue;
@@ -385,8 +395,7 @@ __global__ void __launch_bounds__(ROWS_PER_BLOCK * 32, 4) k_rows(Frame F, uint32
                 bool hit = false;
                 if (g < nl) {
                     gi_l = s_list[g];
-                    const uint2 rc = s_rect[gi_l];
-                    hit = row >= (int)(rc.x >> 16) && row < (int)(rc.y >> 16);
+                    hit = (s_rmask[g] >> w) & 1u;
                 }
                 const unsigned hb = __ballot_sync(0xffffffffu, hit);
                 if (hit) s_buf[w][nb + __popc(hb & lt)] = (uint16_t)gi_l;
