@@ -52,20 +52,23 @@ __device__ __forceinline__ void blend_one(Px& q, float fpx, float fpy, const flo
     if (COUNT && con) ++n_con;
 }
 
-// The contributor/stop update of one pixel once its opacity al (< 0: skip)
-// is known: same operations as blend_one.
-__device__ __forceinline__ void blend_finish(Px& q, float al, const float4& c, float cb, uint32_t pos)
+// The contributor/stop update of one pixel whose opacity al passed the skip
+// tests (ok): same results as blend_one.  A stopping pixel keeps C, T and
+// last (blend_one adds 0 * colour, which leaves the non-negative sums as they
+// are).
+__device__ __forceinline__ void blend_finish(Px& q, bool ok, float al, const float4& c, float cb, uint32_t pos)
 {
-    if (al < 0.0f) return;
     const float tt = __fmul_rn(q.T, __fsub_rn(1.0f, al));
-    const bool con = !(tt < 1e-4f);
-    const float w = con ? __fmul_rn(al, q.T) : 0.0f;
-    q.C0 = __fmaf_rn(c.z, w, q.C0);
-    q.C1 = __fmaf_rn(c.w, w, q.C1);
-    q.C2 = __fmaf_rn(cb, w, q.C2);
-    q.T = con ? tt : q.T;
-    q.last = con ? pos : q.last;
-    q.done = !con;
+    const bool con = ok && !(tt < 1e-4f);
+    if (con) {
+        const float w = __fmul_rn(al, q.T);
+        q.C0 = __fmaf_rn(c.z, w, q.C0);
+        q.C1 = __fmaf_rn(c.w, w, q.C1);
+        q.C2 = __fmaf_rn(cb, w, q.C2);
+        q.T = tt;
+        q.last = pos;
+    }
+    q.done = q.done || (ok && !con);
 }
 
 // Both pixels of a thread against one Gaussian: the two powers, then (if
@@ -83,12 +86,12 @@ __device__ __forceinline__ void blend_pair(Px& q0, Px& q1, bool t0, bool t1, flo
     const bool r0 = t0 && p0 <= 0.0f && p0 >= pf;
     const bool r1 = t1 && p1 <= 0.0f && p1 >= pf;
     if (!(r0 || r1)) return;
-    const float g0 = exp_spec_core(r0 ? p0 : 0.0f), g1 = exp_spec_core(r1 ? p1 : 0.0f);
-    float a0 = fminf(0.99f, __fmul_rn(c.y, g0)), a1 = fminf(0.99f, __fmul_rn(c.y, g1));
-    a0 = (r0 && !(a0 < (1.0f / 255.0f))) ? a0 : -1.0f;
-    a1 = (r1 && !(a1 < (1.0f / 255.0f))) ? a1 : -1.0f;
-    blend_finish(q0, a0, c, cb, pos);
-    blend_finish(q1, a1, c, cb, pos);
+    // a pixel out of range evaluates its exponential too (its result is
+    // dropped: ok below is false)
+    const float g0 = exp_spec_core(p0), g1 = exp_spec_core(p1);
+    const float a0 = fminf(0.99f, __fmul_rn(c.y, g0)), a1 = fminf(0.99f, __fmul_rn(c.y, g1));
+    blend_finish(q0, r0 && !(a0 < (1.0f / 255.0f)), a0, c, cb, pos);
+    blend_finish(q1, r1 && !(a1 < (1.0f / 255.0f)), a1, c, cb, pos);
 }
 
 __device__ __forceinline__ void store_px(const ViewDev& W, const Px& q, int px, int py, float* image, float* Tout,
