@@ -92,10 +92,9 @@ struct BPx {
 __device__ __forceinline__ bool bwd_tail(BPx& q, bool r, float G, float dx, float dy, const float4& a,
                                          const float4& c, float cb, float (&g)[16])
 {
-    if (!r) return false;
     const float raw = __fmul_rn(c.y, G);
     const float al = fminf(0.99f, raw);
-    if (al < (1.0f / 255.0f)) return false;
+    if (!(r && !(al < (1.0f / 255.0f)))) return false;
     const float iom = __fdividef(1.0f, 1.0f - al);   // fast reciprocal: 1 - al >= 0.01
     const float Tb = q.T * iom;
     const float w = al * Tb;
@@ -136,7 +135,8 @@ __device__ __forceinline__ bool bwd_pair(BPx& q0, BPx& q1, bool t0, bool t1, flo
     const bool r0 = t0 && p0 <= 0.0f && p0 >= pf;
     const bool r1 = t1 && p1 <= 0.0f && p1 >= pf;
     if (!(r0 || r1)) return false;
-    const float G0 = exp_spec_core(r0 ? p0 : 0.0f), G1 = exp_spec_core(r1 ? p1 : 0.0f);
+    // a pixel out of range evaluates its exponential too (bwd_tail drops it)
+    const float G0 = exp_spec_core(p0), G1 = exp_spec_core(p1);
     bool any = bwd_tail(q0, r0, G0, dx, dy0, a, c, cb, g);
     any |= bwd_tail(q1, r1, G1, dx, dy1, a, c, cb, g);
     return any;
