@@ -179,13 +179,14 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_fwd(Frame F, const uint
             }
             unsigned m = __ballot_sync(0xffffffffu, hit);
             __syncwarp();
+            const uint32_t pos0 = b - start + 1u;     // list position (1-based) of entry 0 of the batch
             while (m) {
                 const int k = __ffs(m) - 1;
                 m &= m - 1;
                 const float4 a = s0[wid][k];
                 const float4 c = s1[wid][k];
                 const float4 e = s2[wid][k];
-                const uint32_t pos = b - start + (uint32_t)k + 1u;
+                const uint32_t pos = pos0 + (uint32_t)k;
                 if (COUNT) {
                     if (!q0.done) {
                         ++evals;
@@ -199,8 +200,7 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_fwd(Frame F, const uint
                     // per pixel, the power floor e.w decides (no box test: the
                     // warp's box test above already passed, and a pixel outside
                     // the reach box has a power below the floor)
-                    const bool t0 = !q0.done, t1 = !q1.done;
-                    if (t0 || t1) blend_pair(q0, q1, t0, t1, fpx, fpy0, fpy1, a, c, e.x, e.w, pos);
+                    blend_pair(q0, q1, !q0.done, !q1.done, fpx, fpy0, fpy1, a, c, e.x, e.w, pos);
                 }
             }
             __syncwarp();
