@@ -85,9 +85,10 @@ __device__ __forceinline__ void blend_pair(Px& q0, Px& q1, bool t0, bool t1, flo
     const float p1 = __fmaf_rn(ddx, __fmaf_rn(a.z, ddx, __fmul_rn(a.w, dy1)), __fmul_rn(__fmul_rn(c.x, dy1), dy1));
     const bool r0 = t0 && p0 <= 0.0f && p0 >= pf;
     const bool r1 = t1 && p1 <= 0.0f && p1 >= pf;
-    if (!(r0 || r1)) return;
-    // a pixel out of range evaluates its exponential too (its result is
-    // dropped: ok below is false)
+    // skipped by the whole warp when no pixel of its patch is in range (a
+    // warp-uniform branch); a pixel out of range evaluates its exponential too
+    // (its result is dropped: ok below is false)
+    if (!__any_sync(0xffffffffu, r0 || r1)) return;
     const float g0 = exp_spec_core(p0), g1 = exp_spec_core(p1);
     const float a0 = fminf(0.99f, __fmul_rn(c.y, g0)), a1 = fminf(0.99f, __fmul_rn(c.y, g1));
     blend_finish(q0, r0 && !(a0 < (1.0f / 255.0f)), a0, c, cb, pos);
