@@ -127,15 +127,15 @@ __device__ __forceinline__ bool bwd_pair(BPx& q0, BPx& q1, bool t0, bool t1, flo
 {
     t0 = t0 && pos <= q0.last;
     t1 = t1 && pos <= q1.last;
-    if (!(t0 || t1)) return false;
     const float dx = __fsub_rn(a.x, fpx);
     const float dy0 = __fsub_rn(a.y, q0.fy), dy1 = __fsub_rn(a.y, q1.fy);
     const float p0 = __fmaf_rn(dx, __fmaf_rn(a.z, dx, __fmul_rn(a.w, dy0)), __fmul_rn(__fmul_rn(c.x, dy0), dy0));
     const float p1 = __fmaf_rn(dx, __fmaf_rn(a.z, dx, __fmul_rn(a.w, dy1)), __fmul_rn(__fmul_rn(c.x, dy1), dy1));
     const bool r0 = t0 && p0 <= 0.0f && p0 >= pf;
     const bool r1 = t1 && p1 <= 0.0f && p1 >= pf;
-    if (!(r0 || r1)) return false;
-    // a pixel out of range evaluates its exponential too (bwd_tail drops it)
+    // skipped by the whole warp when no pixel is in range (warp-uniform); a
+    // pixel out of range evaluates its exponential too (bwd_tail drops it)
+    if (!__any_sync(0xffffffffu, r0 || r1)) return false;
     const float G0 = exp_spec_core(p0), G1 = exp_spec_core(p1);
     bool any = bwd_tail(q0, r0, G0, dx, dy0, a, c, cb, g);
     any |= bwd_tail(q1, r1, G1, dx, dy1, a, c, cb, g);
