@@ -92,12 +92,14 @@ struct BPx {
 __device__ __forceinline__ bool bwd_tail(BPx& q, bool r, float G, float dx, float dy, const float4& a,
                                          const float4& c, float cb, float (&g)[16])
 {
+    // without branches: a pixel that skips (ok false) adds zeros and keeps its
+    // state, which leaves every sum as it was (they are never -0)
     const float raw = __fmul_rn(c.y, G);
-    const float al = fminf(0.99f, raw);
-    if (!(r && !(al < (1.0f / 255.0f)))) return false;
-    const float iom = __fdividef(1.0f, 1.0f - al);   // fast reciprocal: 1 - al >= 0.01
+    const float al = fminf(0.99f, raw);     // <= 0.99 for any G, so 1 - al >= 0.01
+    const bool ok = r && !(al < (1.0f / 255.0f));
+    const float iom = __fdividef(1.0f, 1.0f - al);   // fast reciprocal
     const float Tb = q.T * iom;
-    const float w = al * Tb;
+    const float w = ok ? al * Tb : 0.0f;
     g[6] += w * q.d0;
     g[7] += w * q.d1;
     g[8] += w * q.d2;
@@ -105,17 +107,17 @@ __device__ __forceinline__ bool bwd_tail(BPx& q, bool r, float G, float dx, floa
     q.S0 += c.z * w;
     q.S1 += c.w * w;
     q.S2 += cb * w;
-    q.T = Tb;
-    if (!(raw > 0.99f)) {
-        g[5] += dal * G;
-        const float gp = dal * al;
-        g[0] += gp * (2.0f * a.z * dx + a.w * dy);
-        g[1] += gp * (a.w * dx + 2.0f * c.x * dy);
-        g[2] += gp * (-0.5f * dx * dx);
-        g[3] += gp * (-dx * dy);
-        g[4] += gp * (-0.5f * dy * dy);
-    }
-    return true;
+    q.T = ok ? Tb : q.T;
+    // alpha = alpha'' G below the 0.99 clamp: gradients through it
+    const bool lin = ok && !(raw > 0.99f);
+    g[5] += lin ? dal * G : 0.0f;
+    const float gp = lin ? dal * al : 0.0f;
+    g[0] += gp * (2.0f * a.z * dx + a.w * dy);
+    g[1] += gp * (a.w * dx + 2.0f * c.x * dy);
+    g[2] += gp * (-0.5f * dx * dx);
+    g[3] += gp * (-dx * dy);
+    g[4] += gp * (-0.5f * dy * dy);
+    return ok;
 }
 
 // Both pixels of a thread against one Gaussian (only if not past their last
