@@ -7,8 +7,8 @@
 //                    The skip decisions are re-taken with the forward's FP32
 //                    sequence, so exactly the forward's contributors are
 //                    visited.  Per-Gaussian 2D gradients (u, v, A, B, C,
-//                    alpha'', r, g, b) are warp-reduced and added with vector
-//                    atomics into a per-(view, Gaussian) buffer.
+//                    alpha'', r, g, b) are warp-reduced and added with 9
+//                    scalar atomics into a per-(view, Gaussian) buffer.
 //   k_preprocess_bwd per Gaussian, over the views: chain rule through the
 //                    conic (inverse 2D covariance), the EWA Jacobian, the
 //                    projection, Sigma = R S S^T R^T, the SH colour and the
@@ -44,35 +44,35 @@ __device__ __forceinline__ float warp_sum(float x)
     return x;
 }
 
-// Sum of 16 values over the 32 lanes of a warp, scattered: afterwards lane l
-// holds the total of value (l >> 1).  Each butterfly step keeps the half of
-// the values whose index bit matches the lane bit and sends the other half.
-__device__ __forceinline__ float warp_reduce16(float (&v)[16])
+// Sum of the 9 values v[0..8] over the 32 lanes of a warp: total 8 by a
+// full butterfly (returned in t8 on every lane), totals 0..7 scattered by
+// halving exchanges over lane bits 4, 3, 2 and full sums over bits 1, 0:
+// afterwards lane l holds the total of value l >> 2.
+__device__ __forceinline__ float warp_reduce9(float (&v)[16], float& t8)
 {
     const int lane = threadIdx.x & 31;
+    float x = v[8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    t8 = x;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
         const bool hi = lane & 16;
-        const float keep = hi ? v[8 + i] : v[i], give = hi ? v[i] : v[8 + i];
+        const float keep = hi ? v[4 + i] : v[i], give = hi ? v[i] : v[4 + i];
         v[i] = keep + __shfl_xor_sync(0xffffffffu, give, 16);
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < 2; ++i) {
         const bool hi = lane & 8;
-        const float keep = hi ? v[4 + i] : v[i], give = hi ? v[i] : v[4 + i];
+        const float keep = hi ? v[2 + i] : v[i], give = hi ? v[i] : v[2 + i];
         v[i] = keep + __shfl_xor_sync(0xffffffffu, give, 8);
     }
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const bool hi = lane & 4;
-        const float keep = hi ? v[2 + i] : v[i], give = hi ? v[i] : v[2 + i];
-        v[i] = keep + __shfl_xor_sync(0xffffffffu, give, 4);
-    }
     {
-        const bool hi = lane & 2;
+        const bool hi = lane & 4;
         const float keep = hi ? v[1] : v[0], give = hi ? v[0] : v[1];
-        v[0] = keep + __shfl_xor_sync(0xffffffffu, give, 2);
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, give, 4);
     }
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
     return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
@@ -237,8 +237,10 @@ __global__ void __launch_bounds__(BWD_THREADS, 8) k_blend_bwd(Frame F, const uin
                 // per pixel, the power floor e.w decides, as in the forward pass
                 const bool any = bwd_pair(q[0], q[1], true, true, fpx, a, c, e.x, e.w, pos, g);
                 if (__any_sync(0xffffffffu, any)) {
-                    const float tot = warp_reduce16(g);
-                    if (!(lane & 1) && lane < 18) atomicAdd(g2d + 12 * sg[wid][k] + (lane >> 1), tot);
+                    float t8;
+                    const float tot = warp_reduce9(g, t8);
+                    if (!(lane & 3)) atomicAdd(g2d + 12 * sg[wid][k] + (lane >> 2), tot);
+                    else if (lane == 1) atomicAdd(g2d + 12 * sg[wid][k] + 8, t8);
                 }
             }
             __syncwarp();
