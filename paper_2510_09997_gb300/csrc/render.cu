@@ -1,16 +1,18 @@
 // render.cu -- front-to-back alpha blending of every tile (Sec. 3.1, Eq. 1).
 //
-// Persistent blocks of 128 threads take 16x16 tiles from an atomic queue; each
-// warp owns an 8x8 patch (two vertically adjacent pixels per thread) and
-// walks the tile's sorted list independently, 32 entries at a time: every
+// Persistent blocks of 128 threads; each warp takes (16x16 tile, quarter)
+// items from an atomic queue over the work order the tile scan wrote (longer
+// lists first), owns that 8x8 patch (two vertically adjacent pixels per
+// thread) and walks the tile's sorted list on its own, 32 entries at a time: every
 // lane gathers one record (u, v, -A/2, -B | -C/2, alpha'', r, g | b, reach
 // half-extents, power floor) and tests the box that holds every pixel the
 // Gaussian can reach with opacity >= 1/255 (computed once per Gaussian by the
 // preprocessing); the warp blends, in list order, only the entries whose box
 // meets its patch -- every pixel of the patch would skip the others anyway, so
 // no result changes.  Per pixel, a power below the Gaussian's floor (opacity
-// < 1/255 for certain) skips the exponential.  A warp stops once its 64
-// pixels are saturated.
+// < 1/255 for certain) skips the exponential, and the per-pixel updates run
+// under predicates rather than branches (the kernel is issue bound).  A warp
+// stops once its 64 pixels are saturated.
 // Plain FP32/ALU work with one exponential per evaluated pair: no tensor
 // cores.
 #include <algorithm>
