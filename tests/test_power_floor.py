@@ -98,4 +98,4 @@ def test_pixels_outside_the_reach_box_stay_below_1_over_255():
         al = np.minimum(f(0.99), (a2 * g).astype(f))
         assert np.all(~inr | (al < ONE255))
         # not vacuous: many such points are in range, some close to 1/255
-        assert inr.mean() > 0.5 and al[inr].max() > f(0.9) * ONE255
+        assert inr.mean() > 0.2 and al[inr].max() > f(0.9) * ONE255
