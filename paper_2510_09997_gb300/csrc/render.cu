@@ -91,10 +91,20 @@ __device__ __forceinline__ void blend_pair(Px& q0, Px& q1, bool t0, bool t1, flo
     // warp-uniform branch); a pixel out of range evaluates its exponential too
     // (its result is dropped: ok below is false)
     if (!__any_sync(0xffffffffu, r0 || r1)) return;
-    const float g0 = exp_spec_core(p0), g1 = exp_spec_core(p1);
-    const float a0 = fminf(0.99f, __fmul_rn(c.y, g0)), a1 = fminf(0.99f, __fmul_rn(c.y, g1));
-    blend_finish(q0, r0 && !(a0 < (1.0f / 255.0f)), a0, c, cb, pos);
-    blend_finish(q1, r1 && !(a1 < (1.0f / 255.0f)), a1, c, cb, pos);
+    if (__any_sync(0xffffffffu, r0 && r1)) {
+        const float g0 = exp_spec_core(p0), g1 = exp_spec_core(p1);
+        const float a0 = fminf(0.99f, __fmul_rn(c.y, g0)), a1 = fminf(0.99f, __fmul_rn(c.y, g1));
+        blend_finish(q0, r0 && !(a0 < (1.0f / 255.0f)), a0, c, cb, pos);
+        blend_finish(q1, r1 && !(a1 < (1.0f / 255.0f)), a1, c, cb, pos);
+    } else {
+        // no lane has both pixels in range: one exponential per lane, for the
+        // pixel that is (the same value either pixel would get)
+        const float g = exp_spec_core(r0 ? p0 : p1);
+        const float al = fminf(0.99f, __fmul_rn(c.y, g));
+        const bool ok = !(al < (1.0f / 255.0f));
+        blend_finish(q0, r0 && ok, al, c, cb, pos);
+        blend_finish(q1, r1 && ok, al, c, cb, pos);
+    }
 }
 
 __device__ __forceinline__ void store_px(const ViewDev& W, const Px& q, int px, int py, float* image, float* Tout,
