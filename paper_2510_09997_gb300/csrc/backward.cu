@@ -138,9 +138,34 @@ __device__ __forceinline__ bool bwd_pair(BPx& q0, BPx& q1, bool t0, bool t1, flo
     // skipped by the whole warp when no pixel is in range (warp-uniform); a
     // pixel out of range evaluates its exponential too (bwd_tail drops it)
     if (!__any_sync(0xffffffffu, r0 || r1)) return false;
-    const float G0 = exp_spec_core(p0), G1 = exp_spec_core(p1);
-    bool any = bwd_tail(q0, r0, G0, dx, dy0, a, c, cb, g);
-    any |= bwd_tail(q1, r1, G1, dx, dy1, a, c, cb, g);
+    if (__any_sync(0xffffffffu, r0 && r1)) {
+        const float G0 = exp_spec_core(p0), G1 = exp_spec_core(p1);
+        bool any = bwd_tail(q0, r0, G0, dx, dy0, a, c, cb, g);
+        any |= bwd_tail(q1, r1, G1, dx, dy1, a, c, cb, g);
+        return any;
+    }
+    // no lane has both pixels in range: one exponential and one gradient tail
+    // per lane, on the pixel that is in range (the other pixel's tail would
+    // add zeros and keep its state); selects, no branches
+    const bool s1 = !r0;
+    BPx q;
+    q.T = s1 ? q1.T : q0.T;
+    q.d0 = s1 ? q1.d0 : q0.d0;
+    q.d1 = s1 ? q1.d1 : q0.d1;
+    q.d2 = s1 ? q1.d2 : q0.d2;
+    q.S0 = s1 ? q1.S0 : q0.S0;
+    q.S1 = s1 ? q1.S1 : q0.S1;
+    q.S2 = s1 ? q1.S2 : q0.S2;
+    const float G = exp_spec_core(s1 ? p1 : p0);
+    const bool any = bwd_tail(q, r0 || r1, G, dx, s1 ? dy1 : dy0, a, c, cb, g);
+    q0.T = s1 ? q0.T : q.T;
+    q0.S0 = s1 ? q0.S0 : q.S0;
+    q0.S1 = s1 ? q0.S1 : q.S1;
+    q0.S2 = s1 ? q0.S2 : q.S2;
+    q1.T = s1 ? q.T : q1.T;
+    q1.S0 = s1 ? q.S0 : q1.S0;
+    q1.S1 = s1 ? q.S1 : q1.S1;
+    q1.S2 = s1 ? q.S2 : q1.S2;
     return any;
 }
 
