@@ -194,3 +194,63 @@ def test_training_step_with_dssim(T):
         total = float(total)
         first = total if first is None else first
     assert total < first
+
+
+def test_lreg_descent_follows_oracle_counts(T):
+    """Gradient descent on L_reg alone (Sec. 3.3, Eq. 3-4) driven by the
+    library (mask counts from clod_preprocess, the straight-through scalar
+    from clod_lreg_grad, the chain rule to opacity and sigma_d in
+    clod_render_bwd) follows the same steps taken with the oracle's counts
+    and FP64 gradients: equal counts before the first update, counts within
+    a few Gaussians afterwards (updates computed in FP32 and FP64 may put a
+    Gaussian that sits on the threshold on either side), and the count falls
+    to the target s_v^-1.5 from above."""
+    import dataclasses
+
+    from oracle import grad64 as G
+    from paper_2510_09997_gb300 import clod as C
+    s_v, lr, w, h = 4.0, 1e3, 64, 64
+    sc0 = S.tiny_scene(n=3000, seed=5, sh_degree=0)
+    v = S.look_at((0.0, 0.0, 3.0), (0.0, 0.0, 0.0), w, h, up=(0.0, 1.0, 0.0), s_v=s_v)
+    L = C.lib()
+    nb = ctypes.c_size_t()
+    C.check("ws", L.clod_backward_workspace_size(sc0.n, 1, ctypes.byref(nb)))
+    s_arr = (ctypes.c_float * 1)(s_v)
+    w_arr = (ctypes.c_float * 1)(1.0)
+
+    def update(sc, g_op, g_dec):
+        a = sc.opacity.astype(np.float64)
+        logit = np.log(a / (1.0 - a)) - lr * g_op * a * (1.0 - a)
+        return dataclasses.replace(sc, opacity=(1.0 / (1.0 + np.exp(-logit))).astype(np.float32),
+                                   decay=(sc.decay.astype(np.float64) - lr * g_dec).astype(np.float32))
+
+    sg = so = sc0
+    counts_g, counts_o = [], []
+    for it in range(8):
+        ds = C.DeviceScene.from_scene(sg)
+        fr = C.render(ds, [v], want_keys=False)
+        dav = torch.zeros(1, dtype=torch.float32, device="cuda")
+        C.check("lreg", L.clod_lreg_grad(C._ptr(fr.counts), sg.n, 1, s_arr, w_arr, ctypes.c_float(1.0), None,
+                                         C._ptr(dav), None, None, None))
+        bws = torch.empty(nb.value, dtype=torch.uint8, device="cuda")
+        grads = [torch.zeros_like(t) for t in (ds.means, ds.scales, ds.quats, ds.opacity, ds.sh, ds.decay)]
+        C.check("bwd", L.clod_render_bwd(ctypes.byref(ds.c), C._ptr(fr.ws), C._ptr(fr.vals), C._ptr(fr.ranges),
+                                         C._ptr(fr.T_final), C._ptr(fr.n_contrib), C._ptr(torch.zeros_like(fr.image)),
+                                         None, C._ptr(dav), C._ptr(bws), bws.numel(), *[C._ptr(g) for g in grads],
+                                         None))
+        torch.cuda.synchronize()
+        counts_g.append(int(fr.counts[0, 0]))
+        sg = update(sg, grads[3].cpu().numpy().astype(np.float64), grads[5].cpu().numpy().astype(np.float64))
+        # the same step on the oracle
+        cnt = int(O.stage1(so, v)["mask"].sum())
+        counts_o.append(cnt)
+        g = OL.dlreg_dalpha_ste(s_v, OL.eta_actual(cnt, so.n), so.n)
+        if it == 0:
+            assert float(dav[0]) == pytest.approx(g, rel=1e-6)
+        gr = G.reference_gradients(so, [v], [np.zeros((3, h, w))], [np.full(so.n, g)])
+        so = update(so, gr["opacity"], gr["decay"])
+    assert counts_g[0] == counts_o[0]
+    assert max(abs(a - b) for a, b in zip(counts_g, counts_o)) <= 3
+    target = OL.eta_target(s_v) * sc0.n
+    assert counts_g[0] > 3 * target and all(b <= a for a, b in zip(counts_g, counts_g[1:]))
+    assert counts_g[-1] <= target + 0.01 * sc0.n
