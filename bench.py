@@ -86,6 +86,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-extras", action="store_true", help="skip the e2e/cpu_baseline/train/serving legs")
+    p.add_argument("--clocks-csv", default=None,
+                   help="keep the raw nvidia-smi samples of the timed region in this file (default: a temp file)")
     p.add_argument("--no-train", action="store_true")
     p.add_argument("--no-serve", action="store_true")
     p.add_argument("--train-steps", type=int, default=10)
@@ -116,14 +118,15 @@ def dist_setup(n):
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
-    def __init__(self, gpu_index):
+    def __init__(self, gpu_index, path=None):
+        import tempfile
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+        self.path = path or os.path.join(tempfile.gettempdir(), "clocks_bench_%d.csv" % os.getpid())
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            os.makedirs(os.path.dirname(os.path.abspath(self.path)), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + q,
                                           "--format=csv,noheader,nounits", "-lms", "100"],
@@ -242,7 +245,10 @@ def run_ours(args):
     fma = fma_peak(C)
     if world > 1:
         dist.barrier()
-    clocks = ClockSampler(local)
+    ck = args.clocks_csv
+    if ck and world > 1:
+        ck = "%s.rank%d" % (ck, rank)
+    clocks = ClockSampler(local, ck)
     torch.cuda.synchronize()
     # timed region 1 (the headline): the sweep with n_fl frames in flight
     t0 = torch.cuda.Event(enable_timing=True)
