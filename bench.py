@@ -352,7 +352,8 @@ def run_ours(args):
         "stage_hbm": stage_bw,
         "roofline": {"bound": "alu", "kernel": "k_blend_fwd", "achieved": round(blend_tflops, 3),
                      "peak": round(fp32_peak, 2), "unit": "TFLOP/s", "frac": round(blend_tflops / fp32_peak, 4),
-                     "traffic": blend_traffic(), "traffic_unit": "bytes per launch (ncu, mean over the sweep)",
+                     "traffic": None if args.frame else blend_traffic(),
+                     "traffic_unit": "bytes per launch (ncu, mean over the sweep)",
                      "flop_model": "9 per visited pair + 33 per exp + 9 per contributor",
                      "pairs_per_frame": {"visited": round(cnt3[0]), "exp": round(cnt3[1]), "contrib": round(cnt3[2])},
                      "peak_basis": ("measured: own FMA microbenchmark (clod_probe_fma), %.2f TFLOP/s; nominal %d SMs x "
