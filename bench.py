@@ -417,7 +417,7 @@ def e2e_leg(C, ds, Rs, views, args):
     streams = [torch.cuda.Stream() for _ in range(n_fl)]
     done = [torch.cuda.Event() for _ in range(n_fl)]
     used = [False] * n_fl
-    steps = min(args.steps, 256)
+    steps = args.steps
 
     def frame(k):
         i = k % n_fl
