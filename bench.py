@@ -404,34 +404,38 @@ def fma_peak(C, iters=20000, reps=5):
     return {"tflops": best, "iters": iters}
 
 
-def e2e_leg(C, ds, Rs, views, args):
+def e2e_leg(C, ds, Rs, views, args, host_ring=None):
     """Same frames through the C ABI with host buffers and len(Rs) frames in
     flight (one renderer and stream each): the frame header and view record
     (248 B) go host->device as launch parameters, and every image comes back
     to pinned host memory on its frame's stream, overlapping the other
-    frames; the host waits for each image before it reuses that buffer.
-    Wall-clock time of the whole loop."""
+    frames.  The pinned images form a ring of host_ring buffers (default
+    twice the frames in flight); the host waits for a buffer's previous image
+    before it reuses the buffer, so with a ring longer than the frames in
+    flight that wait is for an image that left long ago.  Wall-clock time of
+    the whole loop."""
     import torch
     n_fl = len(Rs)
-    hosts = [torch.empty(Rs[0].image.numel(), dtype=torch.float32, pin_memory=True) for _ in range(n_fl)]
+    n_h = host_ring or 2 * n_fl
+    hosts = [torch.empty(Rs[0].image.numel(), dtype=torch.float32, pin_memory=True) for _ in range(n_h)]
     streams = [torch.cuda.Stream() for _ in range(n_fl)]
-    done = [torch.cuda.Event() for _ in range(n_fl)]
-    used = [False] * n_fl
+    done = [torch.cuda.Event() for _ in range(n_h)]
+    used = [False] * n_h
     steps = args.steps
 
     def frame(k):
-        i = k % n_fl
-        if used[i]:
-            done[i].synchronize()             # the host has this buffer's previous image
+        i, h = k % n_fl, k % n_h
+        if used[h]:
+            done[h].synchronize()             # the host has this buffer's previous image
         rr = Rs[i]
         rr.set_views([views[k % len(views)]])
         rr.run(streams[i])
         with torch.cuda.stream(streams[i]):
-            hosts[i].copy_(rr.image, non_blocking=True)
-        done[i].record(streams[i])
-        used[i] = True
+            hosts[h].copy_(rr.image, non_blocking=True)
+        done[h].record(streams[i])
+        used[h] = True
 
-    for k in range(2 * n_fl):
+    for k in range(n_h):
         frame(k)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -445,7 +449,7 @@ def e2e_leg(C, ds, Rs, views, args):
     return {"value": round(steps / dt, 3), "unit": "frames/s", "h2d_bytes_per_step": 248,
             "d2h_bytes_per_step": int(Rs[0].image.numel() * 4), "steps": steps,
             "pipeline": "%d frames in flight (one stream each); each image copy follows its frame on that "
-                        "stream and overlaps the other frames" % n_fl}
+                        "stream and overlaps the other frames; %d pinned host images" % (n_fl, n_h)}
 
 
 def cpu_baseline(sc, views, budget_s=20.0):
