@@ -35,10 +35,10 @@ def real_sh_basis(dirs: np.ndarray, deg: int) -> np.ndarray:
     return np.stack(cols, axis=1)
 
 
-def render_brute(scene, view, sh_signs=None):
-    """FP64 image (3, H, W), transmittance and contributor counts."""
+def _project(scene, view):
+    """FP64 distances, Eq. 2 opacity and mask, projection, conic and 3-sigma
+    tile rectangles of every Gaussian; ``keep`` marks the ones rendered."""
     n = scene.means.shape[0]
-    deg = int(round(math.sqrt(scene.sh.shape[1]))) - 1
     vm = np.asarray(view.viewmat, np.float32).astype(np.float64).reshape(3, 4)
     R, t0 = vm[:, :3], vm[:, 3]
     c = np.asarray(view.campos, np.float32).astype(np.float64)
@@ -97,6 +97,31 @@ def render_brute(scene, view, sh_signs=None):
     y0 = np.floor((v - rad) / 16)
     y1 = np.floor((v + rad) / 16)
     keep &= ~((x1 < 0) | (x0 > TX - 1) | (y1 < 0) | (y0 > TY - 1))
+    return dict(keep=keep, u=u, v=v, tz=tz, conic=conic, a2=a2, x0=x0, x1=x1, y0=y0, y1=y1, mu=mu, c=c, d=d)
+
+
+def tile_lists_brute(scene, view):
+    """Per tile (row-major over the view's tile grid), the rendered Gaussians
+    whose 3-sigma rectangle covers the tile, nearest first (camera depth,
+    then index): each tile checked against every Gaussian."""
+    P = _project(scene, view)
+    TX, TY = (view.width + 15) // 16, (view.height + 15) // 16
+    ids = np.nonzero(P["keep"])[0]
+    out = []
+    for ty_ in range(TY):
+        for tx_ in range(TX):
+            cand = [i for i in ids if P["x0"][i] <= tx_ <= P["x1"][i] and P["y0"][i] <= ty_ <= P["y1"][i]]
+            out.append(sorted(cand, key=lambda i: (P["tz"][i], i)))
+    return out, P
+
+
+def render_brute(scene, view, sh_signs=None):
+    """FP64 image (3, H, W), transmittance and contributor counts."""
+    deg = int(round(math.sqrt(scene.sh.shape[1]))) - 1
+    W, H = view.width, view.height
+    P = _project(scene, view)
+    keep, u, v, tz, conic, a2 = (P[k] for k in ("keep", "u", "v", "tz", "conic", "a2"))
+    x0, x1, y0, y1, mu, c, d = (P[k] for k in ("x0", "x1", "y0", "y1", "mu", "c", "d"))
     dirs = (mu - c) / d[:, None]
     B = real_sh_basis(dirs, deg)
     rgb = np.maximum(np.einsum("nk,nkc->nc", B, scene.sh.astype(np.float64)) + 0.5, 0.0)

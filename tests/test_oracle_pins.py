@@ -376,6 +376,34 @@ def test_pairs_sort_and_ranges_against_numpy():
     assert (r[:, 1] - r[:, 0]).sum() == K
 
 
+def test_tile_lists_against_fp64_brute_force():
+    """Pair emission, sort and ranges together against a brute force written
+    without them: for every tile of two views (the second at a non-zero tile
+    base), the oracle's sorted list equals the rendered Gaussians whose FP64
+    3-sigma rectangle covers the tile, nearest first (FP64 camera depth, then
+    index), each tile checked against every Gaussian.  A transposed tile
+    index, a wrong view offset or a depth other than camera-space z each
+    break it."""
+    import brute64
+    sc = S.tiny_scene(n=3000, seed=23)
+    views = [S.tiny_view(1.0).replace(width=96, height=80, cx=48.0, cy=40.0),
+             S.look_at((2.0, -1.5, 1.0), (0, 0, 0), 72, 56, s_v=3.0)]
+    fr = O.frame(sc, views, with64=False)
+    vals = fr["vals"].astype(np.int64)
+    r = fr["ranges"].astype(np.int64)
+    assert fr["tile_base"][1] > 0
+    reordered = 0
+    for vi, v in enumerate(views):
+        lists, P = brute64.tile_lists_brute(sc, v)
+        base = fr["tile_base"][vi]
+        assert sum(len(x) for x in lists) > 3000 and max(len(x) for x in lists) > 100
+        for t, want in enumerate(lists):
+            got = [int(i) for i in vals[r[base + t, 0]:r[base + t, 1]]]
+            assert got == want, (vi, t)
+            reordered += got != sorted(got)       # depth order is not index order
+    assert reordered > 10
+
+
 # ---------------------------------------------------------------------------
 # Independent FP64 brute force and the FP64 autograd statement
 # ---------------------------------------------------------------------------
