@@ -6,7 +6,6 @@ from __future__ import annotations
 import ctypes
 from typing import Sequence
 
-import numpy as np
 import torch
 
 from . import abi
@@ -119,24 +118,3 @@ class RenderLoss(torch.autograd.Function):
         (grad,) = ctx.saved_tensors
         return grad * g, None, None
 
-
-def smoke_backward() -> None:
-    """Tiny forward + backward on cuda:0 checked against the FP64 oracle."""
-    from oracle import grad64 as G
-    from . import synth as S
-    sc = S.small_scene(n=150, seed=3, sh_degree=2)
-    v = S.look_at((0.4, -1.8, 1.2), (0, 0, 0), 40, 36, s_v=2.0, bg=(0.2, 0.1, 0.0))
-    ps = [torch.tensor(np.asarray(getattr(sc, k), np.float32), device="cuda", requires_grad=True)
-          for k in ("means", "scales", "quats", "opacity", "sh", "decay")]
-    imgs, alpha, _, _ = render(*ps, [v])
-    rng = np.random.default_rng(0)
-    gimg = rng.normal(size=(3, 36, 40)).astype(np.float32)
-    (imgs[0] * torch.tensor(gimg, device="cuda")).sum().backward()
-    ref = G.reference_gradients(sc, [v], [gimg])
-    for k, p in zip(("means", "scales", "quats", "opacity", "sh", "decay"), ps):
-        g = p.grad.detach().cpu().numpy().astype(np.float64)
-        r = ref[k]
-        den = max(np.linalg.norm(r), 1e-12)
-        rel = np.linalg.norm(g - r) / den
-        if rel > 1e-3:
-            raise AssertionError("smoke backward: %s relative error %.3g" % (k, rel))

@@ -60,8 +60,10 @@ def test_single_gaussian_and_degenerate_quaternion(C):
 
 @pytest.mark.parametrize("pile", [3000, 20000])
 def test_oversized_tiles(C, pile):
-    """Tiles whose lists exceed the in-shared-memory sort (2048) and the
-    chunk size (8192) of the large-tile kernel (merge passes)."""
+    """A pile of translucent Gaussians: tile lists longer than the 2048
+    rectangles the emission stages in shared memory at a time, and (with the
+    larger pile) longer than 8192 entries, so that one warp of the blend walks
+    hundreds of 32-entry batches of one list."""
     rng = np.random.default_rng(24)
     sc = S.tiny_scene(n=pile + 2000, seed=24)
     sc.means[:pile] = rng.normal(0.0, 0.02, size=(pile, 3)).astype(np.float32)
