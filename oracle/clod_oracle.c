@@ -700,3 +700,178 @@ int64_t oracle_render(int64_t n, const float* V, const uint8_t* survive, const f
     if (evaluated) *evaluated = evals;
     return total;
 }
+
+/* ======================================================================= */
+/* Stage II with FP64 decisions (Eq. 1 in real arithmetic)                 */
+/* ======================================================================= */
+/* Eq. 1 is stated on real numbers, so its three per-pixel decisions -- skip a
+ * Gaussian whose power is positive, skip an opacity below 1/255, stop before
+ * the transmittance falls below 1e-4 -- are decisions on real values.  This
+ * pass takes all three in FP64, on the FP64 records of oracle_stage1_f64,
+ * over the same candidates in the same order as oracle_render (Stage I's
+ * mask, tile rectangles and depth order: integer outcomes of Stage I).
+ *
+ * Near a threshold a rasterizer working in finite precision may take either
+ * outcome, so a decision whose FP64 quantity lies within a band of its
+ * threshold is flagged and both outcomes are followed to the end of the
+ * pixel.  The band is the relative tolerance `rel` plus a first-order bound
+ * on how far an FP32 evaluation of the same quantity can lie from its FP64
+ * value.  With dx = u - x, dy = v - y (pixel centre x, y), the differences
+ * du, dv, dA, dB, dC, da2 between the FP32 records (oracle_stage1) and the
+ * FP64 records, and U = 2^-24 (FP32 unit roundoff):
+ *   power p = -(A dx^2 + C dy^2)/2 - B dx dy
+ *     dp = |A dx + B dy| (du + U|dx|) + |C dy + B dx| (dv + U|dy|)
+ *        + (dA dx^2 + dC dy^2)/2 + dB |dx dy| + 8 U S,
+ *     S = (|A| dx^2 + |C| dy^2)/2 + |B dx dy|
+ *   opacity a = min(0.99, alpha'' e^p):  ra = dp + da2/alpha'' + 8 U
+ *   transmittance T' = T (1 - a):  rT' = rT + ra a/(1 - a) + 4 U, with rT = 0
+ *     before the first contributor (relative deviations)
+ * Flagged when |p| < dp, |a - 1/255| <= (rel + ra)/255 or
+ * |T' - 1e-4| <= (rel + rT') 1e-4.  dev scales dp, ra and the 4 U of rT'
+ * (1: the bound above; 0: the relative band rel alone).
+ *
+ * Every pixel yields the outcome of the FP64 decisions (the main path) and
+ * one outcome per followed flag, at most max_paths in all (<= 64); flags met
+ * once that many paths exist are counted, not followed.
+ *
+ * Outputs for the listed tiles (3 x H x W / H x W arrays, other pixels
+ * untouched): img64, T64, nc64 (main path), n_paths (outcomes followed),
+ * n_capped (flags not followed, saturating at 255).  The outcomes beyond the
+ * main path are appended to alt_pix (pixel y W + x), alt_val (r, g, b, T) and
+ * alt_nc up to alt_cap entries.  Returns the number of such outcomes, or -1
+ * on allocation failure. */
+typedef struct {
+    int64_t j;          /* candidate at which the path resumes */
+    int flip;           /* decision inverted at candidate j: 0 none, 1 power, 2 opacity, 3 stop */
+    double T, D0, D1, D2, rT;
+    uint32_t last;
+} path64_t;
+
+#define MAX_PATHS64 64
+
+int64_t oracle_render_f64dec(int64_t n, const float* V, const uint8_t* survive, const float* rec,
+                             const int32_t* rect, const double* rec64, const int32_t* tile_list, int64_t n_list,
+                             double rel, double dev, int max_paths, double* img64, double* T64, uint32_t* nc64,
+                             uint8_t* n_paths, uint8_t* n_capped, int64_t* alt_pix, double* alt_val,
+                             uint32_t* alt_nc, int64_t alt_cap)
+{
+    const int W = (int)V[OV_W], H = (int)V[OV_H];
+    const int TX = (W + TILE - 1) / TILE;
+    const double U = 5.9604644775390625e-08;    /* 2^-24 */
+    const double bg[3] = { V[OV_BG], V[OV_BG + 1], V[OV_BG + 2] };
+    if (max_paths < 1) max_paths = 1;
+    if (max_paths > MAX_PATHS64) max_paths = MAX_PATHS64;
+    cand_t* cand = (cand_t*)malloc(sizeof(cand_t) * (n > 0 ? n : 1));
+    if (!cand) return -1;
+    int64_t n_alt = 0;
+    path64_t stack[MAX_PATHS64];
+    for (int64_t li = 0; li < n_list; ++li) {
+        const int tile = tile_list[li];
+        const int tx = tile % TX, ty = tile / TX;
+        int64_t nc = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            if (!survive[i]) continue;
+            const int32_t* r = rect + 4 * i;
+            if (tx >= r[0] && tx < r[2] && ty >= r[1] && ty < r[3]) {
+                cand[nc].depth = f2u(rec[REC * i + 3]);
+                cand[nc].id = (uint32_t)i;
+                ++nc;
+            }
+        }
+        qsort(cand, (size_t)nc, sizeof(cand_t), cand_cmp);
+        for (int py = ty * TILE; py < ty * TILE + TILE && py < H; ++py)
+            for (int px = tx * TILE; px < tx * TILE + TILE && px < W; ++px) {
+                const double x = px + 0.5, y = py + 0.5;
+                const size_t pix = (size_t)py * W + px, plane = (size_t)W * H;
+                int created = 1, top = 0, capped = 0, first = 1;
+                stack[top++] = (path64_t){ 0, 0, 1.0, 0.0, 0.0, 0.0, 0.0, 0u };
+                while (top > 0) {
+                    path64_t P = stack[--top];
+                    const int64_t j0 = P.j;
+                    for (int64_t j = j0; j < nc; ++j) {
+                        /* decisions at or before P.flip at the resume point were
+                         * branched by the parent path: not flagged again */
+                        const int lock = (j == j0) ? P.flip : 0;
+                        const uint32_t g = cand[j].id;
+                        const double* Q = rec64 + REC64 * g;
+                        const float* R = rec + REC * g;
+                        const double dx = Q[0] - x, dy = Q[1] - y;
+                        const double A = Q[3], B = Q[4], C = Q[5];
+                        const double p = -0.5 * (A * dx * dx + C * dy * dy) - B * dx * dy;
+                        const double du = fabs((double)R[0] - Q[0]), dv = fabs((double)R[1] - Q[1]);
+                        const double dA = fabs(-2.0 * (double)R[4] - A), dB = fabs(-(double)R[5] - B);
+                        const double dC = fabs(-2.0 * (double)R[6] - C);
+                        const double S = 0.5 * (fabs(A) * dx * dx + fabs(C) * dy * dy) + fabs(B * dx * dy);
+                        const double dp = dev * (fabs(A * dx + B * dy) * (du + U * fabs(dx)) +
+                                                 fabs(C * dy + B * dx) * (dv + U * fabs(dy)) +
+                                                 0.5 * (dA * dx * dx + dC * dy * dy) + dB * fabs(dx * dy) + 8.0 * U * S);
+                        /* decision 1: a positive power is skipped */
+                        int skip = p > 0.0;
+                        if (lock == 1) skip = !skip;
+                        if (fabs(p) < dp && lock < 1) {
+                            if (created < max_paths) {
+                                stack[top++] = (path64_t){ j, 1, P.T, P.D0, P.D1, P.D2, P.rT, P.last };
+                                ++created;
+                            } else ++capped;
+                        }
+                        if (skip) continue;
+                        /* decision 2: an opacity below 1/255 is skipped */
+                        double a = Q[2] * exp(p);
+                        if (a > 0.99) a = 0.99;
+                        const double ra = dp + dev * (fabs((double)R[2] - Q[2]) / Q[2] + 8.0 * U);
+                        skip = a < 1.0 / 255.0;
+                        if (lock == 2) skip = !skip;
+                        if (fabs(a - 1.0 / 255.0) <= (rel + ra) / 255.0 && lock < 2) {
+                            if (created < max_paths) {
+                                stack[top++] = (path64_t){ j, 2, P.T, P.D0, P.D1, P.D2, P.rT, P.last };
+                                ++created;
+                            } else ++capped;
+                        }
+                        if (skip) continue;
+                        /* decision 3: stop before T' = T (1 - a) falls below 1e-4 */
+                        const double tt = P.T * (1.0 - a);
+                        const double rT = P.rT + ra * a / (1.0 - a) + dev * 4.0 * U;
+                        int stop = tt < 1e-4;
+                        if (lock == 3) stop = !stop;
+                        if (fabs(tt - 1e-4) <= (rel + rT) * 1e-4 && lock < 3) {
+                            if (created < max_paths) {
+                                stack[top++] = (path64_t){ j, 3, P.T, P.D0, P.D1, P.D2, P.rT, P.last };
+                                ++created;
+                            } else ++capped;
+                        }
+                        if (stop) break;
+                        const double wgt = a * P.T;
+                        P.D0 += Q[6] * wgt;
+                        P.D1 += Q[7] * wgt;
+                        P.D2 += Q[8] * wgt;
+                        P.T = tt;
+                        P.rT = rT;
+                        P.last = (uint32_t)(j + 1);
+                    }
+                    const double o0 = P.D0 + P.T * bg[0], o1 = P.D1 + P.T * bg[1], o2 = P.D2 + P.T * bg[2];
+                    if (first) {
+                        img64[pix] = o0;
+                        img64[plane + pix] = o1;
+                        img64[2 * plane + pix] = o2;
+                        T64[pix] = P.T;
+                        nc64[pix] = P.last;
+                        first = 0;
+                    } else {
+                        if (n_alt < alt_cap) {
+                            alt_pix[n_alt] = (int64_t)pix;
+                            alt_val[4 * n_alt] = o0;
+                            alt_val[4 * n_alt + 1] = o1;
+                            alt_val[4 * n_alt + 2] = o2;
+                            alt_val[4 * n_alt + 3] = P.T;
+                            alt_nc[n_alt] = P.last;
+                        }
+                        ++n_alt;
+                    }
+                }
+                n_paths[pix] = (uint8_t)created;
+                n_capped[pix] = (uint8_t)(capped > 255 ? 255 : capped);
+            }
+    }
+    free(cand);
+    return n_alt;
+}

@@ -42,30 +42,38 @@ def build(force: bool = False) -> str:
     return LIB
 
 
+def bind(L):
+    """Declare the argument types of the oracle's C functions on a loaded
+    library (the built oracle, or a test's modified copy of it)."""
+    P = ctypes.c_void_p
+    I64 = ctypes.c_int64
+    L.oracle_exp_spec.argtypes = [ctypes.c_float]
+    L.oracle_exp_spec.restype = ctypes.c_float
+    L.oracle_exp_spec_batch.argtypes = [P, P, I64]
+    L.oracle_exp_spec_monotone_violations.argtypes = [ctypes.c_float, ctypes.c_float, P]
+    L.oracle_exp_spec_monotone_violations.restype = I64
+    L.oracle_sh_basis.argtypes = [P, I64, ctypes.c_int, P]
+    L.oracle_stage1.argtypes = [I64, ctypes.c_int] + [P] * 7 + [P] * 10
+    L.oracle_stage1_f64.argtypes = [I64, ctypes.c_int] + [P] * 7 + [I64, P, P]
+    L.oracle_emit_pairs.argtypes = [I64, P, ctypes.c_uint32, P, P, P, P, P, I64]
+    L.oracle_emit_pairs.restype = I64
+    L.oracle_stable_sort.argtypes = [P, P, I64]
+    L.oracle_stable_sort.restype = ctypes.c_int
+    L.oracle_ranges.argtypes = [P, I64, I64, P]
+    L.oracle_render.argtypes = [I64, P, P, P, P, P, P, I64, P, P, P, P, P, P, P, I64, P]
+    L.oracle_render.restype = I64
+    L.oracle_render_f64dec.argtypes = ([I64, P, P, P, P, P, P, I64, ctypes.c_double, ctypes.c_double, ctypes.c_int]
+                                       + [P] * 8 + [I64])
+    L.oracle_render_f64dec.restype = I64
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
             build()
-            L = ctypes.CDLL(LIB)
-            P = ctypes.c_void_p
-            I64 = ctypes.c_int64
-            L.oracle_exp_spec.argtypes = [ctypes.c_float]
-            L.oracle_exp_spec.restype = ctypes.c_float
-            L.oracle_exp_spec_batch.argtypes = [P, P, I64]
-            L.oracle_exp_spec_monotone_violations.argtypes = [ctypes.c_float, ctypes.c_float, P]
-            L.oracle_exp_spec_monotone_violations.restype = I64
-            L.oracle_sh_basis.argtypes = [P, I64, ctypes.c_int, P]
-            L.oracle_stage1.argtypes = [I64, ctypes.c_int] + [P] * 7 + [P] * 10
-            L.oracle_stage1_f64.argtypes = [I64, ctypes.c_int] + [P] * 7 + [I64, P, P]
-            L.oracle_emit_pairs.argtypes = [I64, P, ctypes.c_uint32, P, P, P, P, P, I64]
-            L.oracle_emit_pairs.restype = I64
-            L.oracle_stable_sort.argtypes = [P, P, I64]
-            L.oracle_stable_sort.restype = ctypes.c_int
-            L.oracle_ranges.argtypes = [P, I64, I64, P]
-            L.oracle_render.argtypes = [I64, P, P, P, P, P, P, I64, P, P, P, P, P, P, P, I64, P]
-            L.oracle_render.restype = I64
-            _lib = L
+            _lib = bind(ctypes.CDLL(LIB))
     return _lib
 
 
@@ -221,11 +229,50 @@ def render(scene, view, s1, rec64=None, tiles: Optional[Sequence[int]] = None, c
     return out
 
 
+def render_f64dec(view, s1, rec64, tiles: Optional[Sequence[int]] = None, rel: float = 1e-5,
+                  max_paths: int = 16, dev: float = 1.0):
+    """Stage II with every per-pixel decision taken in FP64 (see
+    ``oracle_render_f64dec``).  Returns a dict with the main path's img (3,H,W)
+    f64, T, ncontrib; per pixel n_paths (outcomes followed) and n_capped
+    (flags beyond ``max_paths``); and the other outcomes as alt_pix (flat
+    pixel index), alt_val (r, g, b, T) and alt_nc.  Pixels outside ``tiles``
+    hold zeros.  ``dev`` scales the FP32 deviation bound in the bands (0: the
+    relative band ``rel`` alone)."""
+    n = s1["survive"].shape[0]
+    V = pack_view(view)
+    W, H = view.width, view.height
+    tx, ty = tiles_of(view)
+    tl = _c(np.arange(tx * ty) if tiles is None else np.asarray(tiles), np.int32)
+    img = np.zeros((3, H, W), np.float64)
+    T = np.zeros((H, W), np.float64)
+    nc = np.zeros((H, W), np.uint32)
+    npath = np.zeros((H, W), np.uint8)
+    ncap = np.zeros((H, W), np.uint8)
+    L = lib()
+    cap = 1 << 16
+    while True:
+        pix = np.zeros(cap, np.int64)
+        val = np.zeros((cap, 4), np.float64)
+        anc = np.zeros(cap, np.uint32)
+        got = L.oracle_render_f64dec(n, _p(V), _p(s1["survive"]), _p(s1["rec"]), _p(s1["rect"]), _p(rec64),
+                                     _p(tl), tl.size, float(rel), float(dev), int(max_paths), _p(img), _p(T), _p(nc),
+                                     _p(npath), _p(ncap), _p(pix), _p(val), _p(anc), cap)
+        if got < 0:
+            raise MemoryError("oracle render_f64dec")
+        if got <= cap:
+            break
+        cap = int(got)
+    return dict(img=img, T=T, ncontrib=nc, n_paths=npath, n_capped=ncap, alt_pix=pix[:got], alt_val=val[:got],
+                alt_nc=anc[:got])
+
+
 def frame(scene, views: Sequence, with64: bool = True, tiles: Optional[List[Optional[Sequence[int]]]] = None,
-          pairs: bool = True, contrib: bool = False):
+          pairs: bool = True, contrib: bool = False, dec64: bool = False):
     """Whole oracle pipeline over several views: Stage I per view, pairs with
     view-offset tile ids, stable sort and ranges over all views, Stage II per
-    view.  Returns a dict of per-view lists plus the global keys/vals/ranges."""
+    view (and, with ``dec64``, Stage II with FP64 decisions in each view's
+    ``img[v]["dec64"]``).  Returns a dict of per-view lists plus the global
+    keys/vals/ranges."""
     res = dict(s1=[], rec64=[], img=[], tile_base=[])
     base = 0
     all_k, all_v = [], []
@@ -241,6 +288,10 @@ def frame(scene, views: Sequence, with64: bool = True, tiles: Optional[List[Opti
             all_v.append(val)
         tl = None if tiles is None else tiles[vi]
         res["img"].append(render(scene, v, s1, r64, tl, contrib=contrib))
+        if dec64:
+            if r64 is None:
+                raise ValueError("FP64 decisions need the FP64 records (with64=True)")
+            res["img"][-1]["dec64"] = render_f64dec(v, s1, r64, tl)
         tx, ty = tiles_of(v)
         base += tx * ty
     res["n_tiles"] = base

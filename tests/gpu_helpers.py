@@ -5,6 +5,8 @@ import torch
 
 from oracle import oracle as O
 
+from branches import match_fp64_branches
+
 
 def u32(a):
     return np.ascontiguousarray(a).view(np.uint32)
@@ -55,7 +57,10 @@ def assert_stage1_equal(g, s1):
 
 def assert_image_matches(fr, v, ref, tiles=None, tol64=2e-4):
     """GPU image of view v equals the oracle's FP32 evaluation bit for bit and
-    lies within tol64 of the FP64 image (on the listed tiles, or all)."""
+    lies within tol64 of the FP64 image (on the listed tiles, or all).  With
+    the oracle's FP64-decision outcomes in ``ref["dec64"]``, every pixel also
+    lies within tol64 of one of them, with that outcome's contributor count;
+    the flagged pixel counts are printed."""
     img = fr.view_image(v).cpu().numpy()
     T = fr.view_T(v).cpu().numpy()
     nc = fr.view_ncontrib(v).cpu().numpy().view(np.uint32)
@@ -72,6 +77,10 @@ def assert_image_matches(fr, v, ref, tiles=None, tol64=2e-4):
     assert np.array_equal(u32(T[sel]), u32(ref["T32"][sel]))
     for c in range(3):
         assert np.array_equal(u32(img[c][sel]), u32(ref["img32"][c][sel])), c
+    if ref.get("dec64") is not None:
+        m = match_fp64_branches(img, T, nc, ref["dec64"], sel, tol64)
+        print("FP64 decisions, view %d: %s" % (v, m))
+        assert m["bad"] == 0 and m["nc_differs"] == 0, m
     if ref.get("img64") is not None:
         err = np.abs(img.astype(np.float64) - ref["img64"])[:, sel].max()
         assert err <= tol64, err
@@ -85,7 +94,7 @@ def run_and_compare(C, scene, views, tiles=None, with64=True):
     ds = C.DeviceScene.from_scene(scene)
     fr = C.render(ds, views)
     torch.cuda.synchronize()
-    ref = O.frame(scene, views, with64=with64, tiles=tiles)
+    ref = O.frame(scene, views, with64=with64, tiles=tiles, dec64=with64)
     g = frame_stage1(fr, scene.n)
     for v in range(len(views)):
         assert_stage1_equal(g[v], ref["s1"][v])

@@ -3,7 +3,9 @@
 Integer outputs (mask, tile rectangles, counts, sorted keys/values, ranges,
 contributor counts) are compared bit for bit; so are the FP32 records and the
 FP32 image, which follow the same operation sequence as the oracle's FP32
-evaluation.  The image must also lie within 2e-4 of the oracle's FP64 image.
+evaluation.  The image must also lie within 2e-4 of the oracle's FP64 image
+and, pixel by pixel, within 2e-4 of an outcome of the oracle's FP64
+decisions (with that outcome's contributor count).
 """
 import numpy as np
 import pytest

@@ -3,7 +3,8 @@ noise, SH degree 3), 8 views per launch at 3840x2160, s_v in {1, 4, 16, 64}.
 
 Every Stage I output of every view is compared with the oracle bit for bit;
 per view, sampled tiles (the longest lists and random ones) are compared bit
-for bit (image, T, contributor counts) and against the FP64 image, and the
+for bit (image, T, contributor counts), against the FP64 image and against
+the outcomes of the FP64 decisions, and the
 tile list lengths of all tiles against the oracle's rectangles.  The backward
 pass runs at full size and is checked for its structure (finite, zero
 wherever a Gaussian neither contributes nor receives an external gradient).
@@ -56,7 +57,9 @@ def test_city_8x4k_stage1_and_sampled_tiles(city):
         got = ranges[base:base + T, 1] - ranges[base:base + T, 0]
         assert np.array_equal(got, lens)
         tiles = list(np.argsort(lens)[-3:]) + list(rng.choice(T, 5, replace=False))
-        ref = O.render(sc, view, s1, O.stage1_f64(sc, view, s1), tiles=tiles)
+        r64 = O.stage1_f64(sc, view, s1)
+        ref = O.render(sc, view, s1, r64, tiles=tiles)
+        ref["dec64"] = O.render_f64dec(view, s1, r64, tiles)
         assert_image_matches(fr, v, ref, tiles)
         base += T
     assert culled[3] > culled[0]          # s_v = 64 culls more than s_v = 1
