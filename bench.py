@@ -31,10 +31,17 @@ N_CAMS = 64
 SCALES = (1.0, 2.0, 4.0, 8.0, 16.0)
 METRIC = "1080p frames/s at 1M Gaussians (forward, CLoD on)"
 WORKLOAD = "object scene 1M Gaussians SH3, 1920x1080, 64-camera orbit d=2..20, s_v in {1,2,4,8,16}"
-# FP32 FLOPs of the blend's arithmetic (FMA = 2): every visited (pixel,
-# Gaussian) pair: offset 2 + quadratic form 7 = 9; a pair whose power lies in
-# [-5.6, 0]: + exp_spec 31 (13 FMA, 2 subtractions, cap) + opacity 2 = 33; a
-# contributing pair: + transmittance 2 + weight 1 + colour 6 = 9.
+# The blend's roofline model: 15 FP32 operations (offset, quadratic form,
+# opacity, skip and stop tests, transmittance, weight, colour) and one
+# special-function exponential per visited (pixel, Gaussian) pair -- every pair
+# of a tile's list up to the pixel's stop, counted by the kernel's counting
+# variant -- against the FP32 FMA rate (an FMA counted as 2).
+FLOP_ALG = 15
+# Second, labelled figure: the FP32 FLOPs this build issues (FMA = 2), with
+# its software exponential: every visited pair: offset 2 + quadratic form 7
+# = 9; a pair whose power lies in [-5.6, 0]: + exp_spec 31 (13 FMA, 2
+# subtractions, cap) + opacity 2 = 33; a contributing pair: + transmittance 2
+# + weight 1 + colour 6 = 9.
 FLOP_VISIT, FLOP_EXP, FLOP_CONTRIB = 9, 33, 9
 # kernels per frame: k_frame_setup, k_dist_max, k_preprocess; 4 x (k_rs_hist,
 # k_rs_scatter); k_chunk_count, k_chunk_scan, k_scan_tiles, k_rows<emit>;
@@ -55,6 +62,18 @@ def frames_list(only=None):
         c, s = only.split(":")
         return [(int(c), float(s))]
     return [(c, s) for c in range(N_CAMS) for s in SCALES]
+
+
+def step_frames(frames, steps):
+    """The frames the timed steps render, in order: with K steps over the
+    F-frame sweep, step k takes frame floor(k F / K) when K <= F (every
+    camera range and scale sampled evenly: at K = 20 over the 320-frame
+    sweep, cameras 0, 3, ..., 60 with s_v cycling 1, 2, 4, 8, 16), else frame
+    k mod F."""
+    F = len(frames)
+    if steps <= F:
+        return [frames[(k * F) // steps] for k in range(steps)]
+    return [frames[k % F] for k in range(steps)]
 
 
 def shard_frames(frames, rank, world):
@@ -97,6 +116,8 @@ def parse():
     p.add_argument("--no-city", action="store_true")
     p.add_argument("--frame", default=None, help="CAM:S -- time only that frame of the sweep (profiling)")
     p.add_argument("--inflight", type=int, default=8, help="frames in flight (renderers and streams)")
+    p.add_argument("--exact-exp", action="store_true",
+                   help="blend with the reproducible software exponential (default: CLOD_FAST_EXP)")
     p.add_argument("--leg", default="all", choices=["all", "train", "serve", "city"],
                    help="train / serve: run only that leg and print its JSON object (for profiling)")
     return p.parse_args()
@@ -195,9 +216,12 @@ def run_ours(args):
     sc = S.object_scene(N_GAUSS)
     cams = S.orbit_cameras(N_CAMS, WIDTH, HEIGHT)
     allf = frames_list(args.frame)
-    # this rank's frames (replicas: rank r takes frames r, r+N, ...)
+    # this rank's frames (replicas: rank r takes frames r, r+N, ...), then
+    # the ones its steps render (spread over the whole shard)
     mine = shard_frames(allf, rank, world)
-    views = [cams[c].replace(s_v=s) for c, s in mine]
+    timed = step_frames(mine, args.steps)
+    fast_flag = 0 if args.exact_exp else S.FLAG_FAST_EXP
+    views = [cams[c].replace(s_v=s, flags=fast_flag) for c, s in timed]
     ds = C.DeviceScene.from_scene(sc)
 
     # pair capacity: the largest K over this rank's frames (one pre-pass)
@@ -266,6 +290,28 @@ def run_ours(args):
     elapsed = max_over_ranks(t0.elapsed_time(t1) / 1e3, device="cuda")
     for r_ in Rs:
         r_.check()   # every frame fitted the pair capacity (all used K <= kmax)
+    # the same in-flight sweep with the other exponential (the reproducible
+    # software one when the headline uses CLOD_FAST_EXP), for comparison
+    views_main = views
+    views = [v.replace(flags=v.flags ^ S.FLAG_FAST_EXP) for v in views_main]
+    pipelined(max(args.warmup, n_fl))
+    torch.cuda.synchronize()
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for s_ in streams:
+        s_.wait_event(a0)
+    pipelined(args.steps)
+    for s_ in streams:
+        e_ = torch.cuda.Event()
+        e_.record(s_)
+        stream.wait_event(e_)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    elapsed_other = max_over_ranks(a0.elapsed_time(a1) / 1e3, device="cuda")
+    for r_ in Rs:
+        r_.check()
+    views = views_main
     # timed region 2: the same frames one at a time on one stream, with events
     # around each stage (each kernel runs alone: the per-stage times and the
     # roofline come from here)
@@ -316,8 +362,8 @@ def run_ours(args):
     sort_bytes = 80 * n * len(n_surv) + 24 * n_surv.sum() + 4 * n_pairs.sum()
     radix_equiv = 152 * n_pairs.sum()       # 6-pass LSD sort of K (u64 key, u32 value) pairs
     cnt3 = evals.cpu().numpy().astype(np.float64) / args.steps
-    ev_per_frame = float(cnt3[0])
-    flop_per_frame = FLOP_VISIT * cnt3[0] + FLOP_EXP * cnt3[1] + FLOP_CONTRIB * cnt3[2]
+    flop_per_frame = FLOP_ALG * cnt3[0]
+    issued_per_frame = FLOP_VISIT * cnt3[0] + FLOP_EXP * cnt3[1] + FLOP_CONTRIB * cnt3[2]
 
     value = whole_job_rate(args.steps, world, elapsed)
     peaks = measured_peaks()
@@ -326,6 +372,7 @@ def run_ours(args):
     nominal = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12            # TFLOP/s at the sampled clock
     fp32_peak = fma["tflops"] if fma else nominal
     blend_tflops = flop_per_frame / (st_ms[2] / 1e3) / 1e12
+    blend_issued = issued_per_frame / (st_ms[2] / 1e3) / 1e12
     hbm = measured_peaks().get("hbm_gbs", 6772.2)
     T_pre = stage[:, 0].sum() / 1e3
     T_sort = stage[:, 1].sum() / 1e3
@@ -342,8 +389,20 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": round(elapsed * 1e3 / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_gaussians": N_GAUSS, "width": WIDTH, "height": HEIGHT,
-                   "frames_per_rank": len(views), "l2": "inputs larger than L2 (240 MB scene)",
+                   "blend_exponential": ("reproducible software exponential (FP32 specification)" if args.exact_exp
+                                         else "hardware base-2 unit (CLOD_FAST_EXP); images within 2e-4 of the "
+                                              "FP64-decision oracle, integer stages bit-exact"),
+                   "frames_timed_per_rank": len(views), "sweep_frames": len(allf),
+                   "timed_frames": ("step k of K renders frame floor(k F / K) of the rank's F-frame shard of the "
+                                    "sweep (camera-major, s_v minor)" if args.steps <= len(mine) else
+                                    "step k renders frame k mod F of the rank's F-frame shard"),
+                   "l2": "inputs larger than L2 (240 MB scene)",
                    "parallelism": "replicas" if world > 1 else "single", "frames_in_flight": n_fl},
+        ("fast_exp" if args.exact_exp else "exact_exp"): {
+            "value": round(whole_job_rate(args.steps, world, elapsed_other), 3), "unit": "frames/s",
+            "ms_per_step": round(elapsed_other * 1e3 / args.steps, 4),
+            "note": "the same frames in flight with the %s exponential" % ("hardware" if args.exact_exp else
+                                                                          "reproducible software")},
         "sequential": {"value": round(whole_job_rate(args.steps, world, elapsed_seq), 3), "unit": "frames/s",
                        "ms_per_step": round(elapsed_seq * 1e3 / args.steps, 4),
                        "note": "one frame at a time on one stream; stage_ms and roofline are from this pass"},
@@ -354,8 +413,11 @@ def run_ours(args):
                      "peak": round(fp32_peak, 2), "unit": "TFLOP/s", "frac": round(blend_tflops / fp32_peak, 4),
                      "traffic": None if args.frame else blend_traffic(),
                      "traffic_unit": "bytes per launch (ncu, mean over the sweep)",
-                     "flop_model": "9 per visited pair + 33 per exp + 9 per contributor",
+                     "flop_model": "15 FP32 ops + 1 MUFU per visited (pixel, Gaussian) pair (up to the pixel's stop)",
                      "pairs_per_frame": {"visited": round(cnt3[0]), "exp": round(cnt3[1]), "contrib": round(cnt3[2])},
+                     "issued": {"achieved": round(blend_issued, 3), "frac": round(blend_issued / fp32_peak, 4),
+                                "model": "FP32 FLOPs this build issues: 9 per visited pair + 33 per pair whose "
+                                         "power is in [-5.6, 0] (software exponential) + 9 per contributor"},
                      "peak_basis": ("measured: own FMA microbenchmark (clod_probe_fma), %.2f TFLOP/s; nominal %d SMs x "
                                     "128 lanes x 2 x %.0f MHz = %.2f" % (fp32_peak, n_sm, sm_mhz, nominal))
                      if fma else "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (sampled clock)" % (n_sm, sm_mhz)},
@@ -533,7 +595,9 @@ def train_leg(args):
     from paper_2510_09997_gb300 import synth as S
     from paper_2510_09997_gb300 import train as T
     sc = S.outdoor_scene(3_000_000)
-    cams = S.orbit_cameras(16, WIDTH, HEIGHT, d_min=9.0, d_max=16.0, elev_deg=25.0, seed=2)
+    fast = 0 if args.exact_exp else S.FLAG_FAST_EXP
+    cams = [c.replace(flags=c.flags | fast) for c in
+            S.orbit_cameras(16, WIDTH, HEIGHT, d_min=9.0, d_max=16.0, elev_deg=25.0, seed=2)]
     targets = [torch.tensor(S.target_image(HEIGHT, WIDTH, seed=k), device="cuda") for k in range(4)]
     model = T.GaussianModel(sc)
     step = T.TrainStep(model, s_max=16.0, lam_reg=1.0, seed=0, extent=5.0, dssim_weight=0.0)
@@ -585,7 +649,8 @@ def city_leg(args, steps=5):
     from paper_2510_09997_gb300 import clod as C
     from paper_2510_09997_gb300 import synth as S
     sc = S.city_scene()
-    views = S.city_views()
+    fast = 0 if args.exact_exp else S.FLAG_FAST_EXP
+    views = [v.replace(flags=v.flags | fast) for v in S.city_views()]
     V, n = len(views), sc.n
     ds = C.DeviceScene.from_scene(sc)
     probe = C.Renderer(ds, views, pair_capacity=1)
@@ -620,7 +685,8 @@ def city_leg(args, steps=5):
     C.clod_bin_sort(R.ws, R.cap, None, R.vals, R.ranges)
     C.clod_render_fwd(R.ws, R.vals, R.ranges, R.image, R.T, R.nc, evaluated=evals)
     e3 = evals.cpu().numpy().astype(np.float64)
-    flop = FLOP_VISIT * e3[0] + FLOP_EXP * e3[1] + FLOP_CONTRIB * e3[2]
+    flop = FLOP_ALG * e3[0]
+    issued = FLOP_VISIT * e3[0] + FLOP_EXP * e3[1] + FLOP_CONTRIB * e3[2]
     surv = cnt[:, 1].sum()
     # backward of the same launch (dL/dimage = a fixed random image gradient)
     nb = C.ctypes.c_size_t()
@@ -654,6 +720,7 @@ def city_leg(args, steps=5):
             "pairs": K, "sort_GB_s": round(sort_bytes / (stage[1] / 1e3) / 1e9, 1),
             "sort_radix_equivalent_GB_s": round(152 * K / (stage[1] / 1e3) / 1e9, 1),
             "blend_tflops": round(flop / (stage[2] / 1e3) / 1e12, 3),
+            "blend_issued_tflops": round(issued / (stage[2] / 1e3) / 1e12, 3),
             "backward_ms_per_launch": round(float(np.mean(bt)), 3)}
 
 
@@ -673,8 +740,11 @@ def serve_leg(args):
     ds = C.DeviceScene.from_scene(sc)
     rate = 2000.0
     n_req = int(rate * args.serve_seconds)
-    views = S.random_cameras(n_req, sizes, d_range=(1.0, 50.0), s_range=(1.0, 32.0), seed=4)
-    warm = S.random_cameras(32, sizes, d_range=(1.0, 50.0), s_range=(1.0, 32.0), seed=40)
+    fast = 0 if args.exact_exp else S.FLAG_FAST_EXP
+    views = [v.replace(flags=v.flags | fast) for v in
+             S.random_cameras(n_req, sizes, d_range=(1.0, 50.0), s_range=(1.0, 32.0), seed=4)]
+    warm = [v.replace(flags=v.flags | fast) for v in
+            S.random_cameras(32, sizes, d_range=(1.0, 50.0), s_range=(1.0, 32.0), seed=40)]
     arrivals = np.cumsum(np.random.default_rng(44).exponential(1.0 / rate, size=n_req))
     ring = 32
     bufs = {wh: [torch.empty((3, wh[1], wh[0]), device="cuda") for _ in range(ring)] for wh in sizes}
@@ -723,6 +793,7 @@ def serve_leg(args):
 
     def run_server(vs, arr, B=8, slots=args.serve_slots):
         srv = SV.Server(ds, max_views_per_batch=B, n_slots=slots, use_graphs=True, pair_capacity=args.serve_pairs,
+                        fast_exp=bool(fast),
                         max_pixels_per_batch=3840 * 2160 * 2, max_width=3840, max_height=2160)
         for v in warm:
             srv.wait(srv.submit(v, bufs[(v.width, v.height)][0]), 60.0)

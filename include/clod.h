@@ -49,6 +49,16 @@ typedef int32_t clod_status;
 /* view flags */
 #define CLOD_LOD_OFF       1u  /* plain 3DGS: alpha'' = alpha, no level-of-detail cull */
 #define CLOD_NO_NORMALIZE  2u  /* use d_i itself instead of d_i / max d (Sec. 3.2)    */
+/* The blends (forward and backward) evaluate each (pixel, Gaussian) opacity
+ * alpha'' exp(power) of Eq. 1 with the GPU's base-2 exponential unit instead of
+ * the reproducible software exponential.  Opacities then carry a relative
+ * error of a few 1e-7, the images stay within the FP32 rounding of the
+ * real-arithmetic blend, and integer stages (mask, rectangles, keys, ranges)
+ * are unchanged; but a skip or stop decision within that error of its
+ * threshold may fall differently, so the images and contributor counts are no
+ * longer bit-reproducible by another implementation of the FP32 sequence.
+ * All views of one frame must agree on this flag. */
+#define CLOD_FAST_EXP      4u
 
 typedef void* clod_stream;     /* cudaStream_t */
 
@@ -79,7 +89,7 @@ typedef struct clod_view {
     float tau;              /* base opacity threshold tau: M_i = alpha'' > tau s_v */
     float eps;              /* epsilon of Eq. 2                                 */
     float bg[3];            /* background colour                                */
-    uint32_t flags;         /* CLOD_LOD_OFF | CLOD_NO_NORMALIZE                 */
+    uint32_t flags;         /* CLOD_LOD_OFF | CLOD_NO_NORMALIZE | CLOD_FAST_EXP  */
     /* Region of a larger frame (regional level of detail, Sec. 4.4: one image
      * whose vertical bands are rendered at different s_v).  With
      * full_width > 0 the view is the width x height window at pixel
@@ -254,6 +264,14 @@ clod_status clod_render_loss(const float* image, const float* target, int32_t ch
                              int32_t width, float dssim_weight, float grad_scale, void* ws, size_t ws_bytes,
                              float* loss, float* dL_dimage, clod_stream stream);
 
+/* Per-view weights of one training step (Sec. 3.3, Eq. 5, averaged over the
+ * step's views): weight[v] = w_s(s_v[v]) / n_views with
+ * w_s(s) = (1 - 0.5 s / s_max)^2, s_max the largest scale the step's sampler
+ * draws.  Host arrays s_v (> 0) and weight, n_views in [1, 64]; s_max > 0.
+ * The weights scale the rendering loss (clod_render_loss grad_scale) and
+ * the objective of clod_lreg_grad. */
+clod_status clod_step_weights(const float* s_v, int32_t n_views, float s_max, float* weight);
+
 /* Point-count regulariser and total objective of the training step
  * (Sec. 3.3, Eq. 3-5), on the device, for n_views views of one step:
  *   eta_actual_v = counts[2v] / n (the mask counts of clod_preprocess),
@@ -318,7 +336,8 @@ typedef struct clod_server_cfg {
     uint64_t pair_capacity;        /* (view, tile, Gaussian) pairs per slot          */
     int32_t batch_window_us;       /* wait up to this long for a fuller batch (0: no) */
     int32_t max_width, max_height; /* largest view accepted                          */
-    int32_t reserved;
+    int32_t fast_exp;              /* 1: every batch blends with CLOD_FAST_EXP's
+                                      exponential (the requests' own flag is ignored) */
 } clod_server_cfg;
 
 typedef struct clod_req_stats {

@@ -723,7 +723,9 @@ int64_t oracle_render(int64_t n, const float* V, const uint8_t* survive, const f
  *     dp = |A dx + B dy| (du + U|dx|) + |C dy + B dx| (dv + U|dy|)
  *        + (dA dx^2 + dC dy^2)/2 + dB |dx dy| + 8 U S,
  *     S = (|A| dx^2 + |C| dy^2)/2 + |B dx dy|
- *   opacity a = min(0.99, alpha'' e^p):  ra = dp + da2/alpha'' + 8 U
+ *   opacity a = min(0.99, alpha'' e^p):  ra = dp + da2/alpha'' + 16 U, the
+ *     16 U for the FP32 exponential (a few ulp: a software polynomial or a
+ *     hardware base-2 unit after the rounding of p log2 e) and the product
  *   transmittance T' = T (1 - a):  rT' = rT + ra a/(1 - a) + 4 U, with rT = 0
  *     before the first contributor (relative deviations)
  * Flagged when |p| < dp, |a - 1/255| <= (rel + ra)/255 or
@@ -818,7 +820,7 @@ int64_t oracle_render_f64dec(int64_t n, const float* V, const uint8_t* survive, 
                         /* decision 2: an opacity below 1/255 is skipped */
                         double a = Q[2] * exp(p);
                         if (a > 0.99) a = 0.99;
-                        const double ra = dp + dev * (fabs((double)R[2] - Q[2]) / Q[2] + 8.0 * U);
+                        const double ra = dp + dev * (fabs((double)R[2] - Q[2]) / Q[2] + 16.0 * U);
                         skip = a < 1.0 / 255.0;
                         if (lock == 2) skip = !skip;
                         if (fabs(a - 1.0 / 255.0) <= (rel + ra) / 255.0 && lock < 2) {

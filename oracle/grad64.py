@@ -181,3 +181,46 @@ def reference_gradients(scene, views: Sequence, dL_dimage: Sequence[np.ndarray],
     total.backward()
     return {k: (t.grad.numpy().copy() if t.grad is not None else np.zeros(tuple(t.shape)))
             for k, t in P.items()}
+
+
+def frozen_on_tiles(scene, view, tiles, s1=None):
+    """Frozen decisions of one view with the contributor lists of the listed
+    tiles only (the other pixels get no contributors), and its Stage I."""
+    s1 = O.stage1(scene, view) if s1 is None else s1
+    img = O.render(scene, view, s1, None, tiles=tiles, contrib=True)
+    return dict(argmax=int(s1["argmax"][0]), survive=s1["survive"].astype(bool),
+                contrib_pix=img["contrib_pix"], contrib_gid=img["contrib_gid"]), s1
+
+
+def reference_gradients_sparse(scene, views: Sequence, frozen: Sequence, dL_dimage: Sequence[np.ndarray],
+                               dL_dalpha: Optional[Sequence[Optional[np.ndarray]]] = None):
+    """reference_gradients for a loss whose image gradient is non-zero only
+    on pixels that have contributors in ``frozen`` and whose alpha''
+    gradient is non-zero only on a few Gaussians.  Every other Gaussian's
+    gradient is exactly zero, so the same FP64 statement is evaluated on the
+    sub-scene of the contributors, the Gaussians with an alpha'' gradient and
+    each view's farthest in-view Gaussian (which carries d_max), and the
+    result is scattered back into full-size arrays."""
+    n = scene.n
+    keep = np.zeros(n, bool)
+    for vi, fr in enumerate(frozen):
+        keep[np.asarray(fr["contrib_gid"], np.int64)] = True
+        if fr["argmax"] >= 0:
+            keep[fr["argmax"]] = True
+        if dL_dalpha is not None and dL_dalpha[vi] is not None:
+            keep[np.nonzero(np.asarray(dL_dalpha[vi]))[0]] = True
+    idx = np.nonzero(keep)[0]
+    new = np.full(n, -1, np.int64)
+    new[idx] = np.arange(idx.size)
+    sub = scene.subset(idx)
+    fsub = [dict(argmax=int(new[fr["argmax"]]) if fr["argmax"] >= 0 else -1, survive=fr["survive"][idx],
+                 contrib_pix=fr["contrib_pix"], contrib_gid=new[np.asarray(fr["contrib_gid"], np.int64)])
+            for fr in frozen]
+    da = None if dL_dalpha is None else [None if a is None else np.asarray(a)[idx] for a in dL_dalpha]
+    r = reference_gradients(sub, views, dL_dimage, da, frozen=fsub)
+    out = {}
+    for k, g in r.items():
+        full = np.zeros((n,) + g.shape[1:], np.float64)
+        full[idx] = g
+        out[k] = full
+    return out

@@ -17,6 +17,7 @@ CLOD_ERR_NAN = 7
 
 CLOD_LOD_OFF = 1
 CLOD_NO_NORMALIZE = 2
+CLOD_FAST_EXP = 4
 
 STATUS_NAMES = {0: "CLOD_OK", 1: "CLOD_ERR_ARG", 2: "CLOD_ERR_CAPACITY", 3: "CLOD_ERR_CUDA",
                 4: "CLOD_ERR_TIMEOUT", 5: "CLOD_ERR_QUEUE_FULL", 6: "CLOD_ERR_NOT_READY", 7: "CLOD_ERR_NAN"}
@@ -47,7 +48,7 @@ class clod_server_cfg(ctypes.Structure):
                 ("queue_capacity", ctypes.c_int32), ("use_graphs", ctypes.c_int32),
                 ("max_pixels_per_batch", ctypes.c_uint64), ("pair_capacity", ctypes.c_uint64),
                 ("batch_window_us", ctypes.c_int32), ("max_width", ctypes.c_int32),
-                ("max_height", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("max_height", ctypes.c_int32), ("fast_exp", ctypes.c_int32)]
 
 
 class clod_adam_cfg(ctypes.Structure):
@@ -78,6 +79,7 @@ SIGNATURES = {
     "clod_render_loss_workspace_size": ([ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P], c_status),
     "clod_render_loss": ([P, P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, ctypes.c_float, P,
                           ctypes.c_size_t, P, P, P], c_status),
+    "clod_step_weights": ([P, ctypes.c_int32, ctypes.c_float, P], c_status),
     "clod_lreg_grad": ([P, ctypes.c_int64, ctypes.c_int32, P, P, ctypes.c_float, P, P, P, P, P], c_status),
     "clod_adam_state_size": ([ctypes.c_int64, ctypes.c_int32, P], c_status),
     "clod_adam_step": ([P, ctypes.c_int64, ctypes.c_int32, P, P, P, P, P, P, P], c_status),

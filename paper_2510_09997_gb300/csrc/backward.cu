@@ -123,7 +123,8 @@ __device__ __forceinline__ bool bwd_tail(BPx& q, bool r, float G, float dx, floa
 // Both pixels of a thread against one Gaussian (only if not past their last
 // contributor), the two exponentials side by side.  Powers below the
 // Gaussian's floor pf (>= -5.6) give opacity < 1/255, skipped as in the
-// forward pass.
+// forward pass (FAST: with the exponential of CLOD_FAST_EXP, as the forward).
+template <bool FAST>
 __device__ __forceinline__ bool bwd_pair(BPx& q0, BPx& q1, bool t0, bool t1, float fpx, const float4& a,
                                          const float4& c, float cb, float pf, uint32_t pos, float (&g)[16])
 {
@@ -139,7 +140,7 @@ __device__ __forceinline__ bool bwd_pair(BPx& q0, BPx& q1, bool t0, bool t1, flo
     // pixel out of range evaluates its exponential too (bwd_tail drops it)
     if (!__any_sync(0xffffffffu, r0 || r1)) return false;
     if (__any_sync(0xffffffffu, r0 && r1)) {
-        const float G0 = exp_spec_core(p0), G1 = exp_spec_core(p1);
+        const float G0 = blend_exp<FAST>(p0), G1 = blend_exp<FAST>(p1);
         bool any = bwd_tail(q0, r0, G0, dx, dy0, a, c, cb, g);
         any |= bwd_tail(q1, r1, G1, dx, dy1, a, c, cb, g);
         return any;
@@ -156,7 +157,7 @@ __device__ __forceinline__ bool bwd_pair(BPx& q0, BPx& q1, bool t0, bool t1, flo
     q.S0 = s1 ? q1.S0 : q0.S0;
     q.S1 = s1 ? q1.S1 : q0.S1;
     q.S2 = s1 ? q1.S2 : q0.S2;
-    const float G = exp_spec_core(s1 ? p1 : p0);
+    const float G = blend_exp<FAST>(s1 ? p1 : p0);
     const bool any = bwd_tail(q, r0 || r1, G, dx, s1 ? dy1 : dy0, a, c, cb, g);
     q0.T = s1 ? q0.T : q.T;
     q0.S0 = s1 ? q0.S0 : q.S0;
@@ -171,6 +172,7 @@ __device__ __forceinline__ bool bwd_pair(BPx& q0, BPx& q1, bool t0, bool t1, flo
 
 constexpr int BWD_THREADS = 128;   // 4 warps per tile, 8x8 pixels per warp, 2 per thread
 
+template <bool FAST>
 __global__ void __launch_bounds__(BWD_THREADS, 8) k_blend_bwd(Frame F, const uint32_t* __restrict__ vals,
                                                            const uint32_t* __restrict__ ranges,
                                                            const float* __restrict__ Tfin,
@@ -260,7 +262,7 @@ __global__ void __launch_bounds__(BWD_THREADS, 8) k_blend_bwd(Frame F, const uin
 #pragma unroll
                 for (int i = 0; i < 16; ++i) g[i] = 0.0f;
                 // per pixel, the power floor e.w decides, as in the forward pass
-                const bool any = bwd_pair(q[0], q[1], true, true, fpx, a, c, e.x, e.w, pos, g);
+                const bool any = bwd_pair<FAST>(q[0], q[1], true, true, fpx, a, c, e.x, e.w, pos, g);
                 if (__any_sync(0xffffffffu, any)) {
                     float t8;
                     const float tot = warp_reduce9(g, t8);
@@ -653,7 +655,7 @@ static int g_bwd_blocks_per_sm = 0;
 cudaError_t backward_setup()
 {
     int b = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_blend_bwd, BWD_THREADS, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_blend_bwd<false>, BWD_THREADS, 0);
     if (e != cudaSuccess) return e;
     g_bwd_blocks_per_sm = b > 0 ? b : 1;
     return cudaSuccess;
@@ -662,7 +664,7 @@ cudaError_t backward_setup()
 void launch_backward(const Frame& F, const clod_scene& S, uint32_t V, const uint32_t* vals, const uint32_t* ranges,
                      const float* Tfin, const uint32_t* ncon, const float* dimg, const float* g_alpha_ext,
                      const float* g_alpha_view, void* bwd_ws, float* dmeans, float* dscales, float* dquats, float* dopacity, float* dsh,
-                     float* ddecay, int n_sm, cudaStream_t st)
+                     float* ddecay, int n_sm, cudaStream_t st, bool fast)
 {
     const BwdLayout L = bwd_layout((uint64_t)S.n, V);
     char* b = static_cast<char*>(bwd_ws);
@@ -670,8 +672,12 @@ void launch_backward(const Frame& F, const clod_scene& S, uint32_t V, const uint
     float* dmg = reinterpret_cast<float*>(b + L.dmax_grad);
     cudaMemsetAsync(bwd_ws, 0, L.total, st);
     cudaMemsetAsync(&F.hdr->work[1], 0, sizeof(uint32_t), st);
-    k_blend_bwd<<<n_sm * std::max(1, g_bwd_blocks_per_sm), BWD_THREADS, 0, st>>>(F, vals, ranges, Tfin, ncon, dimg,
-                                                                                reinterpret_cast<float*>(g2d));
+    if (fast)
+        k_blend_bwd<true><<<n_sm * std::max(1, g_bwd_blocks_per_sm), BWD_THREADS, 0, st>>>(
+            F, vals, ranges, Tfin, ncon, dimg, reinterpret_cast<float*>(g2d));
+    else
+        k_blend_bwd<false><<<n_sm * std::max(1, g_bwd_blocks_per_sm), BWD_THREADS, 0, st>>>(
+            F, vals, ranges, Tfin, ncon, dimg, reinterpret_cast<float*>(g2d));
     ParamGrads P{dmeans, dscales, dquats, dopacity, dsh, ddecay};
     int blocks = static_cast<int>(std::min<int64_t>((S.n + 127) / 128, (int64_t)n_sm * 16));
     if (blocks < 1) blocks = 1;

@@ -19,14 +19,14 @@ void launch_preprocess(const Frame& F, const clod_scene& S, uint32_t V, uint8_t*
 void launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long long cap, uint64_t* keys, uint32_t* vals,
                      uint32_t* ranges, cudaStream_t st);
 void launch_blend_fwd(const Frame& F, const uint32_t* vals, const uint32_t* ranges, float* image, float* Tout,
-                      uint32_t* ncout, unsigned long long* evaluated, int n_sm, cudaStream_t st);
+                      uint32_t* ncout, unsigned long long* evaluated, int n_sm, cudaStream_t st, bool fast);
 cudaError_t bin_sort_setup();
 cudaError_t render_setup();
 cudaError_t backward_setup();
 void launch_backward(const Frame& F, const clod_scene& S, uint32_t V, const uint32_t* vals, const uint32_t* ranges,
                      const float* Tfin, const uint32_t* ncon, const float* dimg, const float* g_alpha_ext,
                      const float* g_alpha_view, void* bwd_ws, float* dmeans, float* dscales, float* dquats, float* dopacity, float* dsh,
-                     float* ddecay, int n_sm, cudaStream_t st);
+                     float* ddecay, int n_sm, cudaStream_t st, bool fast);
 size_t backward_ws_bytes(uint64_t n, uint32_t V);
 void launch_l1(const float* img, const float* tgt, int64_t count, float scale, float* loss, float* grad, int n_sm,
                cudaStream_t st);
@@ -239,6 +239,9 @@ static clod_status check_views(const clod_view* views, int32_t V, uint64_t n, Vi
         px += (uint64_t)w.width * w.height;
     }
     if (tt > 0x0FFFFFFFull) return fail(CLOD_ERR_ARG, "too many tiles (%llu)", (unsigned long long)tt);
+    for (int v = 1; v < V; ++v)
+        if ((views[v].flags ^ views[0].flags) & CLOD_FAST_EXP)
+            return fail(CLOD_ERR_ARG, "views 0 and %d disagree on CLOD_FAST_EXP (one frame, one exponential)", v);
     G->TT = static_cast<uint32_t>(tt);
     const uint32_t CH = n_chunks_for(n);
     uint64_t rb = 0;
@@ -371,7 +374,8 @@ clod_status clod_preprocess(const clod_scene* scene, const clod_view* views, int
     const uint32_t TT = G.TT;
     if (!ws) return fail(CLOD_ERR_ARG, "ws is NULL");
     if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(CLOD_ERR_ARG, "ws must be 256-byte aligned");
-    const FrameLayout L = frame_layout((uint64_t)scene->n, (uint32_t)n_views, TT, G.rb_total, G.max_tx, G.diff_max);
+    FrameLayout L = frame_layout((uint64_t)scene->n, (uint32_t)n_views, TT, G.rb_total, G.max_tx, G.diff_max);
+    L.fast_exp = (views[0].flags & CLOD_FAST_EXP) ? 1u : 0u;
     if (ws_bytes < L.total)
         return fail(CLOD_ERR_CAPACITY, "frame workspace needs %zu bytes, got %zu", L.total, ws_bytes);
     int n_sm = 0;
@@ -434,7 +438,8 @@ static clod_status render_common(const void* ws, const uint32_t* vals, const uin
     clod_status s = device_ready(&n_sm);
     if (s) return s;
     const Frame F = frame_ptrs(const_cast<void*>(ws), L);
-    launch_blend_fwd(F, vals, ranges, image, T_final, n_contrib, evaluated, n_sm, static_cast<cudaStream_t>(stream));
+    launch_blend_fwd(F, vals, ranges, image, T_final, n_contrib, evaluated, n_sm, static_cast<cudaStream_t>(stream),
+                     L.fast_exp != 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "clod_render_fwd launch");
     return CLOD_OK;
@@ -505,7 +510,7 @@ clod_status clod_render_bwd(const clod_scene* scene, const void* ws, const uint3
     const Frame F = frame_ptrs(const_cast<void*>(ws), L);
     launch_backward(F, *scene, L.n_views, vals, ranges, T_final, n_contrib, dL_dimage, dL_dalpha_eff, dL_dalpha_view,
                     bwd_ws, dmeans,
-                    dscales, dquats, dopacity, dsh, ddecay, n_sm, static_cast<cudaStream_t>(stream));
+                    dscales, dquats, dopacity, dsh, ddecay, n_sm, static_cast<cudaStream_t>(stream), L.fast_exp != 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "clod_render_bwd launch");
     return CLOD_OK;

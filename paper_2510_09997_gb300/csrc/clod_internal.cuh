@@ -80,6 +80,7 @@ struct FrameLayout {
     size_t header, views, dmax_key, n_surv, rec0, rec1, rec2, depth, rect, tile_count, tile_offset, torder,
         key0, val0, key1, val1, srect, rs_hist, cnt, sel, sel_hist, total;
     uint32_t total_tiles, n_views, n_chunks, n_rs_blocks, rb_total, max_tx;
+    uint32_t fast_exp;      // host only: the frame's views carry CLOD_FAST_EXP
     uint64_t n;
     size_t diff_grid_max;   // max over views of (TX + 1) (TY + 1)
 };
@@ -161,6 +162,29 @@ __device__ __forceinline__ float exp_spec(float x)
     if (!(x >= -80.0f)) return 0.0f;
     if (x > 0.0f) x = 0.0f;
     return exp_spec_core(x);
+}
+
+// The blends' exponential when a frame asks for CLOD_FAST_EXP: e^p =
+// 2^(p log2 e) on the special-function unit (ex2.approx; one product and one
+// MUFU instruction instead of the ~24 of exp_spec_core).  For p in [-5.6, 0]
+// its relative error is a few 1e-7 (the rounding of p log2 e and the unit's
+// approximation), so opacities follow the real-arithmetic blend within FP32
+// rounding, but a decision near a threshold may fall differently from the
+// software exponential's: such images are not bit-reproducible by another
+// implementation of the FP32 sequence.
+__device__ __forceinline__ float exp_fast(float p)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(__fmul_rn(p, 1.44269504088896341f)));
+    return y;
+}
+
+// Exponential of a blend power p in [-5.6, 0]: the software exponential
+// (FAST = false, the reproducible decision arithmetic) or exp_fast.
+template <bool FAST>
+__device__ __forceinline__ float blend_exp(float p)
+{
+    return FAST ? exp_fast(p) : exp_spec_core(p);
 }
 
 // Camera-frame point: t_k = R_k0 x + (R_k1 y + (R_k2 z + t_k)), fused.

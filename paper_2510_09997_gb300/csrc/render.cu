@@ -12,7 +12,8 @@
 // no result changes.  Per pixel, a power below the Gaussian's floor (opacity
 // < 1/255 for certain) skips the exponential, and the per-pixel updates run
 // under predicates rather than branches (the kernel is issue bound).  A warp
-// stops once its 64 pixels are saturated.
+// stops once its 64 pixels are saturated.  The exponential is the
+// reproducible software one, or with CLOD_FAST_EXP the special-function unit's.
 // Plain FP32/ALU work with one exponential per evaluated pair: no tensor
 // cores.
 #include <algorithm>
@@ -77,7 +78,8 @@ __device__ __forceinline__ void blend_finish(Px& q, bool ok, float al, const flo
 // either lies in [pf, 0], pf >= -5.6 the Gaussian's power floor) the two
 // exponentials side by side, so that their dependency chains interleave.
 // Below pf the opacity is < 1/255 (skipped either way): every pixel's result
-// is that of blend_one.
+// is that of blend_one (FAST: with the exponential of CLOD_FAST_EXP).
+template <bool FAST>
 __device__ __forceinline__ void blend_pair(Px& q0, Px& q1, bool t0, bool t1, float fpx, float fpy0, float fpy1,
                                            const float4& a, const float4& c, float cb, float pf, uint32_t pos)
 {
@@ -92,14 +94,14 @@ __device__ __forceinline__ void blend_pair(Px& q0, Px& q1, bool t0, bool t1, flo
     // (its result is dropped: ok below is false)
     if (!__any_sync(0xffffffffu, r0 || r1)) return;
     if (__any_sync(0xffffffffu, r0 && r1)) {
-        const float g0 = exp_spec_core(p0), g1 = exp_spec_core(p1);
+        const float g0 = blend_exp<FAST>(p0), g1 = blend_exp<FAST>(p1);
         const float a0 = fminf(0.99f, __fmul_rn(c.y, g0)), a1 = fminf(0.99f, __fmul_rn(c.y, g1));
         blend_finish(q0, r0 && !(a0 < (1.0f / 255.0f)), a0, c, cb, pos);
         blend_finish(q1, r1 && !(a1 < (1.0f / 255.0f)), a1, c, cb, pos);
     } else {
         // no lane has both pixels in range: one exponential per lane, for the
         // pixel that is (the same value either pixel would get)
-        const float g = exp_spec_core(r0 ? p0 : p1);
+        const float g = blend_exp<FAST>(r0 ? p0 : p1);
         const float al = fminf(0.99f, __fmul_rn(c.y, g));
         const bool ok = !(al < (1.0f / 255.0f));
         blend_finish(q0, r0 && ok, al, c, cb, pos);
@@ -130,8 +132,10 @@ constexpr int BLEND_THREADS = 128;   // 4 warps per 16x16 tile, 8x8 pixels per w
 // one record and tests its reach box against the warp's patch; the ballot of
 // hits is then blended in list order from per-warp shared slots.  A warp
 // leaves its patch when all 64 pixels are saturated and takes the next item;
-// nothing waits for the other warps of the block.
-template <bool COUNT>
+// nothing waits for the other warps of the block.  COUNT: the counting
+// variant (every pair visited, software exponential); FAST: the exponential
+// of CLOD_FAST_EXP.
+template <bool COUNT, bool FAST>
 __global__ void __launch_bounds__(BLEND_THREADS) k_blend_fwd(Frame F, const uint32_t* __restrict__ vals,
                                                              const uint32_t* __restrict__ ranges,
                                                              float* __restrict__ image, float* __restrict__ Tout,
@@ -213,7 +217,7 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_fwd(Frame F, const uint
                     // per pixel, the power floor e.w decides (no box test: the
                     // warp's box test above already passed, and a pixel outside
                     // the reach box has a power below the floor)
-                    blend_pair(q0, q1, !q0.done, !q1.done, fpx, fpy0, fpy1, a, c, e.x, e.w, pos);
+                    blend_pair<FAST>(q0, q1, !q0.done, !q1.done, fpx, fpy0, fpy1, a, c, e.x, e.w, pos);
                 }
             }
             __syncwarp();
@@ -243,25 +247,30 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_fwd(Frame F, const uint
     }
 }
 
-static int g_blend_blocks_per_sm = 0;
+static int g_blend_blocks_per_sm[2] = {0, 0};
 
 cudaError_t render_setup()
 {
     int b = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_blend_fwd<false>, BLEND_THREADS, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_blend_fwd<false, false>, BLEND_THREADS, 0);
     if (e != cudaSuccess) return e;
-    g_blend_blocks_per_sm = b > 0 ? b : 1;
+    g_blend_blocks_per_sm[0] = b > 0 ? b : 1;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_blend_fwd<false, true>, BLEND_THREADS, 0);
+    if (e != cudaSuccess) return e;
+    g_blend_blocks_per_sm[1] = b > 0 ? b : 1;
     return cudaSuccess;
 }
 
 void launch_blend_fwd(const Frame& F, const uint32_t* vals, const uint32_t* ranges, float* image, float* Tout,
-                      uint32_t* ncout, unsigned long long* evaluated, int n_sm, cudaStream_t st)
+                      uint32_t* ncout, unsigned long long* evaluated, int n_sm, cudaStream_t st, bool fast)
 {
-    const int blocks = n_sm * std::max(1, g_blend_blocks_per_sm);
+    const int blocks = n_sm * std::max(1, g_blend_blocks_per_sm[fast ? 1 : 0]);
     if (evaluated)
-        k_blend_fwd<true><<<blocks, BLEND_THREADS, 0, st>>>(F, vals, ranges, image, Tout, ncout, evaluated);
+        k_blend_fwd<true, false><<<blocks, BLEND_THREADS, 0, st>>>(F, vals, ranges, image, Tout, ncout, evaluated);
+    else if (fast)
+        k_blend_fwd<false, true><<<blocks, BLEND_THREADS, 0, st>>>(F, vals, ranges, image, Tout, ncout, nullptr);
     else
-        k_blend_fwd<false><<<blocks, BLEND_THREADS, 0, st>>>(F, vals, ranges, image, Tout, ncout, nullptr);
+        k_blend_fwd<false, false><<<blocks, BLEND_THREADS, 0, st>>>(F, vals, ranges, image, Tout, ncout, nullptr);
 }
 
 }  // namespace clod

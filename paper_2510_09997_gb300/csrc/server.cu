@@ -37,7 +37,7 @@ void launch_preprocess(const Frame& F, const clod_scene& S, uint32_t V, uint8_t*
 void launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long long cap, uint64_t* keys, uint32_t* vals,
                      uint32_t* ranges, cudaStream_t st);
 void launch_blend_fwd(const Frame& F, const uint32_t* vals, const uint32_t* ranges, float* image, float* Tout,
-                      uint32_t* ncout, unsigned long long* evaluated, int n_sm, cudaStream_t st);
+                      uint32_t* ncout, unsigned long long* evaluated, int n_sm, cudaStream_t st, bool fast);
 clod_status fail(clod_status s, const char* fmt, ...);
 clod_status cuda_fail(cudaError_t e, const char* what);
 clod_status device_ready(int* n_sm);
@@ -141,7 +141,7 @@ static void enqueue_batch(clod_server* S, Slot& sl, cudaStream_t st, bool select
     cudaMemcpyAsync(F.views, sl.h_views, sizeof(ViewDev) * V, cudaMemcpyHostToDevice, st);
     launch_preprocess(F, S->scene, (uint32_t)V, nullptr, nullptr, nullptr, S->n_sm, st, select);
     launch_bin_sort(F, sl.L, S->cfg.pair_capacity, nullptr, sl.vals, sl.ranges, st);
-    launch_blend_fwd(F, sl.vals, sl.ranges, nullptr, nullptr, nullptr, nullptr, S->n_sm, st);
+    launch_blend_fwd(F, sl.vals, sl.ranges, nullptr, nullptr, nullptr, nullptr, S->n_sm, st, S->cfg.fast_exp != 0);
     cudaMemcpyAsync(sl.h_hdr_down, F.hdr, sizeof(FrameHeader), cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(sl.h_counts, F.n_surv, sizeof(uint32_t) * 2 * V, cudaMemcpyDeviceToHost, st);
 }
@@ -228,7 +228,7 @@ static clod_status render_alone(clod_server* S, Slot& sl, Request& r)
         return cuda_fail(e, "render_alone ranges");
     }
     launch_bin_sort(F, L, K, nullptr, vals, ranges, st);
-    launch_blend_fwd(F, vals, ranges, nullptr, nullptr, nullptr, nullptr, S->n_sm, st);
+    launch_blend_fwd(F, vals, ranges, nullptr, nullptr, nullptr, nullptr, S->n_sm, st, S->cfg.fast_exp != 0);
     FrameHeader out;
     cudaMemcpyAsync(&out, F.hdr, sizeof(out), cudaMemcpyDeviceToHost, st);
     uint32_t cnt[2] = {0, 0};

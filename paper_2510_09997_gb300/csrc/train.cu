@@ -172,6 +172,18 @@ clod_status clod_adam_state_size(int64_t n, int32_t sh_degree, int64_t* elements
     return CLOD_OK;
 }
 
+clod_status clod_step_weights(const float* s_v, int32_t n_views, float s_max, float* weight)
+{
+    if (!s_v || !weight || n_views < 1 || n_views > MAX_VIEWS) return fail(CLOD_ERR_ARG, "bad argument to clod_step_weights");
+    if (!(s_max > 0.0f) || !std::isfinite(s_max)) return fail(CLOD_ERR_ARG, "s_max must be > 0 and finite");
+    for (int v = 0; v < n_views; ++v) {
+        if (!(s_v[v] > 0.0f) || !std::isfinite(s_v[v])) return fail(CLOD_ERR_ARG, "view %d: s_v must be > 0", v);
+        const double r = 1.0 - 0.5 * (double)s_v[v] / (double)s_max;     // Eq. 5
+        weight[v] = (float)(r * r / (double)n_views);
+    }
+    return CLOD_OK;
+}
+
 clod_status clod_lreg_grad(const uint32_t* counts, int64_t n, int32_t n_views, const float* s_v, const float* weight,
                            float lambda_reg, const float* lrender, float* dL_dalpha_view, float* total, float* lreg_out,
                            clod_stream stream)

@@ -16,7 +16,7 @@ class Server:
     def __init__(self, scene: "C.DeviceScene", max_views_per_batch: int = 8, n_slots: int = 2,
                  queue_capacity: int = 100000, use_graphs: bool = True, max_pixels_per_batch: Optional[int] = None,
                  pair_capacity: int = 1 << 25, batch_window_us: int = 0, max_width: int = 3840,
-                 max_height: int = 2160):
+                 max_height: int = 2160, fast_exp: bool = False):
         C.require_cuda()
         self.scene = scene          # keeps the device arrays alive
         cfg = abi.clod_server_cfg()
@@ -29,6 +29,7 @@ class Server:
         cfg.batch_window_us = batch_window_us
         cfg.max_width = max_width
         cfg.max_height = max_height
+        cfg.fast_exp = 1 if fast_exp else 0
         self.cfg = cfg
         self.h = ctypes.c_void_p()
         C.check("clod_server_create", C.lib().clod_server_create(ctypes.byref(scene.c), ctypes.byref(cfg),

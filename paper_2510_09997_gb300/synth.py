@@ -35,6 +35,7 @@ SQRT_PI = math.sqrt(math.pi)
 # view flags (mirrors of the C-ABI flag bits; plain integers)
 FLAG_LOD_OFF = 1
 FLAG_NO_NORMALIZE = 2
+FLAG_FAST_EXP = 4       # blends with the hardware exponential (not bit-reproducible)
 
 
 @dataclasses.dataclass

@@ -45,10 +45,6 @@ def eta_target(s_v: float) -> float:
     return s_v ** -1.5
 
 
-def w_s(s_v: float, s_max: float) -> float:
-    return (1.0 - 0.5 * s_v / s_max) ** 2
-
-
 class GaussianModel:
     """Raw parameters (what Adam updates) and the activated scales and
     opacities the rasterizer reads.  At construction the activated copies are
@@ -138,7 +134,10 @@ class TrainStep:
         st = C._stream(None)
         fr = C.render(self.scene, views, want_keys=False)
         dimg = torch.empty_like(fr.image)
-        weights = [w_s(s, self.s_max) / V for s in scales]
+        s_arr = (ctypes.c_float * V)(*scales)
+        w_arr = (ctypes.c_float * V)()
+        C.check("clod_step_weights", L.clod_step_weights(s_arr, V, self.s_max, w_arr))
+        weights = list(w_arr)
         self.lrender[:V].zero_()
         for k, v in enumerate(views):
             b = 3 * fr.pix_base[k]
@@ -155,8 +154,6 @@ class TrainStep:
                 C._ptr(img), C._ptr(targets[k]), 3, v.height, v.width, self.dssim, weights[k],
                 C._ptr(ws) if ws is not None else None, nbytes, C._ptr(self.lrender[k:]),
                 C._ptr(dimg[b:]), st))
-        s_arr = (ctypes.c_float * V)(*scales)
-        w_arr = (ctypes.c_float * V)(*weights)
         C.check("clod_lreg_grad", L.clod_lreg_grad(C._ptr(fr.counts), self.model.n, V, s_arr, w_arr, self.lam,
                                                    C._ptr(self.lrender), C._ptr(self.dalpha), C._ptr(self.total),
                                                    C._ptr(self.lreg), st))
@@ -167,7 +164,7 @@ class TrainStep:
             ctypes.byref(self.scene.c), C._ptr(fr.ws), C._ptr(fr.vals), C._ptr(fr.ranges), C._ptr(fr.T_final),
             C._ptr(fr.n_contrib), C._ptr(dimg), None, C._ptr(self.dalpha), C._ptr(bws), bws.numel(),
             *[C._ptr(g) for g in self.grads], st))
-        info = dict(views=views, n=self.model.n, scales=list(scales), w_s=[w_s(s, self.s_max) for s in scales],
+        info = dict(views=views, n=self.model.n, scales=list(scales), w_s=[w * V for w in weights],
                     eta_target=[eta_target(s) for s in scales], counts=fr.counts, l_render=self.lrender[:V],
                     l_reg=self.lreg[:V])
         self.last = dict(frame=fr, dimage=dimg, **info)

@@ -106,3 +106,87 @@ def run_and_compare(C, scene, views, tiles=None, with64=True):
     for v in range(len(views)):
         errs.append(assert_image_matches(fr, v, ref["img"][v], None if tiles is None else tiles[v]))
     return fr, ref, errs
+
+
+GRAD_NAMES = ("means", "scales", "quats", "opacity", "sh", "decay")
+
+
+def gpu_grads(A, sc, views, gimgs, galphas=None):
+    """Gradients of sum_v <image_v, gimgs[v]> (+ <alpha''_v, galphas[v]>)
+    through the autograd binding (clod_render_fwd / clod_render_bwd), as
+    FP64 numpy arrays per parameter group."""
+    ps = [torch.tensor(np.asarray(getattr(sc, k), np.float32), device="cuda", requires_grad=True)
+          for k in GRAD_NAMES]
+    imgs, alpha, mask, counts = A.render(*ps, views)
+    loss = sum((im * torch.tensor(g, device="cuda", dtype=torch.float32)).sum() for im, g in zip(imgs, gimgs))
+    if galphas is not None:
+        loss = loss + (alpha * torch.tensor(np.stack(galphas), device="cuda", dtype=torch.float32)).sum()
+    loss.backward()
+    out = {k: p.grad.detach().cpu().numpy().astype(np.float64) for k, p in zip(GRAD_NAMES, ps)}
+    del ps, imgs, alpha, mask, counts, loss
+    return out
+
+
+def rel_errors(g, r):
+    """Per group ||g - r||_2 / ||r||_2 (||g||_2 where r is zero)."""
+    out = {}
+    for k in GRAD_NAMES:
+        den = np.linalg.norm(r[k])
+        out[k] = np.linalg.norm(g[k] - r[k]) / den if den > 0 else np.linalg.norm(g[k])
+    return out
+
+
+def tile_list_lengths(s1, view):
+    """Length of every tile's list (row-major) from the oracle's tile
+    rectangles: a 2D difference array over the survivors' rectangles."""
+    tx, ty = O.tiles_of(view)
+    lens = np.zeros((ty + 1, tx + 1), np.int64)
+    r = s1["rect"][s1["survive"].astype(bool)]
+    np.add.at(lens, (r[:, 1], r[:, 0]), 1)
+    np.add.at(lens, (r[:, 1], r[:, 2]), -1)
+    np.add.at(lens, (r[:, 3], r[:, 0]), -1)
+    np.add.at(lens, (r[:, 3], r[:, 2]), 1)
+    return lens.cumsum(0).cumsum(1)[:ty, :tx].reshape(-1)
+
+
+def run_and_compare_fast(C, scene, views, tiles=None):
+    """As run_and_compare, with every view blended under CLOD_FAST_EXP: the
+    integer stages (Stage I, sorted pairs, ranges) bit for bit; the image,
+    which no longer follows the FP32 decision sequence bit for bit, within
+    2e-4 of the oracle's FP64 image and, pixel by pixel, within 2e-4 of an
+    outcome of the FP64 decisions.  Returns the per-view match summaries."""
+    from paper_2510_09997_gb300 import synth as S
+    fviews = [v.replace(flags=v.flags | S.FLAG_FAST_EXP) for v in views]
+    ds = C.DeviceScene.from_scene(scene)
+    fr = C.render(ds, fviews)
+    torch.cuda.synchronize()
+    ref = O.frame(scene, views, with64=True, tiles=tiles, dec64=True)
+    g = frame_stage1(fr, scene.n)
+    for v in range(len(views)):
+        assert_stage1_equal(g[v], ref["s1"][v])
+    assert np.array_equal(fr.vals.cpu().numpy().view(np.uint32), ref["vals"])
+    assert np.array_equal(fr.ranges.cpu().numpy().view(np.uint32), ref["ranges"])
+    out = []
+    for v, w in enumerate(views):
+        img = fr.view_image(v).cpu().numpy()
+        T = fr.view_T(v).cpu().numpy()
+        nc = fr.view_ncontrib(v).cpu().numpy().view(np.uint32)
+        sel = np.ones((w.height, w.width), bool) if tiles is None else _tile_sel(w, tiles[v])
+        r = ref["img"][v]
+        err = np.abs(img.astype(np.float64) - r["img64"])[:, sel].max()
+        m = match_fp64_branches(img, T, nc, r["dec64"], sel, 2e-4)
+        m["err_fp64_image"] = float(err)
+        m["differs_from_fp32_spec"] = int((np.abs(img - r["img32"]).max(axis=0)[sel] > 0).sum())
+        print("CLOD_FAST_EXP, view %d: %s" % (v, m))
+        assert m["bad"] == 0, m
+        assert err <= 2e-4, err
+        out.append(m)
+    return out
+
+
+def _tile_sel(w, tiles):
+    tx = (w.width + 15) // 16
+    sel = np.zeros((w.height, w.width), bool)
+    for t in tiles:
+        sel[(t // tx) * 16:(t // tx) * 16 + 16, (t % tx) * 16:(t % tx) * 16 + 16] = True
+    return sel

@@ -69,3 +69,33 @@ def test_region_view_validation_without_gpu(L):
     with pytest.raises(ValueError):
         clod.band_views(full, [0, 64, 250], [1.0])
     assert ctypes.sizeof(abi.clod_view) == 136
+
+
+def test_step_weights_closed_form(L):
+    """clod_step_weights gives Eq. 5's w_s(s_v) = (1 - s_v / (2 s_max))^2 per
+    view, divided by the view count (host call, no GPU)."""
+    from oracle import losses as OL
+    from paper_2510_09997_gb300 import abi  # noqa: F401  (declares the signatures)
+    s = [1.0, 3.5, 16.0]
+    sa = (ctypes.c_float * 3)(*s)
+    w = (ctypes.c_float * 3)()
+    assert L.clod_step_weights(sa, 3, 16.0, w) == 0
+    for k in range(3):
+        assert w[k] == pytest.approx(OL.w_s(float(ctypes.c_float(s[k]).value), 16.0) / 3, rel=1e-6)
+    assert w[2] == pytest.approx(0.25 / 3, rel=1e-7)           # w_s(s_max) = 1/4
+    assert L.clod_step_weights(sa, 3, 0.0, w) == 1
+    bad = (ctypes.c_float * 1)(-1.0)
+    assert L.clod_step_weights(bad, 1, 16.0, w) == 1
+
+
+def test_fast_exp_flag_must_agree_across_views(L):
+    """One frame blends with one exponential: views that disagree on
+    CLOD_FAST_EXP are rejected before any device work."""
+    from paper_2510_09997_gb300 import abi, clod, synth as S
+    views = clod.view_array([S.tiny_view(1.0), S.tiny_view(2.0).replace(flags=S.FLAG_FAST_EXP)])
+    nbytes = ctypes.c_size_t()
+    assert L.clod_frame_workspace_size(1000, views, 2, ctypes.byref(nbytes), None) == abi.CLOD_ERR_ARG
+    assert b"CLOD_FAST_EXP" in L.clod_last_error()
+    same = clod.view_array([S.tiny_view(1.0).replace(flags=S.FLAG_FAST_EXP),
+                            S.tiny_view(2.0).replace(flags=S.FLAG_FAST_EXP)])
+    assert L.clod_frame_workspace_size(1000, same, 2, ctypes.byref(nbytes), None) == 0

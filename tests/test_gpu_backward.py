@@ -12,6 +12,8 @@ import torch
 from oracle import grad64 as G
 from paper_2510_09997_gb300 import synth as S
 
+from gpu_helpers import gpu_grads, rel_errors
+
 pytestmark = pytest.mark.gpu
 NAMES = ("means", "scales", "quats", "opacity", "sh", "decay")
 
@@ -21,24 +23,6 @@ def A():
     from paper_2510_09997_gb300 import autograd, clod
     clod.require_cuda()
     return autograd
-
-
-def gpu_grads(A, sc, views, gimgs, galphas=None):
-    ps = [torch.tensor(np.asarray(getattr(sc, k), np.float32), device="cuda", requires_grad=True) for k in NAMES]
-    imgs, alpha, mask, counts = A.render(*ps, views)
-    loss = sum((im * torch.tensor(g, device="cuda", dtype=torch.float32)).sum() for im, g in zip(imgs, gimgs))
-    if galphas is not None:
-        loss = loss + (alpha * torch.tensor(np.stack(galphas), device="cuda", dtype=torch.float32)).sum()
-    loss.backward()
-    return {k: p.grad.detach().cpu().numpy().astype(np.float64) for k, p in zip(NAMES, ps)}
-
-
-def rel_errors(g, r):
-    out = {}
-    for k in NAMES:
-        den = np.linalg.norm(r[k])
-        out[k] = np.linalg.norm(g[k] - r[k]) / den if den > 0 else np.linalg.norm(g[k])
-    return out
 
 
 def check(A, sc, views, seed=0, with_alpha=True, tol=1e-3):
@@ -134,3 +118,14 @@ def test_gpu_gradients_match_central_differences_200_32x32(A):
         fd, gg = np.array(fd), np.array(gg)
         assert np.linalg.norm(fd) > 0, name
         assert np.linalg.norm(gg - fd) <= 2e-3 * np.linalg.norm(fd), (name, np.linalg.norm(gg - fd) / np.linalg.norm(fd))
+
+
+def test_fast_exp_gradients(A):
+    """Forward and backward blends under CLOD_FAST_EXP against the FP64
+    reference gradients (decisions frozen from the FP32 specification; the
+    fast exponential may move a near-threshold decision, which the 1e-3
+    criterion absorbs)."""
+    sc = S.tiny_scene(n=3000, seed=30, sh_degree=1)
+    views = [S.tiny_view(1.5).replace(width=96, height=80, cx=48.0, cy=40.0, flags=S.FLAG_FAST_EXP),
+             S.look_at((2.0, 1.5, 1.0), (0, 0, 0), 64, 64, s_v=3.0, bg=(0.5, 0.5, 0.5), flags=S.FLAG_FAST_EXP)]
+    check(A, sc, views, seed=1)

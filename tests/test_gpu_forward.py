@@ -14,7 +14,8 @@ import torch
 from oracle import oracle as O
 from paper_2510_09997_gb300 import synth as S
 
-from gpu_helpers import assert_image_matches, assert_stage1_equal, frame_stage1, run_and_compare
+from gpu_helpers import (assert_image_matches, assert_stage1_equal, frame_stage1, run_and_compare,
+                         run_and_compare_fast)
 
 pytestmark = pytest.mark.gpu
 
@@ -115,3 +116,44 @@ def test_renderer_fixed_capacity_matches_and_flags_overflow(C):
     with pytest.raises(C.ClodError) as e:
         R2.check()
     assert e.value.status == 2
+
+
+# ---------------------------------------------------------------------------
+# CLOD_FAST_EXP: the blend's opacities from the hardware base-2 exponential
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("s", [1.0, 4.0])
+def test_fast_exp_tiny_scene(C, s):
+    run_and_compare_fast(C, S.tiny_scene(), [S.tiny_view(s)])
+
+
+def test_fast_exp_batched_views(C):
+    sc = S.tiny_scene(n=8000, seed=21, sh_degree=3)
+    views = [S.tiny_view(1.0),
+             S.look_at((2.5, -1.0, 1.0), (0, 0, 0), 250, 130, s_v=2.0, bg=(0.2, 0.3, 0.4)),
+             S.look_at((-1.5, 2.0, -1.0), (0.1, 0, 0), 97, 161, s_v=3.0, flags=S.FLAG_LOD_OFF),
+             S.look_at((0.5, 0.5, 3.5), (0, 0, 0), 64, 48, s_v=1.5, flags=S.FLAG_NO_NORMALIZE, tau=0.01)]
+    run_and_compare_fast(C, sc, views)
+
+
+@pytest.mark.parametrize("cam,s", [(0, 1.0), (20, 1.0), (40, 16.0)])
+def test_fast_exp_object_scene_full_size(C, cam, s):
+    """1M Gaussians, SH degree 3, 1920x1080 under CLOD_FAST_EXP: integer
+    stages bit for bit; sampled tiles (the longest lists and random ones)
+    within 2e-4 of an FP64-decision outcome and of the FP64 image."""
+    sc = S.object_scene()
+    v = S.orbit_cameras(64, 1920, 1080)[cam].replace(s_v=s)
+    s1 = O.stage1(sc, v)
+    k, val = O.emit_pairs(v, s1)
+    lens = np.bincount((k >> np.uint64(32)).astype(np.int64), minlength=v.tiles)
+    rng = np.random.default_rng(cam)
+    tiles = list(np.argsort(lens)[-6:]) + list(rng.choice(v.tiles, 10, replace=False))
+    run_and_compare_fast(C, sc, [v], tiles=[tiles])
+
+
+def test_fast_exp_views_must_agree(C):
+    sc = S.tiny_scene(n=500, seed=26)
+    ds = C.DeviceScene.from_scene(sc)
+    views = [S.tiny_view(1.0), S.tiny_view(2.0).replace(flags=S.FLAG_FAST_EXP)]
+    with pytest.raises(C.ClodError) as e:
+        C.render(ds, views)
+    assert e.value.status == 1

@@ -51,7 +51,7 @@ def test_loss_scalars_match_oracle(T):
         assert info[k]["eta_actual"] == pytest.approx(eta_a, abs=0)
         assert info[k]["l_render"] == pytest.approx(l1, rel=1e-5, abs=1e-7)
         assert info[k]["l_reg"] == pytest.approx(OL.l_reg(s, eta_a), rel=1e-6, abs=1e-12)
-        assert info[k]["w_s"] == pytest.approx(OL.w_s(s, step.s_max), rel=1e-12)
+        assert info[k]["w_s"] == pytest.approx(OL.w_s(s, step.s_max), rel=1e-6)    # f32 weights (clod_step_weights)
         expect += OL.l_total(s, step.s_max, l1, eta_a, 1.0) / len(views)
     assert float(total) == pytest.approx(expect, rel=2e-5)
     assert info[1]["l_reg"] > 0          # s_v = 3 at 4000 Gaussians is above target

@@ -479,6 +479,36 @@ def test_reference_gradients_match_central_differences():
 # ---------------------------------------------------------------------------
 # Training objective scalars (Sec. 3.3, Eq. 3-5)
 # ---------------------------------------------------------------------------
+def test_sparse_reference_gradients_equal_full():
+    """The sub-scene evaluation used at full size gives the same gradients
+    as the whole-scene statement when the image gradient sits on a few tiles
+    and the alpha'' gradient on a few Gaussians (the others are exactly zero)."""
+    from oracle import grad64 as G
+    sc = S.tiny_scene(n=3000, seed=41, sh_degree=2)
+    views = [S.tiny_view(1.5).replace(width=96, height=80, cx=48.0, cy=40.0),
+             S.look_at((2.0, 1.5, 1.0), (0, 0, 0), 64, 64, s_v=3.0, bg=(0.5, 0.5, 0.5))]
+    rng = np.random.default_rng(8)
+    gimgs, galphas, frozen_t, frozen_all = [], [], [], []
+    for v in views:
+        tx, ty = O.tiles_of(v)
+        tiles = sorted(rng.choice(tx * ty, 5, replace=False).tolist())
+        sel = np.zeros((v.height, v.width), bool)
+        for t in tiles:
+            sel[(t // tx) * 16:(t // tx) * 16 + 16, (t % tx) * 16:(t % tx) * 16 + 16] = True
+        gimgs.append(rng.normal(size=(3, v.height, v.width)) * sel[None])
+        ga = np.zeros(sc.n)
+        ga[rng.choice(sc.n, 50, replace=False)] = rng.normal(size=50) * 1e-2
+        galphas.append(ga)
+        frozen_t.append(G.frozen_on_tiles(sc, v, tiles)[0])
+        frozen_all.append(G.frozen_from_oracle(sc, v)[0])
+    sparse = G.reference_gradients_sparse(sc, views, frozen_t, gimgs, galphas)
+    full = G.reference_gradients(sc, views, gimgs, galphas, frozen=frozen_all)
+    for k in full:
+        assert np.linalg.norm(full[k]) > 0, k
+        assert np.abs(sparse[k] - full[k]).max() <= 1e-12 * max(1.0, np.abs(full[k]).max()), k
+    assert (np.abs(full["sh"]).sum(axis=(1, 2)) > 0).sum() < sc.n // 2      # sparse indeed
+
+
 def test_loss_scalars_closed_forms():
     """P7, and the golden values in tests/golden/loss_scalars.txt."""
     assert L.eta_target(1.0) == 1.0
