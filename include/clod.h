@@ -65,7 +65,7 @@ typedef void* clod_stream;     /* cudaStream_t */
 /* A resident Gaussian scene (Sec. 3.1 primitives plus the per-Gaussian decay
  * sigma_d of Sec. 3.2).  All arrays are device memory, float32, row-major. */
 typedef struct clod_scene {
-    int64_t n;              /* number of Gaussians, 0 <= n < 2^31               */
+    int64_t n;              /* number of Gaussians, 0 <= n < 2^28               */
     int32_t sh_degree;      /* 0..3                                             */
     int32_t reserved;
     const float* means;     /* n x 3                                            */
@@ -393,11 +393,12 @@ clod_status clod_server_destroy(clod_server* server);
  * scenes or views are rejected with CLOD_ERR_ARG before any work, a frame
  * with more pairs returns CLOD_ERR_CAPACITY (with the count) and writes no
  * image.  image (3 x H x W), T_final (H x W, may be NULL), n_contrib (H x W,
- * may be NULL) are caller device buffers.  The call waits for the frame on
- * its stream before returning.  Calls share the array: calls whose work
- * overlaps on the GPU race and must be serialised by the caller.  The first
- * call on a device looks up the array's device address; make it before any
- * stream capture. */
+ * may be NULL) are caller device buffers.  The call is synchronous: it
+ * waits for the frame on its stream and reads the frame header back to the
+ * host before returning.  Calls share the array: calls whose work overlaps on
+ * the GPU race and must be serialised by the caller.  The first call on a
+ * device also looks up the array's device address; make that first call
+ * before any stream capture. */
 clod_status clod_render_noalloc(const clod_scene* scene, const clod_view* view,
                                 float* image, float* T_final, uint32_t* n_contrib,
                                 clod_stream stream);

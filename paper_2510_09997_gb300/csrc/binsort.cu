@@ -19,8 +19,8 @@
 //      warp per (chunk, tile row) walks the chunk's rectangles in rank order
 //      and counts, per tile of its row, the pairs the chunk contributes
 //      (k_rows<false>);
-//   3. per tile, an exclusive scan over the chunks (k_chunk_scan), then over
-//      the tiles (k_scan_tiles: tile offsets, K, ranges);
+//   3. per tile, an exclusive scan over the chunks, then over the tiles
+//      (k_tile_scan: tile offsets, K, ranges, the blends' work order);
 //   4. the same walk again (k_rows<true>): pair (Gaussian, tile) goes to
 //      tile_offset + chunk offset + (number of earlier-ranked Gaussians of the
 //      chunk in that tile) -- its final sorted position.
@@ -108,77 +108,91 @@ __device__ __forceinline__ void rs_warp_counts(const uint32_t (&kk)[RS_R], int s
     }
 }
 
-__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const FrameHeader* __restrict__ hdr,
-                                                        const uint32_t* __restrict__ n_surv,
-                                                        const uint32_t* __restrict__ keys, int64_t n, int nb, int shift,
-                                                        uint32_t* __restrict__ hist, uint32_t* __restrict__ totals,
-                                                        uint32_t* __restrict__ sum1, uint32_t* __restrict__ sum2)
+// All four digit histograms of the survivors' depth keys, per view, in one
+// read of the keys (the first pass's input: all n keys of every view,
+// culled ones keyed all ones and skipped): tot[pass][view][digit].  Each
+// warp counts its keys' digits with one vote per bit and adds them into
+// shared counters; the block then adds its non-zero counters to tot.
+__global__ void __launch_bounds__(RS_THREADS) k_rs_hist_all(const FrameHeader* __restrict__ hdr,
+                                                            const uint32_t* __restrict__ keys, int64_t n, int nb,
+                                                            int Vl, uint32_t* __restrict__ tot)
 {
-    __shared__ uint32_t h[RS_THREADS / 32][256];
-    const int b = blockIdx.x, v = b / nb, lb = b % nb;
-    const int64_t base = (int64_t)v * n + (int64_t)lb * RS_ITEMS;
-    // the first pass's keys are loaded before the view check (its count needs
-    // no load); a later pass reads its count first, so blocks past the
-    // survivors move no data
-    uint32_t kk[RS_R];
-    int cnt;
-    if (shift == 0) {
-        cnt = rs_first_count(n, lb);
-        rs_load_keys(keys, base, cnt, kk);
-        if ((uint32_t)v >= hdr->n_views) return;
-    } else {
-        if ((uint32_t)v >= hdr->n_views) return;
-        cnt = rs_later_count(n_surv, v, lb);
-        if (cnt == 0) return;
-        rs_load_keys(keys, base, cnt, kk);
-    }
-    if (cnt == 0) return;     // no items (and none in any later block)
-    rs_warp_counts(kk, shift, h);
+    __shared__ uint32_t h[4][256];
+    for (int k = threadIdx.x; k < 1024; k += blockDim.x) h[k >> 8][k & 255] = 0u;
     __syncthreads();
-    uint32_t s = 0;
-    for (int w = 0; w < RS_THREADS / 32; ++w) s += h[w][threadIdx.x];
-    hist[((size_t)v * nb + lb) * 256 + threadIdx.x] = s;
-    if (s) {
-        atomicAdd(&totals[v * 256 + threadIdx.x], s);
-        atomicAdd(&sum1[((size_t)v * rs_groups(nb, RS_G1) + lb / RS_G1) * 256 + threadIdx.x], s);
-        atomicAdd(&sum2[((size_t)v * rs_groups(nb, RS_G2) + lb / RS_G2) * 256 + threadIdx.x], s);
+    const int b = blockIdx.x, v = b / nb, lb = b % nb;
+    const bool live = (uint32_t)v < hdr->n_views;
+    const int lane = threadIdx.x & 31;
+    if (live) {
+        const int cnt = rs_first_count(n, lb);
+        uint32_t kk[RS_R];
+        rs_load_keys(keys, (int64_t)v * n + (int64_t)lb * RS_ITEMS, cnt, kk);
+#pragma unroll
+        for (int r = 0; r < RS_R; ++r) {
+            const bool valid = kk[r] != 0xFFFFFFFFu;
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                const uint32_t d = valid ? ((kk[r] >> (8 * p)) & 255u) : 256u;
+                const uint32_t peers = match_bits<9>(d);
+                if (valid && (__ffs(peers) - 1) == lane) atomicAdd_block(&h[p][d], __popc(peers));
+            }
+        }
+    }
+    __syncthreads();
+    if (!live) return;
+    for (int k = threadIdx.x; k < 1024; k += blockDim.x) {
+        const uint32_t c = h[k >> 8][k & 255];
+        if (c) atomicAdd(&tot[((size_t)(k >> 8) * Vl + v) * 256 + (k & 255)], c);
     }
 }
 
+// Look-back words of the scatter passes, one per (view, block, digit): a
+// flag (the block's own count, or the count of the view's blocks up to and
+// including it), the pass (the words of a frame are cleared once and reused
+// by the four passes) and the count.
+constexpr uint32_t RS_AGG = 1u << 30, RS_INC = 2u << 30, RS_VAL = (1u << 28) - 1;
+constexpr uint32_t RS_SPIN_LIMIT = 1u << 20;
+
+__device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p)
+{
+    return *reinterpret_cast<const volatile uint32_t*>(p);
+}
+
 // Stable scatter of one digit pass; on the last pass (GATHER) also gathers the
-// tile rectangle of every survivor into rank order.  Keys, values and
-// rectangles are loaded before the counting, so their latency overlaps it.
+// tile rectangle of every survivor into rank order.  Blocks take their place
+// (view, block) from a ticket, so every block they look back at has started.
+// Keys, values and rectangles are loaded before the counting, so their
+// latency overlaps it.  A block's offset within a digit is the count of the
+// digit in the view's earlier blocks, found by walking back over their
+// look-back words until one holds an inclusive count.
 template <bool GATHER>
-__global__ void __launch_bounds__(RS_THREADS, 4) k_rs_scatter(const FrameHeader* __restrict__ hdr,
+__global__ void __launch_bounds__(RS_THREADS, 4) k_rs_scatter(FrameHeader* __restrict__ hdr,
                                                            const uint32_t* __restrict__ n_surv,
                                                            const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                            uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
-                                                           int64_t n, int nb, int shift, const uint32_t* __restrict__ hist,
-                                                           const uint32_t* __restrict__ totals,
-                                                           const uint32_t* __restrict__ sum1,
-                                                           const uint32_t* __restrict__ sum2,
+                                                           int64_t n, int nb, int pass, const uint32_t* __restrict__ tot,
+                                                           uint32_t* __restrict__ lbw, uint32_t* __restrict__ ticket,
                                                            const uint2* __restrict__ rect, uint2* __restrict__ srect)
 {
     __shared__ uint32_t h[RS_THREADS / 32][256];
     __shared__ uint32_t wb[RS_THREADS / 32][256];
     __shared__ uint32_t dbase[256];
     __shared__ uint32_t wsum[RS_THREADS / 32];
-    const int b = blockIdx.x, v = b / nb, lb = b % nb;
+    __shared__ uint32_t s_blk;
+    if (threadIdx.x == 0) s_blk = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const uint32_t b = s_blk;
+    const int v = (int)(b / (uint32_t)nb), lb = (int)(b % (uint32_t)nb);
+    if ((uint32_t)v >= hdr->n_views) return;
+    if (hdr->status & STATUS_TIMEOUT) return;     // an earlier pass gave up: nothing downstream runs
+    const int shift = 8 * pass;
     const int64_t vbase = (int64_t)v * n;
     const int64_t base = vbase + (int64_t)lb * RS_ITEMS;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // keys, values, the view's digit total and this block's digit offsets are
-    // loaded together (in the first pass before the view check; a later pass
-    // reads its item count first, so blocks past the survivors move no data)
-    const bool first = shift == 0;
-    int cnt;
-    if (first) {
-        cnt = rs_first_count(n, lb);
-    } else {
-        if ((uint32_t)v >= hdr->n_views) return;
-        cnt = rs_later_count(n_surv, v, lb);
-        if (cnt == 0) return;
-    }
+    // the first pass reads all n keys of the view (and drops the culled);
+    // later passes read its survivors, so blocks past them move no data
+    const int cnt = pass == 0 ? rs_first_count(n, lb) : rs_later_count(n_surv, v, lb);
+    if (cnt == 0) return;     // no later block of the view has items either: nobody waits on it
     uint32_t kk[RS_R], vv[RS_R];
     uint2 rr[RS_R];
     rs_load_keys(kin, base, cnt, kk);
@@ -187,31 +201,44 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_rs_scatter(const FrameHeader*
         const int idx = w * RS_PER_WARP + r * 32 + lane;
         vv[r] = idx < cnt ? vin[base + idx] : 0u;
     }
-    const uint32_t c_tot = totals[v * 256 + threadIdx.x];
-    // this block's offset within the digit: the counts of the earlier blocks,
-    // as groups of RS_G2 blocks, then groups of RS_G1, then single blocks
-    uint32_t c_blk = 0;
-    {
-        const uint32_t* p2 = sum2 + (size_t)v * rs_groups(nb, RS_G2) * 256 + threadIdx.x;
-        const uint32_t* p1 = sum1 + (size_t)v * rs_groups(nb, RS_G1) * 256 + threadIdx.x;
-        const uint32_t* p0 = hist + (size_t)v * nb * 256 + threadIdx.x;
-        const int q2 = lb / RS_G2, q1 = lb / RS_G1;
-#pragma unroll 8
-        for (int k = 0; k < q2; ++k) c_blk += p2[(size_t)k * 256];
-#pragma unroll
-        for (int k = 0; k < RS_G2 / RS_G1 - 1; ++k)
-            if (q2 * (RS_G2 / RS_G1) + k < q1) c_blk += p1[(size_t)(q2 * (RS_G2 / RS_G1) + k) * 256];
-#pragma unroll
-        for (int k = 0; k < RS_G1 - 1; ++k)
-            if (q1 * RS_G1 + k < lb) c_blk += p0[(size_t)(q1 * RS_G1 + k) * 256];
-    }
-    if (first && (uint32_t)v >= hdr->n_views) return;
-    if (cnt == 0) return;
+    const uint32_t c_tot = tot[v * 256 + threadIdx.x];
     if (GATHER) {
 #pragma unroll
         for (int r = 0; r < RS_R; ++r) rr[r] = kk[r] != 0xFFFFFFFFu ? rect[vbase + vv[r]] : make_uint2(0u, 0u);
     }
     rs_warp_counts(kk, shift, h);
+    __syncthreads();
+    // this block's count of digit threadIdx.x, published; then the view's
+    // earlier blocks' count of it (RS_THREADS == 256: one digit per thread)
+    uint32_t bc = 0;
+    for (int q = 0; q < RS_THREADS / 32; ++q) bc += h[q][threadIdx.x];
+    const uint32_t tag = (uint32_t)pass << 28;
+    uint32_t* mine = lbw + ((size_t)v * nb + lb) * 256 + threadIdx.x;
+    uint32_t c_blk = 0;
+    if (lb == 0) {
+        atomicExch(mine, RS_INC | tag | bc);
+    } else {
+        atomicExch(mine, RS_AGG | tag | bc);
+        bool gave_up = false;
+        for (int j = lb - 1; j >= 0; --j) {
+            const uint32_t* pj = lbw + ((size_t)v * nb + j) * 256 + threadIdx.x;
+            uint32_t x = ld_volatile_u32(pj);
+            uint32_t spins = 0;
+            while ((x >> 30) == 0u || ((x >> 28) & 3u) != (uint32_t)pass) {
+                if (++spins > RS_SPIN_LIMIT) {
+                    gave_up = true;
+                    break;
+                }
+                __nanosleep(32);
+                x = ld_volatile_u32(pj);
+            }
+            if (gave_up) break;
+            c_blk += x & RS_VAL;
+            if ((x >> 30) == 2u) break;
+        }
+        if (gave_up) atomicOr(&hdr->status, STATUS_TIMEOUT | STATUS_OVERFLOW);
+        atomicExch(mine, RS_INC | tag | ((c_blk + bc) & RS_VAL));
+    }
     {
         // exclusive scan of the view's 256 digit totals (RS_THREADS == 256)
         const int wi = threadIdx.x >> 5;
@@ -224,18 +251,19 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_rs_scatter(const FrameHeader*
         if (lane == 31) wsum[wi] = x;
         __syncthreads();
         uint32_t off = 0;
-        for (int w = 0; w < wi; ++w) off += wsum[w];
+        for (int q = 0; q < wi; ++q) off += wsum[q];
         dbase[threadIdx.x] = off + x - c;
     }
     __syncthreads();
     {
         uint32_t run = dbase[threadIdx.x] + c_blk;
-        for (int w = 0; w < RS_THREADS / 32; ++w) {
-            wb[w][threadIdx.x] = run;
-            run += h[w][threadIdx.x];
+        for (int q = 0; q < RS_THREADS / 32; ++q) {
+            wb[q][threadIdx.x] = run;
+            run += h[q][threadIdx.x];
         }
     }
     __syncthreads();
+    if (hdr->status & STATUS_TIMEOUT) return;     // offsets may be wrong: write nothing
     const uint32_t lt = lanemask_lt();
 #pragma unroll
     for (int r = 0; r < RS_R; ++r) {
@@ -301,6 +329,7 @@ __global__ void __launch_bounds__(ROWS_PER_BLOCK * 32, 4) k_rows(Frame F, uint32
     __shared__ uint32_t s_wc[ROWS_PER_BLOCK];
     __shared__ uint16_t s_buf[ROWS_PER_BLOCK][64];
     const FrameHeader* hdr = F.hdr;
+    if (hdr->status & STATUS_TIMEOUT) return;     // a look-back gave up: the rank order is not valid
     if (EMIT && (hdr->status & STATUS_OVERFLOW)) return;
     const uint32_t V = hdr->n_views;
     const uint32_t CH = hdr->n_chunks;
@@ -475,6 +504,7 @@ __global__ void __launch_bounds__(512) k_chunk_count(Frame F)
 {
     extern __shared__ uint32_t g[];
     const FrameHeader* hdr = F.hdr;
+    if (hdr->status & STATUS_TIMEOUT) return;     // a look-back gave up: the rank order is not valid
     const uint32_t CH = hdr->n_chunks;
     const int64_t n = (int64_t)hdr->n;
     const int v = (int)(blockIdx.x / CH);
@@ -521,20 +551,50 @@ __global__ void __launch_bounds__(512) k_chunk_count(Frame F)
     for (uint32_t t = threadIdx.x; t < T; t += blockDim.x) out[t] = g[(t / TX) * GX + (t % TX)];
 }
 
-// 3a. per tile: exclusive scan of the chunk counts; tile_count = total.
-// A block takes 32 tiles (one per lane, so every load of a chunk's counts is
-// coalesced) and cuts the chunks into 8 segments, one per warp: segment
-// sums, their scan across the warps, then each segment rescanned.
+// 3. per tile: exclusive scan of the chunk counts (the chunk offsets within
+// the tile), tile_count = their total; then the exclusive scan over the tiles
+// (tile offsets, K, ranges) chained across blocks by a decoupled look-back,
+// and the blends' work order.  A block takes 32 tiles (one per lane, so every
+// load of a chunk's counts is coalesced) and cuts the chunks into 8
+// segments, one per warp: segment sums, their scan across the warps, then
+// each segment rescanned.  Blocks take their place in the tile order from a
+// ticket, so every block they look back at has started and publishes
+// without waiting on later ones.
 constexpr int CS_TILES = 32, CS_SEG = 8;
 constexpr int CS_MAXPER = (MAX_CHUNKS + CS_SEG - 1) / CS_SEG;
-__global__ void __launch_bounds__(CS_TILES * CS_SEG, 2) k_chunk_scan(Frame F)
+constexpr unsigned long long LB_AGG = 1ull << 62;    // look-back word: the block's own sum
+constexpr unsigned long long LB_INC = 2ull << 62;    //                 the sum up to and including the block
+constexpr unsigned long long LB_VAL = (1ull << 62) - 1;
+constexpr uint32_t LB_SPIN_LIMIT = 1u << 20;         // polls of a missing predecessor before giving up
+
+// Length class of a tile list for the blends' work order: 0 (longest) to 3:
+// lists longer than 2m, than m, than m/2 (m the mean list length), the rest.
+__device__ __forceinline__ uint32_t tile_class(uint32_t c, unsigned long long mean)
+{
+    const unsigned long long cc = c;
+    return cc > 2ull * mean ? 0u : (cc > mean ? 1u : (2ull * cc > mean ? 2u : 3u));
+}
+
+__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p)
+{
+    return *reinterpret_cast<const volatile unsigned long long*>(p);
+}
+
+__global__ void __launch_bounds__(CS_TILES * CS_SEG, 2) k_tile_scan(Frame F, uint32_t* __restrict__ ranges,
+                                                                  unsigned long long cap)
 {
     __shared__ uint32_t part[CS_SEG][CS_TILES];
-    const uint32_t TT = F.hdr->total_tiles;
-    const uint32_t V = F.hdr->n_views;
-    const uint32_t CH = F.hdr->n_chunks;
+    __shared__ uint32_t s_blk;
+    FrameHeader* hdr = F.hdr;
+    if (hdr->status & STATUS_TIMEOUT) return;     // a look-back gave up: the counts are not valid
+    const uint32_t TT = hdr->total_tiles;
+    const uint32_t V = hdr->n_views;
+    const uint32_t CH = hdr->n_chunks;
+    if (threadIdx.x == 0) s_blk = atomicAdd(&F.scan_ctr[4], 1u);
+    __syncthreads();
+    const uint32_t blk = s_blk;
     const int tx = threadIdx.x % CS_TILES, sg = threadIdx.x / CS_TILES;
-    const uint32_t t = blockIdx.x * CS_TILES + tx;
+    const uint32_t t = blk * CS_TILES + tx;
     const bool ok = t < TT;
     uint32_t* col = nullptr;
     uint32_t T = 0, CHe = 0;
@@ -566,185 +626,125 @@ __global__ void __launch_bounds__(CS_TILES * CS_SEG, 2) k_chunk_scan(Frame F)
         if (q < sg) off += x;
         tot += x;
     }
-    if (!ok) return;
+    if (ok) {
 #pragma unroll
-    for (int k = 0; k < CS_MAXPER; ++k) {
-        if (c0 + k < c1) col[(size_t)(c0 + k) * T] = off;
-        off += xs[k];
+        for (int k = 0; k < CS_MAXPER; ++k) {
+            if (c0 + k < c1) col[(size_t)(c0 + k) * T] = off;
+            off += xs[k];
+        }
     }
-    if (sg == 0) F.tile_count[t] = tot;
-}
-
-// 3b. exclusive scan of the tile counts by one block of 1024 threads; writes
-// the tile offsets, the ranges ([0, 0) for empty tiles) and checks K.  Rounds
-// of 4096 tiles: each thread loads 4 consecutive counts (one 16-byte load
-// from the 256-byte aligned array), the block scans, and the offsets go out
-// through shared memory in coalesced stores.
-// Length class of a tile list for the blends' work order: 0 (longest) to 3.
-__device__ __forceinline__ uint32_t tile_class(uint32_t c, unsigned long long mean)
-{
-    const unsigned long long cc = c;
-    return cc > 2ull * mean ? 0u : (cc > mean ? 1u : (2ull * cc > mean ? 2u : 3u));
-}
-
-constexpr int ST_PER = 4;
-constexpr int ST_ROUND = 1024 * ST_PER;
-__global__ void __launch_bounds__(1024) k_scan_tiles(Frame F, uint32_t* __restrict__ ranges, unsigned long long cap)
-{
-    __shared__ unsigned long long wsum[32];
-    __shared__ uint32_t so[ST_ROUND];
-    __shared__ uint32_t sc[ST_ROUND];
-    const uint32_t TT = F.hdr->total_tiles;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    // length classes of the tiles (for the work order below): lists longer
-    // than 2m, than m, than m/2 (m the mean list length), and the rest
-    const unsigned long long mean = F.hdr->n_pairs / (TT ? TT : 1u);
-    __shared__ uint32_t s_cls[4];
-    if (threadIdx.x < 4) s_cls[threadIdx.x] = 0u;
-    __syncthreads();
-    unsigned long long carry = 0;
-    for (uint32_t base = 0; base < TT; base += ST_ROUND) {
-        const uint32_t t0 = base + threadIdx.x * ST_PER;
-        uint32_t c[ST_PER] = {0u, 0u, 0u, 0u};
-        if (t0 + ST_PER <= TT) {
-            const uint4 c4 = *reinterpret_cast<const uint4*>(F.tile_count + t0);
-            c[0] = c4.x; c[1] = c4.y; c[2] = c4.z; c[3] = c4.w;
-        } else {
-            for (int u = 0; u < ST_PER; ++u)
-                if (t0 + u < TT) c[u] = F.tile_count[t0 + u];
-        }
-        const unsigned long long s = (unsigned long long)c[0] + c[1] + c[2] + c[3];
-        {
-            uint32_t k4 = 0;     // per-class counts of this thread's tiles, 8 bits each
-#pragma unroll
-            for (int u = 0; u < ST_PER; ++u)
-                if (t0 + u < TT) k4 += 1u << (8 * tile_class(c[u], mean));
-            // a warp holds at most 128 tiles, so the 8-bit fields never carry
-            const uint32_t w4 = __reduce_add_sync(0xffffffffu, k4);
-            if (lane < 4 && ((w4 >> (8 * lane)) & 0xFFu)) atomicAdd_block(&s_cls[lane], (w4 >> (8 * lane)) & 0xFFu);
-        }
-        unsigned long long x = s;
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) wsum[wid] = x;
-        __syncthreads();
-        if (wid == 0) {
-            unsigned long long w = wsum[lane];
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
-                if (lane >= o) w += y;
+    if (sg != 0) return;
+    // warp 0, one lane per tile: scan over the block's tiles, then over the
+    // blocks before it
+    const int lane = tx;
+    const uint32_t c = ok ? tot : 0u;
+    if (ok) F.tile_count[t] = c;
+    uint32_t x = c;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    const unsigned long long agg = __shfl_sync(0xffffffffu, x, 31);
+    unsigned long long prefix = 0;
+    if (blk == 0) {
+        if (lane == 0) atomicExch(&F.scan_st[0], LB_INC | agg);
+    } else {
+        if (lane == 0) atomicExch(&F.scan_st[blk], LB_AGG | agg);
+        // window of 32 blocks, lane l reading block j - l; "before block 0"
+        // reads as an inclusive sum of 0
+        long long j = (long long)blk - 1;
+        bool gave_up = false;
+        for (;;) {
+            const long long jj = j - lane;
+            unsigned long long w = jj >= 0 ? ld_volatile_u64(&F.scan_st[jj]) : LB_INC;
+            uint32_t spins = 0;
+            for (;;) {
+                const bool ready = (w >> 62) != 0;
+                if (__all_sync(0xffffffffu, ready)) break;
+                if (++spins > LB_SPIN_LIMIT) {     // the same count on every lane
+                    gave_up = true;
+                    break;
+                }
+                __nanosleep(64);
+                if (!ready) w = ld_volatile_u64(&F.scan_st[jj]);
             }
-            wsum[lane] = w;
+            if (gave_up) break;
+            // the nearest inclusive sum ends the walk; the aggregates after it add
+            const unsigned inc = __ballot_sync(0xffffffffu, (w >> 62) == 2ull);
+            const int first = inc ? __ffs(inc) - 1 : 31;
+            unsigned long long add = lane <= first ? (w & LB_VAL) : 0ull;
+            for (int o = 16; o > 0; o >>= 1) add += __shfl_xor_sync(0xffffffffu, add, o);
+            prefix += add;
+            if (inc) break;
+            j -= 32;
         }
-        __syncthreads();
-        unsigned long long run = carry + x - s + (wid ? wsum[wid - 1] : 0ull);
-#pragma unroll
-        for (int u = 0; u < ST_PER; ++u) {
-            so[threadIdx.x * ST_PER + u] = static_cast<uint32_t>(run);
-            sc[threadIdx.x * ST_PER + u] = c[u];
-            run += c[u];
+        if (gave_up) {
+            // a predecessor never published: report it; the blends skip the frame
+            if (lane == 0) atomicOr(&hdr->status, STATUS_TIMEOUT | STATUS_OVERFLOW);
+            return;
         }
-        carry += wsum[31];
-        __syncthreads();
-        const uint32_t m = min((uint32_t)ST_ROUND, TT - base);
-        for (uint32_t k = threadIdx.x; k < m; k += blockDim.x) {
-            const uint32_t o = so[k], cc = sc[k];
-            F.tile_offset[base + k] = o;
-            ranges[2 * (size_t)(base + k)] = cc ? o : 0u;
-            ranges[2 * (size_t)(base + k) + 1] = cc ? o + cc : 0u;
-        }
-        __syncthreads();     // so, sc and wsum are reused by the next round
+        if (lane == 0) atomicExch(&F.scan_st[blk], LB_INC | (prefix + agg));
     }
-    // the blends' work order: the length classes longest first, each class in
-    // tile order -- so the longest items do not start last, and neighbouring
-    // tiles still run together.  Only the order in which warps take tiles: no
-    // result depends on it.  (If K exceeds the capacity the blends do not
-    // run; the order is still a permutation.)
-    __shared__ unsigned long long hsum[32];
-    uint32_t cbase[4];
-    {
-        uint32_t run = 0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            cbase[k] = run;      // tiles of the longer classes come first
-            run += s_cls[k];
-        }
+    if (ok) {
+        const unsigned long long o = prefix + x - c;
+        F.tile_offset[t] = static_cast<uint32_t>(o);
+        ranges[2 * (size_t)t] = c ? static_cast<uint32_t>(o) : 0u;
+        ranges[2 * (size_t)t + 1] = c ? static_cast<uint32_t>(o + c) : 0u;
     }
-    for (uint32_t base = 0; base < TT; base += ST_ROUND) {
-        const uint32_t t0 = base + threadIdx.x * ST_PER;
-        uint32_t cls[ST_PER];
-        unsigned long long h = 0;     // per-class counts of this thread's tiles, 16 bits each
+    // the blends' work order: each tile appended to its length class's list
+    // (warp-aggregated; within a class roughly in tile order).  Only the
+    // order in which warps take tiles: no result depends on it.
+    const unsigned long long mean = hdr->n_pairs / (TT ? TT : 1u);
+    const uint32_t cls = ok ? tile_class(c, mean) : 4u;
+    const uint32_t lt = lanemask_lt();
 #pragma unroll
-        for (int u = 0; u < ST_PER; ++u) {
-            cls[u] = t0 + u < TT ? tile_class(F.tile_count[t0 + u], mean) : 4u;
-            if (cls[u] < 4u) h += 1ull << (16 * cls[u]);
-        }
-        // a round holds at most 4096 tiles: the 16-bit fields never carry
-        unsigned long long x = h;
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) hsum[wid] = x;
-        __syncthreads();
-        unsigned long long before = x - h, round_total = 0;
-        for (int w2 = 0; w2 < 32; ++w2) {
-            const unsigned long long y = hsum[w2];
-            if (w2 < wid) before += y;
-            round_total += y;
-        }
-        uint32_t pos[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) pos[k] = cbase[k] + (uint32_t)((before >> (16 * k)) & 0xFFFFu);
-#pragma unroll
-        for (int u = 0; u < ST_PER; ++u) {
-            if (cls[u] < 4u) {
-                uint32_t q = 0;
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (cls[u] == (uint32_t)k) q = pos[k]++;
-                F.torder[q] = t0 + u;
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) cbase[k] += (uint32_t)((round_total >> (16 * k)) & 0xFFFFu);
-        __syncthreads();     // hsum is rewritten by the next round
+    for (uint32_t k = 0; k < 4; ++k) {
+        const unsigned m = __ballot_sync(0xffffffffu, cls == k);
+        if (!m) continue;
+        const int leader = __ffs(m) - 1;
+        uint32_t base = 0;
+        if (lane == leader) base = atomicAdd(&F.scan_ctr[k], (uint32_t)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (cls == k) F.torder[(size_t)k * TT + base + __popc(m & lt)] = t;
     }
-    if (threadIdx.x == 0) {
-        F.tile_offset[TT] = static_cast<uint32_t>(carry);
-        if (carry != F.hdr->n_pairs || carry > cap || carry > 0xFFFFFFFFull) atomicOr(&F.hdr->status, STATUS_OVERFLOW);
+    if (blk == gridDim.x - 1 && lane == 31) {
+        const unsigned long long K = prefix + agg;
+        F.tile_offset[TT] = static_cast<uint32_t>(K);
+        if (K != hdr->n_pairs || K > cap || K > 0xFFFFFFFFull) atomicOr(&hdr->status, STATUS_OVERFLOW);
     }
 }
 
 constexpr size_t DIFF_SMEM_MAX = 200 * 1024;   // difference grid limit (a 4K view needs 131 KB)
 
-void launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long long cap, uint64_t* keys, uint32_t* vals,
-                     uint32_t* ranges, cudaStream_t st)
+// Returns the result of clearing the digit totals (the launches' own errors
+// surface through cudaGetLastError).
+cudaError_t launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long long cap, uint64_t* keys,
+                            uint32_t* vals, uint32_t* ranges, cudaStream_t st)
 {
+    cudaError_t err = cudaSuccess;
     const int64_t n = (int64_t)L.n;
     const int nb = (int)L.n_rs_blocks;
     const uint32_t V = L.n_views;
+    // the radix region: look-back words [V][nb][256], digit totals [4][V][256],
+    // four pass tickets; then (the next array) the tile scan's look-back
+    // words and counters -- one clear for all
+    uint32_t* lbw = F.rs_hist;
+    uint32_t* tot = lbw + (size_t)V * nb * 256;
+    uint32_t* tickets = tot + (size_t)4 * V * 256;
+    err = cudaMemsetAsync(F.rs_hist, 0, reinterpret_cast<const char*>(F.scan_ctr + 8) -
+                                         reinterpret_cast<const char*>(F.rs_hist), st);
+    if (err != cudaSuccess) return err;
     if (n > 0) {
         uint32_t *ki = F.key0, *vi = F.val0, *ko = F.key1, *vo = F.val1;
-        // after the block counts [V][nb][256]: per pass the digit totals
-        // [V][256] and the group sums [V][groups][256] of both levels
-        const size_t n1 = (size_t)V * 256 * rs_groups(nb, RS_G1), n2 = (size_t)V * 256 * rs_groups(nb, RS_G2);
-        const size_t per_pass = (size_t)V * 256 + n1 + n2;
-        uint32_t* sums = F.rs_hist + (size_t)V * 256 * nb;
-        cudaMemsetAsync(sums, 0, sizeof(uint32_t) * 4 * per_pass, st);
+        k_rs_hist_all<<<V * nb, RS_THREADS, 0, st>>>(F.hdr, ki, n, nb, (int)V, tot);
         for (int pass = 0; pass < 4; ++pass) {
-            uint32_t* tot = sums + (size_t)pass * per_pass;
-            uint32_t* s1 = tot + (size_t)V * 256;
-            uint32_t* s2 = s1 + n1;
-            k_rs_hist<<<V * nb, RS_THREADS, 0, st>>>(F.hdr, F.n_surv, ki, n, nb, 8 * pass, F.rs_hist, tot, s1, s2);
+            const uint32_t* tp = tot + (size_t)pass * V * 256;
             if (pass == 3)
-                k_rs_scatter<true><<<V * nb, RS_THREADS, 0, st>>>(F.hdr, F.n_surv, ki, vi, ko, vo, n, nb, 8 * pass,
-                                                                  F.rs_hist, tot, s1, s2, F.rect, F.srect);
+                k_rs_scatter<true><<<V * nb, RS_THREADS, 0, st>>>(F.hdr, F.n_surv, ki, vi, ko, vo, n, nb, pass, tp, lbw,
+                                                                  tickets + pass, F.rect, F.srect);
             else
-                k_rs_scatter<false><<<V * nb, RS_THREADS, 0, st>>>(F.hdr, F.n_surv, ki, vi, ko, vo, n, nb, 8 * pass,
-                                                                   F.rs_hist, tot, s1, s2, nullptr, nullptr);
+                k_rs_scatter<false><<<V * nb, RS_THREADS, 0, st>>>(F.hdr, F.n_surv, ki, vi, ko, vo, n, nb, pass, tp,
+                                                                   lbw, tickets + pass, nullptr, nullptr);
             std::swap(ki, ko);
             std::swap(vi, vo);
         }
@@ -754,9 +754,9 @@ void launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long long ca
         k_chunk_count<<<V * L.n_chunks, 512, L.diff_grid_max * sizeof(uint32_t), st>>>(F);
     else
         k_rows<false><<<L.rb_total, ROWS_PER_BLOCK * 32, smem, st>>>(F, nullptr, nullptr);
-    k_chunk_scan<<<(L.total_tiles + CS_TILES - 1) / CS_TILES, CS_TILES * CS_SEG, 0, st>>>(F);
-    k_scan_tiles<<<1, 1024, 0, st>>>(F, ranges, cap);
+    k_tile_scan<<<(L.total_tiles + CS_TILES - 1) / CS_TILES, CS_TILES * CS_SEG, 0, st>>>(F, ranges, cap);
     k_rows<true><<<L.rb_total, ROWS_PER_BLOCK * 32, smem, st>>>(F, vals, reinterpret_cast<unsigned long long*>(keys));
+    return err;
 }
 
 cudaError_t bin_sort_setup()

@@ -16,8 +16,8 @@ void launch_frame_setup(const Frame& F, void* ws, const FrameHeader& h, const Vi
                         size_t zero_end, int n_sm, cudaStream_t st);
 void launch_preprocess(const Frame& F, const clod_scene& S, uint32_t V, uint8_t* mask_out, float* alpha_out,
                        unsigned long long* n_pairs_out, int n_sm, cudaStream_t st, bool select);
-void launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long long cap, uint64_t* keys, uint32_t* vals,
-                     uint32_t* ranges, cudaStream_t st);
+cudaError_t launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long long cap, uint64_t* keys,
+                            uint32_t* vals, uint32_t* ranges, cudaStream_t st);
 void launch_blend_fwd(const Frame& F, const uint32_t* vals, const uint32_t* ranges, float* image, float* Tout,
                       uint32_t* ncout, unsigned long long* evaluated, int n_sm, cudaStream_t st, bool fast);
 cudaError_t bin_sort_setup();
@@ -79,7 +79,7 @@ FrameLayout frame_layout(uint64_t n, uint32_t V, uint32_t TT, uint32_t rb_total,
     L.tile_count = take(sizeof(uint32_t) * (size_t)TT);
     L.views = take(sizeof(ViewDev) * V);
     L.tile_offset = take(sizeof(uint32_t) * ((size_t)TT + 1));
-    L.torder = take(sizeof(uint32_t) * (size_t)TT);
+    L.torder = take(sizeof(uint32_t) * 4 * (size_t)TT);
     const size_t vn = (size_t)V * n;
     L.rec0 = take(sizeof(float4) * vn);
     L.rec1 = take(sizeof(float4) * vn);
@@ -95,6 +95,9 @@ FrameLayout frame_layout(uint64_t n, uint32_t V, uint32_t TT, uint32_t rb_total,
     const int nbk = (int)L.n_rs_blocks;
     L.rs_hist = take(sizeof(uint32_t) * 256 * (size_t)V *
                      ((size_t)nbk + 4 * (1 + (size_t)rs_groups(nbk, RS_G1) + (size_t)rs_groups(nbk, RS_G2))));
+    // tile scan (right after the radix sums: one clear covers both): look-back
+    // words of the blocks of 32 tiles, then the class counters and the ticket
+    L.scan = take(sizeof(unsigned long long) * (((size_t)TT + 31) / 32) + sizeof(uint32_t) * 8);
     L.cnt = take(sizeof(uint32_t) * (size_t)L.n_chunks * TT);
     L.sel = take(sizeof(SelState) * V);
     L.sel_hist = take(sizeof(uint32_t) * SEL_BINS * (size_t)V);
@@ -127,6 +130,8 @@ Frame frame_ptrs(void* ws, const FrameLayout& L)
     F.val1 = reinterpret_cast<uint32_t*>(b + L.val1);
     F.srect = reinterpret_cast<uint2*>(b + L.srect);
     F.rs_hist = reinterpret_cast<uint32_t*>(b + L.rs_hist);
+    F.scan_st = reinterpret_cast<unsigned long long*>(b + L.scan);
+    F.scan_ctr = reinterpret_cast<uint32_t*>(b + L.scan + sizeof(unsigned long long) * (((size_t)L.total_tiles + 31) / 32));
     F.cnt = reinterpret_cast<uint32_t*>(b + L.cnt);
     F.sel = reinterpret_cast<SelState*>(b + L.sel);
     F.sel_hist = reinterpret_cast<uint32_t*>(b + L.sel_hist);
@@ -282,7 +287,7 @@ static void make_view_table(const clod_view* views, int32_t V, uint64_t n, std::
 static clod_status check_scene(const clod_scene* S)
 {
     if (!S) return fail(CLOD_ERR_ARG, "scene is NULL");
-    if (S->n < 0 || S->n >= (1ll << 31)) return fail(CLOD_ERR_ARG, "scene n = %lld outside [0, 2^31)", (long long)S->n);
+    if (S->n < 0 || S->n >= (1ll << 28)) return fail(CLOD_ERR_ARG, "scene n = %lld outside [0, 2^28)", (long long)S->n);
     if (S->sh_degree < 0 || S->sh_degree > 3) return fail(CLOD_ERR_ARG, "sh_degree %d outside [0, 3]", S->sh_degree);
     if (S->n > 0 && (!S->means || !S->scales || !S->quats || !S->opacity || !S->sh || !S->decay))
         return fail(CLOD_ERR_ARG, "scene array pointer is NULL");
@@ -338,7 +343,7 @@ clod_status clod_frame_workspace_size(int64_t n, const clod_view* views, int32_t
                                       clod_frame_layout* layout)
 {
     if (!bytes) return fail(CLOD_ERR_ARG, "bytes is NULL");
-    if (n < 0 || n >= (1ll << 31)) return fail(CLOD_ERR_ARG, "n = %lld outside [0, 2^31)", (long long)n);
+    if (n < 0 || n >= (1ll << 28)) return fail(CLOD_ERR_ARG, "n = %lld outside [0, 2^28)", (long long)n);
     ViewGeom G;
     clod_status s = check_views(views, n_views, (uint64_t)n, &G);
     if (s) return s;
@@ -422,8 +427,9 @@ clod_status clod_bin_sort(void* ws, uint64_t pair_capacity, uint64_t* keys_out, 
     clod_status s = device_ready(&n_sm);
     if (s) return s;
     const Frame F = frame_ptrs(ws, L);
-    launch_bin_sort(F, L, pair_capacity, keys_out, vals_out, ranges_out, static_cast<cudaStream_t>(stream));
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_bin_sort(F, L, pair_capacity, keys_out, vals_out, ranges_out, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "clod_bin_sort clear");
+    e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "clod_bin_sort launch");
     return CLOD_OK;
 }
@@ -469,17 +475,17 @@ clod_status clod_frame_check(const void* ws, uint64_t pair_capacity, uint64_t* n
     e = cudaMemcpy(&h, ws, sizeof(h), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "clod_frame_check read");
     if (n_pairs) *n_pairs = h.n_pairs;
+    if (h.status & STATUS_TIMEOUT) return fail(CLOD_ERR_TIMEOUT, "a device wait gave up");
     if ((h.status & STATUS_OVERFLOW) || h.n_pairs > pair_capacity)
         return fail(CLOD_ERR_CAPACITY, "frame needs %llu pairs, capacity %llu", (unsigned long long)h.n_pairs,
                     (unsigned long long)pair_capacity);
-    if (h.status & STATUS_TIMEOUT) return fail(CLOD_ERR_TIMEOUT, "a device wait gave up");
     return CLOD_OK;
 }
 
 clod_status clod_backward_workspace_size(int64_t n, int32_t n_views, size_t* bytes)
 {
     if (!bytes) return fail(CLOD_ERR_ARG, "bytes is NULL");
-    if (n < 0 || n >= (1ll << 31)) return fail(CLOD_ERR_ARG, "n = %lld outside [0, 2^31)", (long long)n);
+    if (n < 0 || n >= (1ll << 28)) return fail(CLOD_ERR_ARG, "n = %lld outside [0, 2^28)", (long long)n);
     if (n_views < 1 || n_views > MAX_VIEWS) return fail(CLOD_ERR_ARG, "n_views = %d outside [1, %d]", n_views, MAX_VIEWS);
     *bytes = backward_ws_bytes((uint64_t)n, (uint32_t)n_views);
     return CLOD_OK;

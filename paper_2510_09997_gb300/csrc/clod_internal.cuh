@@ -78,7 +78,7 @@ struct SelState {
 
 struct FrameLayout {
     size_t header, views, dmax_key, n_surv, rec0, rec1, rec2, depth, rect, tile_count, tile_offset, torder,
-        key0, val0, key1, val1, srect, rs_hist, cnt, sel, sel_hist, total;
+        key0, val0, key1, val1, srect, rs_hist, scan, cnt, sel, sel_hist, total;
     uint32_t total_tiles, n_views, n_chunks, n_rs_blocks, rb_total, max_tx;
     uint32_t fast_exp;      // host only: the frame's views carry CLOD_FAST_EXP
     uint64_t n;
@@ -98,7 +98,9 @@ struct Frame {
     uint2* rect;
     uint32_t* tile_count;
     uint32_t* tile_offset;
-    uint32_t* torder;       // the blends' work order: tiles by descending list length
+    uint32_t* torder;       // the blends' work order: four class lists of capacity total_tiles
+    unsigned long long* scan_st;  // tile scan: per block of 32 tiles, look-back flag and value
+    uint32_t* scan_ctr;     // [0..3] tiles per length class, [4] tile-scan block ticket
     uint32_t* key0;         // depth-rank sort ping-pong: keys (depth bits) / values (index)
     uint32_t* val0;
     uint32_t* key1;
@@ -109,6 +111,21 @@ struct Frame {
     SelState* sel;          // primitive-budget select state [view]
     uint32_t* sel_hist;     // its digit counts [view][SEL_BINS]
 };
+
+// Tile of the blends' i-th work item.  The tile scan writes the work order
+// as four class lists (longest tile lists first), list k at torder + k TT
+// holding scan_ctr[k] tiles; together they hold every tile once.
+__device__ __forceinline__ uint32_t work_tile(const Frame& F, uint32_t i, uint32_t TT)
+{
+    uint32_t k = 0;
+    while (k < 3) {
+        const uint32_t c = F.scan_ctr[k];
+        if (i < c) break;
+        i -= c;
+        ++k;
+    }
+    return F.torder[(size_t)k * TT + i];
+}
 
 // Key of the primitive-budget order: larger key = kept first (alpha''
 // descending, then index ascending).  alpha'' >= 0, so its bits order like

@@ -12,9 +12,10 @@
 // Limits: at most NA_MAX_GAUSSIANS Gaussians, NA_MAX_SIDE pixels per side and
 // NA_MAX_PAIRS (view, tile, Gaussian) pairs.  Calls share the array, so calls
 // whose work overlaps on the GPU (different streams, or different host
-// threads) race; serialise them.  The first call on a device looks up the
-// array's device address (with that device current); make that first call
-// before any stream capture.
+// threads) race; serialise them.  A call is synchronous: it waits for the
+// frame on its stream and reads the frame header back to report overflow.
+// The first call on a device also looks up the array's device address (with
+// that device current); make that first call before any stream capture.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -25,8 +26,8 @@ namespace clod {
 
 void launch_preprocess(const Frame& F, const clod_scene& S, uint32_t V, uint8_t* mask_out, float* alpha_out,
                        unsigned long long* n_pairs_out, int n_sm, cudaStream_t st, bool select);
-void launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long long cap, uint64_t* keys, uint32_t* vals,
-                     uint32_t* ranges, cudaStream_t st);
+cudaError_t launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long long cap, uint64_t* keys,
+                            uint32_t* vals, uint32_t* ranges, cudaStream_t st);
 void launch_blend_fwd(const Frame& F, const uint32_t* vals, const uint32_t* ranges, float* image, float* Tout,
                       uint32_t* ncout, unsigned long long* evaluated, int n_sm, cudaStream_t st, bool fast);
 clod_status fail(clod_status s, const char* fmt, ...);
@@ -57,6 +58,17 @@ static clod_status noalloc_scratch(void** out)
     if (dev < 0 || dev >= 64) return fail(CLOD_ERR_CUDA, "device index %d out of range", dev);
     std::lock_guard<std::mutex> lk(g_na_mu);
     if (!g_na_ptr[dev]) {
+        // the largest admissible frame (NA_MAX_GAUSSIANS, NA_MAX_SIDE^2 pixels)
+        // must fit the frame part of the array; checked once, so that a
+        // change of the workspace layout cannot silently shrink the limits
+        const uint32_t ch = (uint32_t)std::min<int64_t>((NA_MAX_GAUSSIANS + 1023) / 1024, MAX_CHUNKS);
+        const int side = NA_MAX_SIDE / TILE;
+        const FrameLayout big = frame_layout(NA_MAX_GAUSSIANS, 1, (uint32_t)NA_MAX_TILES,
+                                             ch * (uint32_t)((side + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK),
+                                             (uint32_t)side, (size_t)(side + 1) * (side + 1));
+        if (big.total > NA_FRAME_BYTES)
+            return fail(CLOD_ERR_CUDA, "clod_render_noalloc: the largest frame needs %zu bytes, the array holds %zu",
+                        big.total, NA_FRAME_BYTES);
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
@@ -125,7 +137,8 @@ extern "C" clod_status clod_render_noalloc(const clod_scene* scene, const clod_v
     if (e == cudaSuccess) e = cudaMemcpyAsync(F.views, &vd, sizeof(vd), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "clod_render_noalloc upload");
     launch_preprocess(F, *scene, 1, nullptr, nullptr, nullptr, n_sm, st, w.budget > 0);
-    launch_bin_sort(F, L, NA_MAX_PAIRS, nullptr, vals, ranges, st);
+    if ((e = launch_bin_sort(F, L, NA_MAX_PAIRS, nullptr, vals, ranges, st)) != cudaSuccess)
+        return cuda_fail(e, "clod_render_noalloc sort clear");
     launch_blend_fwd(F, vals, ranges, image, T_final, n_contrib, nullptr, n_sm, st, (view->flags & CLOD_FAST_EXP) != 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "clod_render_noalloc launch");
     // the pair count is data dependent: wait for the frame and report overflow

@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(BLEND_THREADS) k_blend_fwd(Frame F, const uint
         if (lane == 0) unit = atomicAdd(&F.hdr->work[0], 1u);
         unit = __shfl_sync(0xffffffffu, unit, 0);
         if ((unit >> 2) >= TT) break;
-        const uint32_t t = F.torder[unit >> 2];     // longest tile lists first
+        const uint32_t t = work_tile(F, unit >> 2, TT);     // longest tile lists first
         const int qd = (int)(unit & 3u);
         int view = 0;
         for (uint32_t u = 1; u < V; ++u)

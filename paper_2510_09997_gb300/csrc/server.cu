@@ -16,8 +16,10 @@
 // largest batch; the kernels take the batch's actual sizes from the frame
 // header uploaded by the graph's first node, so the one graph replays for
 // every batch shape.  A batch whose pairs exceed the slot's capacity is
-// split: its requests are re-run alone, and a request that still does not
-// fit is rendered through a buffer sized from its pair count.
+// split: its requests are re-run alone by a second thread with a stream,
+// workspace and pair buffer of its own (the buffer grows, stream-ordered, to
+// the largest pair count met), so the re-runs overlap the batches that the
+// worker keeps admitting.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -34,8 +36,8 @@ namespace clod {
 
 void launch_preprocess(const Frame& F, const clod_scene& S, uint32_t V, uint8_t* mask_out, float* alpha_out,
                        unsigned long long* n_pairs_out, int n_sm, cudaStream_t st, bool select);
-void launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long long cap, uint64_t* keys, uint32_t* vals,
-                     uint32_t* ranges, cudaStream_t st);
+cudaError_t launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long long cap, uint64_t* keys,
+                            uint32_t* vals, uint32_t* ranges, cudaStream_t st);
 void launch_blend_fwd(const Frame& F, const uint32_t* vals, const uint32_t* ranges, float* image, float* Tout,
                       uint32_t* ncout, unsigned long long* evaluated, int n_sm, cudaStream_t st, bool fast);
 clod_status fail(clod_status s, const char* fmt, ...);
@@ -62,7 +64,6 @@ struct Request {
     uint32_t rendered = 0;
     uint64_t pairs = 0;
     bool done = false;
-    bool solo = false;
 };
 
 struct Slot {
@@ -89,6 +90,13 @@ using namespace clod;
 struct clod_server {
     clod_scene scene{};
     clod_server_cfg cfg{};
+    // re-runs of requests whose batch overflowed its pair capacity
+    std::deque<uint64_t> solo_q;
+    std::condition_variable cv_solo;
+    std::thread solo_worker;
+    clod::Slot solo;                 // its stream, workspace (one view of the largest size), staging
+    uint32_t* solo_vals = nullptr;   // pair buffer, grown with cudaMallocAsync on the solo stream
+    uint64_t solo_cap = 0;
     int device = 0;
     int n_sm = 0;
     uint32_t max_tiles = 0, max_rb = 0, max_tx = 0;
@@ -180,6 +188,27 @@ static clod_status slot_init(clod_server* S, Slot& sl)
     return CLOD_OK;
 }
 
+// The solo lane: a stream, a workspace for one view of the largest size,
+// ranges for its tiles and pinned staging; its pair buffer is allocated on
+// first use.
+static clod_status solo_init(clod_server* S)
+{
+    Slot& sl = S->solo;
+    cudaError_t e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "server solo stream");
+    const uint32_t TX = S->max_tx, TY = (uint32_t)((S->cfg.max_height + TILE - 1) / TILE);
+    const uint32_t rb = chunks_for((uint64_t)S->scene.n) * ((TY + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK);
+    sl.L = frame_layout((uint64_t)S->scene.n, 1, TX * TY, rb, TX, S->max_diff);
+    if ((e = cudaMalloc(&sl.ws, sl.L.total)) != cudaSuccess) return cuda_fail(e, "server solo workspace");
+    if ((e = cudaMalloc(&sl.ranges, sizeof(uint32_t) * 2 * (size_t)TX * TY)) != cudaSuccess)
+        return cuda_fail(e, "server solo ranges");
+    if ((e = cudaMallocHost(&sl.h_views, sizeof(ViewDev))) != cudaSuccess) return cuda_fail(e, "pinned views");
+    if ((e = cudaMallocHost(&sl.h_hdr_down, sizeof(FrameHeader))) != cudaSuccess) return cuda_fail(e, "pinned header");
+    if ((e = cudaMallocHost(&sl.h_counts, sizeof(uint32_t) * 2)) != cudaSuccess) return cuda_fail(e, "pinned counts");
+    std::memset(sl.h_views, 0, sizeof(ViewDev));
+    return CLOD_OK;
+}
+
 static void slot_free(Slot& sl)
 {
     if (sl.graph) cudaGraphExecDestroy(sl.graph);
@@ -196,9 +225,13 @@ static void slot_free(Slot& sl)
     if (sl.stream) cudaStreamDestroy(sl.stream);
 }
 
-// Renders one request alone with a pair buffer of its own (overflow path).
-static clod_status render_alone(clod_server* S, Slot& sl, Request& r)
+// Renders one request alone on the solo lane (overflow path): its pair
+// count is read back after preprocessing, the lane's pair buffer grows
+// (stream-ordered: no device-wide synchronisation) when it is too small, then
+// sort and blend.  Runs on the solo thread; other slots keep running.
+static clod_status render_alone(clod_server* S, Request& r)
 {
+    Slot& sl = S->solo;
     const clod_view& w = r.view;
     const int TX = (w.width + TILE - 1) / TILE, TY = (w.height + TILE - 1) / TILE;
     const uint32_t CH = chunks_for((uint64_t)S->scene.n);
@@ -209,38 +242,65 @@ static clod_status render_alone(clod_server* S, Slot& sl, Request& r)
     FrameHeader h;
     fill_views(S, one, sl, h);
     h.max_tx = (uint32_t)TX;
-    const Frame F = frame_ptrs(sl.ws, L);   // a one-view layout fits inside the slot's workspace
+    const Frame F = frame_ptrs(sl.ws, L);   // the lane's workspace holds one view of the largest size
     cudaStream_t st = sl.stream;
     cudaMemsetAsync(sl.ws, 0, L.views, st);
     cudaMemcpyAsync(F.hdr, &h, sizeof(h), cudaMemcpyHostToDevice, st);
     cudaMemcpyAsync(F.views, sl.h_views, sizeof(ViewDev), cudaMemcpyHostToDevice, st);
     launch_preprocess(F, S->scene, 1, nullptr, nullptr, nullptr, S->n_sm, st, one[0]->view.budget > 0);
-    unsigned long long K = 0;
-    cudaMemcpyAsync(&K, &F.hdr->n_pairs, sizeof(K), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(sl.h_hdr_down, F.hdr, sizeof(FrameHeader), cudaMemcpyDeviceToHost, st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "render_alone");
-    uint32_t* vals = nullptr;
-    uint32_t* ranges = nullptr;
-    if ((e = cudaMalloc(&vals, sizeof(uint32_t) * std::max<unsigned long long>(K, 1))) != cudaSuccess)
-        return cuda_fail(e, "render_alone pairs");
-    if ((e = cudaMalloc(&ranges, sizeof(uint32_t) * 2 * (size_t)TX * TY)) != cudaSuccess) {
-        cudaFree(vals);
-        return cuda_fail(e, "render_alone ranges");
+    const unsigned long long K = sl.h_hdr_down->n_pairs;
+    if (K > 0xFFFFFFFFull) return CLOD_ERR_CAPACITY;
+    if (K > S->solo_cap) {
+        const uint64_t cap = std::min<uint64_t>(0xFFFFFFFFull, K + K / 4 + 1024);
+        if (S->solo_vals) cudaFreeAsync(S->solo_vals, st);
+        S->solo_vals = nullptr;
+        S->solo_cap = 0;
+        if ((e = cudaMallocAsync(reinterpret_cast<void**>(&S->solo_vals), sizeof(uint32_t) * cap, st)) != cudaSuccess)
+            return cuda_fail(e, "render_alone pairs");
+        S->solo_cap = cap;
     }
-    launch_bin_sort(F, L, K, nullptr, vals, ranges, st);
-    launch_blend_fwd(F, vals, ranges, nullptr, nullptr, nullptr, nullptr, S->n_sm, st, S->cfg.fast_exp != 0);
-    FrameHeader out;
-    cudaMemcpyAsync(&out, F.hdr, sizeof(out), cudaMemcpyDeviceToHost, st);
-    uint32_t cnt[2] = {0, 0};
-    cudaMemcpyAsync(cnt, F.n_surv, sizeof(cnt), cudaMemcpyDeviceToHost, st);
-    e = cudaStreamSynchronize(st);
-    cudaFree(vals);
-    cudaFree(ranges);
-    if (e != cudaSuccess) return cuda_fail(e, "render_alone");
-    r.pairs = out.n_pairs;
-    r.rendered = cnt[1];
-    if (out.status & STATUS_OVERFLOW) return CLOD_ERR_CAPACITY;
+    launch_bin_sort(F, L, S->solo_cap, nullptr, S->solo_vals, sl.ranges, st);
+    launch_blend_fwd(F, S->solo_vals, sl.ranges, nullptr, nullptr, nullptr, nullptr, S->n_sm, st, S->cfg.fast_exp != 0);
+    cudaMemcpyAsync(sl.h_hdr_down, F.hdr, sizeof(FrameHeader), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(sl.h_counts, F.n_surv, sizeof(uint32_t) * 2, cudaMemcpyDeviceToHost, st);
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "render_alone");
+    r.pairs = sl.h_hdr_down->n_pairs;
+    r.rendered = sl.h_counts[1];
+    if (sl.h_hdr_down->status & STATUS_OVERFLOW) return CLOD_ERR_CAPACITY;
     return CLOD_OK;
+}
+
+// The solo thread: re-runs, in arrival order, the requests of overflowed batches.
+static void solo_main(clod_server* S)
+{
+    cudaSetDevice(S->device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    while (!S->stop) {
+        if (S->solo_q.empty()) {
+            S->cv_solo.wait(lk);
+            continue;
+        }
+        const uint64_t tk = S->solo_q.front();
+        S->solo_q.pop_front();
+        Request copy = S->reqs[tk];
+        copy.t_launch = now_us();
+        copy.batch = 1;
+        lk.unlock();
+        const clod_status st = render_alone(S, copy);
+        lk.lock();
+        Request& r = S->reqs[tk];
+        r.t_launch = copy.t_launch;
+        r.batch = 1;
+        r.pairs = copy.pairs;
+        r.rendered = copy.rendered;
+        r.status = st;
+        r.done = true;
+        r.t_done = now_us();
+        S->cv_done.notify_all();
+    }
 }
 
 static void worker_main(clod_server* S)
@@ -257,18 +317,17 @@ static void worker_main(clod_server* S)
             const bool overflow = (sl.h_hdr_down->status & STATUS_OVERFLOW) != 0;
             for (size_t k = 0; k < sl.tickets.size(); ++k) {
                 Request& r = S->reqs[sl.tickets[k]];
-                if (overflow) {
-                    r.solo = true;
-                    continue;
-                }
+                if (overflow) continue;     // re-run on the solo lane below
                 r.done = true;
                 r.t_done = t;
                 r.status = CLOD_OK;
                 r.pairs = sl.h_hdr_down->n_pairs;
                 r.rendered = sl.h_counts[2 * k + 1];
             }
-            if (overflow)   // re-run each request alone, keeping arrival order
-                for (size_t k = sl.tickets.size(); k-- > 0;) S->pending.push_front(sl.tickets[k]);
+            if (overflow) {   // re-run each request alone on the solo lane, in arrival order
+                for (uint64_t tk : sl.tickets) S->solo_q.push_back(tk);
+                S->cv_solo.notify_one();
+            }
             sl.tickets.clear();
             sl.busy = false;
             progress = true;
@@ -278,22 +337,6 @@ static void worker_main(clod_server* S)
         for (Slot& sl : S->slots) {
             if (sl.busy || S->pending.empty()) continue;
             Request& first = S->reqs[S->pending.front()];
-            if (first.solo) {
-                const uint64_t tk = S->pending.front();
-                S->pending.pop_front();
-                first.t_launch = now_us();
-                first.batch = 1;
-                lk.unlock();
-                const clod_status st = render_alone(S, sl, first);
-                lk.lock();
-                Request& r = S->reqs[tk];
-                r.status = st;
-                r.done = true;
-                r.t_done = now_us();
-                S->cv_done.notify_all();
-                progress = true;
-                continue;
-            }
             if (S->cfg.batch_window_us > 0 && (int)S->pending.size() < S->cfg.max_views_per_batch &&
                 now_us() - first.t_submit < S->cfg.batch_window_us)
                 continue;   // wait a little for more requests to share the launch
@@ -302,7 +345,7 @@ static void worker_main(clod_server* S)
             while (!S->pending.empty() && (int)batch.size() < S->cfg.max_views_per_batch) {
                 Request& r = S->reqs[S->pending.front()];
                 const uint64_t p = (uint64_t)r.view.width * r.view.height;
-                if (r.solo || (!batch.empty() && pixels + p > S->cfg.max_pixels_per_batch)) break;
+                if (!batch.empty() && pixels + p > S->cfg.max_pixels_per_batch) break;
                 pixels += p;
                 batch.push_back(&r);
                 sl.tickets.push_back(S->pending.front());
@@ -357,7 +400,7 @@ extern "C" {
 clod_status clod_server_create(const clod_scene* scene, const clod_server_cfg* cfg, clod_server** out)
 {
     if (!scene || !cfg || !out) return fail(CLOD_ERR_ARG, "NULL argument to clod_server_create");
-    if (scene->n < 0 || scene->n >= (1ll << 31) || scene->sh_degree < 0 || scene->sh_degree > 3)
+    if (scene->n < 0 || scene->n >= (1ll << 28) || scene->sh_degree < 0 || scene->sh_degree > 3)
         return fail(CLOD_ERR_ARG, "bad scene");
     if (scene->n > 0 && (!scene->means || !scene->scales || !scene->quats || !scene->opacity || !scene->sh || !scene->decay))
         return fail(CLOD_ERR_ARG, "scene array pointer is NULL");
@@ -390,7 +433,14 @@ clod_status clod_server_create(const clod_scene* scene, const clod_server_cfg* c
             return s;
         }
     }
+    if ((s = solo_init(S)) != CLOD_OK) {
+        for (Slot& q : S->slots) slot_free(q);
+        slot_free(S->solo);
+        delete S;
+        return s;
+    }
     S->worker = std::thread(worker_main, S);
+    S->solo_worker = std::thread(solo_main, S);
     *out = S;
     return CLOD_OK;
 }
@@ -470,8 +520,15 @@ clod_status clod_server_destroy(clod_server* S)
         S->stop = true;
     }
     S->cv_work.notify_all();
+    S->cv_solo.notify_all();
     if (S->worker.joinable()) S->worker.join();
+    if (S->solo_worker.joinable()) S->solo_worker.join();
     for (Slot& sl : S->slots) slot_free(sl);
+    if (S->solo_vals) {
+        cudaFreeAsync(S->solo_vals, S->solo.stream);
+        cudaStreamSynchronize(S->solo.stream);
+    }
+    slot_free(S->solo);
     delete S;
     return CLOD_OK;
 }
