@@ -113,7 +113,7 @@ def parse():
     p.add_argument("--serve-seconds", type=float, default=10.0, help="length of the 2000 requests/s trace")
     p.add_argument("--serve-sweep-seconds", type=float, default=2.0, help="length of each trace of the rate sweep")
     p.add_argument("--serve-slots", type=int, default=6, help="server slots (batches in flight)")
-    p.add_argument("--serve-pairs", type=int, default=1 << 26, help="pair capacity of a server slot")
+    p.add_argument("--serve-pairs", type=int, default=1 << 28, help="pair capacity of a server slot")
     p.add_argument("--no-city", action="store_true")
     p.add_argument("--frame", default=None, help="CAM:S -- time only that frame of the sweep (profiling)")
     p.add_argument("--inflight", type=int, default=8, help="frames in flight (renderers and streams)")
@@ -868,7 +868,8 @@ def serve_leg(args):
            "latency": "completion minus scheduled arrival",
            "sustained": "all requests done without falling 2 s behind, and >= 95% of the arrival rate delivered"}
     res["at_2000_per_s"] = measure(rate, args.serve_seconds)
-    sweep = [measure(lam, args.serve_sweep_seconds) for lam in (250.0, 500.0, 1000.0, 1500.0, 2000.0, 2500.0, 3000.0)]
+    sweep = [measure(lam, args.serve_sweep_seconds)
+             for lam in (100.0, 200.0, 300.0, 500.0, 750.0, 1000.0, 1500.0, 2000.0, 2500.0)]
     res["sweep"] = sweep
     best = {}
     for path in ("server", "plain"):

@@ -65,7 +65,7 @@ typedef void* clod_stream;     /* cudaStream_t */
 /* A resident Gaussian scene (Sec. 3.1 primitives plus the per-Gaussian decay
  * sigma_d of Sec. 3.2).  All arrays are device memory, float32, row-major. */
 typedef struct clod_scene {
-    int64_t n;              /* number of Gaussians, 0 <= n < 2^28               */
+    int64_t n;              /* number of Gaussians, 0 <= n < 2^31               */
     int32_t sh_degree;      /* 0..3                                             */
     int32_t reserved;
     const float* means;     /* n x 3                                            */

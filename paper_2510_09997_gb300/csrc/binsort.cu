@@ -108,91 +108,77 @@ __device__ __forceinline__ void rs_warp_counts(const uint32_t (&kk)[RS_R], int s
     }
 }
 
-// All four digit histograms of the survivors' depth keys, per view, in one
-// read of the keys (the first pass's input: all n keys of every view,
-// culled ones keyed all ones and skipped): tot[pass][view][digit].  Each
-// warp counts its keys' digits with one vote per bit and adds them into
-// shared counters; the block then adds its non-zero counters to tot.
-__global__ void __launch_bounds__(RS_THREADS) k_rs_hist_all(const FrameHeader* __restrict__ hdr,
-                                                            const uint32_t* __restrict__ keys, int64_t n, int nb,
-                                                            int Vl, uint32_t* __restrict__ tot)
+__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const FrameHeader* __restrict__ hdr,
+                                                        const uint32_t* __restrict__ n_surv,
+                                                        const uint32_t* __restrict__ keys, int64_t n, int nb, int shift,
+                                                        uint32_t* __restrict__ hist, uint32_t* __restrict__ totals,
+                                                        uint32_t* __restrict__ sum1, uint32_t* __restrict__ sum2)
 {
-    __shared__ uint32_t h[4][256];
-    for (int k = threadIdx.x; k < 1024; k += blockDim.x) h[k >> 8][k & 255] = 0u;
-    __syncthreads();
+    __shared__ uint32_t h[RS_THREADS / 32][256];
     const int b = blockIdx.x, v = b / nb, lb = b % nb;
-    const bool live = (uint32_t)v < hdr->n_views;
-    const int lane = threadIdx.x & 31;
-    if (live) {
-        const int cnt = rs_first_count(n, lb);
-        uint32_t kk[RS_R];
-        rs_load_keys(keys, (int64_t)v * n + (int64_t)lb * RS_ITEMS, cnt, kk);
-#pragma unroll
-        for (int r = 0; r < RS_R; ++r) {
-            const bool valid = kk[r] != 0xFFFFFFFFu;
-#pragma unroll
-            for (int p = 0; p < 4; ++p) {
-                const uint32_t d = valid ? ((kk[r] >> (8 * p)) & 255u) : 256u;
-                const uint32_t peers = match_bits<9>(d);
-                if (valid && (__ffs(peers) - 1) == lane) atomicAdd_block(&h[p][d], __popc(peers));
-            }
-        }
+    const int64_t base = (int64_t)v * n + (int64_t)lb * RS_ITEMS;
+    // the first pass's keys are loaded before the view check (its count needs
+    // no load); a later pass reads its count first, so blocks past the
+    // survivors move no data
+    uint32_t kk[RS_R];
+    int cnt;
+    if (shift == 0) {
+        cnt = rs_first_count(n, lb);
+        rs_load_keys(keys, base, cnt, kk);
+        if ((uint32_t)v >= hdr->n_views) return;
+    } else {
+        if ((uint32_t)v >= hdr->n_views) return;
+        cnt = rs_later_count(n_surv, v, lb);
+        if (cnt == 0) return;
+        rs_load_keys(keys, base, cnt, kk);
     }
+    if (cnt == 0) return;     // no items (and none in any later block)
+    rs_warp_counts(kk, shift, h);
     __syncthreads();
-    if (!live) return;
-    for (int k = threadIdx.x; k < 1024; k += blockDim.x) {
-        const uint32_t c = h[k >> 8][k & 255];
-        if (c) atomicAdd(&tot[((size_t)(k >> 8) * Vl + v) * 256 + (k & 255)], c);
+    uint32_t s = 0;
+    for (int w = 0; w < RS_THREADS / 32; ++w) s += h[w][threadIdx.x];
+    hist[((size_t)v * nb + lb) * 256 + threadIdx.x] = s;
+    if (s) {
+        atomicAdd(&totals[v * 256 + threadIdx.x], s);
+        atomicAdd(&sum1[((size_t)v * rs_groups(nb, RS_G1) + lb / RS_G1) * 256 + threadIdx.x], s);
+        atomicAdd(&sum2[((size_t)v * rs_groups(nb, RS_G2) + lb / RS_G2) * 256 + threadIdx.x], s);
     }
-}
-
-// Look-back words of the scatter passes, one per (view, block, digit): a
-// flag (the block's own count, or the count of the view's blocks up to and
-// including it), the pass (the words of a frame are cleared once and reused
-// by the four passes) and the count.
-constexpr uint32_t RS_AGG = 1u << 30, RS_INC = 2u << 30, RS_VAL = (1u << 28) - 1;
-constexpr uint32_t RS_SPIN_LIMIT = 1u << 20;
-
-__device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p)
-{
-    return *reinterpret_cast<const volatile uint32_t*>(p);
 }
 
 // Stable scatter of one digit pass; on the last pass (GATHER) also gathers the
-// tile rectangle of every survivor into rank order.  Blocks take their place
-// (view, block) from a ticket, so every block they look back at has started.
-// Keys, values and rectangles are loaded before the counting, so their
-// latency overlaps it.  A block's offset within a digit is the count of the
-// digit in the view's earlier blocks, found by walking back over their
-// look-back words until one holds an inclusive count.
+// tile rectangle of every survivor into rank order.  Keys, values and
+// rectangles are loaded before the counting, so their latency overlaps it.
 template <bool GATHER>
-__global__ void __launch_bounds__(RS_THREADS, 4) k_rs_scatter(FrameHeader* __restrict__ hdr,
+__global__ void __launch_bounds__(RS_THREADS, 4) k_rs_scatter(const FrameHeader* __restrict__ hdr,
                                                            const uint32_t* __restrict__ n_surv,
                                                            const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                            uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
-                                                           int64_t n, int nb, int pass, const uint32_t* __restrict__ tot,
-                                                           uint32_t* __restrict__ lbw, uint32_t* __restrict__ ticket,
+                                                           int64_t n, int nb, int shift, const uint32_t* __restrict__ hist,
+                                                           const uint32_t* __restrict__ totals,
+                                                           const uint32_t* __restrict__ sum1,
+                                                           const uint32_t* __restrict__ sum2,
                                                            const uint2* __restrict__ rect, uint2* __restrict__ srect)
 {
     __shared__ uint32_t h[RS_THREADS / 32][256];
     __shared__ uint32_t wb[RS_THREADS / 32][256];
     __shared__ uint32_t dbase[256];
     __shared__ uint32_t wsum[RS_THREADS / 32];
-    __shared__ uint32_t s_blk;
-    if (threadIdx.x == 0) s_blk = atomicAdd(ticket, 1u);
-    __syncthreads();
-    const uint32_t b = s_blk;
-    const int v = (int)(b / (uint32_t)nb), lb = (int)(b % (uint32_t)nb);
-    if ((uint32_t)v >= hdr->n_views) return;
-    if (hdr->status & STATUS_TIMEOUT) return;     // an earlier pass gave up: nothing downstream runs
-    const int shift = 8 * pass;
+    const int b = blockIdx.x, v = b / nb, lb = b % nb;
     const int64_t vbase = (int64_t)v * n;
     const int64_t base = vbase + (int64_t)lb * RS_ITEMS;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // the first pass reads all n keys of the view (and drops the culled);
-    // later passes read its survivors, so blocks past them move no data
-    const int cnt = pass == 0 ? rs_first_count(n, lb) : rs_later_count(n_surv, v, lb);
-    if (cnt == 0) return;     // no later block of the view has items either: nobody waits on it
+    // keys, values, the view's digit total and this block's digit offsets are
+    // loaded together (in the first pass before the view check; a later pass
+    // reads its item count first, so blocks past the survivors move no data)
+    const bool first = shift == 0;
+    int cnt;
+    if (first) {
+        cnt = rs_first_count(n, lb);
+    } else {
+        if ((uint32_t)v >= hdr->n_views) return;
+        cnt = rs_later_count(n_surv, v, lb);
+        if (cnt == 0) return;
+    }
     uint32_t kk[RS_R], vv[RS_R];
     uint2 rr[RS_R];
     rs_load_keys(kin, base, cnt, kk);
@@ -201,44 +187,31 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_rs_scatter(FrameHeader* __res
         const int idx = w * RS_PER_WARP + r * 32 + lane;
         vv[r] = idx < cnt ? vin[base + idx] : 0u;
     }
-    const uint32_t c_tot = tot[v * 256 + threadIdx.x];
+    const uint32_t c_tot = totals[v * 256 + threadIdx.x];
+    // this block's offset within the digit: the counts of the earlier blocks,
+    // as groups of RS_G2 blocks, then groups of RS_G1, then single blocks
+    uint32_t c_blk = 0;
+    {
+        const uint32_t* p2 = sum2 + (size_t)v * rs_groups(nb, RS_G2) * 256 + threadIdx.x;
+        const uint32_t* p1 = sum1 + (size_t)v * rs_groups(nb, RS_G1) * 256 + threadIdx.x;
+        const uint32_t* p0 = hist + (size_t)v * nb * 256 + threadIdx.x;
+        const int q2 = lb / RS_G2, q1 = lb / RS_G1;
+#pragma unroll 8
+        for (int k = 0; k < q2; ++k) c_blk += p2[(size_t)k * 256];
+#pragma unroll
+        for (int k = 0; k < RS_G2 / RS_G1 - 1; ++k)
+            if (q2 * (RS_G2 / RS_G1) + k < q1) c_blk += p1[(size_t)(q2 * (RS_G2 / RS_G1) + k) * 256];
+#pragma unroll
+        for (int k = 0; k < RS_G1 - 1; ++k)
+            if (q1 * RS_G1 + k < lb) c_blk += p0[(size_t)(q1 * RS_G1 + k) * 256];
+    }
+    if (first && (uint32_t)v >= hdr->n_views) return;
+    if (cnt == 0) return;
     if (GATHER) {
 #pragma unroll
         for (int r = 0; r < RS_R; ++r) rr[r] = kk[r] != 0xFFFFFFFFu ? rect[vbase + vv[r]] : make_uint2(0u, 0u);
     }
     rs_warp_counts(kk, shift, h);
-    __syncthreads();
-    // this block's count of digit threadIdx.x, published; then the view's
-    // earlier blocks' count of it (RS_THREADS == 256: one digit per thread)
-    uint32_t bc = 0;
-    for (int q = 0; q < RS_THREADS / 32; ++q) bc += h[q][threadIdx.x];
-    const uint32_t tag = (uint32_t)pass << 28;
-    uint32_t* mine = lbw + ((size_t)v * nb + lb) * 256 + threadIdx.x;
-    uint32_t c_blk = 0;
-    if (lb == 0) {
-        atomicExch(mine, RS_INC | tag | bc);
-    } else {
-        atomicExch(mine, RS_AGG | tag | bc);
-        bool gave_up = false;
-        for (int j = lb - 1; j >= 0; --j) {
-            const uint32_t* pj = lbw + ((size_t)v * nb + j) * 256 + threadIdx.x;
-            uint32_t x = ld_volatile_u32(pj);
-            uint32_t spins = 0;
-            while ((x >> 30) == 0u || ((x >> 28) & 3u) != (uint32_t)pass) {
-                if (++spins > RS_SPIN_LIMIT) {
-                    gave_up = true;
-                    break;
-                }
-                __nanosleep(32);
-                x = ld_volatile_u32(pj);
-            }
-            if (gave_up) break;
-            c_blk += x & RS_VAL;
-            if ((x >> 30) == 2u) break;
-        }
-        if (gave_up) atomicOr(&hdr->status, STATUS_TIMEOUT | STATUS_OVERFLOW);
-        atomicExch(mine, RS_INC | tag | ((c_blk + bc) & RS_VAL));
-    }
     {
         // exclusive scan of the view's 256 digit totals (RS_THREADS == 256)
         const int wi = threadIdx.x >> 5;
@@ -251,19 +224,18 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_rs_scatter(FrameHeader* __res
         if (lane == 31) wsum[wi] = x;
         __syncthreads();
         uint32_t off = 0;
-        for (int q = 0; q < wi; ++q) off += wsum[q];
+        for (int w = 0; w < wi; ++w) off += wsum[w];
         dbase[threadIdx.x] = off + x - c;
     }
     __syncthreads();
     {
         uint32_t run = dbase[threadIdx.x] + c_blk;
-        for (int q = 0; q < RS_THREADS / 32; ++q) {
-            wb[q][threadIdx.x] = run;
-            run += h[q][threadIdx.x];
+        for (int w = 0; w < RS_THREADS / 32; ++w) {
+            wb[w][threadIdx.x] = run;
+            run += h[w][threadIdx.x];
         }
     }
     __syncthreads();
-    if (hdr->status & STATUS_TIMEOUT) return;     // offsets may be wrong: write nothing
     const uint32_t lt = lanemask_lt();
 #pragma unroll
     for (int r = 0; r < RS_R; ++r) {
@@ -645,11 +617,29 @@ __global__ void __launch_bounds__(CS_TILES * CS_SEG, 2) k_tile_scan(Frame F, uin
         if (lane >= o) x += y;
     }
     const unsigned long long agg = __shfl_sync(0xffffffffu, x, 31);
+    // the block's tiles per length class (for the blends' work order), packed
+    // two per word; published beside the pair count, before its flag
+    const unsigned long long mean = hdr->n_pairs / (TT ? TT : 1u);
+    const uint32_t cls = ok ? tile_class(c, mean) : 4u;
+    uint32_t ccount[4];
+#pragma unroll
+    for (uint32_t k = 0; k < 4; ++k) ccount[k] = (uint32_t)__popc(__ballot_sync(0xffffffffu, cls == k));
+    const ulonglong2 cagg = make_ulonglong2(ccount[0] | ((unsigned long long)ccount[1] << 32),
+                                            ccount[2] | ((unsigned long long)ccount[3] << 32));
+    ulonglong2 cpre = make_ulonglong2(0ull, 0ull);     // class counts of the blocks before
     unsigned long long prefix = 0;
     if (blk == 0) {
-        if (lane == 0) atomicExch(&F.scan_st[0], LB_INC | agg);
+        if (lane == 0) {
+            F.scan_cls[2 * blk + 1] = cagg;
+            __threadfence();
+            atomicExch(&F.scan_st[0], LB_INC | agg);
+        }
     } else {
-        if (lane == 0) atomicExch(&F.scan_st[blk], LB_AGG | agg);
+        if (lane == 0) {
+            F.scan_cls[2 * blk] = cagg;
+            __threadfence();
+            atomicExch(&F.scan_st[blk], LB_AGG | agg);
+        }
         // window of 32 blocks, lane l reading block j - l; "before block 0"
         // reads as an inclusive sum of 0
         long long j = (long long)blk - 1;
@@ -673,8 +663,23 @@ __global__ void __launch_bounds__(CS_TILES * CS_SEG, 2) k_tile_scan(Frame F, uin
             const unsigned inc = __ballot_sync(0xffffffffu, (w >> 62) == 2ull);
             const int first = inc ? __ffs(inc) - 1 : 31;
             unsigned long long add = lane <= first ? (w & LB_VAL) : 0ull;
-            for (int o = 16; o > 0; o >>= 1) add += __shfl_xor_sync(0xffffffffu, add, o);
+            // the class counts published with the flag just read: the block's
+            // own (aggregate) or up to and including it (inclusive)
+            __threadfence();
+            ulonglong2 cw = make_ulonglong2(0ull, 0ull);
+            if (lane <= first && jj >= 0) {
+                const volatile unsigned long long* cp = reinterpret_cast<const volatile unsigned long long*>(
+                    &F.scan_cls[2 * jj + ((w >> 62) == 2ull ? 1 : 0)]);
+                cw = make_ulonglong2(cp[0], cp[1]);
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                add += __shfl_xor_sync(0xffffffffu, add, o);
+                cw.x += __shfl_xor_sync(0xffffffffu, cw.x, o);
+                cw.y += __shfl_xor_sync(0xffffffffu, cw.y, o);
+            }
             prefix += add;
+            cpre.x += cw.x;
+            cpre.y += cw.y;
             if (inc) break;
             j -= 32;
         }
@@ -683,7 +688,11 @@ __global__ void __launch_bounds__(CS_TILES * CS_SEG, 2) k_tile_scan(Frame F, uin
             if (lane == 0) atomicOr(&hdr->status, STATUS_TIMEOUT | STATUS_OVERFLOW);
             return;
         }
-        if (lane == 0) atomicExch(&F.scan_st[blk], LB_INC | (prefix + agg));
+        if (lane == 0) {
+            F.scan_cls[2 * blk + 1] = make_ulonglong2(cpre.x + cagg.x, cpre.y + cagg.y);
+            __threadfence();
+            atomicExch(&F.scan_st[blk], LB_INC | (prefix + agg));
+        }
     }
     if (ok) {
         const unsigned long long o = prefix + x - c;
@@ -691,26 +700,27 @@ __global__ void __launch_bounds__(CS_TILES * CS_SEG, 2) k_tile_scan(Frame F, uin
         ranges[2 * (size_t)t] = c ? static_cast<uint32_t>(o) : 0u;
         ranges[2 * (size_t)t + 1] = c ? static_cast<uint32_t>(o + c) : 0u;
     }
-    // the blends' work order: each tile appended to its length class's list
-    // (warp-aggregated; within a class roughly in tile order).  Only the
+    // the blends' work order: each class's list in tile order (neighbouring
+    // tiles share Gaussians, so running them together reuses L2).  Only the
     // order in which warps take tiles: no result depends on it.
-    const unsigned long long mean = hdr->n_pairs / (TT ? TT : 1u);
-    const uint32_t cls = ok ? tile_class(c, mean) : 4u;
     const uint32_t lt = lanemask_lt();
 #pragma unroll
     for (uint32_t k = 0; k < 4; ++k) {
         const unsigned m = __ballot_sync(0xffffffffu, cls == k);
-        if (!m) continue;
-        const int leader = __ffs(m) - 1;
-        uint32_t base = 0;
-        if (lane == leader) base = atomicAdd(&F.scan_ctr[k], (uint32_t)__popc(m));
-        base = __shfl_sync(0xffffffffu, base, leader);
-        if (cls == k) F.torder[(size_t)k * TT + base + __popc(m & lt)] = t;
+        const uint32_t before = (uint32_t)((k & 1u) ? ((k < 2 ? cpre.x : cpre.y) >> 32)
+                                                   : ((k < 2 ? cpre.x : cpre.y) & 0xFFFFFFFFull));
+        if (cls == k) F.torder[(size_t)k * TT + before + __popc(m & lt)] = t;
     }
     if (blk == gridDim.x - 1 && lane == 31) {
         const unsigned long long K = prefix + agg;
         F.tile_offset[TT] = static_cast<uint32_t>(K);
         if (K != hdr->n_pairs || K > cap || K > 0xFFFFFFFFull) atomicOr(&hdr->status, STATUS_OVERFLOW);
+        // the class totals, for the blends' walk over the four lists
+        const unsigned long long a = cpre.x + cagg.x, b = cpre.y + cagg.y;
+        F.scan_ctr[0] = (uint32_t)(a & 0xFFFFFFFFull);
+        F.scan_ctr[1] = (uint32_t)(a >> 32);
+        F.scan_ctr[2] = (uint32_t)(b & 0xFFFFFFFFull);
+        F.scan_ctr[3] = (uint32_t)(b >> 32);
     }
 }
 
@@ -725,26 +735,27 @@ cudaError_t launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long 
     const int64_t n = (int64_t)L.n;
     const int nb = (int)L.n_rs_blocks;
     const uint32_t V = L.n_views;
-    // the radix region: look-back words [V][nb][256], digit totals [4][V][256],
-    // four pass tickets; then (the next array) the tile scan's look-back
-    // words and counters -- one clear for all
-    uint32_t* lbw = F.rs_hist;
-    uint32_t* tot = lbw + (size_t)V * nb * 256;
-    uint32_t* tickets = tot + (size_t)4 * V * 256;
-    err = cudaMemsetAsync(F.rs_hist, 0, reinterpret_cast<const char*>(F.scan_ctr + 8) -
-                                         reinterpret_cast<const char*>(F.rs_hist), st);
+    // after the block counts [V][nb][256]: per pass the digit totals [V][256]
+    // and the group sums [V][groups][256] of both levels; then (the next
+    // array) the tile scan's look-back words and counters: one clear for all
+    const size_t n1 = (size_t)V * 256 * rs_groups(nb, RS_G1), n2 = (size_t)V * 256 * rs_groups(nb, RS_G2);
+    const size_t per_pass = (size_t)V * 256 + n1 + n2;
+    uint32_t* sums = F.rs_hist + (size_t)V * 256 * nb;
+    err = cudaMemsetAsync(sums, 0, reinterpret_cast<const char*>(F.scan_ctr + 8) - reinterpret_cast<const char*>(sums), st);
     if (err != cudaSuccess) return err;
     if (n > 0) {
         uint32_t *ki = F.key0, *vi = F.val0, *ko = F.key1, *vo = F.val1;
-        k_rs_hist_all<<<V * nb, RS_THREADS, 0, st>>>(F.hdr, ki, n, nb, (int)V, tot);
         for (int pass = 0; pass < 4; ++pass) {
-            const uint32_t* tp = tot + (size_t)pass * V * 256;
+            uint32_t* tot = sums + (size_t)pass * per_pass;
+            uint32_t* s1 = tot + (size_t)V * 256;
+            uint32_t* s2 = s1 + n1;
+            k_rs_hist<<<V * nb, RS_THREADS, 0, st>>>(F.hdr, F.n_surv, ki, n, nb, 8 * pass, F.rs_hist, tot, s1, s2);
             if (pass == 3)
-                k_rs_scatter<true><<<V * nb, RS_THREADS, 0, st>>>(F.hdr, F.n_surv, ki, vi, ko, vo, n, nb, pass, tp, lbw,
-                                                                  tickets + pass, F.rect, F.srect);
+                k_rs_scatter<true><<<V * nb, RS_THREADS, 0, st>>>(F.hdr, F.n_surv, ki, vi, ko, vo, n, nb, 8 * pass,
+                                                                  F.rs_hist, tot, s1, s2, F.rect, F.srect);
             else
-                k_rs_scatter<false><<<V * nb, RS_THREADS, 0, st>>>(F.hdr, F.n_surv, ki, vi, ko, vo, n, nb, pass, tp,
-                                                                   lbw, tickets + pass, nullptr, nullptr);
+                k_rs_scatter<false><<<V * nb, RS_THREADS, 0, st>>>(F.hdr, F.n_surv, ki, vi, ko, vo, n, nb, 8 * pass,
+                                                                   F.rs_hist, tot, s1, s2, nullptr, nullptr);
             std::swap(ki, ko);
             std::swap(vi, vo);
         }

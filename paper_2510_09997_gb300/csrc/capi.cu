@@ -98,6 +98,7 @@ FrameLayout frame_layout(uint64_t n, uint32_t V, uint32_t TT, uint32_t rb_total,
     // tile scan (right after the radix sums: one clear covers both): look-back
     // words of the blocks of 32 tiles, then the class counters and the ticket
     L.scan = take(sizeof(unsigned long long) * (((size_t)TT + 31) / 32) + sizeof(uint32_t) * 8);
+    L.scan_cls = take(sizeof(ulonglong2) * 2 * (((size_t)TT + 31) / 32));
     L.cnt = take(sizeof(uint32_t) * (size_t)L.n_chunks * TT);
     L.sel = take(sizeof(SelState) * V);
     L.sel_hist = take(sizeof(uint32_t) * SEL_BINS * (size_t)V);
@@ -131,6 +132,7 @@ Frame frame_ptrs(void* ws, const FrameLayout& L)
     F.srect = reinterpret_cast<uint2*>(b + L.srect);
     F.rs_hist = reinterpret_cast<uint32_t*>(b + L.rs_hist);
     F.scan_st = reinterpret_cast<unsigned long long*>(b + L.scan);
+    F.scan_cls = reinterpret_cast<ulonglong2*>(b + L.scan_cls);
     F.scan_ctr = reinterpret_cast<uint32_t*>(b + L.scan + sizeof(unsigned long long) * (((size_t)L.total_tiles + 31) / 32));
     F.cnt = reinterpret_cast<uint32_t*>(b + L.cnt);
     F.sel = reinterpret_cast<SelState*>(b + L.sel);
@@ -287,7 +289,7 @@ static void make_view_table(const clod_view* views, int32_t V, uint64_t n, std::
 static clod_status check_scene(const clod_scene* S)
 {
     if (!S) return fail(CLOD_ERR_ARG, "scene is NULL");
-    if (S->n < 0 || S->n >= (1ll << 28)) return fail(CLOD_ERR_ARG, "scene n = %lld outside [0, 2^28)", (long long)S->n);
+    if (S->n < 0 || S->n >= (1ll << 31)) return fail(CLOD_ERR_ARG, "scene n = %lld outside [0, 2^31)", (long long)S->n);
     if (S->sh_degree < 0 || S->sh_degree > 3) return fail(CLOD_ERR_ARG, "sh_degree %d outside [0, 3]", S->sh_degree);
     if (S->n > 0 && (!S->means || !S->scales || !S->quats || !S->opacity || !S->sh || !S->decay))
         return fail(CLOD_ERR_ARG, "scene array pointer is NULL");
@@ -343,7 +345,7 @@ clod_status clod_frame_workspace_size(int64_t n, const clod_view* views, int32_t
                                       clod_frame_layout* layout)
 {
     if (!bytes) return fail(CLOD_ERR_ARG, "bytes is NULL");
-    if (n < 0 || n >= (1ll << 28)) return fail(CLOD_ERR_ARG, "n = %lld outside [0, 2^28)", (long long)n);
+    if (n < 0 || n >= (1ll << 31)) return fail(CLOD_ERR_ARG, "n = %lld outside [0, 2^31)", (long long)n);
     ViewGeom G;
     clod_status s = check_views(views, n_views, (uint64_t)n, &G);
     if (s) return s;
@@ -485,7 +487,7 @@ clod_status clod_frame_check(const void* ws, uint64_t pair_capacity, uint64_t* n
 clod_status clod_backward_workspace_size(int64_t n, int32_t n_views, size_t* bytes)
 {
     if (!bytes) return fail(CLOD_ERR_ARG, "bytes is NULL");
-    if (n < 0 || n >= (1ll << 28)) return fail(CLOD_ERR_ARG, "n = %lld outside [0, 2^28)", (long long)n);
+    if (n < 0 || n >= (1ll << 31)) return fail(CLOD_ERR_ARG, "n = %lld outside [0, 2^31)", (long long)n);
     if (n_views < 1 || n_views > MAX_VIEWS) return fail(CLOD_ERR_ARG, "n_views = %d outside [1, %d]", n_views, MAX_VIEWS);
     *bytes = backward_ws_bytes((uint64_t)n, (uint32_t)n_views);
     return CLOD_OK;

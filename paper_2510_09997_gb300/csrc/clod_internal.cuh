@@ -78,7 +78,7 @@ struct SelState {
 
 struct FrameLayout {
     size_t header, views, dmax_key, n_surv, rec0, rec1, rec2, depth, rect, tile_count, tile_offset, torder,
-        key0, val0, key1, val1, srect, rs_hist, scan, cnt, sel, sel_hist, total;
+        key0, val0, key1, val1, srect, rs_hist, scan, scan_cls, cnt, sel, sel_hist, total;
     uint32_t total_tiles, n_views, n_chunks, n_rs_blocks, rb_total, max_tx;
     uint32_t fast_exp;      // host only: the frame's views carry CLOD_FAST_EXP
     uint64_t n;
@@ -100,6 +100,7 @@ struct Frame {
     uint32_t* tile_offset;
     uint32_t* torder;       // the blends' work order: four class lists of capacity total_tiles
     unsigned long long* scan_st;  // tile scan: per block of 32 tiles, look-back flag and value
+    ulonglong2* scan_cls;   // tile scan: per block, its tiles per length class, own and inclusive
     uint32_t* scan_ctr;     // [0..3] tiles per length class, [4] tile-scan block ticket
     uint32_t* key0;         // depth-rank sort ping-pong: keys (depth bits) / values (index)
     uint32_t* val0;

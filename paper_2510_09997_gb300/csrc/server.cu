@@ -400,7 +400,7 @@ extern "C" {
 clod_status clod_server_create(const clod_scene* scene, const clod_server_cfg* cfg, clod_server** out)
 {
     if (!scene || !cfg || !out) return fail(CLOD_ERR_ARG, "NULL argument to clod_server_create");
-    if (scene->n < 0 || scene->n >= (1ll << 28) || scene->sh_degree < 0 || scene->sh_degree > 3)
+    if (scene->n < 0 || scene->n >= (1ll << 31) || scene->sh_degree < 0 || scene->sh_degree > 3)
         return fail(CLOD_ERR_ARG, "bad scene");
     if (scene->n > 0 && (!scene->means || !scene->scales || !scene->quats || !scene->opacity || !scene->sh || !scene->decay))
         return fail(CLOD_ERR_ARG, "scene array pointer is NULL");
