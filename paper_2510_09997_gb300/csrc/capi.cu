@@ -51,18 +51,12 @@ clod_status cuda_fail(cudaError_t e, const char* what)
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-static uint32_t n_chunks_for(uint64_t n)
-{
-    uint64_t c = (n + 1023) / 1024;
-    return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(c, MAX_CHUNKS));
-}
-
-FrameLayout frame_layout(uint64_t n, uint32_t V, uint32_t TT, uint32_t rb_total, uint32_t max_tx,
+FrameLayout frame_layout(uint64_t n, uint32_t V, uint32_t TT, uint32_t n_chunks, uint32_t rb_total, uint32_t max_tx,
                          size_t diff_grid_max)
 {
     FrameLayout L{};
     L.diff_grid_max = diff_grid_max;
-    L.n_chunks = n_chunks_for(n);
+    L.n_chunks = n_chunks;
     L.n_rs_blocks = (uint32_t)((n + RS_ITEMS - 1) / RS_ITEMS);
     L.rb_total = rb_total;
     L.max_tx = max_tx;
@@ -174,7 +168,7 @@ clod_status device_ready(int* n_sm)
 }
 
 struct ViewGeom {
-    uint32_t TT, rb_total, max_tx;
+    uint32_t TT, n_chunks, rb_total, max_tx;
     size_t diff_max;
 };
 
@@ -250,29 +244,30 @@ static clod_status check_views(const clod_view* views, int32_t V, uint64_t n, Vi
         if ((views[v].flags ^ views[0].flags) & CLOD_FAST_EXP)
             return fail(CLOD_ERR_ARG, "views 0 and %d disagree on CLOD_FAST_EXP (one frame, one exponential)", v);
     G->TT = static_cast<uint32_t>(tt);
-    const uint32_t CH = n_chunks_for(n);
-    uint64_t rb = 0;
+    uint64_t bands = 0;
     uint32_t mtx = 1;
     size_t dmx = 0;
     for (int v = 0; v < V; ++v) {
         const int TX = (views[v].width + TILE - 1) / TILE, TY = (views[v].height + TILE - 1) / TILE;
-        rb += (uint64_t)CH * ((TY + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK);
+        bands += (uint64_t)((TY + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK);
         mtx = std::max<uint32_t>(mtx, (uint32_t)TX);
         dmx = std::max<size_t>(dmx, (size_t)(TX + 1) * (TY + 1));
     }
+    const uint32_t CH = chunk_count(n, bands);
+    const uint64_t rb = (uint64_t)CH * bands;
     G->diff_max = dmx;
     if (rb > 0x7FFFFFFFull) return fail(CLOD_ERR_ARG, "frame too large");
+    G->n_chunks = CH;
     G->rb_total = (uint32_t)rb;
     G->max_tx = mtx;
     return CLOD_OK;
 }
 
-static void make_view_table(const clod_view* views, int32_t V, uint64_t n, std::vector<ViewDev>& out)
+static void make_view_table(const clod_view* views, int32_t V, uint32_t CH, std::vector<ViewDev>& out)
 {
     out.resize(V);
     uint32_t tile_base = 0, rb_base = 0;
     uint64_t pix_base = 0;
-    const uint32_t CH = n_chunks_for(n);
     for (int v = 0; v < V; ++v) {
         const clod_view& w = views[v];
         ViewDev& d = out[v];
@@ -350,7 +345,7 @@ clod_status clod_frame_workspace_size(int64_t n, const clod_view* views, int32_t
     clod_status s = check_views(views, n_views, (uint64_t)n, &G);
     if (s) return s;
     const uint32_t TT = G.TT;
-    const FrameLayout L = frame_layout((uint64_t)n, (uint32_t)n_views, TT, G.rb_total, G.max_tx, G.diff_max);
+    const FrameLayout L = frame_layout((uint64_t)n, (uint32_t)n_views, TT, G.n_chunks, G.rb_total, G.max_tx, G.diff_max);
     *bytes = L.total;
     if (layout) {
         layout->total_bytes = L.total;
@@ -381,7 +376,7 @@ clod_status clod_preprocess(const clod_scene* scene, const clod_view* views, int
     const uint32_t TT = G.TT;
     if (!ws) return fail(CLOD_ERR_ARG, "ws is NULL");
     if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(CLOD_ERR_ARG, "ws must be 256-byte aligned");
-    FrameLayout L = frame_layout((uint64_t)scene->n, (uint32_t)n_views, TT, G.rb_total, G.max_tx, G.diff_max);
+    FrameLayout L = frame_layout((uint64_t)scene->n, (uint32_t)n_views, TT, G.n_chunks, G.rb_total, G.max_tx, G.diff_max);
     L.fast_exp = (views[0].flags & CLOD_FAST_EXP) ? 1u : 0u;
     if (ws_bytes < L.total)
         return fail(CLOD_ERR_CAPACITY, "frame workspace needs %zu bytes, got %zu", L.total, ws_bytes);
@@ -390,7 +385,7 @@ clod_status clod_preprocess(const clod_scene* scene, const clod_view* views, int
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const Frame F = frame_ptrs(ws, L);
     std::vector<ViewDev> table;
-    make_view_table(views, n_views, (uint64_t)scene->n, table);
+    make_view_table(views, n_views, G.n_chunks, table);
     FrameHeader h{};
     h.n = (uint64_t)scene->n;
     h.n_views = (uint32_t)n_views;

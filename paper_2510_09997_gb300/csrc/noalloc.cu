@@ -63,7 +63,7 @@ static clod_status noalloc_scratch(void** out)
         // change of the workspace layout cannot silently shrink the limits
         const uint32_t ch = (uint32_t)std::min<int64_t>((NA_MAX_GAUSSIANS + 1023) / 1024, MAX_CHUNKS);
         const int side = NA_MAX_SIDE / TILE;
-        const FrameLayout big = frame_layout(NA_MAX_GAUSSIANS, 1, (uint32_t)NA_MAX_TILES,
+        const FrameLayout big = frame_layout(NA_MAX_GAUSSIANS, 1, (uint32_t)NA_MAX_TILES, ch,
                                              ch * (uint32_t)((side + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK),
                                              (uint32_t)side, (size_t)(side + 1) * (side + 1));
         if (big.total > NA_FRAME_BYTES)
@@ -108,9 +108,11 @@ extern "C" clod_status clod_render_noalloc(const clod_scene* scene, const clod_v
 
     const uint64_t n = (uint64_t)scene->n;
     const int TX = (w.width + TILE - 1) / TILE, TY = (w.height + TILE - 1) / TILE;
-    const uint32_t CH = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((n + 1023) / 1024, MAX_CHUNKS));
-    const uint32_t rb_total = CH * (uint32_t)((TY + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK);
-    const FrameLayout L = frame_layout(n, 1, (uint32_t)(TX * TY), rb_total, (uint32_t)TX, (size_t)(TX + 1) * (TY + 1));
+    const uint32_t bands = (uint32_t)((TY + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK);
+    const uint32_t CH = chunk_count(n, bands);
+    const uint32_t rb_total = CH * bands;
+    const FrameLayout L = frame_layout(n, 1, (uint32_t)(TX * TY), CH, rb_total, (uint32_t)TX,
+                                       (size_t)(TX + 1) * (TY + 1));
     if (L.total > NA_FRAME_BYTES) return fail(CLOD_ERR_CAPACITY, "frame needs %zu bytes of scratch, %zu available",
                                               L.total, NA_FRAME_BYTES);
     char* b = static_cast<char*>(base);

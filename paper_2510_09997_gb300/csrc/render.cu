@@ -109,26 +109,6 @@ __device__ __forceinline__ void blend_pair(Px& q0, Px& q1, bool t0, bool t1, flo
     }
 }
 
-// blend_pair for one lane on its own (no warp votes: in the sparse mode the
-// lanes of a warp blend different Gaussians at the same time).  The same
-// per-pixel operations as blend_pair, so the same results.
-template <bool FAST>
-__device__ __forceinline__ void blend_lane(Px& q0, Px& q1, float fpx, float fpy0, float fpy1, const float4& a,
-                                           const float4& c, float cb, float pf, uint32_t pos)
-{
-    const float ddx = __fsub_rn(a.x, fpx);
-    const float dy0 = __fsub_rn(a.y, fpy0), dy1 = __fsub_rn(a.y, fpy1);
-    const float p0 = __fmaf_rn(ddx, __fmaf_rn(a.z, ddx, __fmul_rn(a.w, dy0)), __fmul_rn(__fmul_rn(c.x, dy0), dy0));
-    const float p1 = __fmaf_rn(ddx, __fmaf_rn(a.z, ddx, __fmul_rn(a.w, dy1)), __fmul_rn(__fmul_rn(c.x, dy1), dy1));
-    const bool r0 = !q0.done && p0 <= 0.0f && p0 >= pf;
-    const bool r1 = !q1.done && p1 <= 0.0f && p1 >= pf;
-    if (!(r0 || r1)) return;
-    const float g0 = blend_exp<FAST>(r0 ? p0 : 0.0f), g1 = blend_exp<FAST>(r1 ? p1 : 0.0f);
-    const float a0 = fminf(0.99f, __fmul_rn(c.y, g0)), a1 = fminf(0.99f, __fmul_rn(c.y, g1));
-    blend_finish(q0, r0 && !(a0 < (1.0f / 255.0f)), a0, c, cb, pos);
-    blend_finish(q1, r1 && !(a1 < (1.0f / 255.0f)), a1, c, cb, pos);
-}
-
 __device__ __forceinline__ void store_px(const ViewDev& W, const Px& q, int px, int py, float* image, float* Tout,
                                          uint32_t* ncout)
 {
@@ -156,7 +136,7 @@ constexpr int BLEND_THREADS = 128;   // 4 warps per 16x16 tile, 8x8 pixels per w
 // variant (every pair visited, software exponential); FAST: the exponential
 // of CLOD_FAST_EXP.
 template <bool COUNT, bool FAST>
-__global__ void __launch_bounds__(BLEND_THREADS, 9) k_blend_fwd(Frame F, const uint32_t* __restrict__ vals,
+__global__ void __launch_bounds__(BLEND_THREADS) k_blend_fwd(Frame F, const uint32_t* __restrict__ vals,
                                                              const uint32_t* __restrict__ ranges,
                                                              float* __restrict__ image, float* __restrict__ Tout,
                                                              uint32_t* __restrict__ ncout,
@@ -215,43 +195,8 @@ __global__ void __launch_bounds__(BLEND_THREADS, 9) k_blend_fwd(Frame F, const u
                 else hit = !(fabsf(a.x - wcx) > e.y + 3.5f || fabsf(a.y - wcy) > e.z + 3.5f);
             }
             unsigned m = __ballot_sync(0xffffffffu, hit);
-            // entries whose reach box is at most 5 pixels wide reach a few
-            // of the patch's 64 pixels
-            const unsigned small = __ballot_sync(0xffffffffu, hit && !COUNT && s2[wid][lane].y <= 2.5f &&
-                                                               s2[wid][lane].z <= 2.5f);
             __syncwarp();
             const uint32_t pos0 = b - start + 1u;     // list position (1-based) of entry 0 of the batch
-            if (!COUNT && __popc(m) >= 4 && 2 * __popc(small) >= __popc(m)) {
-                // sparse batch: each lane walks, in list order, only the hit
-                // entries whose reach box holds one of its two pixels, and the
-                // lanes of the warp blend different entries at once.  Every
-                // other entry would be skipped by the lane's pixels anyway
-                // (outside the reach box the opacity is below 1/255), and each
-                // pixel still takes its Gaussians in list order: the results
-                // are those of the loop below.
-                uint32_t cov = 0;
-                if (!(q0.done && q1.done)) {
-                    const float fpym = __fadd_rn(fpy0, 0.5f);     // between the lane's two pixel rows
-                    for (unsigned mm = m; mm; mm &= mm - 1) {
-                        const int k = __ffs(mm) - 1;
-                        const float4 a = s0[wid][k];
-                        const float4 e = s2[wid][k];
-                        if (!(fabsf(a.x - fpx) > e.y) && !(fabsf(a.y - fpym) > e.z + 0.5f)) cov |= 1u << k;
-                    }
-                }
-                while (__any_sync(0xffffffffu, cov != 0u)) {
-                    if (cov) {
-                        const int k = __ffs(cov) - 1;
-                        cov &= cov - 1;
-                        const float4 a = s0[wid][k];
-                        const float4 c = s1[wid][k];
-                        const float4 e = s2[wid][k];
-                        blend_lane<FAST>(q0, q1, fpx, fpy0, fpy1, a, c, e.x, e.w, pos0 + (uint32_t)k);
-                        if (q0.done && q1.done) cov = 0u;
-                    }
-                }
-                m = 0u;
-            }
             while (m) {
                 const int k = __ffs(m) - 1;
                 m &= m - 1;

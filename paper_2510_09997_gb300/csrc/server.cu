@@ -50,10 +50,6 @@ static double now_us()
     return duration<double, std::micro>(steady_clock::now().time_since_epoch()).count();
 }
 
-static uint32_t chunks_for(uint64_t n)
-{
-    return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((n + 1023) / 1024, MAX_CHUNKS));
-}
 
 struct Request {
     clod_view view;
@@ -100,6 +96,8 @@ struct clod_server {
     int device = 0;
     int n_sm = 0;
     uint32_t max_tiles = 0, max_rb = 0, max_tx = 0;
+    uint32_t ch = 1;        // rank chunks per view of the largest batch (the slots' layouts)
+    uint32_t solo_ch = 1;   // the same for the solo lane's one view of the largest size
     size_t max_diff = 0;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -114,9 +112,27 @@ struct clod_server {
 
 namespace clod {
 
+// The batch's rank chunks per view: chunk_count for its own views, within
+// what the slot's layout and captured grids hold (the per (chunk, tile)
+// counts, the emission blocks and the counting blocks).
+static uint32_t batch_chunks(clod_server* S, const std::vector<const Request*>& batch, const FrameLayout& L)
+{
+    uint64_t tiles = 0, bands = 0;
+    for (const Request* r : batch) {
+        const uint64_t TX = (r->view.width + TILE - 1) / TILE, TY = (r->view.height + TILE - 1) / TILE;
+        tiles += TX * TY;
+        bands += (TY + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK;
+    }
+    uint64_t c = chunk_count((uint64_t)S->scene.n, bands);
+    c = std::min<uint64_t>(c, (uint64_t)L.n_chunks * L.total_tiles / std::max<uint64_t>(1, tiles));
+    c = std::min<uint64_t>(c, (uint64_t)L.rb_total / std::max<uint64_t>(1, bands));
+    c = std::min<uint64_t>(c, (uint64_t)L.n_chunks * L.n_views / std::max<uint64_t>(1, batch.size()));
+    return (uint32_t)std::max<uint64_t>(1, c);
+}
+
 static void fill_views(clod_server* S, const std::vector<const Request*>& batch, Slot& sl, FrameHeader& h)
 {
-    const uint32_t CH = chunks_for((uint64_t)S->scene.n);
+    const uint32_t CH = batch_chunks(S, batch, sl.L);
     uint32_t tile_base = 0, rb_base = 0, mtx = 1;
     for (size_t v = 0; v < batch.size(); ++v) {
         const clod_view& w = batch[v]->view;
@@ -160,7 +176,7 @@ static clod_status slot_init(clod_server* S, Slot& sl)
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_fail(e, "server slot stream");
     const uint32_t V = (uint32_t)S->cfg.max_views_per_batch;
-    sl.L = frame_layout((uint64_t)S->scene.n, V, S->max_tiles, S->max_rb, S->max_tx, S->max_diff);
+    sl.L = frame_layout((uint64_t)S->scene.n, V, S->max_tiles, S->ch, S->max_rb, S->max_tx, S->max_diff);
     if ((e = cudaMalloc(&sl.ws, sl.L.total)) != cudaSuccess) return cuda_fail(e, "server workspace");
     if ((e = cudaMalloc(&sl.vals, sizeof(uint32_t) * std::max<uint64_t>(1, S->cfg.pair_capacity))) != cudaSuccess)
         return cuda_fail(e, "server pair buffer");
@@ -197,8 +213,8 @@ static clod_status solo_init(clod_server* S)
     cudaError_t e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cuda_fail(e, "server solo stream");
     const uint32_t TX = S->max_tx, TY = (uint32_t)((S->cfg.max_height + TILE - 1) / TILE);
-    const uint32_t rb = chunks_for((uint64_t)S->scene.n) * ((TY + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK);
-    sl.L = frame_layout((uint64_t)S->scene.n, 1, TX * TY, rb, TX, S->max_diff);
+    const uint32_t rb = S->solo_ch * ((TY + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK);
+    sl.L = frame_layout((uint64_t)S->scene.n, 1, TX * TY, S->solo_ch, rb, TX, S->max_diff);
     if ((e = cudaMalloc(&sl.ws, sl.L.total)) != cudaSuccess) return cuda_fail(e, "server solo workspace");
     if ((e = cudaMalloc(&sl.ranges, sizeof(uint32_t) * 2 * (size_t)TX * TY)) != cudaSuccess)
         return cuda_fail(e, "server solo ranges");
@@ -234,13 +250,13 @@ static clod_status render_alone(clod_server* S, Request& r)
     Slot& sl = S->solo;
     const clod_view& w = r.view;
     const int TX = (w.width + TILE - 1) / TILE, TY = (w.height + TILE - 1) / TILE;
-    const uint32_t CH = chunks_for((uint64_t)S->scene.n);
-    const uint32_t rb = CH * (uint32_t)((TY + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK);
-    const FrameLayout L = frame_layout((uint64_t)S->scene.n, 1, (uint32_t)(TX * TY), rb, (uint32_t)TX,
-                                       (size_t)(TX + 1) * (TY + 1));
     std::vector<const Request*> one{&r};
     FrameHeader h;
-    fill_views(S, one, sl, h);
+    fill_views(S, one, sl, h);     // chunks within the solo layout's
+    const uint32_t CH = h.n_chunks;
+    const uint32_t rb = CH * (uint32_t)((TY + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK);
+    const FrameLayout L = frame_layout((uint64_t)S->scene.n, 1, (uint32_t)(TX * TY), CH, rb, (uint32_t)TX,
+                                       (size_t)(TX + 1) * (TY + 1));
     h.max_tx = (uint32_t)TX;
     const Frame F = frame_ptrs(sl.ws, L);   // the lane's workspace holds one view of the largest size
     cudaStream_t st = sl.stream;
@@ -422,7 +438,10 @@ clod_status clod_server_create(const clod_scene* scene, const clod_server_cfg* c
     const uint64_t B = (uint64_t)cfg->max_views_per_batch;
     const uint64_t tiles_by_px = cfg->max_pixels_per_batch / (TILE * TILE) + B * (TXm + TYm + 1);
     S->max_tiles = (uint32_t)std::min<uint64_t>(B * TXm * TYm, tiles_by_px);
-    S->max_rb = (uint32_t)(B * chunks_for((uint64_t)scene->n) * ((TYm + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK));
+    // every batch takes the chunk count of the largest (B views of the largest size)
+    S->ch = chunk_count((uint64_t)scene->n, B * ((TYm + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK));
+    S->max_rb = (uint32_t)(B * S->ch * ((TYm + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK));
+    S->solo_ch = chunk_count((uint64_t)scene->n, (TYm + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK);
     S->max_tx = (uint32_t)TXm;
     S->max_diff = (size_t)(TXm + 1) * (TYm + 1);
     S->slots.resize(cfg->n_slots);
