@@ -581,14 +581,12 @@ __global__ void __launch_bounds__(CS_TILES * CS_SEG, 2) k_tile_scan(Frame F, uin
     }
     const uint32_t per = (CHe + CS_SEG - 1) / CS_SEG;     // <= CS_MAXPER
     const uint32_t c0 = min(CHe, sg * per), c1 = min(CHe, c0 + per);
-    // the segment's counts are held in registers: one round of loads
-    uint32_t xs[CS_MAXPER];
+    // the segment's counts: summed, then (the second read hits L2) rewritten
+    // as offsets
     uint32_t sum = 0;
-#pragma unroll
-    for (int k = 0; k < CS_MAXPER; ++k) {
-        xs[k] = (ok && c0 + k < c1) ? col[(size_t)(c0 + k) * T] : 0u;
-        sum += xs[k];
-    }
+#pragma unroll 8
+    for (int k = 0; k < CS_MAXPER; ++k)
+        if (ok && c0 + k < c1) sum += col[(size_t)(c0 + k) * T];
     part[sg][tx] = sum;
     __syncthreads();
     uint32_t off = 0, tot = 0;
@@ -599,10 +597,14 @@ __global__ void __launch_bounds__(CS_TILES * CS_SEG, 2) k_tile_scan(Frame F, uin
         tot += x;
     }
     if (ok) {
-#pragma unroll
+#pragma unroll 8
         for (int k = 0; k < CS_MAXPER; ++k) {
-            if (c0 + k < c1) col[(size_t)(c0 + k) * T] = off;
-            off += xs[k];
+            if (c0 + k < c1) {
+                uint32_t* p = col + (size_t)(c0 + k) * T;
+                const uint32_t x = *p;
+                *p = off;
+                off += x;
+            }
         }
     }
     if (sg != 0) return;

@@ -253,7 +253,7 @@ static clod_status check_views(const clod_view* views, int32_t V, uint64_t n, Vi
         mtx = std::max<uint32_t>(mtx, (uint32_t)TX);
         dmx = std::max<size_t>(dmx, (size_t)(TX + 1) * (TY + 1));
     }
-    const uint32_t CH = chunk_count(n, bands);
+    const uint32_t CH = chunk_count(n, tt);
     const uint64_t rb = (uint64_t)CH * bands;
     G->diff_max = dmx;
     if (rb > 0x7FFFFFFFull) return fail(CLOD_ERR_ARG, "frame too large");

@@ -26,23 +26,24 @@ constexpr int RS_G1 = 8, RS_G2 = 64;    // radix-sort blocks per group of the tw
 __host__ __device__ inline int rs_groups(int nb, int g) { return (nb + g - 1) / g; }
 constexpr int ROWS_PER_BLOCK = 8;       // tile rows per emission block (one warp each)
 constexpr int MAX_CHUNKS = 256;         // rank chunks per view
-constexpr uint64_t EMIT_TARGET_BLOCKS = 2432;   // emission blocks aimed at (16 per SM of a GB300)
+constexpr int STAGE = 2048;             // rectangles staged in shared memory at a time
+constexpr uint64_t CHUNK_COUNT_WORDS = 1ull << 24;   // per (chunk, tile) counts aimed at: 64 MB, within L2
 
-// Rank chunks per view of a launch whose views have `bands` emission bands
-// (ROWS_PER_BLOCK tile rows) in all: one per 1024 Gaussians, at most
-// MAX_CHUNKS, and no more than keep the emission near EMIT_TARGET_BLOCKS
-// blocks -- the per (chunk, tile) counts are n_chunks x total_tiles words,
-// so a launch of several 4K views takes few chunks.
-inline uint32_t chunk_count(uint64_t n, uint64_t bands)
+// Rank chunks per view of a launch with `tiles` tiles in all: one per 1024
+// Gaussians, at most MAX_CHUNKS, and no more than keep the per (chunk, tile)
+// counts (chunks x tiles words, written, scanned and read by the emission)
+// near CHUNK_COUNT_WORDS -- but at least 32, so that the emission keeps
+// enough blocks (a launch of eight 4K views takes 64).
+inline uint32_t chunk_count(uint64_t n, uint64_t tiles)
 {
     const uint64_t by_n = (n + 1023) / 1024;
-    const uint64_t by_blocks = (EMIT_TARGET_BLOCKS + (bands ? bands : 1) - 1) / (bands ? bands : 1);
-    uint64_t c = by_n < by_blocks ? by_n : by_blocks;
+    uint64_t by_mem = CHUNK_COUNT_WORDS / (tiles ? tiles : 1);
+    if (by_mem < 32) by_mem = 32;
+    uint64_t c = by_n < by_mem ? by_n : by_mem;
     if (c < 1) c = 1;
     if (c > (uint64_t)MAX_CHUNKS) c = MAX_CHUNKS;
     return (uint32_t)c;
 }
-constexpr int STAGE = 2048;             // rectangles staged in shared memory at a time
 
 // Frame header at offset 0 of a frame workspace.
 struct FrameHeader {

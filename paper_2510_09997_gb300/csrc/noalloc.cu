@@ -109,7 +109,7 @@ extern "C" clod_status clod_render_noalloc(const clod_scene* scene, const clod_v
     const uint64_t n = (uint64_t)scene->n;
     const int TX = (w.width + TILE - 1) / TILE, TY = (w.height + TILE - 1) / TILE;
     const uint32_t bands = (uint32_t)((TY + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK);
-    const uint32_t CH = chunk_count(n, bands);
+    const uint32_t CH = chunk_count(n, (uint64_t)TX * TY);
     const uint32_t rb_total = CH * bands;
     const FrameLayout L = frame_layout(n, 1, (uint32_t)(TX * TY), CH, rb_total, (uint32_t)TX,
                                        (size_t)(TX + 1) * (TY + 1));

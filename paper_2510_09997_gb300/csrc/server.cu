@@ -123,7 +123,7 @@ static uint32_t batch_chunks(clod_server* S, const std::vector<const Request*>& 
         tiles += TX * TY;
         bands += (TY + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK;
     }
-    uint64_t c = chunk_count((uint64_t)S->scene.n, bands);
+    uint64_t c = chunk_count((uint64_t)S->scene.n, tiles);
     c = std::min<uint64_t>(c, (uint64_t)L.n_chunks * L.total_tiles / std::max<uint64_t>(1, tiles));
     c = std::min<uint64_t>(c, (uint64_t)L.rb_total / std::max<uint64_t>(1, bands));
     c = std::min<uint64_t>(c, (uint64_t)L.n_chunks * L.n_views / std::max<uint64_t>(1, batch.size()));
@@ -439,9 +439,9 @@ clod_status clod_server_create(const clod_scene* scene, const clod_server_cfg* c
     const uint64_t tiles_by_px = cfg->max_pixels_per_batch / (TILE * TILE) + B * (TXm + TYm + 1);
     S->max_tiles = (uint32_t)std::min<uint64_t>(B * TXm * TYm, tiles_by_px);
     // every batch takes the chunk count of the largest (B views of the largest size)
-    S->ch = chunk_count((uint64_t)scene->n, B * ((TYm + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK));
+    S->ch = chunk_count((uint64_t)scene->n, S->max_tiles);
     S->max_rb = (uint32_t)(B * S->ch * ((TYm + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK));
-    S->solo_ch = chunk_count((uint64_t)scene->n, (TYm + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK);
+    S->solo_ch = chunk_count((uint64_t)scene->n, TXm * TYm);
     S->max_tx = (uint32_t)TXm;
     S->max_diff = (size_t)(TXm + 1) * (TYm + 1);
     S->slots.resize(cfg->n_slots);
