@@ -957,18 +957,24 @@ def run_reference(args):
     allf = frames_list()
     per_step_budget = max(0.05, 120.0 / max(1, args.steps + args.warmup))
     rng = np.random.default_rng(0)
-    times = []
+    frames = step_frames(allf, args.warmup + args.steps)
+    times, walls = [], []
     for k in range(args.warmup + args.steps):
-        c, s = allf[k % len(allf)]
+        c, s = frames[k]
+        a = time.perf_counter()
         t = oracle_frame_sample(O, sc, cams[c].replace(s_v=s), rng, per_step_budget)
         if k >= args.warmup:
             times.append(t)
+            walls.append(time.perf_counter() - a)
     value = len(times) / sum(times)
     sample = ("per step one frame of the sweep: full Stage I and pair emission, the stable sort of at most 2M "
               "random pairs scaled by the pair count, blending of random tiles (8 at a time, %.2f s budget) "
               "scaled to the frame" % per_step_budget)
     out = {"metric": METRIC, "value": round(value, 5), "unit": "frames/s", "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": round(1e3 * sum(times) / len(times), 2), "higher_is_better": True,
+           "warmup": args.warmup, "ms_per_step": round(1e3 * sum(walls) / len(walls), 2), "higher_is_better": True,
+           "frame_ms_extrapolated": round(1e3 * sum(times) / len(times), 2),
+           "step": "one bounded sample of a sweep frame (ms_per_step is its wall time); value is frames/s "
+                   "extrapolated from the samples to whole frames",
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "impl": "reference",
            "config": {"workload": WORKLOAD, "n_gaussians": N_GAUSS, "width": WIDTH, "height": HEIGHT},
            "cpu_baseline": {"value": round(value, 5), "unit": "frames/s", "cores": 1, "kind": "oracle",

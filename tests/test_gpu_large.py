@@ -116,3 +116,22 @@ def test_city_8x4k_backward_parity_on_sampled_tiles(city, city_stage1):
     C, sc, views, ds, fr = city
     _, longest = sparse_check(A, sc, views, seed=12, s1s=city_stage1)
     assert longest > 1000
+
+
+def test_city_8x4k_whole_sorted_list(city, city_stage1):
+    """The whole sorted pair list of the 8 x 4K launch (all ~38 M values and
+    every tile range) bit for bit against the oracle's emission of every
+    survivor's tiles in index order and its stable sort by (tile, depth)."""
+    C, sc, views, ds, fr = city
+    keys, vals, base = [], [], 0
+    for v, view in enumerate(views):
+        k, val = O.emit_pairs(view, city_stage1[v], base)
+        keys.append(k)
+        vals.append(val)
+        tx, ty = O.tiles_of(view)
+        base += tx * ty
+    sk, sv = O.stable_sort(np.concatenate(keys), np.concatenate(vals))
+    del keys, vals
+    assert int(fr.n_pairs) == len(sv)
+    assert np.array_equal(fr.vals[:len(sv)].cpu().numpy().view(np.uint32), sv)
+    assert np.array_equal(fr.ranges.cpu().numpy().view(np.uint32), O.ranges(sk, base))
