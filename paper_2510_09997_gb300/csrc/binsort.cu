@@ -582,11 +582,15 @@ __global__ void __launch_bounds__(CS_TILES * CS_SEG, 2) k_tile_scan(Frame F, uin
     const uint32_t per = (CHe + CS_SEG - 1) / CS_SEG;     // <= CS_MAXPER
     const uint32_t c0 = min(CHe, sg * per), c1 = min(CHe, c0 + per);
     // the segment's counts: summed, then (the second read hits L2) rewritten
-    // as offsets
+    // as offsets; both passes load eight counts at a time, independently
     uint32_t sum = 0;
-#pragma unroll 8
-    for (int k = 0; k < CS_MAXPER; ++k)
-        if (ok && c0 + k < c1) sum += col[(size_t)(c0 + k) * T];
+    for (uint32_t k0 = c0; k0 < c1; k0 += 8) {
+        uint32_t x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = k0 + u < c1 ? col[(size_t)(k0 + u) * T] : 0u;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) sum += x[u];
+    }
     part[sg][tx] = sum;
     __syncthreads();
     uint32_t off = 0, tot = 0;
@@ -596,15 +600,14 @@ __global__ void __launch_bounds__(CS_TILES * CS_SEG, 2) k_tile_scan(Frame F, uin
         if (q < sg) off += x;
         tot += x;
     }
-    if (ok) {
-#pragma unroll 8
-        for (int k = 0; k < CS_MAXPER; ++k) {
-            if (c0 + k < c1) {
-                uint32_t* p = col + (size_t)(c0 + k) * T;
-                const uint32_t x = *p;
-                *p = off;
-                off += x;
-            }
+    for (uint32_t k0 = c0; k0 < c1; k0 += 8) {
+        uint32_t x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = k0 + u < c1 ? col[(size_t)(k0 + u) * T] : 0u;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (k0 + u < c1) col[(size_t)(k0 + u) * T] = off;
+            off += x[u];
         }
     }
     if (sg != 0) return;
