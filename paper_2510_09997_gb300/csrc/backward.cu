@@ -139,7 +139,9 @@ __device__ __forceinline__ bool bwd_pair(BPx& q0, BPx& q1, bool t0, bool t1, flo
     // skipped by the whole warp when no pixel is in range (warp-uniform); a
     // pixel out of range evaluates its exponential too (bwd_tail drops it)
     if (!__any_sync(0xffffffffu, r0 || r1)) return false;
-    if (__any_sync(0xffffffffu, r0 && r1)) {
+    // (with the hardware exponential a second exponential is cheaper than
+    // the vote that would avoid it)
+    if (FAST || __any_sync(0xffffffffu, r0 && r1)) {
         const float G0 = blend_exp<FAST>(p0), G1 = blend_exp<FAST>(p1);
         bool any = bwd_tail(q0, r0, G0, dx, dy0, a, c, cb, g);
         any |= bwd_tail(q1, r1, G1, dx, dy1, a, c, cb, g);
@@ -173,7 +175,7 @@ __device__ __forceinline__ bool bwd_pair(BPx& q0, BPx& q1, bool t0, bool t1, flo
 constexpr int BWD_THREADS = 128;   // 4 warps per tile, 8x8 pixels per warp, 2 per thread
 
 template <bool FAST>
-__global__ void __launch_bounds__(BWD_THREADS, 8) k_blend_bwd(Frame F, const uint32_t* __restrict__ vals,
+__global__ void __launch_bounds__(BWD_THREADS, 6) k_blend_bwd(Frame F, const uint32_t* __restrict__ vals,
                                                            const uint32_t* __restrict__ ranges,
                                                            const float* __restrict__ Tfin,
                                                            const uint32_t* __restrict__ ncon,

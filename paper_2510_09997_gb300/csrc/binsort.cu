@@ -157,7 +157,8 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_rs_scatter(const FrameHeader*
                                                            const uint32_t* __restrict__ totals,
                                                            const uint32_t* __restrict__ sum1,
                                                            const uint32_t* __restrict__ sum2,
-                                                           const uint2* __restrict__ rect, uint2* __restrict__ srect)
+                                                           const uint2* __restrict__ rect, uint2* __restrict__ srect,
+                                                           uint16_t* __restrict__ sband)
 {
     __shared__ uint32_t h[RS_THREADS / 32][256];
     __shared__ uint32_t wb[RS_THREADS / 32][256];
@@ -246,7 +247,12 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_rs_scatter(const FrameHeader*
             const uint32_t pos = wb[w][d] + __popc(peers & lt);
             kout[vbase + pos] = kk[r];
             vout[vbase + pos] = vv[r];
-            if (GATHER) srect[vbase + pos] = rr[r];
+            if (GATHER) {
+                srect[vbase + pos] = rr[r];
+                // the rectangle's band range (ROWS_PER_BLOCK tile rows), for the emission
+                sband[vbase + pos] = (uint16_t)((rr[r].x >> 16) / ROWS_PER_BLOCK |
+                                                (((rr[r].y >> 16) - 1u) / ROWS_PER_BLOCK) << 8);
+            }
         }
         __syncwarp();
         if (valid && (__ffs(peers) - 1) == lane) wb[w][d] += __popc(peers);
@@ -296,7 +302,6 @@ __global__ void __launch_bounds__(ROWS_PER_BLOCK * 32, 4) k_rows(Frame F, uint32
     __shared__ uint2 s_rect[STAGE];
     __shared__ uint32_t s_id[STAGE];
     __shared__ uint32_t s_key[STAGE];
-    __shared__ uint16_t s_list[STAGE];
     __shared__ uint8_t s_rmask[STAGE];      // per listed rectangle: the band's rows it covers
     __shared__ uint32_t s_wc[ROWS_PER_BLOCK];
     __shared__ uint16_t s_buf[ROWS_PER_BLOCK][64];
@@ -330,38 +335,28 @@ __global__ void __launch_bounds__(ROWS_PER_BLOCK * 32, 4) k_rows(Frame F, uint32
         for (int x = lane; x < TX; x += 32)
             ctr[x] = EMIT ? F.tile_offset[W.tile_base + row * TX + x] + cnt_row[x] : 0u;
     const int64_t vb = (int64_t)v * n;
+    const uint32_t bnd = rb;     // this block's band (ROWS_PER_BLOCK tile rows)
     for (uint32_t s0 = r0; s0 < r1; s0 += STAGE) {
         const int m = (int)min((uint32_t)STAGE, r1 - s0);
         __syncthreads();
-        for (int k = threadIdx.x; k < m; k += blockDim.x) {
-            s_rect[k] = F.srect[vb + s0 + k];
-            if (EMIT) {
-                s_id[k] = F.val0[vb + s0 + k];
-                if (keys) s_key[k] = F.key0[vb + s0 + k];
-            }
-        }
-        __syncthreads();
-        // Order-preserving compaction of the staged rectangles that meet this
-        // block's rows: thread t tests entries [t * per, (t + 1) * per), and
-        // an exclusive scan of the hit counts over the threads places them.
+        // Order-preserving compaction of the round's ranks whose rectangle
+        // meets this block's band, from the band ranges the last radix pass
+        // wrote (2 bytes per rank): thread t tests ranks [t * per, (t + 1) * per),
+        // an exclusive scan of the hit counts over the threads places them,
+        // and only the hits' rectangles and indices are fetched.
         int nl;
         {
-            const int band0 = (int)rb * ROWS_PER_BLOCK, band1 = band0 + ROWS_PER_BLOCK;
-            const int per = (m + (int)blockDim.x - 1) / (int)blockDim.x;
+            const int per = (m + (int)blockDim.x - 1) / (int)blockDim.x;     // <= STAGE / blockDim
             const int k0 = (int)threadIdx.x * per;
             uint32_t hm = 0u;
-            unsigned long long rmasks = 0ull;     // 8 bits per tested entry (per <= 8)
             int c = 0;
             for (int j = 0; j < per; ++j) {
                 const int k = k0 + j;
                 if (k < m) {
-                    const uint2 rc = s_rect[k];
-                    const int y0 = (int)(rc.x >> 16), y1 = (int)(rc.y >> 16);
-                    if (y0 < band1 && y1 > band0) {
+                    const uint32_t br = F.sband[vb + s0 + k];
+                    if ((br & 0xFFu) <= bnd && bnd <= (br >> 8)) {
                         hm |= 1u << j;
                         ++c;
-                        const int lo = max(y0, band0) - band0, hi = min(y1, band1) - band0;
-                        rmasks |= (unsigned long long)(((1u << hi) - 1u) & ~((1u << lo) - 1u)) << (8 * j);
                     }
                 }
             }
@@ -378,10 +373,20 @@ __global__ void __launch_bounds__(ROWS_PER_BLOCK * 32, 4) k_rows(Frame F, uint32
                 if (q < w) pos += (int)s_wc[q];
                 nl += (int)s_wc[q];
             }
+            const int band0 = (int)bnd * ROWS_PER_BLOCK, band1 = band0 + ROWS_PER_BLOCK;
             for (int j = 0; hm; ++j, hm >>= 1)
                 if (hm & 1u) {
-                    s_rmask[pos] = (uint8_t)(rmasks >> (8 * j));
-                    s_list[pos++] = (uint16_t)(k0 + j);
+                    const int64_t g = vb + s0 + k0 + j;
+                    const uint2 rc = F.srect[g];
+                    s_rect[pos] = rc;
+                    if (EMIT) {
+                        s_id[pos] = F.val0[g];
+                        if (keys) s_key[pos] = F.key0[g];
+                    }
+                    const int y0 = (int)(rc.x >> 16), y1 = (int)(rc.y >> 16);
+                    const int lo = max(y0, band0) - band0, hi = min(y1, band1) - band0;
+                    s_rmask[pos] = (uint8_t)(((1u << hi) - 1u) & ~((1u << lo) - 1u));
+                    ++pos;
                 }
             __syncthreads();
         }
@@ -395,7 +400,7 @@ __global__ void __launch_bounds__(ROWS_PER_BLOCK * 32, 4) k_rows(Frame F, uint32
                 uint32_t gi_l = 0u;
                 bool hit = false;
                 if (g < nl) {
-                    gi_l = s_list[g];
+                    gi_l = (uint32_t)g;
                     hit = (s_rmask[g] >> w) & 1u;
                 }
                 const unsigned hb = __ballot_sync(0xffffffffu, hit);
@@ -757,10 +762,10 @@ cudaError_t launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long 
             k_rs_hist<<<V * nb, RS_THREADS, 0, st>>>(F.hdr, F.n_surv, ki, n, nb, 8 * pass, F.rs_hist, tot, s1, s2);
             if (pass == 3)
                 k_rs_scatter<true><<<V * nb, RS_THREADS, 0, st>>>(F.hdr, F.n_surv, ki, vi, ko, vo, n, nb, 8 * pass,
-                                                                  F.rs_hist, tot, s1, s2, F.rect, F.srect);
+                                                                  F.rs_hist, tot, s1, s2, F.rect, F.srect, F.sband);
             else
                 k_rs_scatter<false><<<V * nb, RS_THREADS, 0, st>>>(F.hdr, F.n_surv, ki, vi, ko, vo, n, nb, 8 * pass,
-                                                                   F.rs_hist, tot, s1, s2, nullptr, nullptr);
+                                                                   F.rs_hist, tot, s1, s2, nullptr, nullptr, nullptr);
             std::swap(ki, ko);
             std::swap(vi, vo);
         }

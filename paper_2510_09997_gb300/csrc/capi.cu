@@ -85,6 +85,7 @@ FrameLayout frame_layout(uint64_t n, uint32_t V, uint32_t TT, uint32_t n_chunks,
     L.key1 = take(sizeof(uint32_t) * vn);
     L.val1 = take(sizeof(uint32_t) * vn);
     L.srect = take(sizeof(uint2) * vn);
+    L.sband = take(sizeof(uint16_t) * vn);
     // block counts + 4 passes of digit totals and of the two levels of group sums
     const int nbk = (int)L.n_rs_blocks;
     L.rs_hist = take(sizeof(uint32_t) * 256 * (size_t)V *
@@ -124,6 +125,7 @@ Frame frame_ptrs(void* ws, const FrameLayout& L)
     F.key1 = reinterpret_cast<uint32_t*>(b + L.key1);
     F.val1 = reinterpret_cast<uint32_t*>(b + L.val1);
     F.srect = reinterpret_cast<uint2*>(b + L.srect);
+    F.sband = reinterpret_cast<uint16_t*>(b + L.sband);
     F.rs_hist = reinterpret_cast<uint32_t*>(b + L.rs_hist);
     F.scan_st = reinterpret_cast<unsigned long long*>(b + L.scan);
     F.scan_cls = reinterpret_cast<ulonglong2*>(b + L.scan_cls);

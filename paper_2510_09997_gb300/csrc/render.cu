@@ -93,7 +93,9 @@ __device__ __forceinline__ void blend_pair(Px& q0, Px& q1, bool t0, bool t1, flo
     // warp-uniform branch); a pixel out of range evaluates its exponential too
     // (its result is dropped: ok below is false)
     if (!__any_sync(0xffffffffu, r0 || r1)) return;
-    if (__any_sync(0xffffffffu, r0 && r1)) {
+    // (with the hardware exponential a second exponential is cheaper than
+    // the vote that would avoid it)
+    if (FAST || __any_sync(0xffffffffu, r0 && r1)) {
         const float g0 = blend_exp<FAST>(p0), g1 = blend_exp<FAST>(p1);
         const float a0 = fminf(0.99f, __fmul_rn(c.y, g0)), a1 = fminf(0.99f, __fmul_rn(c.y, g1));
         blend_finish(q0, r0 && !(a0 < (1.0f / 255.0f)), a0, c, cb, pos);
