@@ -69,11 +69,15 @@ def sparse_check(A, sc, views, seed, s1s=None, n_alpha=4000, tol=1e-3):
     return err, longest
 
 
-def test_outdoor_3m_four_views_1080p():
+@pytest.mark.parametrize("flags", [0, S.FLAG_FAST_EXP], ids=["exact", "fast_exp"])
+def test_outdoor_3m_four_views_1080p(flags):
+    """With CLOD_FAST_EXP (the training bench's setting) the blends' decisions
+    may move near a threshold against the oracle's frozen FP32 ones; the
+    1e-3 criterion stands."""
     from paper_2510_09997_gb300 import autograd, clod
     clod.require_cuda()
     sc = S.outdoor_scene(3_000_000)
     cams = S.orbit_cameras(16, 1920, 1080, d_min=9.0, d_max=16.0, elev_deg=25.0, seed=2)
-    views = [cams[k].replace(s_v=s) for k, s in zip((0, 5, 10, 15), (1.0, 2.5, 5.0, 9.0))]
+    views = [cams[k].replace(s_v=s, flags=flags) for k, s in zip((0, 5, 10, 15), (1.0, 2.5, 5.0, 9.0))]
     _, longest = sparse_check(autograd, sc, views, seed=11)
     assert longest > 1000

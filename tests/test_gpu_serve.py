@@ -118,3 +118,20 @@ def test_partial_batches_reuse_one_slot(env, graphs):
         for i, o in zip(idx, outs):
             assert torch.equal(o, solo[i]), i
     srv.close()
+
+
+def test_fast_exp_server_equals_solo(env):
+    """A server with fast_exp blends every batch with CLOD_FAST_EXP's
+    exponential: each request equals the same view rendered alone with the
+    flag, bit for bit, in whatever batch it lands."""
+    C, serve, ds, views, _ = env
+    fviews = [v.replace(flags=v.flags | S.FLAG_FAST_EXP) for v in views]
+    solo = []
+    for v in fviews:
+        fr = C.render(ds, [v], want_keys=False)
+        solo.append(fr.view_image(0).clone())
+    torch.cuda.synchronize()
+    outs, stats = run(serve, ds, views, max_views_per_batch=6, n_slots=2, use_graphs=True, fast_exp=True)
+    assert max(st.batch_size for st in stats) > 1
+    for k, (o, want) in enumerate(zip(outs, solo)):
+        assert torch.equal(o, want), k
