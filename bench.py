@@ -80,21 +80,22 @@ def sort_bytes_model(n, n_surv, n_pairs, width, height, views=1):
     """Bytes the sort stage moves as built, for one launch of ``views`` views
     of width x height with n Gaussians, n_surv survivors and n_pairs pairs
     (sums over the views):
-      radix pass 1: every view's n depth keys read for the counts (4 B), keys
-        and values read and the survivors' written (8 B each);
+      radix pass 1: every view's n depth keys read twice, for the counts and
+        the scatter (4 B each; the values are the indices, not read), and the
+        survivors' keys and values written (8 B);
       passes 2-4: the survivors' keys counted (4 B), keys and values read and
         written (16 B); the last also gathers each survivor's rectangle into
-        rank order (8 B read, 8 B written);
+        rank order (8 B read, 8 B written) and writes its band range (2 B);
       chunk counts: the survivors' rectangles read (8 B); per (chunk, tile) a
         count written, scanned (read, written) and read by the emission (16 B);
       tile scan: per tile its count, offset, range and work-order entry (20 B);
-      emission: the survivors' rectangles and indices read (12 B), one 4 B
-        index written per pair.
+      emission: the survivors' band ranges, rectangles and indices read (14 B),
+        one 4 B index written per pair.
     The chunks are min(256, ceil(n_surv / 1024)) per view."""
     T = views * ((width + 15) // 16) * ((height + 15) // 16)
     chunks = min(256, max(1, -(-int(n_surv) // (1024 * views))))
-    return (12 * n * views + 8 * n_surv + 3 * 20 * n_surv + 16 * n_surv + 8 * n_surv + 16 * chunks * T + 20 * T
-            + 12 * n_surv + 4 * n_pairs)
+    return (8 * n * views + 8 * n_surv + 3 * 20 * n_surv + 18 * n_surv + 8 * n_surv + 16 * chunks * T + 20 * T
+            + 14 * n_surv + 4 * n_pairs)
 
 
 def shard_frames(frames, rank, world):
@@ -375,9 +376,9 @@ def run_ours(args):
     n = float(N_GAUSS)
     sh_bytes = 12 * 16
     # preprocess: means twice (distance pass + main pass), opacity, decay, and per
-    # Gaussian rect + sort key/value written; per survivor scales, quats, SH read
+    # Gaussian rect + depth key written; per survivor scales, quats, SH read
     # and the 52 B of records written (three float4 and the depth)
-    pre_bytes = (12 + 12 + 8 + 16) * n * len(n_surv) + (28 + sh_bytes + 52) * n_surv.sum()
+    pre_bytes = (12 + 12 + 8 + 12) * n * len(n_surv) + (28 + sh_bytes + 52) * n_surv.sum()
     sort_bytes = sum(sort_bytes_model(n, s_, k_, WIDTH, HEIGHT) for s_, k_ in zip(n_surv, n_pairs))
     radix_equiv = 152 * n_pairs.sum()       # 6-pass LSD sort of K (u64 key, u32 value) pairs
     cnt3 = evals.cpu().numpy().astype(np.float64) / args.steps

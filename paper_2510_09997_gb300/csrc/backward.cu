@@ -181,6 +181,7 @@ __global__ void __launch_bounds__(BWD_THREADS, 6) k_blend_bwd(Frame F, const uin
                                                            const uint32_t* __restrict__ ncon,
                                                            const float* __restrict__ dimg, float* __restrict__ g2d)
 {
+    pdl_wait();
     __shared__ float4 s0[4][32];
     __shared__ float4 s1[4][32];
     __shared__ float4 s2[4][32];
@@ -347,6 +348,7 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(Frame F, clod_scene S, c
                                                         const float* __restrict__ g_alpha_view,
                                                         float* __restrict__ dmax_grad, ParamGrads P)
 {
+    pdl_wait();
     __shared__ ViewDev sv[MAX_VIEWS];
     __shared__ float sdmax[MAX_VIEWS];
     __shared__ float sdmg[MAX_VIEWS];
@@ -613,6 +615,7 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(Frame F, clod_scene S, c
 // d_max = d_{j*}: dL/dmu_{j*} += (dL/d d_max) (mu_{j*} - c) / d_{j*}.
 __global__ void k_dmax_bwd(Frame F, clod_scene S, const float* __restrict__ dmax_grad, float* __restrict__ dmeans)
 {
+    pdl_wait();
     const uint32_t V = F.hdr->n_views;
     for (uint32_t v = threadIdx.x; v < V; v += blockDim.x) {
         const unsigned long long key = F.dmax_key[v];
@@ -634,6 +637,7 @@ __global__ void k_dmax_bwd(Frame F, clod_scene S, const float* __restrict__ dmax
 __global__ void k_l1_loss(const float* __restrict__ img, const float* __restrict__ tgt, int64_t count, float scale,
                           float* __restrict__ loss, float* __restrict__ grad)
 {
+    pdl_wait();
     float acc = 0.f;
     const float w = scale / static_cast<float>(count);
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x) {
@@ -675,23 +679,23 @@ void launch_backward(const Frame& F, const clod_scene& S, uint32_t V, const uint
     cudaMemsetAsync(bwd_ws, 0, L.total, st);
     cudaMemsetAsync(&F.hdr->work[1], 0, sizeof(uint32_t), st);
     if (fast)
-        k_blend_bwd<true><<<n_sm * std::max(1, g_bwd_blocks_per_sm), BWD_THREADS, 0, st>>>(
-            F, vals, ranges, Tfin, ncon, dimg, reinterpret_cast<float*>(g2d));
+        launch(k_blend_bwd<true>, n_sm * std::max(1, g_bwd_blocks_per_sm), BWD_THREADS, 0, st, F, vals, ranges, Tfin,
+               ncon, dimg, reinterpret_cast<float*>(g2d));
     else
-        k_blend_bwd<false><<<n_sm * std::max(1, g_bwd_blocks_per_sm), BWD_THREADS, 0, st>>>(
-            F, vals, ranges, Tfin, ncon, dimg, reinterpret_cast<float*>(g2d));
+        launch(k_blend_bwd<false>, n_sm * std::max(1, g_bwd_blocks_per_sm), BWD_THREADS, 0, st, F, vals, ranges, Tfin,
+               ncon, dimg, reinterpret_cast<float*>(g2d));
     ParamGrads P{dmeans, dscales, dquats, dopacity, dsh, ddecay};
     int blocks = static_cast<int>(std::min<int64_t>((S.n + 127) / 128, (int64_t)n_sm * 16));
     if (blocks < 1) blocks = 1;
     if (S.n > 0) {
         switch (S.sh_degree) {
-        case 0: k_preprocess_bwd<0><<<blocks, 128, 0, st>>>(F, S, g2d, g_alpha_ext, g_alpha_view, dmg, P); break;
-        case 1: k_preprocess_bwd<1><<<blocks, 128, 0, st>>>(F, S, g2d, g_alpha_ext, g_alpha_view, dmg, P); break;
-        case 2: k_preprocess_bwd<2><<<blocks, 128, 0, st>>>(F, S, g2d, g_alpha_ext, g_alpha_view, dmg, P); break;
-        default: k_preprocess_bwd<3><<<blocks, 128, 0, st>>>(F, S, g2d, g_alpha_ext, g_alpha_view, dmg, P); break;
+        case 0: launch(k_preprocess_bwd<0>, blocks, 128, 0, st, F, S, g2d, g_alpha_ext, g_alpha_view, dmg, P); break;
+        case 1: launch(k_preprocess_bwd<1>, blocks, 128, 0, st, F, S, g2d, g_alpha_ext, g_alpha_view, dmg, P); break;
+        case 2: launch(k_preprocess_bwd<2>, blocks, 128, 0, st, F, S, g2d, g_alpha_ext, g_alpha_view, dmg, P); break;
+        default: launch(k_preprocess_bwd<3>, blocks, 128, 0, st, F, S, g2d, g_alpha_ext, g_alpha_view, dmg, P); break;
         }
     }
-    k_dmax_bwd<<<1, 64, 0, st>>>(F, S, dmg, dmeans);
+    launch(k_dmax_bwd, 1, 64, 0, st, F, S, dmg, dmeans);
 }
 
 size_t backward_ws_bytes(uint64_t n, uint32_t V) { return bwd_layout(n, V).total; }
@@ -701,7 +705,7 @@ void launch_l1(const float* img, const float* tgt, int64_t count, float scale, f
 {
     int blocks = static_cast<int>(std::min<int64_t>((count + 255) / 256, (int64_t)n_sm * 4));
     if (blocks < 1) blocks = 1;
-    k_l1_loss<<<blocks, 256, 0, st>>>(img, tgt, count, scale, loss, grad);
+    launch(k_l1_loss, blocks, 256, 0, st, img, tgt, count, scale, loss, grad);
 }
 
 }  // namespace clod

@@ -114,6 +114,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const FrameHeader* __res
                                                         uint32_t* __restrict__ hist, uint32_t* __restrict__ totals,
                                                         uint32_t* __restrict__ sum1, uint32_t* __restrict__ sum2)
 {
+    pdl_wait();
     __shared__ uint32_t h[RS_THREADS / 32][256];
     const int b = blockIdx.x, v = b / nb, lb = b % nb;
     const int64_t base = (int64_t)v * n + (int64_t)lb * RS_ITEMS;
@@ -160,6 +161,7 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_rs_scatter(const FrameHeader*
                                                            const uint2* __restrict__ rect, uint2* __restrict__ srect,
                                                            uint16_t* __restrict__ sband)
 {
+    pdl_wait();
     __shared__ uint32_t h[RS_THREADS / 32][256];
     __shared__ uint32_t wb[RS_THREADS / 32][256];
     __shared__ uint32_t dbase[256];
@@ -183,10 +185,12 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_rs_scatter(const FrameHeader*
     uint32_t kk[RS_R], vv[RS_R];
     uint2 rr[RS_R];
     rs_load_keys(kin, base, cnt, kk);
+    // the first pass's values are the Gaussian indices themselves (item idx
+    // of block lb is Gaussian lb * RS_ITEMS + idx); later passes load them
 #pragma unroll
     for (int r = 0; r < RS_R; ++r) {
         const int idx = w * RS_PER_WARP + r * 32 + lane;
-        vv[r] = idx < cnt ? vin[base + idx] : 0u;
+        vv[r] = first ? (uint32_t)(lb * RS_ITEMS + idx) : (idx < cnt ? vin[base + idx] : 0u);
     }
     const uint32_t c_tot = totals[v * 256 + threadIdx.x];
     // this block's offset within the digit: the counts of the earlier blocks,
@@ -298,6 +302,7 @@ template <bool EMIT>
 __global__ void __launch_bounds__(ROWS_PER_BLOCK * 32, 4) k_rows(Frame F, uint32_t* __restrict__ vals,
                                                              unsigned long long* __restrict__ keys)
 {
+    pdl_wait();
     extern __shared__ uint32_t sm[];
     __shared__ uint2 s_rect[STAGE];
     __shared__ uint32_t s_id[STAGE];
@@ -473,12 +478,45 @@ __global__ void __launch_bounds__(ROWS_PER_BLOCK * 32, 4) k_rows(Frame F, uint32
         for (int x = lane; x < TX; x += 32) cnt_row[x] = ctr[x];
 }
 
+// Inclusive prefix sums of `lines` lines of `len` words of g: element j of
+// line i at g[i * line_stride + j * step].  Called by every thread of the
+// block (the shuffles take whole warps).
+constexpr int CC_SEG = 4;
+__device__ __forceinline__ void chunk_prefix_lines(uint32_t* g, int lines, int len, int line_stride, int step)
+{
+    const int per_sweep = (int)blockDim.x / CC_SEG;
+    const int li = (int)threadIdx.x / CC_SEG, sg = (int)threadIdx.x % CC_SEG;
+    const int L = (len + CC_SEG - 1) / CC_SEG;
+    const int ja = min(len, sg * L), jb = min(len, ja + L);
+    for (int i0 = 0; i0 < lines; i0 += per_sweep) {
+        const int i = i0 + li;
+        uint32_t* line = g + (size_t)min(i, lines - 1) * line_stride;
+        const bool ok = i < lines;
+        uint32_t sum = 0;
+        if (ok)
+            for (int j = ja; j < jb; ++j) sum += line[j * step];
+        uint32_t inc = sum;
+#pragma unroll
+        for (int o = 1; o < CC_SEG; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, inc, o, CC_SEG);
+            if (sg >= o) inc += u;
+        }
+        uint32_t run = inc - sum;
+        if (ok)
+            for (int j = ja; j < jb; ++j) {
+                run += line[j * step];
+                line[j * step] = run;
+            }
+    }
+}
+
 // 2'. per (view, chunk): the chunk's pair count of every tile from a 2D
 // difference array in shared memory -- each rectangle [x0,x1)x[y0,y1) adds
 // +1 at (x0,y0), (x1,y1) and -1 at (x1,y0), (x0,y1) -- and a 2D prefix sum.
 // Used when the (TX+1)(TY+1) grid fits in shared memory.
 __global__ void __launch_bounds__(512) k_chunk_count(Frame F)
 {
+    pdl_wait();
     extern __shared__ uint32_t g[];
     const FrameHeader* hdr = F.hdr;
     if (hdr->status & STATUS_TIMEOUT) return;     // a look-back gave up: the rank order is not valid
@@ -507,21 +545,13 @@ __global__ void __launch_bounds__(512) k_chunk_count(Frame F)
         atomicAdd_block(&g[y1 * GX + x1], 1u);
     }
     __syncthreads();
-    for (int y = threadIdx.x; y < TY; y += blockDim.x) {
-        uint32_t run = 0;
-        for (int x = 0; x < TX; ++x) {
-            run += g[y * GX + x];
-            g[y * GX + x] = run;
-        }
-    }
+    // inclusive prefix along each row, then along each column; a line is cut
+    // into CC_SEG segments, one per lane of a group of CC_SEG consecutive
+    // lanes: each lane sums its segment, the group scans the sums, and each
+    // lane rewrites its segment from its offset
+    chunk_prefix_lines(g, TY, TX, GX, 1);
     __syncthreads();
-    for (int x = threadIdx.x; x < TX; x += blockDim.x) {
-        uint32_t run = 0;
-        for (int y = 0; y < TY; ++y) {
-            run += g[y * GX + x];
-            g[y * GX + x] = run;
-        }
-    }
+    chunk_prefix_lines(g, TX, TY, 1, GX);
     __syncthreads();
     const uint32_t T = (uint32_t)(TX * TY);
     uint32_t* out = F.cnt + (size_t)CH * W.tile_base + (size_t)c * T;
@@ -560,6 +590,7 @@ __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned lon
 __global__ void __launch_bounds__(CS_TILES * CS_SEG, 2) k_tile_scan(Frame F, uint32_t* __restrict__ ranges,
                                                                   unsigned long long cap)
 {
+    pdl_wait();
     __shared__ uint32_t part[CS_SEG][CS_TILES];
     __shared__ uint32_t s_blk;
     FrameHeader* hdr = F.hdr;
@@ -586,34 +617,27 @@ __global__ void __launch_bounds__(CS_TILES * CS_SEG, 2) k_tile_scan(Frame F, uin
     }
     const uint32_t per = (CHe + CS_SEG - 1) / CS_SEG;     // <= CS_MAXPER
     const uint32_t c0 = min(CHe, sg * per), c1 = min(CHe, c0 + per);
-    // the segment's counts: summed, then (the second read hits L2) rewritten
-    // as offsets; both passes load eight counts at a time, independently
+    // the segment's counts, all loaded at once (one round trip) and held:
+    // summed, then rewritten as offsets
+    uint32_t xs[CS_MAXPER];
+#pragma unroll
+    for (int u = 0; u < CS_MAXPER; ++u) xs[u] = c0 + u < c1 ? col[(size_t)(c0 + u) * T] : 0u;
     uint32_t sum = 0;
-    for (uint32_t k0 = c0; k0 < c1; k0 += 8) {
-        uint32_t x[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) x[u] = k0 + u < c1 ? col[(size_t)(k0 + u) * T] : 0u;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) sum += x[u];
-    }
+    for (int u = 0; u < CS_MAXPER; ++u) sum += xs[u];
     part[sg][tx] = sum;
     __syncthreads();
     uint32_t off = 0, tot = 0;
 #pragma unroll
     for (int q = 0; q < CS_SEG; ++q) {
-        const uint32_t x = part[q][tx];
-        if (q < sg) off += x;
-        tot += x;
+        const uint32_t y = part[q][tx];
+        if (q < sg) off += y;
+        tot += y;
     }
-    for (uint32_t k0 = c0; k0 < c1; k0 += 8) {
-        uint32_t x[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) x[u] = k0 + u < c1 ? col[(size_t)(k0 + u) * T] : 0u;
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            if (k0 + u < c1) col[(size_t)(k0 + u) * T] = off;
-            off += x[u];
-        }
+    for (int u = 0; u < CS_MAXPER; ++u) {
+        if (c0 + u < c1) col[(size_t)(c0 + u) * T] = off;
+        off += xs[u];
     }
     if (sg != 0) return;
     // warp 0, one lane per tile: scan over the block's tiles, then over the
@@ -736,8 +760,17 @@ __global__ void __launch_bounds__(CS_TILES * CS_SEG, 2) k_tile_scan(Frame F, uin
 
 constexpr size_t DIFF_SMEM_MAX = 200 * 1024;   // difference grid limit (a 4K view needs 131 KB)
 
-// Returns the result of clearing the digit totals (the launches' own errors
-// surface through cudaGetLastError).
+// Clears n words: the radix passes' digit sums and the tile scan's look-back
+// words and counters, in the stream's chain of dependent launches.
+__global__ void __launch_bounds__(256) k_clear(uint32_t* __restrict__ p, size_t n)
+{
+    pdl_wait();
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+        p[k] = 0u;
+}
+
+// Returns the error of the first launch, the clear (the later launches'
+// errors surface through cudaGetLastError).
 cudaError_t launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long long cap, uint64_t* keys,
                             uint32_t* vals, uint32_t* ranges, cudaStream_t st)
 {
@@ -751,32 +784,35 @@ cudaError_t launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long 
     const size_t n1 = (size_t)V * 256 * rs_groups(nb, RS_G1), n2 = (size_t)V * 256 * rs_groups(nb, RS_G2);
     const size_t per_pass = (size_t)V * 256 + n1 + n2;
     uint32_t* sums = F.rs_hist + (size_t)V * 256 * nb;
-    err = cudaMemsetAsync(sums, 0, reinterpret_cast<const char*>(F.scan_ctr + 8) - reinterpret_cast<const char*>(sums), st);
+    const size_t words = static_cast<size_t>(F.scan_ctr + 8 - sums);
+    err = launch(k_clear, (unsigned)std::max<size_t>(1, std::min<size_t>((words + 255) / 256, 1024)), 256, 0, st, sums,
+                 words);
     if (err != cudaSuccess) return err;
     if (n > 0) {
+        // the first pass reads no values (they are the indices): vi is unused there
         uint32_t *ki = F.key0, *vi = F.val0, *ko = F.key1, *vo = F.val1;
         for (int pass = 0; pass < 4; ++pass) {
             uint32_t* tot = sums + (size_t)pass * per_pass;
             uint32_t* s1 = tot + (size_t)V * 256;
             uint32_t* s2 = s1 + n1;
-            k_rs_hist<<<V * nb, RS_THREADS, 0, st>>>(F.hdr, F.n_surv, ki, n, nb, 8 * pass, F.rs_hist, tot, s1, s2);
+            launch(k_rs_hist, V * nb, RS_THREADS, 0, st, F.hdr, F.n_surv, ki, n, nb, 8 * pass, F.rs_hist, tot, s1, s2);
             if (pass == 3)
-                k_rs_scatter<true><<<V * nb, RS_THREADS, 0, st>>>(F.hdr, F.n_surv, ki, vi, ko, vo, n, nb, 8 * pass,
-                                                                  F.rs_hist, tot, s1, s2, F.rect, F.srect, F.sband);
+                launch(k_rs_scatter<true>, V * nb, RS_THREADS, 0, st, F.hdr, F.n_surv, ki, vi, ko, vo, n, nb, 8 * pass,
+                       F.rs_hist, tot, s1, s2, F.rect, F.srect, F.sband);
             else
-                k_rs_scatter<false><<<V * nb, RS_THREADS, 0, st>>>(F.hdr, F.n_surv, ki, vi, ko, vo, n, nb, 8 * pass,
-                                                                   F.rs_hist, tot, s1, s2, nullptr, nullptr, nullptr);
+                launch(k_rs_scatter<false>, V * nb, RS_THREADS, 0, st, F.hdr, F.n_surv, ki, vi, ko, vo, n, nb, 8 * pass,
+                       F.rs_hist, tot, s1, s2, nullptr, nullptr, nullptr);
             std::swap(ki, ko);
             std::swap(vi, vo);
         }
     }
     const size_t smem = (size_t)ROWS_PER_BLOCK * L.max_tx * sizeof(uint32_t);
     if (L.diff_grid_max * sizeof(uint32_t) <= DIFF_SMEM_MAX)
-        k_chunk_count<<<V * L.n_chunks, 512, L.diff_grid_max * sizeof(uint32_t), st>>>(F);
+        launch(k_chunk_count, V * L.n_chunks, 512, L.diff_grid_max * sizeof(uint32_t), st, F);
     else
-        k_rows<false><<<L.rb_total, ROWS_PER_BLOCK * 32, smem, st>>>(F, nullptr, nullptr);
-    k_tile_scan<<<(L.total_tiles + CS_TILES - 1) / CS_TILES, CS_TILES * CS_SEG, 0, st>>>(F, ranges, cap);
-    k_rows<true><<<L.rb_total, ROWS_PER_BLOCK * 32, smem, st>>>(F, vals, reinterpret_cast<unsigned long long*>(keys));
+        launch(k_rows<false>, L.rb_total, ROWS_PER_BLOCK * 32, smem, st, F, nullptr, nullptr);
+    launch(k_tile_scan, (L.total_tiles + CS_TILES - 1) / CS_TILES, CS_TILES * CS_SEG, 0, st, F, ranges, cap);
+    launch(k_rows<true>, L.rb_total, ROWS_PER_BLOCK * 32, smem, st, F, vals, reinterpret_cast<unsigned long long*>(keys));
     return err;
 }
 

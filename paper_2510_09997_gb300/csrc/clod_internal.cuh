@@ -15,6 +15,37 @@
 
 namespace clod {
 
+// Programmatic dependent launch.  The library launches its kernels with
+// launch() below, which lets the next kernel of the stream be launched while
+// this one drains: a dependent launch gap (about 4 us on a 152-SM part for a
+// grid of a wave or more) shrinks to about 1.4 us.  Every kernel therefore
+// begins with pdl_wait(), before any access to global memory: it returns once
+// every earlier kernel of the stream has completed and its writes are visible
+// (at once for a launch without the dependency), so no kernel overlaps its
+// predecessor's accesses.  No kernel releases its dependents early: blocks
+// waiting in pdl_wait would hold SM slots that kernels of other streams (other
+// frames in flight) could use.
+__device__ __forceinline__ void pdl_wait()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+template <typename... P, typename... A>
+inline cudaError_t launch(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, A... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 constexpr int TILE = 16;
 constexpr int BLOCK_PIX = TILE * TILE;  // 256 threads per tile block
 constexpr int MAX_VIEWS = 64;

@@ -56,6 +56,7 @@ __global__ void __launch_bounds__(SS_T * SS_T) k_ssim_fwd(const float* __restric
                                                           int W, int H, float lam, float inv_n, float* __restrict__ loss,
                                                           float* __restrict__ maps)
 {
+    pdl_wait();
     __shared__ float sx[SS_H][SS_H], sy[SS_H][SS_H];
     __shared__ float hb[5][SS_H][SS_T];
     const int c = blockIdx.z;
@@ -128,6 +129,7 @@ __global__ void __launch_bounds__(SS_T * SS_T) k_ssim_bwd(const float* __restric
                                                           int W, int H, float lam, float ginv_n,
                                                           const float* __restrict__ maps, float* __restrict__ grad)
 {
+    pdl_wait();
     __shared__ float sm[3][SS_H][SS_H];
     __shared__ float hb[3][SS_H][SS_T];
     const int c = blockIdx.z;
@@ -174,6 +176,7 @@ __global__ void __launch_bounds__(256) k_l1_term(const float* __restrict__ img, 
                                                  int64_t count, float inv_n, float ginv_n, float* __restrict__ loss,
                                                  float* __restrict__ grad)
 {
+    pdl_wait();
     float acc = 0.0f;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < count; k += (int64_t)gridDim.x * blockDim.x) {
         const float d = img[k] - tgt[k];
@@ -236,17 +239,17 @@ clod_status clod_render_loss(const float* image, const float* target, int32_t ch
     const float inv_n = 1.0f / (float)count;
     if (dssim_weight == 0.0f) {
         const int blocks = static_cast<int>(std::min<int64_t>((count + 255) / 256, (int64_t)n_sm * 4));
-        k_l1_term<<<blocks, 256, 0, st>>>(image, target, count, inv_n, grad_scale * inv_n, loss, dL_dimage);
+        launch(k_l1_term, blocks, 256, 0, st, image, target, count, inv_n, grad_scale * inv_n, loss, dL_dimage);
     } else {
         if (dL_dimage && (!ws || ws_bytes < need))
             return fail(CLOD_ERR_CAPACITY, "render-loss workspace needs %zu bytes, got %zu", need, ws_bytes);
         if ((s = window_ready())) return s;
         const dim3 grid((width + SS_T - 1) / SS_T, (height + SS_T - 1) / SS_T, channels);
         float* maps = dL_dimage ? static_cast<float*>(ws) : nullptr;
-        k_ssim_fwd<<<grid, SS_T * SS_T, 0, st>>>(image, target, width, height, dssim_weight, inv_n, loss, maps);
+        launch(k_ssim_fwd, grid, SS_T * SS_T, 0, st, image, target, width, height, dssim_weight, inv_n, loss, maps);
         if (dL_dimage)
-            k_ssim_bwd<<<grid, SS_T * SS_T, 0, st>>>(image, target, width, height, dssim_weight, grad_scale * inv_n,
-                                                     maps, dL_dimage);
+            launch(k_ssim_bwd, grid, SS_T * SS_T, 0, st, image, target, width, height, dssim_weight,
+                   grad_scale * inv_n, maps, dL_dimage);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "clod_render_loss launch");

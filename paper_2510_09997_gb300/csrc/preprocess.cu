@@ -41,6 +41,7 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long x)
 // distances, the lowest index.  0 means "no Gaussian in the frustum".
 __global__ void __launch_bounds__(256) k_dist_max(Frame F, const float* __restrict__ means, int64_t n)
 {
+    pdl_wait();
     const uint32_t V = F.hdr->n_views;
     __shared__ ViewDev sv[MAX_VIEWS];
     __shared__ unsigned long long wmax[8];
@@ -96,6 +97,7 @@ __global__ void __launch_bounds__(256, 4) k_preprocess(Frame F, clod_scene S, ui
                                                     float* __restrict__ alpha_out,
                                                     unsigned long long* __restrict__ n_pairs_out)
 {
+    pdl_wait();
     const uint32_t V = F.hdr->n_views;
     __shared__ ViewDev sv[MAX_VIEWS];
     __shared__ float sdmax[MAX_VIEWS];
@@ -319,7 +321,6 @@ __global__ void __launch_bounds__(256, 4) k_preprocess(Frame F, clod_scene S, ui
             if (active) {
                 F.rect[o] = rect;
                 F.key0[o] = dkey;
-                F.val0[o] = static_cast<uint32_t>(i);
             }
             // per-view counts: warp-aggregated, then one shared atomic per warp
             const unsigned bm = __ballot_sync(0xffffffffu, M);
@@ -365,6 +366,7 @@ template <int MAXV>
 __global__ void __launch_bounds__(256) k_frame_setup(const SetupArgs<MAXV> a, Frame F, char* base, size_t zero_begin,
                                                      size_t zero_end)
 {
+    pdl_wait();
     uint32_t* z = reinterpret_cast<uint32_t*>(base + zero_begin);
     const size_t words = (zero_end - zero_begin) / 4;
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < words; k += (size_t)gridDim.x * blockDim.x)
@@ -387,7 +389,7 @@ static void setup_launch(const Frame& F, void* ws, const FrameHeader& h, const V
     for (uint32_t v = 0; v < h.n_views; ++v) a.views[v] = views[v];
     const size_t words = (zero_end - zero_begin) / 4;
     const int blocks = static_cast<int>(std::max<size_t>(1, std::min<size_t>((words + 255) / 256, (size_t)n_sm * 2)));
-    k_frame_setup<MAXV><<<blocks, 256, 0, st>>>(a, F, static_cast<char*>(ws), zero_begin, zero_end);
+    launch(k_frame_setup<MAXV>, blocks, 256, 0, st, a, F, static_cast<char*>(ws), zero_begin, zero_end);
 }
 
 void launch_frame_setup(const Frame& F, void* ws, const FrameHeader& h, const ViewDev* views, size_t zero_begin,
@@ -409,14 +411,14 @@ void launch_preprocess(const Frame& F, const clod_scene& S, uint32_t V, uint8_t*
     int blocks = static_cast<int>(std::min<int64_t>((n + 255) / 256, (int64_t)n_sm * 4));
     if (blocks < 1) blocks = 1;
     const int dm_blocks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((n + 1023) / 1024, (int64_t)n_sm * 4)));
-    if (n > 0) k_dist_max<<<dm_blocks, 256, 0, st>>>(F, S.means, n);
+    if (n > 0) launch(k_dist_max, dm_blocks, 256, 0, st, F, S.means, n);
     if (n > 0 && select) launch_budget_select(F, S, V, n_sm, st);
     if (n > 0) {
         switch (S.sh_degree) {
-        case 0: k_preprocess<0><<<blocks, 256, 0, st>>>(F, S, mask_out, alpha_out, n_pairs_out); break;
-        case 1: k_preprocess<1><<<blocks, 256, 0, st>>>(F, S, mask_out, alpha_out, n_pairs_out); break;
-        case 2: k_preprocess<2><<<blocks, 256, 0, st>>>(F, S, mask_out, alpha_out, n_pairs_out); break;
-        default: k_preprocess<3><<<blocks, 256, 0, st>>>(F, S, mask_out, alpha_out, n_pairs_out); break;
+        case 0: launch(k_preprocess<0>, blocks, 256, 0, st, F, S, mask_out, alpha_out, n_pairs_out); break;
+        case 1: launch(k_preprocess<1>, blocks, 256, 0, st, F, S, mask_out, alpha_out, n_pairs_out); break;
+        case 2: launch(k_preprocess<2>, blocks, 256, 0, st, F, S, mask_out, alpha_out, n_pairs_out); break;
+        default: launch(k_preprocess<3>, blocks, 256, 0, st, F, S, mask_out, alpha_out, n_pairs_out); break;
         }
     }
     if (n_pairs_out && n <= 0)   // otherwise k_preprocess's last block writes it

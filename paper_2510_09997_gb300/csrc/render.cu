@@ -146,6 +146,7 @@ __global__ void __launch_bounds__(BLEND_THREADS, 9) k_blend_fwd(Frame F, const u
                                                              uint32_t* __restrict__ ncout,
                                                              unsigned long long* __restrict__ evaluated)
 {
+    pdl_wait();
     __shared__ float4 s0[4][32];
     __shared__ float4 s1[4][32];
     __shared__ float4 s2[4][32];
@@ -270,11 +271,11 @@ void launch_blend_fwd(const Frame& F, const uint32_t* vals, const uint32_t* rang
 {
     const int blocks = n_sm * std::max(1, g_blend_blocks_per_sm[fast ? 1 : 0]);
     if (evaluated)
-        k_blend_fwd<true, false><<<blocks, BLEND_THREADS, 0, st>>>(F, vals, ranges, image, Tout, ncout, evaluated);
+        launch(k_blend_fwd<true, false>, blocks, BLEND_THREADS, 0, st, F, vals, ranges, image, Tout, ncout, evaluated);
     else if (fast)
-        k_blend_fwd<false, true><<<blocks, BLEND_THREADS, 0, st>>>(F, vals, ranges, image, Tout, ncout, nullptr);
+        launch(k_blend_fwd<false, true>, blocks, BLEND_THREADS, 0, st, F, vals, ranges, image, Tout, ncout, nullptr);
     else
-        k_blend_fwd<false, false><<<blocks, BLEND_THREADS, 0, st>>>(F, vals, ranges, image, Tout, ncout, nullptr);
+        launch(k_blend_fwd<false, false>, blocks, BLEND_THREADS, 0, st, F, vals, ranges, image, Tout, ncout, nullptr);
 }
 
 }  // namespace clod

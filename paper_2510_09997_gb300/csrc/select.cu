@@ -28,6 +28,7 @@ __constant__ int c_sel_bits[SEL_PASSES] = {11, 11, 10, 11, 11, 10};
 
 __global__ void __launch_bounds__(256) k_sel_init(Frame F)
 {
+    pdl_wait();
     const uint32_t v = blockIdx.x;
     if (v >= F.hdr->n_views) return;
     const ViewDev& W = F.views[v];
@@ -45,6 +46,7 @@ __global__ void __launch_bounds__(256) k_sel_init(Frame F)
 
 __global__ void __launch_bounds__(256) k_sel_count(Frame F, clod_scene S, int pass)
 {
+    pdl_wait();
     __shared__ uint32_t h[SEL_BINS];
     __shared__ ViewDev W;
     __shared__ SelState st;
@@ -92,6 +94,7 @@ __global__ void __launch_bounds__(256) k_sel_count(Frame F, clod_scene S, int pa
 // of keys above each bin.
 __global__ void __launch_bounds__(1024) k_sel_pick(Frame F, int pass)
 {
+    pdl_wait();
     __shared__ uint32_t wsum[32];
     __shared__ int found;
     const uint32_t v = blockIdx.x;
@@ -156,10 +159,10 @@ void launch_budget_select(const Frame& F, const clod_scene& S, uint32_t V, int n
     const int64_t n = S.n;
     if (n <= 0) return;
     const int blocks = static_cast<int>(std::min<int64_t>((n + 255) / 256, (int64_t)n_sm * 4));
-    k_sel_init<<<V, 256, 0, st>>>(F);
+    launch(k_sel_init, V, 256, 0, st, F);
     for (int p = 0; p < SEL_PASSES; ++p) {
-        k_sel_count<<<std::max(blocks, 1), 256, 0, st>>>(F, S, p);
-        k_sel_pick<<<V, 1024, 0, st>>>(F, p);
+        launch(k_sel_count, std::max(blocks, 1), 256, 0, st, F, S, p);
+        launch(k_sel_pick, V, 1024, 0, st, F, p);
     }
 }
 

@@ -32,6 +32,7 @@ __global__ void k_lreg(const uint32_t* __restrict__ counts, double inv_n, float 
                        const float* __restrict__ lrender, float* __restrict__ dalpha, float* __restrict__ total,
                        float* __restrict__ lreg_out)
 {
+    pdl_wait();
     __shared__ float part[MAX_VIEWS];
     const int v = threadIdx.x;
     float t = 0.0f;
@@ -88,6 +89,7 @@ __device__ __forceinline__ float activate(int gi, float p)
 // load issued before any store; a scalar tail finishes each group.
 __global__ void __launch_bounds__(256) k_adam(AdamArgs A, float* __restrict__ m, float* __restrict__ v)
 {
+    pdl_wait();
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int gi = 0; gi < 6; ++gi) {
@@ -199,8 +201,8 @@ clod_status clod_lreg_grad(const uint32_t* counts, int64_t n, int32_t n_views, c
     int n_sm = 0;
     clod_status s = device_ready(&n_sm);
     if (s) return s;
-    k_lreg<<<1, MAX_VIEWS, 0, static_cast<cudaStream_t>(stream)>>>(counts, 1.0 / (double)n, lambda_reg, n_views, a,
-                                                                    lrender, dL_dalpha_view, total, lreg_out);
+    launch(k_lreg, 1, MAX_VIEWS, 0, static_cast<cudaStream_t>(stream), counts, 1.0 / (double)n, lambda_reg, n_views, a,
+           lrender, dL_dalpha_view, total, lreg_out);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "clod_lreg_grad launch");
     return CLOD_OK;
@@ -242,7 +244,7 @@ clod_status clod_adam_step(const clod_adam_cfg* cfg, int64_t n, int32_t sh_degre
     const int64_t E = A.off[6];
     // one resident wave (78 registers: 3 blocks of 256 per SM)
     const int blocks = static_cast<int>(std::min<int64_t>((E + 255) / 256, (int64_t)n_sm * 3));
-    k_adam<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(A, m, v);
+    launch(k_adam, blocks, 256, 0, static_cast<cudaStream_t>(stream), A, m, v);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "clod_adam_step launch");
     return CLOD_OK;
