@@ -18,10 +18,10 @@
 //   2. the survivors of a view are cut into chunks of consecutive ranks; one
 //      warp per (chunk, tile row) walks the chunk's rectangles in rank order
 //      and counts, per tile of its row, the pairs the chunk contributes
-//      (k_rows<false>);
+//      (k_rows<false, false>);
 //   3. per tile, an exclusive scan over the chunks, then over the tiles
 //      (k_tile_scan: tile offsets, K, ranges, the blends' work order);
-//   4. the same walk again (k_rows<true>): pair (Gaussian, tile) goes to
+//   4. the same walk again (k_rows<true, KEYS>): pair (Gaussian, tile) goes to
 //      tile_offset + chunk offset + (number of earlier-ranked Gaussians of the
 //      chunk in that tile) -- its final sorted position.
 //
@@ -299,7 +299,7 @@ __device__ __forceinline__ int find_view_rb(const ViewDev* views, uint32_t V, ui
 //                 the slots of the same tile).
 static_assert(ROWS_PER_BLOCK <= 8, "a band's row mask is 8 bits");
 static_assert(STAGE <= 8 * ROWS_PER_BLOCK * 32, "the compaction holds at most 8 entries' row masks per thread");
-template <bool EMIT>
+template <bool EMIT, bool KEYS>
 __global__ void __launch_bounds__(ROWS_PER_BLOCK * 32, 4) k_rows(Frame F, uint32_t* __restrict__ vals,
                                                              unsigned long long* __restrict__ keys)
 {
@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(ROWS_PER_BLOCK * 32, 4) k_rows(Frame F, uint32
     extern __shared__ uint32_t sm[];
     __shared__ uint2 s_rect[STAGE];
     __shared__ uint32_t s_id[STAGE];
-    __shared__ uint32_t s_key[STAGE];
+    __shared__ uint32_t s_key[KEYS ? STAGE : 1];     // depth keys, only when the 64-bit keys are written
     __shared__ uint8_t s_rmask[STAGE];      // per listed rectangle: the band's rows it covers
     __shared__ uint32_t s_wc[ROWS_PER_BLOCK];
     __shared__ uint16_t s_buf[ROWS_PER_BLOCK][64];
@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(ROWS_PER_BLOCK * 32, 4) k_rows(Frame F, uint32
                     s_rect[pos] = rc;
                     if (EMIT) {
                         s_id[pos] = F.val0[g];
-                        if (keys) s_key[pos] = F.key0[g];
+                        if (KEYS) s_key[pos] = F.key0[g];
                     }
                     const int y0 = (int)(rc.x >> 16), y1 = (int)(rc.y >> 16);
                     const int lo = max(y0, band0) - band0, hi = min(y1, band1) - band0;
@@ -438,7 +438,7 @@ __global__ void __launch_bounds__(ROWS_PER_BLOCK * 32, 4) k_rows(Frame F, uint32
             // 1024 tiles, so total <= 32768), and the Gaussian index (and key)
             const uint32_t xst = (st << 16) | x0;
             const uint32_t gid = (EMIT && lane < gsz) ? s_id[gi_l] : 0u;
-            const uint32_t gkey = (EMIT && keys && lane < gsz) ? s_key[gi_l] : 0u;
+            const uint32_t gkey = (EMIT && KEYS && lane < gsz) ? s_key[gi_l] : 0u;
             // the members beyond the group move to the front of the buffer
             const uint32_t carry = lane + 32 < nb ? (uint32_t)s_buf[w][lane + 32] : 0u;
             __syncwarp();
@@ -468,7 +468,7 @@ __global__ void __launch_bounds__(ROWS_PER_BLOCK * 32, 4) k_rows(Frame F, uint32
                 const uint32_t peers = valid ? pm[x] : (1u << lane);
                 __syncwarp();
                 if (valid && (31 - __clz(peers)) == lane) pm[x] = 0u;
-                if (EMIT && keys) {
+                if (EMIT && KEYS) {
                     const uint32_t key_o = __shfl_sync(0xffffffffu, gkey, o);
                     if (valid) {
                         const uint32_t p = ctr[x] + __popc(peers & lt);
@@ -822,17 +822,22 @@ cudaError_t launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long 
     if (L.diff_grid_max * sizeof(uint32_t) <= DIFF_SMEM_MAX)
         launch(k_chunk_count, V * L.n_chunks, 512, L.diff_grid_max * sizeof(uint32_t), st, F);
     else
-        launch(k_rows<false>, L.rb_total, ROWS_PER_BLOCK * 32, smem, st, F, nullptr, nullptr);
+        launch(k_rows<false, false>, L.rb_total, ROWS_PER_BLOCK * 32, smem, st, F, nullptr, nullptr);
     launch(k_tile_scan, (L.total_tiles + CS_TILES - 1) / CS_TILES, CS_TILES * CS_SEG, 0, st, F, ranges, cap);
-    launch(k_rows<true>, L.rb_total, ROWS_PER_BLOCK * 32, smem, st, F, vals, reinterpret_cast<unsigned long long*>(keys));
+    if (keys)
+        launch(k_rows<true, true>, L.rb_total, ROWS_PER_BLOCK * 32, smem, st, F, vals,
+               reinterpret_cast<unsigned long long*>(keys));
+    else
+        launch(k_rows<true, false>, L.rb_total, ROWS_PER_BLOCK * 32, smem, st, F, vals, nullptr);
     return err;
 }
 
 cudaError_t bin_sort_setup()
 {
     const int bytes = 2 * ROWS_PER_BLOCK * 1024 * (int)sizeof(uint32_t);
-    cudaError_t e = cudaFuncSetAttribute(k_rows<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rows<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e = cudaFuncSetAttribute(k_rows<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rows<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rows<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_chunk_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DIFF_SMEM_MAX);
     return e;
 }
