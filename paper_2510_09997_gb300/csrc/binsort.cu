@@ -92,8 +92,10 @@ __device__ __forceinline__ int rs_later_count(const uint32_t* n_surv, int v, int
     return (int)max((int64_t)0, min((int64_t)RS_ITEMS, (int64_t)n_surv[2 * v + 1] - (int64_t)lb * RS_ITEMS));
 }
 
-// Per-warp digit counts of the held keys, in h[w][digit].
-__device__ __forceinline__ void rs_warp_counts(const uint32_t (&kk)[RS_R], int shift, uint32_t (*h)[256])
+// Per-warp digit counts of the held keys, in h[w][digit]; each key's set of
+// same-digit lanes is returned in peers[] (the scatter places the keys with it).
+__device__ __forceinline__ void rs_warp_counts(const uint32_t (&kk)[RS_R], int shift, uint32_t (*h)[256],
+                                               uint32_t (&peers)[RS_R])
 {
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int k = lane; k < 256; k += 32) h[w][k] = 0;
@@ -102,8 +104,8 @@ __device__ __forceinline__ void rs_warp_counts(const uint32_t (&kk)[RS_R], int s
     for (int r = 0; r < RS_R; ++r) {
         const bool valid = kk[r] != 0xFFFFFFFFu;
         const uint32_t d = valid ? ((kk[r] >> shift) & 255u) : 256u;
-        const uint32_t peers = match_bits<9>(d);     // d <= 256
-        if (valid && (__ffs(peers) - 1) == lane) h[w][d] += __popc(peers);
+        peers[r] = match_bits<9>(d);     // d <= 256
+        if (valid && (__ffs(peers[r]) - 1) == lane) h[w][d] += __popc(peers[r]);
         __syncwarp();
     }
 }
@@ -134,7 +136,8 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const FrameHeader* __res
         rs_load_keys(keys, base, cnt, kk);
     }
     if (cnt == 0) return;     // no items (and none in any later block)
-    rs_warp_counts(kk, shift, h);
+    uint32_t peers[RS_R];
+    rs_warp_counts(kk, shift, h, peers);
     __syncthreads();
     uint32_t s = 0;
     for (int w = 0; w < RS_THREADS / 32; ++w) s += h[w][threadIdx.x];
@@ -216,7 +219,8 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_rs_scatter(const FrameHeader*
 #pragma unroll
         for (int r = 0; r < RS_R; ++r) rr[r] = kk[r] != 0xFFFFFFFFu ? rect[vbase + vv[r]] : make_uint2(0u, 0u);
     }
-    rs_warp_counts(kk, shift, h);
+    uint32_t pk[RS_R];
+    rs_warp_counts(kk, shift, h, pk);
     {
         // exclusive scan of the view's 256 digit totals (RS_THREADS == 256)
         const int wi = threadIdx.x >> 5;
@@ -246,7 +250,7 @@ __global__ void __launch_bounds__(RS_THREADS, 4) k_rs_scatter(const FrameHeader*
     for (int r = 0; r < RS_R; ++r) {
         const bool valid = kk[r] != 0xFFFFFFFFu;     // culled keys are dropped here
         const uint32_t d = valid ? ((kk[r] >> shift) & 255u) : 256u;
-        const uint32_t peers = match_bits<9>(d);     // d <= 256
+        const uint32_t peers = pk[r];     // lanes holding the same digit (from the counting)
         if (valid) {
             const uint32_t pos = wb[w][d] + __popc(peers & lt);
             kout[vbase + pos] = kk[r];
@@ -772,17 +776,10 @@ __global__ void __launch_bounds__(CS_TILES * CS_SEG, 2) k_tile_scan(Frame F, uin
 
 constexpr size_t DIFF_SMEM_MAX = 200 * 1024;   // difference grid limit (a 4K view needs 131 KB)
 
-// Clears n words: the radix passes' digit sums and the tile scan's look-back
-// words and counters, in the stream's chain of dependent launches.
-__global__ void __launch_bounds__(256) k_clear(uint32_t* __restrict__ p, size_t n)
-{
-    pdl_wait();
-    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
-        p[k] = 0u;
-}
-
-// Returns the error of the first launch, the clear (the later launches'
-// errors surface through cudaGetLastError).
+// Returns the error of the first launch (the later launches' errors surface
+// through cudaGetLastError).  The digit sums and the tile scan's look-back
+// words it accumulates into were zeroed by the frame set-up of the
+// clod_preprocess call before it (one sort per preprocessing).
 cudaError_t launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long long cap, uint64_t* keys,
                             uint32_t* vals, uint32_t* ranges, cudaStream_t st)
 {
@@ -790,16 +787,11 @@ cudaError_t launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long 
     const int64_t n = (int64_t)L.n;
     const int nb = (int)L.n_rs_blocks;
     const uint32_t V = L.n_views;
-    // after the block counts [V][nb][256]: per pass the digit totals [V][256]
-    // and the group sums [V][groups][256] of both levels; then (the next
-    // array) the tile scan's look-back words and counters: one clear for all
+    // per pass: the digit totals [V][256] and the group sums [V][groups][256]
+    // of both levels
     const size_t n1 = (size_t)V * 256 * rs_groups(nb, RS_G1), n2 = (size_t)V * 256 * rs_groups(nb, RS_G2);
     const size_t per_pass = (size_t)V * 256 + n1 + n2;
-    uint32_t* sums = F.rs_hist + (size_t)V * 256 * nb;
-    const size_t words = static_cast<size_t>(F.scan_ctr + 8 - sums);
-    err = launch(k_clear, (unsigned)std::max<size_t>(1, std::min<size_t>((words + 255) / 256, 1024)), 256, 0, st, sums,
-                 words);
-    if (err != cudaSuccess) return err;
+    uint32_t* sums = F.rs_sums;
     if (n > 0) {
         // the first pass reads no values (they are the indices): vi is unused there
         uint32_t *ki = F.key0, *vi = F.val0, *ko = F.key1, *vo = F.val1;
@@ -807,7 +799,9 @@ cudaError_t launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long 
             uint32_t* tot = sums + (size_t)pass * per_pass;
             uint32_t* s1 = tot + (size_t)V * 256;
             uint32_t* s2 = s1 + n1;
-            launch(k_rs_hist, V * nb, RS_THREADS, 0, st, F.hdr, F.n_surv, ki, n, nb, 8 * pass, F.rs_hist, tot, s1, s2);
+            const cudaError_t e = launch(k_rs_hist, V * nb, RS_THREADS, 0, st, F.hdr, F.n_surv, ki, n, nb, 8 * pass,
+                                         F.rs_hist, tot, s1, s2);
+            if (pass == 0) err = e;
             if (pass == 3)
                 launch(k_rs_scatter<true>, V * nb, RS_THREADS, 0, st, F.hdr, F.n_surv, ki, vi, ko, vo, n, nb, 8 * pass,
                        F.rs_hist, tot, s1, s2, F.rect, F.srect, F.sband);

@@ -66,11 +66,18 @@ FrameLayout frame_layout(uint64_t n, uint32_t V, uint32_t TT, uint32_t n_chunks,
         o = align256(o + bytes);
         return at;
     };
-    // zero-initialised block first: header, d_max keys, counts, tile counts
+    // zero-initialised block first: header, d_max keys, counts, tile counts,
+    // the radix passes' digit sums (4 passes of digit totals and of the two
+    // levels of group sums, added by the counting kernels' atomics) and the
+    // tile scan's look-back words, class counters and ticket
+    const int nbk = (int)L.n_rs_blocks;
     L.header = take(sizeof(FrameHeader));
     L.dmax_key = take(sizeof(unsigned long long) * V);
     L.n_surv = take(sizeof(uint32_t) * 2 * V);
     L.tile_count = take(sizeof(uint32_t) * (size_t)TT);
+    L.rs_sums = take(sizeof(uint32_t) * 256 * (size_t)V *
+                     (4 * (1 + (size_t)rs_groups(nbk, RS_G1) + (size_t)rs_groups(nbk, RS_G2))));
+    L.scan = take(sizeof(unsigned long long) * (((size_t)TT + 31) / 32) + sizeof(uint32_t) * 8);
     L.views = take(sizeof(ViewDev) * V);
     L.tile_offset = take(sizeof(uint32_t) * ((size_t)TT + 1));
     L.torder = take(sizeof(uint32_t) * 4 * (size_t)TT);
@@ -86,13 +93,8 @@ FrameLayout frame_layout(uint64_t n, uint32_t V, uint32_t TT, uint32_t n_chunks,
     L.val1 = take(sizeof(uint32_t) * vn);
     L.srect = take(sizeof(uint2) * vn);
     L.sband = take(sizeof(uint16_t) * vn);
-    // block counts + 4 passes of digit totals and of the two levels of group sums
-    const int nbk = (int)L.n_rs_blocks;
-    L.rs_hist = take(sizeof(uint32_t) * 256 * (size_t)V *
-                     ((size_t)nbk + 4 * (1 + (size_t)rs_groups(nbk, RS_G1) + (size_t)rs_groups(nbk, RS_G2))));
-    // tile scan (right after the radix sums: one clear covers both): look-back
-    // words of the blocks of 32 tiles, then the class counters and the ticket
-    L.scan = take(sizeof(unsigned long long) * (((size_t)TT + 31) / 32) + sizeof(uint32_t) * 8);
+    // per radix block its digit counts (plain stores: no clear needed)
+    L.rs_hist = take(sizeof(uint32_t) * 256 * (size_t)V * (size_t)nbk);
     L.scan_cls = take(sizeof(ulonglong2) * 2 * (((size_t)TT + 31) / 32));
     L.cnt = take(sizeof(uint32_t) * (size_t)L.n_chunks * TT);
     L.sel = take(sizeof(SelState) * V);
@@ -127,6 +129,7 @@ Frame frame_ptrs(void* ws, const FrameLayout& L)
     F.srect = reinterpret_cast<uint2*>(b + L.srect);
     F.sband = reinterpret_cast<uint16_t*>(b + L.sband);
     F.rs_hist = reinterpret_cast<uint32_t*>(b + L.rs_hist);
+    F.rs_sums = reinterpret_cast<uint32_t*>(b + L.rs_sums);
     F.scan_st = reinterpret_cast<unsigned long long*>(b + L.scan);
     F.scan_cls = reinterpret_cast<ulonglong2*>(b + L.scan_cls);
     F.scan_ctr = reinterpret_cast<uint32_t*>(b + L.scan + sizeof(unsigned long long) * (((size_t)L.total_tiles + 31) / 32));
@@ -427,7 +430,7 @@ clod_status clod_bin_sort(void* ws, uint64_t pair_capacity, uint64_t* keys_out, 
     if (s) return s;
     const Frame F = frame_ptrs(ws, L);
     cudaError_t e = launch_bin_sort(F, L, pair_capacity, keys_out, vals_out, ranges_out, static_cast<cudaStream_t>(stream));
-    if (e != cudaSuccess) return cuda_fail(e, "clod_bin_sort clear");
+    if (e != cudaSuccess) return cuda_fail(e, "clod_bin_sort launch");
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "clod_bin_sort launch");
     return CLOD_OK;

@@ -126,7 +126,7 @@ struct SelState {
 
 struct FrameLayout {
     size_t header, views, dmax_key, n_surv, rec0, rec1, rec2, depth, rect, tile_count, tile_offset, torder,
-        key0, val0, key1, val1, srect, sband, rs_hist, scan, scan_cls, cnt, sel, sel_hist, total;
+        key0, val0, key1, val1, srect, sband, rs_hist, rs_sums, scan, scan_cls, cnt, sel, sel_hist, total;
     uint32_t total_tiles, n_views, n_chunks, n_rs_blocks, rb_total, max_tx;
     uint32_t fast_exp;      // host only: the frame's views carry CLOD_FAST_EXP
     uint64_t n;
@@ -156,7 +156,8 @@ struct Frame {
     uint32_t* val1;
     uint2* srect;           // tile rectangles in depth-rank order
     uint16_t* sband;        // their emission bands, first | last << 8, in depth-rank order
-    uint32_t* rs_hist;      // radix-sort digit counts [view][block][256], totals, superblock sums
+    uint32_t* rs_hist;      // radix-sort digit counts [view][block][256]
+    uint32_t* rs_sums;      // per pass: digit totals [view][256], then the two levels of group sums (zeroed at set-up)
     uint32_t* cnt;          // per (view, chunk, tile) pair counts, then offsets
     SelState* sel;          // primitive-budget select state [view]
     uint32_t* sel_hist;     // its digit counts [view][SEL_BINS]

@@ -140,7 +140,7 @@ extern "C" clod_status clod_render_noalloc(const clod_scene* scene, const clod_v
     if (e != cudaSuccess) return cuda_fail(e, "clod_render_noalloc upload");
     launch_preprocess(F, *scene, 1, nullptr, nullptr, nullptr, n_sm, st, w.budget > 0);
     if ((e = launch_bin_sort(F, L, NA_MAX_PAIRS, nullptr, vals, ranges, st)) != cudaSuccess)
-        return cuda_fail(e, "clod_render_noalloc sort clear");
+        return cuda_fail(e, "clod_render_noalloc sort launch");
     launch_blend_fwd(F, vals, ranges, image, T_final, n_contrib, nullptr, n_sm, st, (view->flags & CLOD_FAST_EXP) != 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "clod_render_noalloc launch");
     // the pair count is data dependent: wait for the frame and report overflow
