@@ -40,19 +40,19 @@ FLOP_ALG = 15
 # Second, labelled figure: the FP32 FLOPs this build issues (FMA = 2), with
 # its software exponential: every visited pair: offset 2 + quadratic form 7
 # = 9; a pair whose power lies in [-5.6, 0]: + exp_spec 31 (13 FMA, 2
-# subtractions, cap) + opacity 2 = 33; a contributing pair: + transmittance 2
-# + weight 1 + colour 6 = 9.
-FLOP_VISIT, FLOP_EXP, FLOP_CONTRIB = 9, 33, 9
+# subtractions, cap) + opacity 2 = 33; with the hardware exponential of
+# CLOD_FAST_EXP: the scaling product 1 (and one MUFU ex2) + opacity 2 = 3;
+# a contributing pair: + transmittance 2 + weight 1 + colour 6 = 9.
+FLOP_VISIT, FLOP_EXP, FLOP_EXP_FAST, FLOP_CONTRIB = 9, 33, 3, 9
 # kernels per frame: k_frame_setup, k_dist_max, k_preprocess; 4 x (k_rs_hist,
-# k_rs_scatter); k_chunk_count, k_chunk_scan, k_scan_tiles, k_rows<emit>;
-# k_blend_fwd
-LAUNCHES_PER_FRAME = 16
+# k_rs_scatter); k_chunk_count, k_tile_scan, k_rows<emit>; k_blend_fwd
+LAUNCHES_PER_FRAME = 15
 # DRAM traffic of k_blend_fwd (dram__bytes_read.sum + dram__bytes_write.sum,
 # one ncu pass), mean per launch over the 320 frames of the sweep in the
 # one-frame-at-a-time pass, for the kernel sources whose SHA-256 (render.cu,
 # then clod_internal.cuh) starts with "sources"; reported as null once those
 # sources differ from the captured build
-BLEND_TRAFFIC = {"bytes_per_launch": 33461640, "read": 26822963, "write": 6638677, "sources": "c5a14bdf6006e1ec"}
+BLEND_TRAFFIC = {"bytes_per_launch": 33208740, "read": 26767738, "write": 6441002, "sources": "0bc354dbf6e9f213"}
 
 
 def frames_list(only=None):
@@ -383,7 +383,8 @@ def run_ours(args):
     radix_equiv = 152 * n_pairs.sum()       # 6-pass LSD sort of K (u64 key, u32 value) pairs
     cnt3 = evals.cpu().numpy().astype(np.float64) / args.steps
     flop_per_frame = FLOP_ALG * cnt3[0]
-    issued_per_frame = FLOP_VISIT * cnt3[0] + FLOP_EXP * cnt3[1] + FLOP_CONTRIB * cnt3[2]
+    flop_exp = FLOP_EXP if args.exact_exp else FLOP_EXP_FAST
+    issued_per_frame = FLOP_VISIT * cnt3[0] + flop_exp * cnt3[1] + FLOP_CONTRIB * cnt3[2]
 
     value = whole_job_rate(args.steps, world, elapsed)
     peaks = measured_peaks()
@@ -440,8 +441,10 @@ def run_ours(args):
                      "flop_model": "15 FP32 ops + 1 MUFU per visited (pixel, Gaussian) pair (up to the pixel's stop)",
                      "pairs_per_frame": {"visited": round(cnt3[0]), "exp": round(cnt3[1]), "contrib": round(cnt3[2])},
                      "issued": {"achieved": round(blend_issued, 3), "frac": round(blend_issued / fp32_peak, 4),
-                                "model": "FP32 FLOPs this build issues: 9 per visited pair + 33 per pair whose "
-                                         "power is in [-5.6, 0] (software exponential) + 9 per contributor"},
+                                "model": "FP32 FLOPs the timed blend issues: 9 per visited pair + %d per pair whose "
+                                         "power is in [-5.6, 0] (%s) + 9 per contributor"
+                                         % (flop_exp, "software exponential" if args.exact_exp else
+                                            "hardware exponential: 1 product + 1 MUFU ex2")},
                      "peak_basis": ("measured: own FMA microbenchmark (clod_probe_fma), %.2f TFLOP/s; nominal %d SMs x "
                                     "128 lanes x 2 x %.0f MHz = %.2f" % (fp32_peak, n_sm, sm_mhz, nominal))
                      if fma else "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (sampled clock)" % (n_sm, sm_mhz)},
@@ -715,7 +718,7 @@ def city_leg(args, steps=5):
     C.clod_render_fwd(R.ws, R.vals, R.ranges, R.image, R.T, R.nc, evaluated=evals)
     e3 = evals.cpu().numpy().astype(np.float64)
     flop = FLOP_ALG * e3[0]
-    issued = FLOP_VISIT * e3[0] + FLOP_EXP * e3[1] + FLOP_CONTRIB * e3[2]
+    issued = FLOP_VISIT * e3[0] + (FLOP_EXP if args.exact_exp else FLOP_EXP_FAST) * e3[1] + FLOP_CONTRIB * e3[2]
     surv = cnt[:, 1].sum()
     # backward of the same launch (dL/dimage = a fixed random image gradient)
     nb = C.ctypes.c_size_t()
