@@ -395,10 +395,11 @@ clod_status clod_server_destroy(clod_server* server);
  * image.  image (3 x H x W), T_final (H x W, may be NULL), n_contrib (H x W,
  * may be NULL) are caller device buffers.  The call is synchronous: it
  * waits for the frame on its stream and reads the frame header back to the
- * host before returning.  Calls share the array: calls whose work overlaps on
- * the GPU race and must be serialised by the caller.  The first call on a
- * device also looks up the array's device address; make that first call
- * before any stream capture. */
+ * host before returning, so it must not be called while its stream (or any
+ * stream it depends on) is being captured into a CUDA graph.  Calls share the
+ * array: calls whose work overlaps on the GPU race and must be serialised by
+ * the caller.  The first call on a device also looks up the array's device
+ * address, with that device current. */
 clod_status clod_render_noalloc(const clod_scene* scene, const clod_view* view,
                                 float* image, float* T_final, uint32_t* n_contrib,
                                 clod_stream stream);

@@ -13,9 +13,9 @@
 // NA_MAX_PAIRS (view, tile, Gaussian) pairs.  Calls share the array, so calls
 // whose work overlaps on the GPU (different streams, or different host
 // threads) race; serialise them.  A call is synchronous: it waits for the
-// frame on its stream and reads the frame header back to report overflow.
-// The first call on a device also looks up the array's device address (with
-// that device current); make that first call before any stream capture.
+// frame on its stream and reads the frame header back to report overflow, so
+// it cannot run inside a stream capture.  The first call on a device also
+// looks up the array's device address (with that device current).
 #include <algorithm>
 #include <cstring>
 #include <mutex>
