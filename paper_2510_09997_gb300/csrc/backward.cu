@@ -333,6 +333,27 @@ __device__ __forceinline__ void sh_term(int k, float x, float y, float z, float 
     }
 }
 
+// Rotation matrix (row-major) of the unit quaternion (w, x, y, z).
+__device__ __forceinline__ void rotation(float qw, float qx, float qy, float qz, float (&r)[9])
+{
+    r[0] = 1.f - 2.f * (qy * qy + qz * qz);
+    r[1] = 2.f * (qx * qy - qw * qz);
+    r[2] = 2.f * (qx * qz + qw * qy);
+    r[3] = 2.f * (qx * qy + qw * qz);
+    r[4] = 1.f - 2.f * (qx * qx + qz * qz);
+    r[5] = 2.f * (qy * qz - qw * qx);
+    r[6] = 2.f * (qx * qz - qw * qy);
+    r[7] = 2.f * (qy * qz + qw * qx);
+    r[8] = 1.f - 2.f * (qx * qx + qy * qy);
+}
+
+// Index of entry (a, b) of a symmetric 3x3 matrix stored as its upper
+// triangle: 00 01 02 11 12 22.
+__host__ __device__ constexpr int sym3(int a, int b)
+{
+    return a <= b ? (a == 0 ? b : (a == 1 ? 2 + b : 5)) : (b == 0 ? a : (b == 1 ? 2 + a : 5));
+}
+
 struct ParamGrads {
     float* dmeans;
     float* dscales;
@@ -374,8 +395,15 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(Frame F, clod_scene S, c
     for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = base + threadIdx.x;
         const bool active = i < n;
-        float gm0 = 0.f, gm1 = 0.f, gm2 = 0.f, gs0 = 0.f, gs1 = 0.f, gs2 = 0.f;
-        float gq0 = 0.f, gq1 = 0.f, gq2 = 0.f, gq3 = 0.f, gop = 0.f, gdec = 0.f;
+        float gm0 = 0.f, gm1 = 0.f, gm2 = 0.f, gop = 0.f, gdec = 0.f;
+        // Sigma (upper triangle, sym3 order) from the first surviving view
+        // on, and the sum over the views of dL/dSigma + its transpose: the
+        // chain through M = R(q) diag(s) is linear in it, so it runs once
+        // per Gaussian after the views
+        bool geo = false;
+        float Sg[6], gSy[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) Sg[k] = gSy[k] = 0.f;
         float mx = 0.f, my = 0.f, mz = 0.f, alpha = 0.f, sigma = 0.f;
         bool sh_any = false;
         if (active) {
@@ -442,29 +470,25 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(Frame F, clod_scene S, c
                 gm1 += (gdy - dy * dotg) * inv_d;
                 gm2 += (gdz - dz * dotg) * inv_d;
 
+                // ---- Sigma = M M^T, M = R(q) diag(s): the same for every view,
+                // formed at the Gaussian's first surviving view ------------------
+                if (!geo) {
+                    const float4 q = reinterpret_cast<const float4*>(S.quats)[i];
+                    const float qn = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+                    float r[9], Mm[9];
+                    rotation(q.x / qn, q.y / qn, q.z / qn, q.w / qn, r);
+                    const float sc[3] = {S.scales[3 * i], S.scales[3 * i + 1], S.scales[3 * i + 2]};
+                    for (int a_ = 0; a_ < 3; ++a_)
+                        for (int b_ = 0; b_ < 3; ++b_) Mm[3 * a_ + b_] = r[3 * a_ + b_] * sc[b_];
+                    for (int a_ = 0; a_ < 3; ++a_)
+                        for (int b_ = a_; b_ < 3; ++b_)
+                            Sg[sym3(a_, b_)] = Mm[3 * a_] * Mm[3 * b_] + Mm[3 * a_ + 1] * Mm[3 * b_ + 1] +
+                                               Mm[3 * a_ + 2] * Mm[3 * b_ + 2];
+                    geo = true;
+                }
                 // ---- forward recomputation of the projection --------------------
                 float tx, ty, tz;
                 cam_point(W, mx, my, mz, tx, ty, tz);
-                const float4 q = reinterpret_cast<const float4*>(S.quats)[i];
-                const float qn = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
-                const float qw = q.x / qn, qx = q.y / qn, qy = q.z / qn, qz = q.w / qn;
-                float r[9];
-                r[0] = 1.f - 2.f * (qy * qy + qz * qz);
-                r[1] = 2.f * (qx * qy - qw * qz);
-                r[2] = 2.f * (qx * qz + qw * qy);
-                r[3] = 2.f * (qx * qy + qw * qz);
-                r[4] = 1.f - 2.f * (qx * qx + qz * qz);
-                r[5] = 2.f * (qy * qz - qw * qx);
-                r[6] = 2.f * (qx * qz - qw * qy);
-                r[7] = 2.f * (qy * qz + qw * qx);
-                r[8] = 1.f - 2.f * (qx * qx + qy * qy);
-                const float sc[3] = {S.scales[3 * i], S.scales[3 * i + 1], S.scales[3 * i + 2]};
-                float Mm[9], Sg[9];
-                for (int a_ = 0; a_ < 3; ++a_)
-                    for (int b_ = 0; b_ < 3; ++b_) Mm[3 * a_ + b_] = r[3 * a_ + b_] * sc[b_];
-                for (int a_ = 0; a_ < 3; ++a_)
-                    for (int b_ = 0; b_ < 3; ++b_)
-                        Sg[3 * a_ + b_] = Mm[3 * a_] * Mm[3 * b_] + Mm[3 * a_ + 1] * Mm[3 * b_ + 1] + Mm[3 * a_ + 2] * Mm[3 * b_ + 2];
                 const float limx = 1.3f * (0.5f * (float)W.FW / W.fx), limy = 1.3f * (0.5f * (float)W.FH / W.fy);
                 const float txz = tx / tz, tyz = ty / tz;
                 const bool clx = txz < -limx || txz > limx, cly = tyz < -limy || tyz > limy;
@@ -480,8 +504,8 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(Frame F, clod_scene S, c
                 }
                 float ST0[3], ST1[3];  // Sigma T0^T, Sigma T1^T
                 for (int k = 0; k < 3; ++k) {
-                    ST0[k] = Sg[3 * k] * T0[0] + Sg[3 * k + 1] * T0[1] + Sg[3 * k + 2] * T0[2];
-                    ST1[k] = Sg[3 * k] * T1[0] + Sg[3 * k + 1] * T1[1] + Sg[3 * k + 2] * T1[2];
+                    ST0[k] = Sg[sym3(k, 0)] * T0[0] + Sg[sym3(k, 1)] * T0[1] + Sg[sym3(k, 2)] * T0[2];
+                    ST1[k] = Sg[sym3(k, 0)] * T1[0] + Sg[sym3(k, 1)] * T1[1] + Sg[sym3(k, 2)] * T1[2];
                 }
                 const float ca = T0[0] * ST0[0] + T0[1] * ST0[1] + T0[2] * ST0[2] + 0.3f;
                 const float cb = T0[0] * ST1[0] + T0[1] * ST1[1] + T0[2] * ST1[2];
@@ -492,11 +516,12 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(Frame F, clod_scene S, c
                 const float g_ca = g_A * (-cc * cc * id2) + g_B * (cb * cc * id2) + g_C * (id - ca * cc * id2);
                 const float g_cb = g_A * (2.f * cb * cc * id2) + g_B * (-id - 2.f * cb * cb * id2) + g_C * (2.f * ca * cb * id2);
                 const float g_cc = g_A * (id - ca * cc * id2) + g_B * (ca * cb * id2) + g_C * (-ca * ca * id2);
-                // ---- 2D covariance -> Sigma and T ---------------------------------
-                float gS[9];
+                // ---- 2D covariance -> Sigma (summed over the views as the
+                // symmetric dL/dSigma + its transpose) and T ----------------------
                 for (int k = 0; k < 3; ++k)
-                    for (int l = 0; l < 3; ++l)
-                        gS[3 * k + l] = g_ca * T0[k] * T0[l] + g_cb * T0[k] * T1[l] + g_cc * T1[k] * T1[l];
+                    for (int l = k; l < 3; ++l)
+                        gSy[sym3(k, l)] += 2.f * g_ca * T0[k] * T0[l] + g_cb * (T0[k] * T1[l] + T1[k] * T0[l]) +
+                                           2.f * g_cc * T1[k] * T1[l];
                 float gT0[3], gT1[3];
                 for (int k = 0; k < 3; ++k) {
                     gT0[k] = 2.f * g_ca * ST0[k] + g_cb * ST1[k];
@@ -529,32 +554,6 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(Frame F, clod_scene S, c
                 gm0 += W.R[0] * gtx + W.R[3] * gty + W.R[6] * gtz;
                 gm1 += W.R[1] * gtx + W.R[4] * gty + W.R[7] * gtz;
                 gm2 += W.R[2] * gtx + W.R[5] * gty + W.R[8] * gtz;
-                // ---- Sigma = M M^T, M = R(q) diag(s) ------------------------------
-                float gM[9];
-                for (int a_ = 0; a_ < 3; ++a_)
-                    for (int b_ = 0; b_ < 3; ++b_) {
-                        float acc = 0.f;
-                        for (int k = 0; k < 3; ++k) acc += (gS[3 * a_ + k] + gS[3 * k + a_]) * Mm[3 * k + b_];
-                        gM[3 * a_ + b_] = acc;
-                    }
-                float gR[9];
-                for (int a_ = 0; a_ < 3; ++a_)
-                    for (int b_ = 0; b_ < 3; ++b_) gR[3 * a_ + b_] = gM[3 * a_ + b_] * sc[b_];
-                gs0 += gM[0] * r[0] + gM[3] * r[3] + gM[6] * r[6];
-                gs1 += gM[1] * r[1] + gM[4] * r[4] + gM[7] * r[7];
-                gs2 += gM[2] * r[2] + gM[5] * r[5] + gM[8] * r[8];
-                const float gw = 2.f * (-qz * gR[1] + qy * gR[2] + qz * gR[3] - qx * gR[5] - qy * gR[6] + qx * gR[7]);
-                const float gx = 2.f * (qy * gR[1] + qz * gR[2] + qy * gR[3] - 2.f * qx * gR[4] - qw * gR[5] + qz * gR[6] +
-                                        qw * gR[7] - 2.f * qx * gR[8]);
-                const float gy = 2.f * (-2.f * qy * gR[0] + qx * gR[1] + qw * gR[2] + qx * gR[3] + qz * gR[5] - qw * gR[6] +
-                                        qz * gR[7] - 2.f * qy * gR[8]);
-                const float gz = 2.f * (-2.f * qz * gR[0] - qw * gR[1] + qx * gR[2] + qw * gR[3] - 2.f * qz * gR[4] +
-                                        qy * gR[5] + qx * gR[6] + qy * gR[7]);
-                const float dot = gw * qw + gx * qx + gy * qy + gz * qz;
-                gq0 += (gw - qw * dot) / qn;
-                gq1 += (gx - qx * dot) / qn;
-                gq2 += (gy - qy * dot) / qn;
-                gq3 += (gz - qz * dot) / qn;
             }
             // ---- attenuated opacity (Eq. 2) ----------------------------------------
             if (g_a2 != 0.0f) {
@@ -592,17 +591,45 @@ __global__ void __launch_bounds__(128) k_preprocess_bwd(Frame F, clod_scene S, c
 #pragma unroll
             for (int j = 0; j < 3 * K; ++j) dshp[j] += s_dsh[j][threadIdx.x];
         }
+        if (geo) {
+            // ---- Sigma = M M^T, M = R(q) diag(s), with the views' summed
+            // dL/dSigma + transpose: dM = G M, dR = dM diag(s), ds, dq ----------
+            const float4 q = reinterpret_cast<const float4*>(S.quats)[i];
+            const float qn = sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+            const float qw = q.x / qn, qx = q.y / qn, qy = q.z / qn, qz = q.w / qn;
+            float r[9];
+            rotation(qw, qx, qy, qz, r);
+            const float sc[3] = {S.scales[3 * i], S.scales[3 * i + 1], S.scales[3 * i + 2]};
+            float gM[9];
+            for (int a_ = 0; a_ < 3; ++a_)
+                for (int b_ = 0; b_ < 3; ++b_) {
+                    float acc = 0.f;
+                    for (int k = 0; k < 3; ++k) acc += gSy[sym3(a_, k)] * (r[3 * k + b_] * sc[b_]);
+                    gM[3 * a_ + b_] = acc;
+                }
+            float gR[9];
+            for (int a_ = 0; a_ < 3; ++a_)
+                for (int b_ = 0; b_ < 3; ++b_) gR[3 * a_ + b_] = gM[3 * a_ + b_] * sc[b_];
+            P.dscales[3 * i] += gM[0] * r[0] + gM[3] * r[3] + gM[6] * r[6];
+            P.dscales[3 * i + 1] += gM[1] * r[1] + gM[4] * r[4] + gM[7] * r[7];
+            P.dscales[3 * i + 2] += gM[2] * r[2] + gM[5] * r[5] + gM[8] * r[8];
+            const float gw = 2.f * (-qz * gR[1] + qy * gR[2] + qz * gR[3] - qx * gR[5] - qy * gR[6] + qx * gR[7]);
+            const float gx = 2.f * (qy * gR[1] + qz * gR[2] + qy * gR[3] - 2.f * qx * gR[4] - qw * gR[5] + qz * gR[6] +
+                                    qw * gR[7] - 2.f * qx * gR[8]);
+            const float gy = 2.f * (-2.f * qy * gR[0] + qx * gR[1] + qw * gR[2] + qx * gR[3] + qz * gR[5] - qw * gR[6] +
+                                    qz * gR[7] - 2.f * qy * gR[8]);
+            const float gz = 2.f * (-2.f * qz * gR[0] - qw * gR[1] + qx * gR[2] + qw * gR[3] - 2.f * qz * gR[4] +
+                                    qy * gR[5] + qx * gR[6] + qy * gR[7]);
+            const float dot = gw * qw + gx * qx + gy * qy + gz * qz;
+            P.dquats[4 * i] += (gw - qw * dot) / qn;
+            P.dquats[4 * i + 1] += (gx - qx * dot) / qn;
+            P.dquats[4 * i + 2] += (gy - qy * dot) / qn;
+            P.dquats[4 * i + 3] += (gz - qz * dot) / qn;
+        }
         if (active) {
             P.dmeans[3 * i] += gm0;
             P.dmeans[3 * i + 1] += gm1;
             P.dmeans[3 * i + 2] += gm2;
-            P.dscales[3 * i] += gs0;
-            P.dscales[3 * i + 1] += gs1;
-            P.dscales[3 * i + 2] += gs2;
-            P.dquats[4 * i] += gq0;
-            P.dquats[4 * i + 1] += gq1;
-            P.dquats[4 * i + 2] += gq2;
-            P.dquats[4 * i + 3] += gq3;
             P.dopacity[i] += gop;
             P.ddecay[i] += gdec;
         }
