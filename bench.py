@@ -781,7 +781,8 @@ def serve_leg(args):
     ds = C.DeviceScene.from_scene(sc)
     rate = 2000.0
     fast = 0 if args.exact_exp else S.FLAG_FAST_EXP
-    n_max = int(rate * args.serve_seconds)
+    sweep_rates = (100.0, 200.0, 300.0, 500.0, 750.0, 1000.0, 1250.0, 1500.0, 1750.0, 2000.0, 2500.0)
+    n_max = int(max(rate * args.serve_seconds, max(sweep_rates) * args.serve_sweep_seconds))
     views = [v.replace(flags=v.flags | fast) for v in
              S.random_cameras(n_max, sizes, d_range=(1.0, 50.0), s_range=(1.0, 32.0), seed=4)]
     warm = [v.replace(flags=v.flags | fast) for v in
@@ -901,9 +902,9 @@ def serve_leg(args):
            "latency": "completion minus scheduled arrival",
            "sustained": "all requests done without falling 2 s behind, and >= 95% of the arrival rate delivered"}
     res["at_2000_per_s"] = measure(rate, args.serve_seconds)
-    sweep = [measure(lam, args.serve_sweep_seconds)
-             for lam in (100.0, 200.0, 300.0, 500.0, 750.0, 1000.0, 1500.0, 2000.0, 2500.0)]
+    sweep = [measure(lam, args.serve_sweep_seconds) for lam in sweep_rates]
     res["sweep"] = sweep
+    res["sweep_trace_seconds"] = args.serve_sweep_seconds
     best = {}
     for path in ("server", "plain"):
         for bound in (50.0, 200.0):
