@@ -364,7 +364,7 @@ struct ParamGrads {
 };
 
 template <int DEG>
-__global__ void __launch_bounds__(128) k_preprocess_bwd(Frame F, clod_scene S, const float4* __restrict__ g2d,
+__global__ void __launch_bounds__(128, 5) k_preprocess_bwd(Frame F, clod_scene S, const float4* __restrict__ g2d,
                                                         const float* __restrict__ g_alpha_ext,
                                                         const float* __restrict__ g_alpha_view,
                                                         float* __restrict__ dmax_grad, ParamGrads P)
@@ -684,6 +684,7 @@ __global__ void k_l1_loss(const float* __restrict__ img, const float* __restrict
 }
 
 static int g_bwd_blocks_per_sm = 0;
+static int g_pbwd_blocks_per_sm = 0;
 
 cudaError_t backward_setup()
 {
@@ -691,6 +692,10 @@ cudaError_t backward_setup()
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_blend_bwd<false>, BWD_THREADS, 0);
     if (e != cudaSuccess) return e;
     g_bwd_blocks_per_sm = b > 0 ? b : 1;
+    // the degree-3 kernel uses the most registers: its residency bounds the others'
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_preprocess_bwd<3>, 128, 0);
+    if (e != cudaSuccess) return e;
+    g_pbwd_blocks_per_sm = b > 0 ? b : 1;
     return cudaSuccess;
 }
 
@@ -712,7 +717,9 @@ void launch_backward(const Frame& F, const clod_scene& S, uint32_t V, const uint
         launch(k_blend_bwd<false>, n_sm * std::max(1, g_bwd_blocks_per_sm), BWD_THREADS, 0, st, F, vals, ranges, Tfin,
                ncon, dimg, reinterpret_cast<float*>(g2d));
     ParamGrads P{dmeans, dscales, dquats, dopacity, dsh, ddecay};
-    int blocks = static_cast<int>(std::min<int64_t>((S.n + 127) / 128, (int64_t)n_sm * 16));
+    // one resident wave (the loop strides over the rest): each block walks many
+    // Gaussians, so the uneven ends of its warps' walks weigh little
+    int blocks = static_cast<int>(std::min<int64_t>((S.n + 127) / 128, (int64_t)n_sm * std::max(1, g_pbwd_blocks_per_sm)));
     if (blocks < 1) blocks = 1;
     if (S.n > 0) {
         switch (S.sh_degree) {
