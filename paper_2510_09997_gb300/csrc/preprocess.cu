@@ -91,6 +91,65 @@ __global__ void __launch_bounds__(256) k_dist_max(Frame F, const float* __restri
     }
 }
 
+// Pass A for 2..MV views: each thread reads the centres of DM Gaussians
+// once and tests them against every view in turn (one view's camera in
+// registers at a time); its per-view maxima live in its own column of
+// shared memory.  The same keys and maxima as k_dist_max.
+template <int MV>
+__global__ void __launch_bounds__(256) k_dist_max_views(Frame F, const float* __restrict__ means, int64_t n)
+{
+    pdl_wait();
+    const uint32_t V = F.hdr->n_views;
+    __shared__ ViewDev sv[MV];
+    __shared__ unsigned long long s_best[MV][256];
+    load_views(sv, F.views, V);
+    for (uint32_t v = 0; v < V; ++v) s_best[v][threadIdx.x] = 0ull;
+    __syncthreads();
+    constexpr int DM = 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < n; i0 += DM * stride) {
+        float x[DM], y[DM], z[DM];
+#pragma unroll
+        for (int u = 0; u < DM; ++u) {
+            const int64_t i = i0 + u * stride;
+            x[u] = y[u] = z[u] = 0.0f;
+            if (i < n) {
+                x[u] = means[3 * i];
+                y[u] = means[3 * i + 1];
+                z[u] = means[3 * i + 2];
+            }
+        }
+#pragma unroll 1
+        for (uint32_t v = 0; v < V; ++v) {
+            const ViewDev& W = sv[v];
+            unsigned long long best = s_best[v][threadIdx.x];
+#pragma unroll
+            for (int u = 0; u < DM; ++u) {
+                const int64_t i = i0 + u * stride;
+                float tx, ty, tz, e0, e1, e2;
+                cam_point(W, x[u], y[u], z[u], tx, ty, tz);
+                const float d = cam_dist(W, x[u], y[u], z[u], e0, e1, e2);
+                if (i < n && in_frustum(W, tx, ty, tz)) {
+                    const unsigned long long key =
+                        (static_cast<unsigned long long>(__float_as_uint(d)) << 32) |
+                        static_cast<unsigned long long>(0xFFFFFFFFu - static_cast<uint32_t>(i));
+                    best = key > best ? key : best;
+                }
+            }
+            s_best[v][threadIdx.x] = best;
+        }
+    }
+    __syncthreads();
+    // per view: warp maxima, then one warp over the block's eight
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (uint32_t v = (uint32_t)w; v < V; v += blockDim.x >> 5) {
+        unsigned long long b = 0ull;
+        for (int t = lane; t < (int)blockDim.x; t += 32) b = s_best[v][t] > b ? s_best[v][t] : b;
+        b = warp_max_u64(b);
+        if (lane == 0 && b) atomicMax(&F.dmax_key[v], b);
+    }
+}
+
 // Pass B (DEG: the scene's SH degree, so the basis stays in registers).
 template <int DEG>
 __global__ void __launch_bounds__(256, 4) k_preprocess(Frame F, clod_scene S, uint8_t* __restrict__ mask_out,
@@ -411,7 +470,12 @@ void launch_preprocess(const Frame& F, const clod_scene& S, uint32_t V, uint8_t*
     int blocks = static_cast<int>(std::min<int64_t>((n + 255) / 256, (int64_t)n_sm * 4));
     if (blocks < 1) blocks = 1;
     const int dm_blocks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>((n + 1023) / 1024, (int64_t)n_sm * 4)));
-    if (n > 0) launch(k_dist_max, dm_blocks, 256, 0, st, F, S.means, n);
+    if (n > 0) {
+        if (V == 1) launch(k_dist_max, dm_blocks, 256, 0, st, F, S.means, n);
+        else if (V <= 4) launch(k_dist_max_views<4>, dm_blocks, 256, 0, st, F, S.means, n);
+        else if (V <= 8) launch(k_dist_max_views<8>, dm_blocks, 256, 0, st, F, S.means, n);
+        else launch(k_dist_max, dm_blocks, 256, 0, st, F, S.means, n);
+    }
     if (n > 0 && select) launch_budget_select(F, S, V, n_sm, st);
     if (n > 0) {
         switch (S.sh_degree) {
