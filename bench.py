@@ -137,6 +137,8 @@ def parse():
     p.add_argument("--serve-slots", type=int, default=6, help="server slots (batches in flight)")
     p.add_argument("--serve-pairs", type=int, default=1 << 28, help="pair capacity of a server slot")
     p.add_argument("--no-city", action="store_true")
+    p.add_argument("--city-gaussians", type=int, default=6_000_000,
+                   help="Gaussians of the large-scene leg (6M; smaller for profiling captures)")
     p.add_argument("--frame", default=None, help="CAM:S -- time only that frame of the sweep (profiling)")
     p.add_argument("--inflight", type=int, default=8, help="frames in flight (renderers and streams)")
     p.add_argument("--exact-exp", action="store_true",
@@ -680,7 +682,7 @@ def city_leg(args, steps=5):
     import torch
     from paper_2510_09997_gb300 import clod as C
     from paper_2510_09997_gb300 import synth as S
-    sc = S.city_scene()
+    sc = S.city_scene(n=args.city_gaussians)
     fast = 0 if args.exact_exp else S.FLAG_FAST_EXP
     views = [v.replace(flags=v.flags | fast) for v in S.city_views()]
     V, n = len(views), sc.n
@@ -743,7 +745,8 @@ def city_leg(args, steps=5):
     ms = float(stage.sum())
     del R, ds
     torch.cuda.empty_cache()
-    return {"workload": "city block 6M Gaussians SH3, 8 views/launch 3840x2160, s_v in {1,4,16,64} x2",
+    return {"workload": "city block %gM Gaussians SH3, 8 views/launch 3840x2160, s_v in {1,4,16,64} x2"
+                        % (sc.n / 1e6),
             "views_per_s": round(V / (ms / 1e3), 2), "ms_per_launch": round(ms, 3),
             "stage_ms": {"preprocess": round(float(stage[0]), 3), "bin_sort": round(float(stage[1]), 3),
                          "blend": round(float(stage[2]), 3)},
