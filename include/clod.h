@@ -243,6 +243,19 @@ clod_status clod_render_bwd(const clod_scene* scene, const void* ws, const uint3
                             float* dmeans, float* dscales, float* dquats, float* dopacity,
                             float* dsh, float* ddecay, clod_stream stream);
 
+/* As clod_render_bwd, but the six gradient arrays are OVERWRITTEN: every
+ * element is written (zero for a Gaussian that survives in no view), so the
+ * caller need not zero them first.  Same arguments, layouts and errors.  A
+ * training step that runs one backward per update (followed by
+ * clod_adam_step with keep_grads = 1) then reads and writes each gradient
+ * once instead of zeroing, reading and adding to it. */
+clod_status clod_render_bwd_set(const clod_scene* scene, const void* ws, const uint32_t* vals,
+                                const uint32_t* ranges, const float* T_final, const uint32_t* n_contrib,
+                                const float* dL_dimage, const float* dL_dalpha_eff, const float* dL_dalpha_view,
+                                void* bwd_ws, size_t bwd_ws_bytes,
+                                float* dmeans, float* dscales, float* dquats, float* dopacity,
+                                float* dsh, float* ddecay, clod_stream stream);
+
 /* L1 term of the rendering loss (Sec. 3.3): *loss += scale * mean |image -
  * target| over count elements (device f32 scalar, may be NULL) and
  * dL_dimage = scale * sign(image - target) / count (may be NULL). */
@@ -294,6 +307,9 @@ typedef struct clod_adam_cfg {
     float lr[6];
     float beta1, beta2, eps;
     int32_t step;           /* t >= 1 */
+    int32_t keep_grads;     /* 0: zero the six gradient arrays after the update;
+                               1: leave them (a backward with overwritten outputs,
+                               clod_render_bwd_set, refills them every step) */
 } clod_adam_cfg;
 
 /* One Adam step fused with the activations.  raw: host array of 6 device
@@ -302,7 +318,7 @@ typedef struct clod_adam_cfg {
  * grads: host array of 6 device pointers, the gradients with respect to the
  * ACTIVATED parameters (clod_render_bwd's outputs); the log-scale and logit
  * gradients are formed inside (times scale, times a (1 - a)); all six are
- * zeroed afterwards.  scales, opacity: the activated copies the rasterizer
+ * zeroed afterwards unless cfg->keep_grads.  scales, opacity: the activated copies the rasterizer
  * reads (exp(log-scale), sigmoid(logit)), read for the chain rule and
  * rewritten from the updated raw values.  m, v: device f32 moments of
  * clod_adam_state_size() elements each (zero before the first step), the six

@@ -53,7 +53,7 @@ class clod_server_cfg(ctypes.Structure):
 
 class clod_adam_cfg(ctypes.Structure):
     _fields_ = [("lr", ctypes.c_float * 6), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
-                ("eps", ctypes.c_float), ("step", ctypes.c_int32)]
+                ("eps", ctypes.c_float), ("step", ctypes.c_int32), ("keep_grads", ctypes.c_int32)]
 
 
 class clod_req_stats(ctypes.Structure):
@@ -74,6 +74,7 @@ SIGNATURES = {
     # backward
     "clod_backward_workspace_size": ([ctypes.c_int64, ctypes.c_int32, P], c_status),
     "clod_render_bwd": ([P, P, P, P, P, P, P, P, P, P, ctypes.c_size_t, P, P, P, P, P, P, P], c_status),
+    "clod_render_bwd_set": ([P, P, P, P, P, P, P, P, P, P, ctypes.c_size_t, P, P, P, P, P, P, P], c_status),
     "clod_l1_loss": ([P, P, ctypes.c_int64, ctypes.c_float, P, P, P], c_status),
     "clod_probe_fma": ([ctypes.c_int32, P, P, P], c_status),
     "clod_render_loss_workspace_size": ([ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P], c_status),

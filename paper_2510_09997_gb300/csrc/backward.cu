@@ -333,6 +333,14 @@ __device__ __forceinline__ void sh_term(int k, float x, float y, float z, float 
     }
 }
 
+// dst = x (SET) or dst += x.
+template <bool SET>
+__device__ __forceinline__ void put(float& dst, float x)
+{
+    if (SET) dst = x;
+    else dst += x;
+}
+
 // Rotation matrix (row-major) of the unit quaternion (w, x, y, z).
 __device__ __forceinline__ void rotation(float qw, float qx, float qy, float qz, float (&r)[9])
 {
@@ -363,7 +371,9 @@ struct ParamGrads {
     float* ddecay;
 };
 
-template <int DEG>
+// SET: the parameter gradients are overwritten (every element written,
+// zeros where the Gaussian survives in no view) instead of accumulated.
+template <int DEG, bool SET>
 __global__ void __launch_bounds__(128, 5) k_preprocess_bwd(Frame F, clod_scene S, const float4* __restrict__ g2d,
                                                         const float* __restrict__ g_alpha_ext,
                                                         const float* __restrict__ g_alpha_view,
@@ -376,7 +386,7 @@ __global__ void __launch_bounds__(128, 5) k_preprocess_bwd(Frame F, clod_scene S
     __shared__ float sgav[MAX_VIEWS];
     // each thread's SH gradient summed over the views, element-major (no bank
     // conflicts); added to the gradient buffer once per Gaussian
-    __shared__ float s_dsh[48][128];
+    __shared__ float s_dsh[48][129];     // padded: the warps' row-wise read-out is conflict free
     const uint32_t V = F.hdr->n_views;
     {
         const int words = static_cast<int>(V * sizeof(ViewDev) / 4);
@@ -586,10 +596,33 @@ __global__ void __launch_bounds__(128, 5) k_preprocess_bwd(Frame F, clod_scene S
                 }
             }
         }
-        if (sh_any) {
+        if (SET) {
+            // the warp's 32 SH gradient rows are contiguous: written by the
+            // whole warp, element by element in address order, each element
+            // read from its Gaussian's column of s_dsh (zero for a Gaussian
+            // whose colour got no gradient)
+            constexpr int R = 3 * K;
+            const unsigned has = __ballot_sync(0xffffffffu, sh_any);
+            const int lane = threadIdx.x & 31, col0 = threadIdx.x & ~31;
+            const int64_t i0 = i - lane;
+            const int cnt = (int)min((int64_t)32, n - i0);
+            __syncwarp();
+            float* dst = P.dsh + (size_t)max((int64_t)0, i0) * R;
+            for (int e = lane; e < cnt * R; e += 32) {
+                const int t = e / R, j = e - t * R;
+                dst[e] = ((has >> t) & 1u) ? s_dsh[j][col0 + t] : 0.0f;
+            }
+            __syncwarp();     // before a lane reuses its column for the next Gaussian
+        } else if (sh_any) {
+            // added row by row (measured faster than the warp's read-modify-
+            // write of whole rows)
             float* dshp = P.dsh + (size_t)i * K * 3;
 #pragma unroll
             for (int j = 0; j < 3 * K; ++j) dshp[j] += s_dsh[j][threadIdx.x];
+        }
+        if (SET && active && !geo) {
+            P.dscales[3 * i] = P.dscales[3 * i + 1] = P.dscales[3 * i + 2] = 0.0f;
+            P.dquats[4 * i] = P.dquats[4 * i + 1] = P.dquats[4 * i + 2] = P.dquats[4 * i + 3] = 0.0f;
         }
         if (geo) {
             // ---- Sigma = M M^T, M = R(q) diag(s), with the views' summed
@@ -610,9 +643,9 @@ __global__ void __launch_bounds__(128, 5) k_preprocess_bwd(Frame F, clod_scene S
             float gR[9];
             for (int a_ = 0; a_ < 3; ++a_)
                 for (int b_ = 0; b_ < 3; ++b_) gR[3 * a_ + b_] = gM[3 * a_ + b_] * sc[b_];
-            P.dscales[3 * i] += gM[0] * r[0] + gM[3] * r[3] + gM[6] * r[6];
-            P.dscales[3 * i + 1] += gM[1] * r[1] + gM[4] * r[4] + gM[7] * r[7];
-            P.dscales[3 * i + 2] += gM[2] * r[2] + gM[5] * r[5] + gM[8] * r[8];
+            put<SET>(P.dscales[3 * i], gM[0] * r[0] + gM[3] * r[3] + gM[6] * r[6]);
+            put<SET>(P.dscales[3 * i + 1], gM[1] * r[1] + gM[4] * r[4] + gM[7] * r[7]);
+            put<SET>(P.dscales[3 * i + 2], gM[2] * r[2] + gM[5] * r[5] + gM[8] * r[8]);
             const float gw = 2.f * (-qz * gR[1] + qy * gR[2] + qz * gR[3] - qx * gR[5] - qy * gR[6] + qx * gR[7]);
             const float gx = 2.f * (qy * gR[1] + qz * gR[2] + qy * gR[3] - 2.f * qx * gR[4] - qw * gR[5] + qz * gR[6] +
                                     qw * gR[7] - 2.f * qx * gR[8]);
@@ -621,17 +654,17 @@ __global__ void __launch_bounds__(128, 5) k_preprocess_bwd(Frame F, clod_scene S
             const float gz = 2.f * (-2.f * qz * gR[0] - qw * gR[1] + qx * gR[2] + qw * gR[3] - 2.f * qz * gR[4] +
                                     qy * gR[5] + qx * gR[6] + qy * gR[7]);
             const float dot = gw * qw + gx * qx + gy * qy + gz * qz;
-            P.dquats[4 * i] += (gw - qw * dot) / qn;
-            P.dquats[4 * i + 1] += (gx - qx * dot) / qn;
-            P.dquats[4 * i + 2] += (gy - qy * dot) / qn;
-            P.dquats[4 * i + 3] += (gz - qz * dot) / qn;
+            put<SET>(P.dquats[4 * i], (gw - qw * dot) / qn);
+            put<SET>(P.dquats[4 * i + 1], (gx - qx * dot) / qn);
+            put<SET>(P.dquats[4 * i + 2], (gy - qy * dot) / qn);
+            put<SET>(P.dquats[4 * i + 3], (gz - qz * dot) / qn);
         }
         if (active) {
-            P.dmeans[3 * i] += gm0;
-            P.dmeans[3 * i + 1] += gm1;
-            P.dmeans[3 * i + 2] += gm2;
-            P.dopacity[i] += gop;
-            P.ddecay[i] += gdec;
+            put<SET>(P.dmeans[3 * i], gm0);
+            put<SET>(P.dmeans[3 * i + 1], gm1);
+            put<SET>(P.dmeans[3 * i + 2], gm2);
+            put<SET>(P.dopacity[i], gop);
+            put<SET>(P.ddecay[i], gdec);
         }
     }
     __syncthreads();
@@ -693,7 +726,7 @@ cudaError_t backward_setup()
     if (e != cudaSuccess) return e;
     g_bwd_blocks_per_sm = b > 0 ? b : 1;
     // the degree-3 kernel uses the most registers: its residency bounds the others'
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_preprocess_bwd<3>, 128, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_preprocess_bwd<3, false>, 128, 0);
     if (e != cudaSuccess) return e;
     g_pbwd_blocks_per_sm = b > 0 ? b : 1;
     return cudaSuccess;
@@ -702,7 +735,7 @@ cudaError_t backward_setup()
 void launch_backward(const Frame& F, const clod_scene& S, uint32_t V, const uint32_t* vals, const uint32_t* ranges,
                      const float* Tfin, const uint32_t* ncon, const float* dimg, const float* g_alpha_ext,
                      const float* g_alpha_view, void* bwd_ws, float* dmeans, float* dscales, float* dquats, float* dopacity, float* dsh,
-                     float* ddecay, int n_sm, cudaStream_t st, bool fast)
+                     float* ddecay, int n_sm, cudaStream_t st, bool fast, bool set)
 {
     const BwdLayout L = bwd_layout((uint64_t)S.n, V);
     char* b = static_cast<char*>(bwd_ws);
@@ -722,11 +755,20 @@ void launch_backward(const Frame& F, const clod_scene& S, uint32_t V, const uint
     int blocks = static_cast<int>(std::min<int64_t>((S.n + 127) / 128, (int64_t)n_sm * std::max(1, g_pbwd_blocks_per_sm)));
     if (blocks < 1) blocks = 1;
     if (S.n > 0) {
-        switch (S.sh_degree) {
-        case 0: launch(k_preprocess_bwd<0>, blocks, 128, 0, st, F, S, g2d, g_alpha_ext, g_alpha_view, dmg, P); break;
-        case 1: launch(k_preprocess_bwd<1>, blocks, 128, 0, st, F, S, g2d, g_alpha_ext, g_alpha_view, dmg, P); break;
-        case 2: launch(k_preprocess_bwd<2>, blocks, 128, 0, st, F, S, g2d, g_alpha_ext, g_alpha_view, dmg, P); break;
-        default: launch(k_preprocess_bwd<3>, blocks, 128, 0, st, F, S, g2d, g_alpha_ext, g_alpha_view, dmg, P); break;
+        if (set) {
+            switch (S.sh_degree) {
+            case 0: launch(k_preprocess_bwd<0, true>, blocks, 128, 0, st, F, S, g2d, g_alpha_ext, g_alpha_view, dmg, P); break;
+            case 1: launch(k_preprocess_bwd<1, true>, blocks, 128, 0, st, F, S, g2d, g_alpha_ext, g_alpha_view, dmg, P); break;
+            case 2: launch(k_preprocess_bwd<2, true>, blocks, 128, 0, st, F, S, g2d, g_alpha_ext, g_alpha_view, dmg, P); break;
+            default: launch(k_preprocess_bwd<3, true>, blocks, 128, 0, st, F, S, g2d, g_alpha_ext, g_alpha_view, dmg, P); break;
+            }
+        } else {
+            switch (S.sh_degree) {
+            case 0: launch(k_preprocess_bwd<0, false>, blocks, 128, 0, st, F, S, g2d, g_alpha_ext, g_alpha_view, dmg, P); break;
+            case 1: launch(k_preprocess_bwd<1, false>, blocks, 128, 0, st, F, S, g2d, g_alpha_ext, g_alpha_view, dmg, P); break;
+            case 2: launch(k_preprocess_bwd<2, false>, blocks, 128, 0, st, F, S, g2d, g_alpha_ext, g_alpha_view, dmg, P); break;
+            default: launch(k_preprocess_bwd<3, false>, blocks, 128, 0, st, F, S, g2d, g_alpha_ext, g_alpha_view, dmg, P); break;
+            }
         }
     }
     launch(k_dmax_bwd, 1, 64, 0, st, F, S, dmg, dmeans);

@@ -26,7 +26,7 @@ cudaError_t backward_setup();
 void launch_backward(const Frame& F, const clod_scene& S, uint32_t V, const uint32_t* vals, const uint32_t* ranges,
                      const float* Tfin, const uint32_t* ncon, const float* dimg, const float* g_alpha_ext,
                      const float* g_alpha_view, void* bwd_ws, float* dmeans, float* dscales, float* dquats, float* dopacity, float* dsh,
-                     float* ddecay, int n_sm, cudaStream_t st, bool fast);
+                     float* ddecay, int n_sm, cudaStream_t st, bool fast, bool set);
 size_t backward_ws_bytes(uint64_t n, uint32_t V);
 void launch_l1(const float* img, const float* tgt, int64_t count, float scale, float* loss, float* grad, int n_sm,
                cudaStream_t st);
@@ -493,12 +493,12 @@ clod_status clod_backward_workspace_size(int64_t n, int32_t n_views, size_t* byt
     return CLOD_OK;
 }
 
-clod_status clod_render_bwd(const clod_scene* scene, const void* ws, const uint32_t* vals, const uint32_t* ranges,
-                            const float* T_final, const uint32_t* n_contrib, const float* dL_dimage,
-                            const float* dL_dalpha_eff, const float* dL_dalpha_view, void* bwd_ws,
-                            size_t bwd_ws_bytes, float* dmeans,
-                            float* dscales, float* dquats, float* dopacity, float* dsh, float* ddecay,
-                            clod_stream stream)
+static clod_status render_bwd(const clod_scene* scene, const void* ws, const uint32_t* vals, const uint32_t* ranges,
+                              const float* T_final, const uint32_t* n_contrib, const float* dL_dimage,
+                              const float* dL_dalpha_eff, const float* dL_dalpha_view, void* bwd_ws,
+                              size_t bwd_ws_bytes, float* dmeans,
+                              float* dscales, float* dquats, float* dopacity, float* dsh, float* ddecay,
+                              clod_stream stream, bool set)
 {
     clod_status s = check_scene(scene);
     if (s) return s;
@@ -518,10 +518,33 @@ clod_status clod_render_bwd(const clod_scene* scene, const void* ws, const uint3
     const Frame F = frame_ptrs(const_cast<void*>(ws), L);
     launch_backward(F, *scene, L.n_views, vals, ranges, T_final, n_contrib, dL_dimage, dL_dalpha_eff, dL_dalpha_view,
                     bwd_ws, dmeans,
-                    dscales, dquats, dopacity, dsh, ddecay, n_sm, static_cast<cudaStream_t>(stream), L.fast_exp != 0);
+                    dscales, dquats, dopacity, dsh, ddecay, n_sm, static_cast<cudaStream_t>(stream), L.fast_exp != 0,
+                    set);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "clod_render_bwd launch");
     return CLOD_OK;
+}
+
+clod_status clod_render_bwd(const clod_scene* scene, const void* ws, const uint32_t* vals, const uint32_t* ranges,
+                            const float* T_final, const uint32_t* n_contrib, const float* dL_dimage,
+                            const float* dL_dalpha_eff, const float* dL_dalpha_view, void* bwd_ws,
+                            size_t bwd_ws_bytes, float* dmeans,
+                            float* dscales, float* dquats, float* dopacity, float* dsh, float* ddecay,
+                            clod_stream stream)
+{
+    return render_bwd(scene, ws, vals, ranges, T_final, n_contrib, dL_dimage, dL_dalpha_eff, dL_dalpha_view, bwd_ws,
+                      bwd_ws_bytes, dmeans, dscales, dquats, dopacity, dsh, ddecay, stream, false);
+}
+
+clod_status clod_render_bwd_set(const clod_scene* scene, const void* ws, const uint32_t* vals,
+                                const uint32_t* ranges, const float* T_final, const uint32_t* n_contrib,
+                                const float* dL_dimage, const float* dL_dalpha_eff, const float* dL_dalpha_view,
+                                void* bwd_ws, size_t bwd_ws_bytes, float* dmeans,
+                                float* dscales, float* dquats, float* dopacity, float* dsh, float* ddecay,
+                                clod_stream stream)
+{
+    return render_bwd(scene, ws, vals, ranges, T_final, n_contrib, dL_dimage, dL_dalpha_eff, dL_dalpha_view, bwd_ws,
+                      bwd_ws_bytes, dmeans, dscales, dquats, dopacity, dsh, ddecay, stream, true);
 }
 
 clod_status clod_l1_loss(const float* image, const float* target, int64_t count, float scale, float* loss,

@@ -87,7 +87,9 @@ __device__ __forceinline__ float activate(int gi, float p)
 // Group by group, four elements per vector access (the groups' moments start
 // at multiples of four elements), two vectors per thread and round with every
 // load issued before any store; a scalar tail finishes each group.
-__global__ void __launch_bounds__(256) k_adam(AdamArgs A, float* __restrict__ m, float* __restrict__ v)
+// ZERO: clear the gradients after the update.
+template <bool ZERO>
+__global__ void __launch_bounds__(256, 3) k_adam(AdamArgs A, float* __restrict__ m, float* __restrict__ v)
 {
     pdl_wait();
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -127,7 +129,7 @@ __global__ void __launch_bounds__(256) k_adam(AdamArgs A, float* __restrict__ m,
                     reinterpret_cast<float4*>(M)[j] = m4[u];
                     reinterpret_cast<float4*>(Vv)[j] = v4[u];
                     reinterpret_cast<float4*>(P)[j] = pn;
-                    reinterpret_cast<float4*>(G)[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (ZERO) reinterpret_cast<float4*>(G)[j] = make_float4(0.f, 0.f, 0.f, 0.f);
                     if (act)
                         reinterpret_cast<float4*>(Act)[j] =
                             make_float4(activate(gi, pn.x), activate(gi, pn.y), activate(gi, pn.z), activate(gi, pn.w));
@@ -140,7 +142,7 @@ __global__ void __launch_bounds__(256) k_adam(AdamArgs A, float* __restrict__ m,
             M[j] = mm;
             Vv[j] = vv;
             P[j] = pn;
-            G[j] = 0.0f;
+            if (ZERO) G[j] = 0.0f;
             if (act) Act[j] = activate(gi, pn);
         }
     }
@@ -244,7 +246,8 @@ clod_status clod_adam_step(const clod_adam_cfg* cfg, int64_t n, int32_t sh_degre
     const int64_t E = A.off[6];
     // one resident wave (78 registers: 3 blocks of 256 per SM)
     const int blocks = static_cast<int>(std::min<int64_t>((E + 255) / 256, (int64_t)n_sm * 3));
-    launch(k_adam, blocks, 256, 0, static_cast<cudaStream_t>(stream), A, m, v);
+    if (cfg->keep_grads) launch(k_adam<false>, blocks, 256, 0, static_cast<cudaStream_t>(stream), A, m, v);
+    else launch(k_adam<true>, blocks, 256, 0, static_cast<cudaStream_t>(stream), A, m, v);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "clod_adam_step launch");
     return CLOD_OK;

@@ -21,8 +21,10 @@ Every step runs in libclod's kernels: the forward (clod_preprocess,
 clod_bin_sort, clod_render_fwd), the loss and its image gradient
 (clod_render_loss, written straight into the packed gradient), L_reg, the
 total and the per-view straight-through scalars (clod_lreg_grad), the
-backward (clod_render_bwd) and Adam fused with the parameter activations
-(clod_adam_step: raw log-scales and opacity logits, exp / sigmoid).  Python
+backward (clod_render_bwd_set, which overwrites the gradients) and Adam
+fused with the parameter activations (clod_adam_step: raw log-scales and
+opacity logits, exp / sigmoid; keep_grads, as the next backward refills
+them).  Python
 only allocates the buffers once and passes pointers.  sigma_d has learning
 rate 1e-2 and lambda_reg = 1 (Sec. 4.1).
 """
@@ -125,7 +127,8 @@ class TrainStep:
 
     def forward_backward(self, views: Sequence, targets: Sequence[torch.Tensor], scales: Optional[List[float]] = None):
         """Forward, loss, L_reg, backward: the six activated-parameter
-        gradients accumulate into self.grads.  Returns (frame, per-view info)."""
+        gradients of this call overwrite self.grads.  Returns (frame, per-view
+        info)."""
         if scales is None:
             scales = [self.sample_scale() for _ in views]
         views = [v.replace(s_v=s) for v, s in zip(views, scales)]
@@ -160,7 +163,7 @@ class TrainStep:
         nb = ctypes.c_size_t()
         C.check("clod_backward_workspace_size", L.clod_backward_workspace_size(self.model.n, V, ctypes.byref(nb)))
         bws = self._workspace("_bws", nb.value)
-        C.check("clod_render_bwd", L.clod_render_bwd(
+        C.check("clod_render_bwd_set", L.clod_render_bwd_set(
             ctypes.byref(self.scene.c), C._ptr(fr.ws), C._ptr(fr.vals), C._ptr(fr.ranges), C._ptr(fr.T_final),
             C._ptr(fr.n_contrib), C._ptr(dimg), None, C._ptr(self.dalpha), C._ptr(bws), bws.numel(),
             *[C._ptr(g) for g in self.grads], st))
@@ -172,7 +175,7 @@ class TrainStep:
 
     def loss(self, views, targets, scales=None):
         """L_total (device scalar) and per-view diagnostics, without the update
-        (the gradients are left accumulated in self.grads)."""
+        (this call's gradients are left in self.grads)."""
         fr, info = self.forward_backward(views, targets, scales)
         return self.total, info
 
@@ -185,6 +188,7 @@ class TrainStep:
         for k in range(6):
             cfg.lr[k] = self.lr[k]
         cfg.beta1, cfg.beta2, cfg.eps, cfg.step = self.betas[0], self.betas[1], self.eps, self.t
+        cfg.keep_grads = 1     # the next step's backward overwrites them
         P = ctypes.c_void_p * 6
         raw = P(*[C._ptr(p) for p in self.model.raw()])
         grads = P(*[C._ptr(g) for g in self.grads])
