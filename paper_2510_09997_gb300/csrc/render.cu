@@ -128,6 +128,7 @@ __device__ __forceinline__ void store_px(const ViewDev& W, const Px& q, int px, 
 }
 
 constexpr int BLEND_THREADS = 128;   // 4 warps per 16x16 tile, 8x8 pixels per warp, 2 per thread
+constexpr int BLEND_BLOCKS_PER_SM_MAX = 5;
 
 // Each warp takes (tile, 8x8 quarter) work items from an atomic queue and
 // walks the tile's list on its own, 32 entries at a time: every lane gathers
@@ -136,9 +137,10 @@ constexpr int BLEND_THREADS = 128;   // 4 warps per 16x16 tile, 8x8 pixels per w
 // leaves its patch when all 64 pixels are saturated and takes the next item;
 // nothing waits for the other warps of the block.  COUNT: the counting
 // variant (every pair visited, software exponential); FAST: the exponential
-// of CLOD_FAST_EXP.  Nine blocks per SM: left to itself, ptxas fits the
-// kernel in 48 registers with a 4-byte spill inside the list walk, which
-// measured 20 % slower over the orbit sweep than 55 registers without one.
+// of CLOD_FAST_EXP.  Registers for nine blocks per SM (the grid launches at
+// most BLEND_BLOCKS_PER_SM_MAX): left to itself, ptxas fits the kernel in 48
+// registers with a 4-byte spill inside the list walk, which measured 20 %
+// slower over the orbit sweep than 55 registers without one.
 template <bool COUNT, bool FAST>
 __global__ void __launch_bounds__(BLEND_THREADS, 9) k_blend_fwd(Frame F, const uint32_t* __restrict__ vals,
                                                              const uint32_t* __restrict__ ranges,
@@ -269,7 +271,15 @@ cudaError_t render_setup()
 void launch_blend_fwd(const Frame& F, const uint32_t* vals, const uint32_t* ranges, float* image, float* Tout,
                       uint32_t* ncout, unsigned long long* evaluated, int n_sm, cudaStream_t st, bool fast)
 {
-    const int blocks = n_sm * std::max(1, g_blend_blocks_per_sm[fast ? 1 : 0]);
+    // at most five resident blocks per SM: the issue-bound blend keeps most
+    // of its rate with 20 warps per SM, and the register file it leaves free
+    // lets other streams' latency-bound kernels (the preprocessing and sort
+    // of frames in flight) run beside it.  Eight 1080p frames in flight over
+    // the orbit sweep: 4195 frames/s at nine blocks per SM (its occupancy
+    // limit), 4371 at five, 4459 at four; one frame at a time 2094 / 2082 /
+    // 2049.  Five blocks with the registers of five (69 instead of 56) gave
+    // 4228 in flight
+    const int blocks = n_sm * std::min(BLEND_BLOCKS_PER_SM_MAX, std::max(1, g_blend_blocks_per_sm[fast ? 1 : 0]));
     if (evaluated)
         launch(k_blend_fwd<true, false>, blocks, BLEND_THREADS, 0, st, F, vals, ranges, image, Tout, ncout, evaluated);
     else if (fast)
