@@ -19,7 +19,7 @@ void launch_preprocess(const Frame& F, const clod_scene& S, uint32_t V, uint8_t*
 cudaError_t launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long long cap, uint64_t* keys,
                             uint32_t* vals, uint32_t* ranges, cudaStream_t st);
 void launch_blend_fwd(const Frame& F, const uint32_t* vals, const uint32_t* ranges, float* image, float* Tout,
-                      uint32_t* ncout, unsigned long long* evaluated, int n_sm, cudaStream_t st, bool fast);
+                      uint32_t* ncout, unsigned long long* evaluated, int n_sm, cudaStream_t st, bool fast, uint32_t tiles);
 cudaError_t bin_sort_setup();
 cudaError_t render_setup();
 cudaError_t backward_setup();
@@ -447,7 +447,7 @@ static clod_status render_common(const void* ws, const uint32_t* vals, const uin
     if (s) return s;
     const Frame F = frame_ptrs(const_cast<void*>(ws), L);
     launch_blend_fwd(F, vals, ranges, image, T_final, n_contrib, evaluated, n_sm, static_cast<cudaStream_t>(stream),
-                     L.fast_exp != 0);
+                     L.fast_exp != 0, L.total_tiles);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "clod_render_fwd launch");
     return CLOD_OK;

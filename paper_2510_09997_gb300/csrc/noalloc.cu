@@ -29,7 +29,7 @@ void launch_preprocess(const Frame& F, const clod_scene& S, uint32_t V, uint8_t*
 cudaError_t launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long long cap, uint64_t* keys,
                             uint32_t* vals, uint32_t* ranges, cudaStream_t st);
 void launch_blend_fwd(const Frame& F, const uint32_t* vals, const uint32_t* ranges, float* image, float* Tout,
-                      uint32_t* ncout, unsigned long long* evaluated, int n_sm, cudaStream_t st, bool fast);
+                      uint32_t* ncout, unsigned long long* evaluated, int n_sm, cudaStream_t st, bool fast, uint32_t tiles);
 clod_status fail(clod_status s, const char* fmt, ...);
 clod_status cuda_fail(cudaError_t e, const char* what);
 clod_status device_ready(int* n_sm);
@@ -141,7 +141,8 @@ extern "C" clod_status clod_render_noalloc(const clod_scene* scene, const clod_v
     launch_preprocess(F, *scene, 1, nullptr, nullptr, nullptr, n_sm, st, w.budget > 0);
     if ((e = launch_bin_sort(F, L, NA_MAX_PAIRS, nullptr, vals, ranges, st)) != cudaSuccess)
         return cuda_fail(e, "clod_render_noalloc sort launch");
-    launch_blend_fwd(F, vals, ranges, image, T_final, n_contrib, nullptr, n_sm, st, (view->flags & CLOD_FAST_EXP) != 0);
+    launch_blend_fwd(F, vals, ranges, image, T_final, n_contrib, nullptr, n_sm, st, (view->flags & CLOD_FAST_EXP) != 0,
+                     (uint32_t)(TX * TY));
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "clod_render_noalloc launch");
     // the pair count is data dependent: wait for the frame and report overflow
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "clod_render_noalloc sync");

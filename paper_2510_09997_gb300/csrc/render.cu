@@ -128,7 +128,8 @@ __device__ __forceinline__ void store_px(const ViewDev& W, const Px& q, int px, 
 }
 
 constexpr int BLEND_THREADS = 128;   // 4 warps per 16x16 tile, 8x8 pixels per warp, 2 per thread
-constexpr int BLEND_BLOCKS_PER_SM_MAX = 5;
+constexpr int BLEND_BLOCKS_PER_SM_MAX = 5;        // resident blocks per SM for small frames
+constexpr uint32_t BLEND_SMALL_TILES = 16384;      // tiles of a frame below which that holds
 
 // Each warp takes (tile, 8x8 quarter) work items from an atomic queue and
 // walks the tile's list on its own, 32 entries at a time: every lane gathers
@@ -269,17 +270,22 @@ cudaError_t render_setup()
 }
 
 void launch_blend_fwd(const Frame& F, const uint32_t* vals, const uint32_t* ranges, float* image, float* Tout,
-                      uint32_t* ncout, unsigned long long* evaluated, int n_sm, cudaStream_t st, bool fast)
+                      uint32_t* ncout, unsigned long long* evaluated, int n_sm, cudaStream_t st, bool fast,
+                      uint32_t tiles)
 {
-    // at most five resident blocks per SM: the issue-bound blend keeps most
-    // of its rate with 20 warps per SM, and the register file it leaves free
+    // A frame of fewer than BLEND_SMALL_TILES tiles (one 1080p view) takes at
+    // most five resident blocks per SM: the issue-bound blend keeps most of
+    // its rate with 20 warps per SM, and the register file it leaves free
     // lets other streams' latency-bound kernels (the preprocessing and sort
     // of frames in flight) run beside it.  Eight 1080p frames in flight over
     // the orbit sweep: 4195 frames/s at nine blocks per SM (its occupancy
     // limit), 4371 at five, 4459 at four; one frame at a time 2094 / 2082 /
-    // 2049.  Five blocks with the registers of five (69 instead of 56) gave
-    // 4228 in flight
-    const int blocks = n_sm * std::min(BLEND_BLOCKS_PER_SM_MAX, std::max(1, g_blend_blocks_per_sm[fast ? 1 : 0]));
+    // 2049 (five blocks with the registers of five, 69 instead of 56: 4228 in
+    // flight).  Larger frames (training batches, 4K views, eight 4K views)
+    // fill the GPU alone and keep every resident block: eight 4K views' blend
+    // took 4.85 ms at nine blocks per SM, 5.05 at five.
+    const int occ = std::max(1, g_blend_blocks_per_sm[fast ? 1 : 0]);
+    const int blocks = n_sm * (tiles < BLEND_SMALL_TILES ? std::min(BLEND_BLOCKS_PER_SM_MAX, occ) : occ);
     if (evaluated)
         launch(k_blend_fwd<true, false>, blocks, BLEND_THREADS, 0, st, F, vals, ranges, image, Tout, ncout, evaluated);
     else if (fast)

@@ -39,7 +39,7 @@ void launch_preprocess(const Frame& F, const clod_scene& S, uint32_t V, uint8_t*
 cudaError_t launch_bin_sort(const Frame& F, const FrameLayout& L, unsigned long long cap, uint64_t* keys,
                             uint32_t* vals, uint32_t* ranges, cudaStream_t st);
 void launch_blend_fwd(const Frame& F, const uint32_t* vals, const uint32_t* ranges, float* image, float* Tout,
-                      uint32_t* ncout, unsigned long long* evaluated, int n_sm, cudaStream_t st, bool fast);
+                      uint32_t* ncout, unsigned long long* evaluated, int n_sm, cudaStream_t st, bool fast, uint32_t tiles);
 clod_status fail(clod_status s, const char* fmt, ...);
 clod_status cuda_fail(cudaError_t e, const char* what);
 clod_status device_ready(int* n_sm);
@@ -165,7 +165,8 @@ static void enqueue_batch(clod_server* S, Slot& sl, cudaStream_t st, bool select
     cudaMemcpyAsync(F.views, sl.h_views, sizeof(ViewDev) * V, cudaMemcpyHostToDevice, st);
     launch_preprocess(F, S->scene, (uint32_t)V, nullptr, nullptr, nullptr, S->n_sm, st, select);
     launch_bin_sort(F, sl.L, S->cfg.pair_capacity, nullptr, sl.vals, sl.ranges, st);
-    launch_blend_fwd(F, sl.vals, sl.ranges, nullptr, nullptr, nullptr, nullptr, S->n_sm, st, S->cfg.fast_exp != 0);
+    launch_blend_fwd(F, sl.vals, sl.ranges, nullptr, nullptr, nullptr, nullptr, S->n_sm, st, S->cfg.fast_exp != 0,
+                     sl.L.total_tiles);
     cudaMemcpyAsync(sl.h_hdr_down, F.hdr, sizeof(FrameHeader), cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(sl.h_counts, F.n_surv, sizeof(uint32_t) * 2 * V, cudaMemcpyDeviceToHost, st);
 }
@@ -279,7 +280,8 @@ static clod_status render_alone(clod_server* S, Request& r)
         S->solo_cap = cap;
     }
     launch_bin_sort(F, L, S->solo_cap, nullptr, S->solo_vals, sl.ranges, st);
-    launch_blend_fwd(F, S->solo_vals, sl.ranges, nullptr, nullptr, nullptr, nullptr, S->n_sm, st, S->cfg.fast_exp != 0);
+    launch_blend_fwd(F, S->solo_vals, sl.ranges, nullptr, nullptr, nullptr, nullptr, S->n_sm, st, S->cfg.fast_exp != 0,
+                     L.total_tiles);
     cudaMemcpyAsync(sl.h_hdr_down, F.hdr, sizeof(FrameHeader), cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(sl.h_counts, F.n_surv, sizeof(uint32_t) * 2, cudaMemcpyDeviceToHost, st);
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "render_alone");
