@@ -49,6 +49,12 @@ def test_validation_without_gpu(L):
     assert L.clod_preprocess(None, views, 1, None, 0, None, None, None, None, None) == abi.CLOD_ERR_ARG
     assert L.clod_bin_sort(None, 0, None, None, None, None) == abi.CLOD_ERR_ARG
     assert L.clod_backward_workspace_size(5, 0, ctypes.byref(nbytes)) == abi.CLOD_ERR_ARG
+    for bwd in (L.clod_render_bwd, L.clod_render_bwd_set):
+        assert bwd(None, None, None, None, None, None, None, None, None, None, 0,
+                   None, None, None, None, None, None, None) == abi.CLOD_ERR_ARG
+    # the Adam configuration struct as the header lays it out (keep_grads last)
+    assert ctypes.sizeof(abi.clod_adam_cfg) == 4 * 10 + 4
+    assert abi.clod_adam_cfg.keep_grads.offset == 40
 
 
 def test_region_view_validation_without_gpu(L):
